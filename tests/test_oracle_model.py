@@ -1,0 +1,85 @@
+"""Pins of the oracle's attenuation model (Sec. II-A, II-B) against closed forms."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import alg1, model
+from synthetic import phantoms as ph
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _kn_fixture():
+    with open(os.path.join(GOLD, "klein_nishina.json")) as f:
+        return json.load(f)
+
+
+def test_kn_thomson_limit_and_series():
+    fx = _kn_fixture()
+    r0 = fx["r0_cm"]
+    sigma_t = 8.0 * np.pi / 3.0 * r0 * r0 / 1e-24
+    for g in (1e-3, 3e-3, 1e-2):
+        E = g * model.MEC2_KEV
+        series = sigma_t * sum(c * g ** k for k, c in enumerate(fx["series"]))
+        # next series term is 544/7 g^5: bounded error
+        assert abs(model.klein_nishina_barn(E) - series) <= sigma_t * (80 * g ** 5 + 1e-9)
+
+
+def test_kn_high_energy_asymptote():
+    fx = _kn_fixture()
+    r0 = fx["r0_cm"]
+    sigma_t = 8.0 * np.pi / 3.0 * r0 * r0 / 1e-24
+    g = fx["asymptote_gamma"]
+    asym = 0.375 * sigma_t * (np.log(2 * g) + 0.5) / g
+    assert abs(model.klein_nishina_barn(g * model.MEC2_KEV) / asym - 1) < fx["asymptote_rtol"]
+
+
+def test_kn_decreasing_positive():
+    E = np.linspace(10, 500, 200)
+    kn = model.klein_nishina_barn(E)
+    assert np.all(kn > 0) and np.all(np.diff(kn) < 0)
+
+
+def test_water_attenuation_magnitude():
+    # mu(E) = rho_e n_w (K Z^3.8 / E^3.2 + sigma_KN): water at 60 keV is about
+    # 0.02 /mm (0.2 /cm), the textbook order of magnitude.
+    mu = model.mu_mm(1.0, 7.45, 60.0)
+    assert 0.018 < mu < 0.022
+
+
+@pytest.mark.parametrize("Z,rhoe", [(7.45, 1.0), (13.0, 1.7), (7.5, 0.25), (20.0, 1.9), (5.5, 0.2)])
+@pytest.mark.parametrize("arms", ["mono", "kramers"])
+def test_exact_recovery_uniform(Z, rhoe, arms):
+    """Noiseless uniform material: Cramer decomposition, synthesis at E1/E2
+    and the closed forms eq. rho_e / eq. Z_m give back (Z, rho_e) exactly,
+    because every material of the model lies in the span of two bases."""
+    acq = ph.acquisition("small" if arms == "mono" else "clinical", n=128)
+    tab = model.Tables(acq.low, acq.high)
+    muL = np.full((4, 4), sum(w * model.mu_hat(rhoe, Z, E) for E, w in zip(*tab.arms[0])))
+    muH = np.full((4, 4), sum(w * model.mu_hat(rhoe, Z, E) for E, w in zip(*tab.arms[1])))
+    st = alg1.init_state(muL, muH, tab)
+    assert np.allclose(st["rhoe"], rhoe, rtol=1e-12, atol=0)
+    assert np.allclose(model.z_from_ztilde(st["zt"]), Z, rtol=1e-12, atol=0)
+
+
+def test_recovery_direct_model_values():
+    """The two closed forms invert eq. mac_E1_eff/E2_eff directly."""
+    tab = model.Tables(ph.Spectrum("mono", kev=60.0), ph.Spectrum("mono", kev=90.0))
+    Z, rhoe = 13.0, 1.7
+    m1 = model.mu_hat(rhoe, Z, 50.0)
+    m2 = model.mu_hat(rhoe, Z, 200.0)
+    assert abs(model.rhoe_closed_form(m1, m2, tab) - rhoe) < 1e-13
+    a, b = model.z_coefficients(m1, m2, tab)
+    assert abs(model.z_from_ztilde(b / a) - Z) < 1e-12
+
+
+def test_spectrum_weights():
+    s = ph.Spectrum("kramers", kvp=140.0, filters=(ph.AL_2MM, ph.SN_04MM))
+    E, w = model.spectrum_bins(s)
+    assert E[0] == 10.0 and E[-1] == 139.0
+    assert abs(w.sum() - 1) < 1e-14 and np.all(w >= 0)
+    lo = model.spectrum_bins(ph.Spectrum("kramers", kvp=80.0, filters=(ph.AL_2MM,)))
+    # tin filtration hardens the high arm: its mean energy is far above the low arm's
+    assert (E * w).sum() > (lo[0] * lo[1]).sum() + 20
