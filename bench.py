@@ -1,0 +1,372 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the one-step Z / rho_e estimation (Algorithm 1).
+
+A step is one full solve of one batch of synthetic fan-beam scans: FBP of the
+low and high -log sinograms, initialisation, ``iters`` iterations of
+Algorithm 1 (threshold, FFT-diagonalised f1 / f2 / rho_e updates, Z^m PCG,
+beta continuation) and the FP64-Newton extraction of Z.  The metric is
+slice-iterations per second (slices x iterations / time).
+
+Default workload 'volume': 160 contiguous 512^2 slices (1 mm), ellipsoidal
+inserts spanning 5-40 slices, mono 60/90 keV, 720 views x 736 bins, I0 5e4,
+150 iterations.  Inputs are synthetic (seeded phantoms; scans simulated on
+the GPU by the library's projector with Gaussian-approximated Poisson noise).
+Multi-GPU: one process per GPU, each solving its own volume (weak scaling, no
+collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "slice-iters/s on 512^2 (FP32+batched vs plain FP64, same GB300), HBM GB/s, p99"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
+    ap.add_argument("--workload", choices=["volume", "clinical", "uneven", "small"], default="volume")
+    ap.add_argument("--slices", type=int, default=None)
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--precision", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def workload(args, rank):
+    """Truth maps, acquisitions and iteration count of this rank's batch."""
+    from synthetic import phantoms as ph
+    seed = 1000 + 7919 * rank
+    if args.workload == "volume":
+        n_sl = args.slices or 160
+        V = ph.volume_phantom(seed, n_slices=n_sl)
+        acq = ph.acquisition("volume")
+        slices = [(V["Z"][k], V["rhoe"][k], acq) for k in range(n_sl)]
+        iters = args.iters or acq.iters
+        name = f"volume {n_sl}x512^2, mono 60/90 keV, 720 views x 736 bins, I0 5e4"
+    elif args.workload == "clinical":
+        n_sl = args.slices or 1
+        acq = ph.acquisition("clinical")
+        slices = []
+        for k in range(n_sl):
+            P = ph.clinical_phantom(seed + k)
+            slices.append((P["Z"].astype(np.float32), P["rhoe"].astype(np.float32), acq))
+        iters = args.iters or acq.iters
+        name = f"clinical {n_sl}x512^2, Kramers 80/140 kVp (Al, +Sn), 720 views x 736 bins, I0 1e5"
+    elif args.workload == "uneven":
+        sizes = ph.uneven_sizes(seed, args.slices or 64)
+        slices = []
+        for k, n in enumerate(sizes):
+            P = ph.small_phantom(seed + k, n=n)
+            slices.append((P["Z"].astype(np.float32), P["rhoe"].astype(np.float32), ph.acquisition("uneven", n=n)))
+        iters = args.iters or 100
+        name = f"uneven {len(sizes)} slices of 256^2..512^2, mono 60/90 keV, views/bins scaled, I0 1e5"
+    else:
+        n_sl = args.slices or 1
+        acq = ph.acquisition("small")
+        slices = []
+        for k in range(n_sl):
+            P = ph.small_phantom(seed + k)
+            slices.append((P["Z"].astype(np.float32), P["rhoe"].astype(np.float32), acq))
+        iters = args.iters or acq.iters
+        name = f"small {n_sl}x128^2, mono 60/90 keV, 180 views x 192 bins, I0 1e5"
+    return slices, iters, name
+
+
+def make_scans(rc, torch, slices, seed):
+    """Simulate the sinograms of every slice on the GPU (grouped by geometry)."""
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    lo_parts, hi_parts = [], []
+    for Z, rho, acq in slices:
+        g = rc.geometry_from_acq(acq)
+        p = rc.default_params(low=acq.low, high=acq.high)
+        nr = acq.n_views * acq.n_bins
+        dZ = torch.from_numpy(np.ascontiguousarray(Z, np.float32)).cuda()
+        dR = torch.from_numpy(np.ascontiguousarray(rho, np.float32)).cuda()
+        noise = torch.randn(2 * nr, device="cuda", generator=gen)
+        lo = torch.empty(nr, device="cuda")
+        hi = torch.empty(nr, device="cuda")
+        rc.simulate(g, p, 1, dZ, dR, noise, acq.i0, lo, hi)
+        lo_parts.append(lo)
+        hi_parts.append(hi)
+    torch.cuda.synchronize()
+    return torch.cat(lo_parts), torch.cat(hi_parts)
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), reasons=parts[4:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        seen = set()
+        for r in rows:
+            for nm, v in zip(names, r["reasons"][1:]):
+                if v.lower() in ("active", "1", "yes"):
+                    seen.add(nm)
+        return dict(sm_mhz=statistics.median(r["sm"] for r in rows), sm_max_mhz=max(r["smax"] for r in rows),
+                    reasons=sorted(seen), samples=len(rows))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU FP64 oracle
+# ---------------------------------------------------------------------------
+
+def oracle_sample(slices, iters_sample):
+    """Time the oracle on one slice of the workload for a bounded number of
+    iterations (image-domain inputs made by the oracle's own model)."""
+    from oracle import alg1, model
+    from synthetic import phantoms as ph
+    Z, rho, acq = slices[0]
+    Z = np.asarray(Z, np.float64)
+    rho = np.asarray(rho, np.float64)
+    ny, nx = Z.shape
+    E = [model.spectrum_bins(s) for s in (acq.low, acq.high)]
+    mus = []
+    for k, (Eb, wb) in enumerate(E):
+        m = sum(w * model.mu_mm(rho, Z, e) for e, w in zip(Eb, wb))
+        mus.append(m * (1 + 0.01 * ph.normal_field((ny, nx), 77 + k)))
+    tab = model.Tables(acq.low, acq.high)
+    prm = alg1.Params(iters=iters_sample)
+    t0 = time.perf_counter()
+    alg1.solve_mm(mus[0], mus[1], tab, prm)
+    dt = time.perf_counter() - t0
+    return dict(value=iters_sample / dt, seconds=dt, nx=nx, ny=ny, iters=iters_sample)
+
+
+def cpu_cores_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    slices, iters, name = workload(args, 0)
+    ny, nx = slices[0][0].shape
+    it = 3 if nx >= 512 else 10
+    vals = []
+    for _ in range(args.warmup):
+        oracle_sample(slices, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(slices, it)["value"])
+    dt = time.perf_counter() - t0
+    value = float(np.mean(vals))
+    cores = cpu_cores_used()
+    line = dict(metric=METRIC, value=value, unit="slice-iters/s", n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000 * dt / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=name, iters=iters, slices=len(slices)),
+                cpu_baseline=dict(value=value, unit="slice-iters/s", cores=cores, kind="oracle",
+                                  sample=f"one {nx}x{ny} slice of the workload, {it} iterations per step, "
+                                         "image-domain inputs from the oracle's model"),
+                e2e=dict(value=value, unit="slice-iters/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# main arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2308_01290_gb300 import build_lib
+    build_lib.build()
+    from paper_2308_01290_gb300 import recon as rc
+
+    slices, iters, name = workload(args, rank)
+    sino_lo, sino_hi = make_scans(rc, torch, slices, seed=4242 + rank)
+    geoms = [rc.geometry_from_acq(acq) for _, _, acq in slices]
+    params = [rc.default_params(low=acq.low, high=acq.high, iters=iters, precision=args.precision)
+              for _, _, acq in slices]
+    solver = rc.Solver(geoms, params)
+    npx = sum(g.nx * g.ny for g in geoms)
+    outZ = torch.empty(npx, device="cuda")
+    outR = torch.empty(npx, device="cuda")
+
+    def step():
+        solver.set_data(sino_lo, sino_hi, on_device=True)
+        solver.step(iters)
+        solver.get(Z=outZ, rhoe=outR, on_device=True)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = solver.launches()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t_start.record()
+    for _ in range(args.steps):
+        step()
+    t_end.record()
+    barrier()
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    launches = (solver.launches() - l0) // args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    units = len(slices) * iters * args.steps * world
+    value = units / (ms / 1000.0)
+
+    # end to end through the public API: pinned host sinograms in, host maps out
+    h_lo = sino_lo.cpu().pin_memory()
+    h_hi = sino_hi.cpu().pin_memory()
+    h_Z = torch.empty(npx, dtype=torch.float32).pin_memory()
+    h_R = torch.empty(npx, dtype=torch.float32).pin_memory()
+
+    def step_e2e():
+        solver.set_data(h_lo.data_ptr(), h_hi.data_ptr(), on_device=False)
+        solver.step(iters)
+        solver.get(Z=h_Z.data_ptr(), rhoe=h_R.data_ptr(), on_device=False)
+
+    step_e2e()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step_e2e()
+    e1.record()
+    barrier()
+    e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+    e2e = dict(value=units / (e_ms / 1000.0), unit="slice-iters/s",
+               h2d_bytes_per_step=int(h_lo.numel() + h_hi.numel()) * 4,
+               d2h_bytes_per_step=int(h_Z.numel() + h_R.numel()) * 4)
+
+    extra = {}
+    if rank == 0 and not args.no_fp64:
+        # plain FP64 path: same algorithm in double, one slice at a time
+        Zs, Rs, acq0 = slices[0]
+        g0 = rc.geometry_from_acq(acq0)
+        it64 = min(iters, 20)
+        p64 = rc.default_params(low=acq0.low, high=acq0.high, iters=it64, precision=0)
+        s64 = rc.Solver(g0, p64)
+        nr = acq0.n_views * acq0.n_bins
+        s64.set_data(sino_lo[:nr], sino_hi[:nr], on_device=True)
+        s64.step(2)
+        torch.cuda.synchronize()
+        s64.set_data(sino_lo[:nr], sino_hi[:nr], on_device=True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        s64.step(it64)
+        b.record()
+        torch.cuda.synchronize()
+        v64 = it64 / (a.elapsed_time(b) / 1000.0)
+        extra["fp64_plain"] = dict(value=v64, unit="slice-iters/s",
+                                   sample=f"one {g0.nx}x{g0.ny} slice, {it64} iterations, precision FP64, "
+                                          "one slice per launch sequence")
+        s64.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        r = oracle_sample(slices, 3 if slices[0][0].shape[1] >= 512 else 10)
+        cpu = dict(value=r["value"], unit="slice-iters/s", cores=cpu_cores_used(), kind="oracle",
+                   sample=f"one {r['nx']}x{r['ny']} slice of the workload, {r['iters']} iterations, "
+                          f"{r['seconds']:.1f} s, image-domain inputs from the oracle's model")
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit="slice-iters/s", n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak",
+                    vs_baseline=None, dtype="f32" if args.precision == 1 else "f64", data="synthetic",
+                    config=dict(workload=name, slices=len(slices), iters=iters, precision=args.precision,
+                                l2="working set > L2 (no flush needed)"),
+                    e2e=e2e, gpu_launches=int(launches), clocks=clk, roofline=None, cpu_baseline=cpu, **extra)
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,247 @@
+/*
+ * recon.h -- C ABI of librecon: one-step iterative estimation of effective
+ * atomic number (Z) and relative electron density (rho_e) maps from
+ * dual-energy CT with multi-domain gradient-L0 regularisation
+ * (Wang et al., "One-step Iterative Estimation of Effective Atomic Number
+ * and Electron Density for Dual Energy CT", arXiv 2308.01290).
+ *
+ * The library runs Algorithm 1 of Sec. II-D on the GPU: per iteration the
+ * hard threshold of the auxiliary gradients of f1, f2, rho_e and Z^m
+ * (eq. sol_hv), the FFT-diagonalised updates of f1, f2 and rho_e, and the
+ * Z^m quadratic update (a preconditioned CG solve), followed by the beta
+ * continuation.  Inputs are either reconstructed mu images at the low and
+ * high energy (the paper's input, Sec. III) or -log sinograms of a fan-beam
+ * scan, which the library reconstructs by FBP first.
+ *
+ * Conventions, for every function below:
+ *  - return 0 (RECON_OK) on success, a negative RECON_E* code otherwise; no
+ *    C++ exception crosses this boundary; recon_last_error() gives a message;
+ *  - images are row-major float32, ny rows of nx values, concatenated slice
+ *    after slice (no padding); sinograms are n_views rows of n_bins values;
+ *  - pointers marked "device" are CUDA device pointers on the current
+ *    device, "host" are host pointers; the caller owns every buffer passed
+ *    in and the library only borrows it for the duration of the call (for
+ *    device buffers: until the work queued on the handle's stream finishes);
+ *  - attenuation images are in 1/mm; energies in keV;
+ *  - a handle is not thread-safe; distinct handles may be used from
+ *    different threads; all work of a handle is queued on its CUDA stream.
+ */
+#ifndef RECON_H
+#define RECON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RECON_OK 0
+#define RECON_EINVAL (-1)   /* bad argument (sizes, geometry, parameters) */
+#define RECON_ENOMEM (-2)   /* device or host allocation failed */
+#define RECON_ECUDA (-3)    /* a CUDA call failed */
+#define RECON_ETIMEOUT (-4) /* a bounded device wait expired */
+#define RECON_ENAN (-5)     /* non-finite values in inputs or results */
+#define RECON_EBUDGET (-6)  /* request exceeds the configured memory budget */
+#define RECON_ESTATE (-7)   /* call out of order (e.g. step before set_data) */
+
+#define RECON_MAX_FILTERS 4
+#define RECON_MAX_SIDE 2048
+
+/* Scan and image geometry.  Image: nx x ny pixels of pixel_mm centred on the
+ * isocentre (row j at y = (j - (ny-1)/2) pixel_mm).  Fan beam: source at
+ * sid_mm (cos t, sin t), t = start_rad + arc_rad k / n_views; flat detector
+ * at sdd_mm from the source, bin b centred at (b - (n_bins-1)/2) bin_mm.
+ * n_views = 0 means the inputs are images, not sinograms. */
+typedef struct recon_geometry {
+    int32_t nx, ny;
+    double pixel_mm;
+    int32_t n_views, n_bins;
+    double sid_mm, sdd_mm, bin_mm;
+    double start_rad, arc_rad;
+} recon_geometry;
+
+typedef struct recon_filter {
+    double Z, rhoe, thickness_mm;
+} recon_filter;
+
+/* One energy arm.  kind 0: monoenergetic at kev.  kind 1: Kramers spectrum
+ * (kvp - E)/E on 1 keV bins E = 10 .. kvp-1 keV, filtered by the listed
+ * filters through the attenuation model, photon-counting detection. */
+typedef struct recon_spectrum {
+    int32_t kind;
+    int32_t n_filters;
+    double kev;
+    double kvp;
+    recon_filter filters[RECON_MAX_FILTERS];
+} recon_spectrum;
+
+/* Parameters of Algorithm 1.  The paper prints none of lambda, beta0,
+ * beta_max, tau, kappa ("experimentally optimized", Sec. IV);
+ * recon_default_params() fills the values this library was validated with. */
+typedef struct recon_params {
+    recon_spectrum low, high;        /* acquisition arms E_L, E_H */
+    double e1_kev, e2_kev;           /* synthesis energies (50, 200 keV, Sec. II-A) */
+    double basis_z[2], basis_rhoe[2];/* basis materials 1, 2 (Z, rho_e) */
+    double lambda;                   /* L0 weight (normalised units) */
+    double beta0, beta_max, tau;     /* beta schedule, beta~ = tau beta */
+    double kappa;                    /* <= 0: (beta_max/beta0)^(1/iters) */
+    int32_t iters;                   /* iterations of Algorithm 1 */
+    int32_t precision;               /* 1: FP32 maps + FP64 reductions/Newton; 0: FP64 */
+    int32_t order;                   /* 0: f1,f2 Jacobi as printed; 1: Gauss-Seidel */
+    int32_t cg_max_iters;            /* cap of the Z^m PCG per iteration */
+    double cg_tol;                   /* relative residual of the Z^m PCG */
+    double z_clip_max;               /* initial Z^m clipped to Z <= z_clip_max */
+    double rho_air;                  /* initial Z^m set to water where rho_e < rho_air */
+} recon_params;
+
+/* Per-slice statistics of the last iteration run by recon_step.  The
+ * objective terms are those of eq. obj_unconstraint at the iterate the
+ * iteration started from, with its own thresholded gradients. */
+typedef struct recon_stats {
+    int32_t k;                 /* iterations done */
+    int32_t cg_iters;          /* PCG steps of the last Z^m solve */
+    double beta;               /* beta of the last iteration */
+    double fid_low, fid_high;  /* ||f1 mu1 + f2 mu2 - mu||^2 at E_L, E_H */
+    double model_e1, model_e2; /* model-consistency terms at E1, E2 */
+    double relax;              /* beta sum_g ||d g - (h_g, v_g)||^2 */
+    double l0;                 /* lambda sum_g C(h_g, v_g) */
+    int64_t nnz[4];            /* C(h_g, v_g) for f1, f2, rho_e, Z^m */
+    double cg_rel_residual;    /* final relative residual of the Z^m PCG */
+} recon_stats;
+
+typedef struct recon_ctx recon_ctx;
+
+/* Fill p with the library defaults: mono 60/90 keV arms, E1/E2 = 50/200 keV,
+ * bone-like (13, 1.7) and water (7.45, 1.0) bases, lambda 1e-2,
+ * beta0 = 2 lambda, beta_max 1e5, tau 1, iters 50, precision 1, order 0,
+ * cg_max_iters 64, cg_tol 1e-6, z_clip_max 30, rho_air 0.1. */
+int recon_default_params(recon_params* p);
+
+/* Create a handle for one slice (recon_init) or a batch of n slices of
+ * possibly different sizes and parameters (recon_init_batch; geoms and
+ * params are host arrays of n entries; every entry must have the same
+ * precision).  stream: a cudaStream_t (NULL = legacy default stream).
+ * Allocates all device memory of the solve up front.  Errors: EINVAL for
+ * sizes outside [1, RECON_MAX_SIDE] or sizes whose prime factors are not all
+ * in {2, 3, 5, 7}, ENOMEM, ECUDA. */
+int recon_init(const recon_geometry* geom, const recon_params* params, void* stream, recon_ctx** out);
+int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params* params, void* stream,
+                     recon_ctx** out);
+
+/* Load the inputs of every slice and run the initialisation of Algorithm 1
+ * (Cramer decomposition, synthesis, closed-form rho_e and Z^m).  low/high:
+ * mu images (1/mm) when the geometry has n_views = 0, else -log sinograms
+ * which are reconstructed by FBP; host or device (on_device = 1) buffers.
+ * Resets the iteration counter and beta. */
+int recon_set_data(recon_ctx* ctx, const float* low, const float* high, int on_device);
+
+/* Run n_iters iterations of Algorithm 1 on every slice that has not yet done
+ * its params.iters iterations (slices that finish stop early).  stats: NULL
+ * or a host array of one recon_stats per slice (computing them adds
+ * reductions).  Resumable: successive calls continue the same solve. */
+int recon_step(recon_ctx* ctx, int32_t n_iters, recon_stats* stats);
+
+/* Copy results out: Z = Z_w (Z^m/Z_w^m)^(1/m) by FP64 Newton (1 where
+ * Z^m <= 0), rho_e, f1, f2; any pointer may be NULL; host or device. */
+int recon_get(recon_ctx* ctx, float* Z, float* rhoe, float* f1, float* f2, int on_device);
+
+/* Blocks until the handle's queued work is done. */
+int recon_sync(recon_ctx* ctx);
+
+void recon_destroy(recon_ctx* ctx);
+
+/* One-shot solve of one slice with default parameters (lambda, beta0 = beta,
+ * iters overridden): init + set_data + step + get + destroy.  lowE/highE are
+ * host images or sinograms (see recon_set_data); Z_out and rhoe_out host. */
+int recon_solve(const float* lowE, const float* highE, const recon_geometry* geom, double lambda, double beta,
+                int32_t iters, float* Z_out, float* rhoe_out);
+
+const char* recon_strerror(int code);
+const char* recon_last_error(void);
+
+/* ---- fan-beam input stage (n slices of the same geometry, device buffers,
+ * queued on stream) ---- */
+
+/* sino = A img: Joseph ray-driven line integrals (mm * 1/mm). */
+int recon_project(const recon_geometry* geom, int32_t n, const float* img, float* sino, void* stream);
+/* img = A^T sino: the exact transpose of recon_project (scatter; img is
+ * overwritten). */
+int recon_backproject(const recon_geometry* geom, int32_t n, const float* sino, float* img, void* stream);
+/* Flat-detector fan-beam FBP of a full scan (cosine weight, Ram-Lak ramp,
+ * 1/U^2 weighted pixel-driven backprojection). */
+int recon_fbp(const recon_geometry* geom, int32_t n, const float* sino, float* img, void* stream);
+/* Synthetic scan: -log sinograms of both arms of params for truth maps Z and
+ * rho_e (images, device).  noise: NULL (noiseless) or 2 * n * n_views *
+ * n_bins standard normal deviates (low arm first) used as the Gaussian
+ * approximation of Poisson counting noise at i0 photons per bin; counts are
+ * floored at 0.5 before the log. */
+int recon_simulate(const recon_geometry* geom, const recon_params* params, int32_t n, const float* Z,
+                   const float* rhoe, const float* noise, double i0, float* sino_low, float* sino_high,
+                   void* stream);
+
+/* ---- introspection for tests (operators of one iteration) ---- */
+
+/* Scalar tables the solve uses (host FP64): out[0..3] basis at (E_L, E_H)
+ * a11 a12 a21 a22 (a_ki = mu_k(E_i) / S), out[4..7] at (E1, E2) b11 b12 b21
+ * b22, out[8..9] P1 P2, out[10..11] psi1 psi2, out[12] r = (E1/E2)^n,
+ * out[13..14] c_f1 c_f2, out[15] c_rho, out[16] a_w, out[17] S (1/mm per
+ * barn).  Returns the number of values written (18). */
+int recon_model_tables(const recon_params* params, double* out);
+
+/* Field identifiers for recon_debug_field. */
+#define RECON_F_F1 0
+#define RECON_F_F2 1
+#define RECON_F_RHO 2
+#define RECON_F_Z 3
+#define RECON_F_MUL 4
+#define RECON_F_MUH 5
+#define RECON_F_RHS_F1 6
+#define RECON_F_RHS_F2 7
+#define RECON_F_DIV_RHO 8
+#define RECON_F_DIV_Z 9
+#define RECON_F_RHS_RHO 10
+#define RECON_F_A2 11
+#define RECON_F_RHS_Z 12
+#define RECON_F_CG_R 13
+#define RECON_F_CG_P0 14
+#define RECON_F_CG_P1 15
+#define RECON_F_CG_Q 16
+#define RECON_F_CG_Y 17
+#define RECON_F_COUNT 18
+
+/* Device pointer of field f of slice s (storage: float, or double when
+ * precision = 0; row pitch in elements in *pitch). */
+int recon_debug_field(recon_ctx* ctx, int32_t field, int32_t slice, void** dev_ptr, int32_t* pitch,
+                      int32_t* elem_bytes);
+
+/* Copy field f of slice s to (to_device = 0) or from (to_device = 1) a host
+ * FP64 array of ny * nx values (row-major, no padding); synchronous. */
+int recon_debug_io(recon_ctx* ctx, int32_t field, int32_t slice, double* host, int32_t to_device);
+
+/* Operator identifiers for recon_debug_op: each runs one stage of an
+ * iteration on every active slice at the handle's current beta. */
+#define RECON_OP_INIT 0        /* mu images -> f1, f2, rho_e, z */
+#define RECON_OP_THRESH_RHS 1  /* eq. sol_hv + right-hand sides of f1, f2; beta~ div(h,v) of rho_e, z */
+#define RECON_OP_SOLVE_F 2     /* FFT solves of f1, f2 */
+#define RECON_OP_SYNTH 3       /* mu(E_j) from new f; rhs of rho_e; a^2, rhs of Z^m */
+#define RECON_OP_SOLVE_RHO 4   /* FFT solve of rho_e */
+#define RECON_OP_SOLVE_Z 5     /* PCG of Z^m */
+#define RECON_OP_NEXT_BETA 6   /* beta <- kappa beta, k <- k + 1 */
+int recon_debug_op(recon_ctx* ctx, int32_t op);
+
+/* Per-slice scalars: out[0] beta, [1] beta~, [2] k, [3] mean a^2, [4] PCG
+ * steps of the last solve, [5] final relative residual. */
+int recon_debug_scalars(recon_ctx* ctx, int32_t slice, double* out);
+
+/* Number of kernels this handle has launched since creation (counting
+ * each launch of each of the library's kernels). */
+int64_t recon_kernel_launches(recon_ctx* ctx);
+
+/* sizeof of recon_geometry, recon_spectrum, recon_params, recon_stats as
+ * compiled into the library (for bindings to check their layouts). */
+int recon_abi_sizes(int64_t* out4);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RECON_H */

@@ -1,0 +1,367 @@
+// Fan-beam input stage: Joseph ray-driven projector A, its exact transpose
+// A^T, flat-detector fan-beam FBP, and the synthetic scan used to make test
+// and benchmark inputs.
+//
+// Geometry (shared by all kernels): image pixel (row j, column i) centre
+// x = (i - (nx-1)/2) p, y = (j - (ny-1)/2) p; view k at angle
+// t = start + arc k / n_views with source sid (cos t, sin t); detector bin b
+// at source - sdd (cos t, sin t) + u_b (-sin t, cos t),
+// u_b = (b - (n_bins-1)/2) bin_mm.
+//
+// A: along the dominant axis of the ray the line is sampled once per pixel
+// column (row) and linearly interpolated between the two pixels it passes
+// between (zero outside the grid); each sample weighs p |r| / |r_dominant|.
+// Per-ray set-up is FP64; the marching is FP32 with the fractional index
+// evaluated as start + i * slope from FP64-rounded start and slope.
+#include <cmath>
+#include <vector>
+
+#include "ctx.h"
+
+namespace recon {
+
+namespace {
+
+struct RaySetup {
+    int xmajor;        // 1: march over columns, 0: over rows
+    float f0, df;      // fractional cross index at march index 0 and its slope
+    float w;           // step weight
+};
+
+__device__ __forceinline__ RaySetup ray_setup(const recon_geometry& g, int view, int bin) {
+    const double t = g.start_rad + g.arc_rad * (double)view / (double)g.n_views;
+    double s, c;
+    sincos(t, &s, &c);
+    const double u = ((double)bin - 0.5 * (g.n_bins - 1)) * g.bin_mm;
+    const double Sx = g.sid_mm * c, Sy = g.sid_mm * s;
+    const double rx = -g.sdd_mm * c - u * s;
+    const double ry = -g.sdd_mm * s + u * c;
+    const double p = g.pixel_mm;
+    const double len = sqrt(rx * rx + ry * ry);
+    RaySetup r;
+    if (fabs(rx) >= fabs(ry)) {
+        r.xmajor = 1;
+        // column i: x_i = (i - (nx-1)/2) p; y = Sy + (x_i - Sx) ry/rx; jf = y/p + (ny-1)/2
+        const double x0 = -0.5 * (g.nx - 1) * p;
+        const double y0 = Sy + (x0 - Sx) * ry / rx;
+        r.f0 = (float)(y0 / p + 0.5 * (g.ny - 1));
+        r.df = (float)(ry / rx);
+        r.w = (float)(p * len / fabs(rx));
+    } else {
+        r.xmajor = 0;
+        const double y0 = -0.5 * (g.ny - 1) * p;
+        const double x0 = Sx + (y0 - Sy) * rx / ry;
+        r.f0 = (float)(x0 / p + 0.5 * (g.nx - 1));
+        r.df = (float)(rx / ry);
+        r.w = (float)(p * len / fabs(ry));
+    }
+    return r;
+}
+
+// one thread per ray; sino[(slice * n_views + view) * n_bins + bin]
+__global__ void k_project(recon_geometry g, int n, const float* __restrict__ img, float* __restrict__ sino) {
+    const long long nr = (long long)g.n_views * g.n_bins;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nr * n) return;
+    const int sl = (int)(tid / nr);
+    const int ray = (int)(tid - (long long)sl * nr);
+    const int view = ray / g.n_bins, bin = ray - view * g.n_bins;
+    const RaySetup r = ray_setup(g, view, bin);
+    const float* im = img + (long long)sl * g.nx * g.ny;
+    float acc = 0.f;
+    if (r.xmajor) {
+        for (int i = 0; i < g.nx; ++i) {
+            const float jf = fmaf((float)i, r.df, r.f0);
+            const float fl = floorf(jf);
+            const int j0 = (int)fl;
+            const float w1 = jf - fl;
+            if (j0 >= 0 && j0 < g.ny) acc += (1.f - w1) * __ldg(im + (long long)j0 * g.nx + i);
+            if (j0 + 1 >= 0 && j0 + 1 < g.ny) acc += w1 * __ldg(im + (long long)(j0 + 1) * g.nx + i);
+        }
+    } else {
+        for (int j = 0; j < g.ny; ++j) {
+            const float xf = fmaf((float)j, r.df, r.f0);
+            const float fl = floorf(xf);
+            const int i0 = (int)fl;
+            const float w1 = xf - fl;
+            const float* row = im + (long long)j * g.nx;
+            if (i0 >= 0 && i0 < g.nx) acc += (1.f - w1) * __ldg(row + i0);
+            if (i0 + 1 >= 0 && i0 + 1 < g.nx) acc += w1 * __ldg(row + i0 + 1);
+        }
+    }
+    sino[tid] = acc * r.w;
+}
+
+// exact transpose of k_project (same samples, scattered with atomics)
+__global__ void k_backproject(recon_geometry g, int n, const float* __restrict__ sino, float* img) {
+    const long long nr = (long long)g.n_views * g.n_bins;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= nr * n) return;
+    const int sl = (int)(tid / nr);
+    const int ray = (int)(tid - (long long)sl * nr);
+    const int view = ray / g.n_bins, bin = ray - view * g.n_bins;
+    const RaySetup r = ray_setup(g, view, bin);
+    float* im = img + (long long)sl * g.nx * g.ny;
+    const float v = sino[tid] * r.w;
+    if (v == 0.f) return;
+    if (r.xmajor) {
+        for (int i = 0; i < g.nx; ++i) {
+            const float jf = fmaf((float)i, r.df, r.f0);
+            const float fl = floorf(jf);
+            const int j0 = (int)fl;
+            const float w1 = jf - fl;
+            if (j0 >= 0 && j0 < g.ny) atomicAdd(im + (long long)j0 * g.nx + i, (1.f - w1) * v);
+            if (j0 + 1 >= 0 && j0 + 1 < g.ny) atomicAdd(im + (long long)(j0 + 1) * g.nx + i, w1 * v);
+        }
+    } else {
+        for (int j = 0; j < g.ny; ++j) {
+            const float xf = fmaf((float)j, r.df, r.f0);
+            const float fl = floorf(xf);
+            const int i0 = (int)fl;
+            const float w1 = xf - fl;
+            float* row = im + (long long)j * g.nx;
+            if (i0 >= 0 && i0 < g.nx) atomicAdd(row + i0, (1.f - w1) * v);
+            if (i0 + 1 >= 0 && i0 + 1 < g.nx) atomicAdd(row + i0 + 1, w1 * v);
+        }
+    }
+}
+
+// FBP step 1: cosine weight sid / sqrt(sid^2 + s^2) (s at the isocentre
+// plane) and Ram-Lak ramp h(0) = 1/(4 ds^2), h(odd m) = -1/(pi m ds)^2,
+// q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view).
+__global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ sino, float* __restrict__ q) {
+    extern __shared__ float wrow[];
+    const int sv = blockIdx.x;   // slice * n_views + view
+    if (sv >= n * g.n_views) return;
+    const int nb = g.n_bins;
+    const double ds = g.bin_mm * g.sid_mm / g.sdd_mm;
+    const float* src = sino + (long long)sv * nb;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const double s = ((double)b - 0.5 * (nb - 1)) * ds;
+        wrow[b] = (float)((double)src[b] * g.sid_mm / sqrt(g.sid_mm * g.sid_mm + s * s));
+    }
+    __syncthreads();
+    const float h0 = (float)(0.25 / ds);                    // ds * 1/(4 ds^2)
+    const float hodd = (float)(-1.0 / (M_PI * M_PI * ds));  // ds * (-1/(pi^2 ds^2)) / m^2
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        float acc = 0.f;
+        // odd offsets m = b - k, both signs
+        for (int m = 1; m < nb; m += 2) {
+            const float hm = hodd / ((float)m * (float)m);
+            float pair = 0.f;
+            if (b - m >= 0) pair += wrow[b - m];
+            if (b + m < nb) pair += wrow[b + m];
+            acc = fmaf(hm, pair, acc);
+        }
+        q[(long long)sv * nb + b] = fmaf(h0, wrow[b], acc);
+    }
+}
+
+// FBP step 2: pixel-driven backprojection of the filtered rows with weight
+// 1/U^2, U = (sid - x cos t - y sin t) / sid, detector coordinate at the
+// isocentre s' = sid (-x sin t + y cos t) / (U sid), linear interpolation,
+// times (arc / n_views) / 2 for a full scan.
+__global__ void k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q, float* __restrict__ img) {
+    extern __shared__ float trig[];   // cos, sin per view
+    for (int v = threadIdx.x; v < g.n_views; v += blockDim.x) {
+        double s, c;
+        sincos(g.start_rad + g.arc_rad * (double)v / (double)g.n_views, &s, &c);
+        trig[2 * v] = (float)c;
+        trig[2 * v + 1] = (float)s;
+    }
+    __syncthreads();
+    const long long npx = (long long)g.nx * g.ny;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= npx * n) return;
+    const int sl = (int)(tid / npx);
+    const int pix = (int)(tid - (long long)sl * npx);
+    const int j = pix / g.nx, i = pix - j * g.nx;
+    const float x = (float)(((double)i - 0.5 * (g.nx - 1)) * g.pixel_mm);
+    const float y = (float)(((double)j - 0.5 * (g.ny - 1)) * g.pixel_mm);
+    const float sid = (float)g.sid_mm;
+    const float inv_ds = (float)(g.sdd_mm / (g.bin_mm * g.sid_mm));
+    const float bc = 0.5f * (g.n_bins - 1);
+    const float* qs = q + (long long)sl * g.n_views * g.n_bins;
+    float acc = 0.f;
+    for (int v = 0; v < g.n_views; ++v) {
+        const float c = trig[2 * v], s = trig[2 * v + 1];
+        const float L = sid - (x * c + y * s);
+        const float invL = 1.f / L;
+        const float sp = sid * (y * c - x * s) * invL;
+        const float bf = fmaf(sp, inv_ds, bc);
+        const float fl = floorf(bf);
+        const int b0 = (int)fl;
+        const float w1 = bf - fl;
+        const float* row = qs + (long long)v * g.n_bins;
+        float val = 0.f;
+        if (b0 >= 0 && b0 < g.n_bins) val += (1.f - w1) * __ldg(row + b0);
+        if (b0 + 1 >= 0 && b0 + 1 < g.n_bins) val += w1 * __ldg(row + b0 + 1);
+        const float U = L / sid;
+        acc += val / (U * U);
+    }
+    img[tid] = acc * (float)(0.5 * g.arc_rad / g.n_views);
+}
+
+// rho_e z with z = (Z / Z_w)^m (the photoelectric line-integral map)
+__global__ void k_rho_z(long long npx, const float* Z, const float* rho, float* out, float zw, float m) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npx) return;
+    out[i] = rho[i] * powf(Z[i] / zw, m);
+}
+
+// expected counts I0 sum_b w_b exp(-S (P_b A1 + KN_b A2)), Gaussian noise,
+// floor 0.5, -log(counts / I0)
+__global__ void k_counts(long long nrays, const float* A1, const float* A2, const double* tab, int nb_lo, int nb_hi,
+                         const float* noise, double i0, double S, float* lo, float* hi) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nrays) return;
+    const double a1 = A1[i], a2 = A2[i];
+    for (int arm = 0; arm < 2; ++arm) {
+        const int nb = arm ? nb_hi : nb_lo;
+        const double* t = tab + (arm ? 3 * nb_lo : 0);
+        double lam = 0.0;
+        for (int b = 0; b < nb; ++b) lam += t[3 * b] * exp(-S * (t[3 * b + 1] * a1 + t[3 * b + 2] * a2));
+        lam *= i0;
+        double cnt = lam;
+        if (noise) cnt = lam + sqrt(lam) * (double)noise[arm * nrays + i];
+        cnt = cnt < 0.5 ? 0.5 : cnt;
+        (arm ? hi : lo)[i] = (float)(-log(cnt / i0));
+    }
+}
+
+int check_geom(const recon_geometry& g) {
+    if (g.nx < 1 || g.ny < 1 || g.nx > RECON_MAX_SIDE || g.ny > RECON_MAX_SIDE || g.n_views < 1 || g.n_bins < 1 ||
+        !(g.pixel_mm > 0) || !(g.sid_mm > 0) || !(g.sdd_mm > g.sid_mm) || !(g.bin_mm > 0)) {
+        set_error("invalid fan-beam geometry");
+        return RECON_EINVAL;
+    }
+    const double half_diag = 0.5 * g.pixel_mm * std::sqrt((double)g.nx * g.nx + (double)g.ny * g.ny);
+    if (half_diag >= g.sid_mm) {
+        set_error("image reaches the source circle");
+        return RECON_EINVAL;
+    }
+    return RECON_OK;
+}
+
+}  // namespace
+
+int ct_project(const recon_geometry& g, int n, const float* img, float* sino, cudaStream_t st, long long* launches) {
+    int rc = check_geom(g);
+    if (rc) return rc;
+    const long long total = (long long)n * g.n_views * g.n_bins;
+    k_project<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, img, sino);
+    if (launches) *launches += 1;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
+int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img, cudaStream_t st,
+                   long long* launches) {
+    int rc = check_geom(g);
+    if (rc) return rc;
+    RECON_CUDA(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)n * g.nx * g.ny, st));
+    const long long total = (long long)n * g.n_views * g.n_bins;
+    k_backproject<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, sino, img);
+    if (launches) *launches += 1;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
+int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,
+           long long* launches) {
+    int rc = check_geom(g);
+    if (rc) return rc;
+    if (g.n_views * 2 * sizeof(float) > 96 * 1024 || g.n_bins * sizeof(float) > 96 * 1024) {
+        set_error("too many views or bins");
+        return RECON_EINVAL;
+    }
+    k_fbp_filter<<<n * g.n_views, 256, g.n_bins * sizeof(float), st>>>(g, n, sino, scratch);
+    const long long total = (long long)n * g.nx * g.ny;
+    k_fbp_backproject<<<(unsigned)((total + 255) / 256), 256, 2 * g.n_views * sizeof(float), st>>>(g, n, scratch,
+                                                                                                   img);
+    if (launches) *launches += 2;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
+}  // namespace recon
+
+using namespace recon;
+
+extern "C" int recon_project(const recon_geometry* geom, int32_t n, const float* img, float* sino, void* stream) {
+    if (!geom || n < 1 || !img || !sino) {
+        set_error("recon_project: bad arguments");
+        return RECON_EINVAL;
+    }
+    return ct_project(*geom, n, img, sino, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int recon_backproject(const recon_geometry* geom, int32_t n, const float* sino, float* img, void* stream) {
+    if (!geom || n < 1 || !img || !sino) {
+        set_error("recon_backproject: bad arguments");
+        return RECON_EINVAL;
+    }
+    return ct_backproject(*geom, n, sino, img, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int recon_fbp(const recon_geometry* geom, int32_t n, const float* sino, float* img, void* stream) {
+    if (!geom || n < 1 || !img || !sino) {
+        set_error("recon_fbp: bad arguments");
+        return RECON_EINVAL;
+    }
+    float* scratch = nullptr;
+    const size_t bytes = sizeof(float) * (size_t)n * geom->n_views * geom->n_bins;
+    cudaError_t e = cudaMallocAsync((void**)&scratch, bytes, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+    int rc = ct_fbp(*geom, n, sino, img, scratch, (cudaStream_t)stream, nullptr);
+    cudaFreeAsync(scratch, (cudaStream_t)stream);
+    return rc;
+}
+
+extern "C" int recon_simulate(const recon_geometry* geom, const recon_params* params, int32_t n, const float* Z,
+                              const float* rhoe, const float* noise, double i0, float* sino_low, float* sino_high,
+                              void* stream) {
+    if (!geom || !params || n < 1 || !Z || !rhoe || !sino_low || !sino_high || !(i0 > 0)) {
+        set_error("recon_simulate: bad arguments");
+        return RECON_EINVAL;
+    }
+    const cudaStream_t st = (cudaStream_t)stream;
+    const long long npx = (long long)n * geom->nx * geom->ny;
+    const long long nrays = (long long)n * geom->n_views * geom->n_bins;
+    // per-bin table (weight, P(E_b), KN(E_b)) of both arms
+    std::vector<double> e, w, tab;
+    int nbs[2];
+    const recon_spectrum* arms[2] = {&params->low, &params->high};
+    for (int a = 0; a < 2; ++a) {
+        spectrum_bins(*arms[a], e, w);
+        nbs[a] = (int)e.size();
+        for (size_t b = 0; b < e.size(); ++b) {
+            tab.push_back(w[b]);
+            tab.push_back(photo_per_z(e[b]));
+            tab.push_back(klein_nishina_barn(e[b]));
+        }
+    }
+    float *rz = nullptr, *A1 = nullptr, *A2 = nullptr;
+    double* dtab = nullptr;
+    RECON_CUDA(cudaMallocAsync((void**)&rz, sizeof(float) * npx, st));
+    RECON_CUDA(cudaMallocAsync((void**)&A1, sizeof(float) * nrays, st));
+    RECON_CUDA(cudaMallocAsync((void**)&A2, sizeof(float) * nrays, st));
+    RECON_CUDA(cudaMallocAsync((void**)&dtab, sizeof(double) * tab.size(), st));
+    RECON_CUDA(cudaMemcpyAsync(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
+    k_rho_z<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(npx, Z, rhoe, rz, (float)water_z(), (float)z_exponent());
+    int rc = ct_project(*geom, n, rz, A1, st, nullptr);
+    if (!rc) rc = ct_project(*geom, n, rhoe, A2, st, nullptr);
+    if (!rc) {
+        k_counts<<<(unsigned)((nrays + 255) / 256), 256, 0, st>>>(nrays, A1, A2, dtab, nbs[0], nbs[1], noise, i0,
+                                                                  scale_per_mm(), sino_low, sino_high);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) rc = cuda_fail(err, "k_counts");
+    }
+    // the host table must outlive the async copy
+    cudaStreamSynchronize(st);
+    cudaFreeAsync(rz, st);
+    cudaFreeAsync(A1, st);
+    cudaFreeAsync(A2, st);
+    cudaFreeAsync(dtab, st);
+    return rc;
+}

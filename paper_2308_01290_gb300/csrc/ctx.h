@@ -1,0 +1,91 @@
+// Host-side solve handle shared by the C ABI and the solver orchestration.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "model_tables.h"
+#include "recon.h"
+
+namespace recon {
+
+constexpr int kNumFields = RECON_F_COUNT;
+constexpr int kNumSpectra = 3;
+
+struct DevItemList {
+    std::vector<Item> h_items;
+    std::vector<int> h_lo, h_cnt;
+    Item* items = nullptr;
+    int* lo = nullptr;
+    int* cnt = nullptr;
+    double* partials = nullptr;
+    unsigned int* counters = nullptr;
+    int n = 0;
+    ItemList view() const { return ItemList{items, n, lo, cnt, partials, counters}; }
+};
+
+struct Ctx {
+    int n = 0;             // slices
+    int precision = 1;     // 1: float maps, 0: double maps
+    size_t elem = 4;       // bytes per real element
+    cudaStream_t stream = nullptr;
+    std::vector<recon_geometry> geo;
+    std::vector<recon_params> prm;
+    std::vector<Tables> tab;
+    std::vector<SliceGeom> sg;
+    long long pool_elems = 0;    // real elements per field pool
+    long long spec_elems = 0;    // complex elements per spectrum pool
+    long long ext_elems = 0;     // unpadded image elements over all slices
+    int max_nx = 0, max_ny = 0;
+    bool sino_input = false;
+    long long sino_elems = 0;
+    std::vector<long long> sino_off;
+
+    // device memory
+    SliceGeom* d_geom = nullptr;
+    SliceConst* d_const = nullptr;
+    SliceState* d_state = nullptr;
+    void* field[kNumFields] = {};
+    void* spec[kNumSpectra] = {};
+    float* d_stage[2] = {};      // unpadded float staging (inputs / outputs)
+    float* d_sino[2] = {};       // sinogram staging when inputs are sinograms
+    float* d_filt = nullptr;     // filtered sinogram scratch (one slice)
+    int* d_cg_pending = nullptr;
+    int* h_cg_pending = nullptr; // pinned
+
+    DevItemList tiles, rows, cols;
+    bool has_data = false;
+    int cg_parity = 0;
+    long long launches = 0;
+    int sm_count = 152;
+    std::vector<void*> allocations;
+};
+
+// Solver entry points (solver.cu); all queue work on ctx.stream.
+int solver_setup(Ctx& c);                      // item lists, constants, scratch
+int solver_load_images(Ctx& c, const float* low, const float* high, int on_device);
+int solver_init_maps(Ctx& c);
+int solver_iterate(Ctx& c, bool stats);        // one iteration of Algorithm 1
+int solver_op(Ctx& c, int op);
+int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int on_device);
+int solver_read_state(Ctx& c, std::vector<SliceState>& out);
+
+// Input stage (ct.cu), float device buffers.
+int ct_project(const recon_geometry& g, int n, const float* img, float* sino, cudaStream_t st, long long* launches);
+int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img, cudaStream_t st,
+                   long long* launches);
+int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,
+           long long* launches);
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define RECON_CUDA(call)                                  \
+    do {                                                  \
+        cudaError_t _e = (call);                          \
+        if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+    } while (0)
+
+}  // namespace recon

@@ -136,7 +136,7 @@ def _place_discs(rng, n_ins, semi_a, semi_b, r_lo, r_hi, margin):
 
 def disc_phantom(n: int, seed: int, *, n_inserts: int = 8, semi_px=(56.0, 44.0),
                  radius_px=(6.0, 12.0), z_range=(5.5, 20.0), rho_range=(0.2, 1.9),
-                 fixed=()) -> dict:
+                 fixed=(), margin=2.0) -> dict:
     """Water ellipse with circular inserts on an n x n grid.
 
     The default arguments are the 128^2 small workload; ``scaled_disc_phantom``
@@ -147,7 +147,7 @@ def disc_phantom(n: int, seed: int, *, n_inserts: int = 8, semi_px=(56.0, 44.0),
     """
     rng = np.random.default_rng(seed)
     a, b = semi_px
-    discs = _place_discs(rng, n_inserts, a, b, radius_px[0], radius_px[1], margin=2.0)
+    discs = _place_discs(rng, n_inserts, a, b, radius_px[0], radius_px[1], margin=margin)
     c = (n - 1) / 2.0
     jj, ii = np.mgrid[0:n, 0:n]
     x = ii - c
@@ -170,9 +170,11 @@ def disc_phantom(n: int, seed: int, *, n_inserts: int = 8, semi_px=(56.0, 44.0),
 
 
 def small_phantom(seed: int, n: int = 128) -> dict:
-    """128^2 workload: 56x44 px water ellipse, 8 inserts r in [6,12] px."""
+    """128^2 workload: 56x44 px water ellipse, 8 inserts r in [6,12] px
+    (scaled with n; fewer inserts below 64 px)."""
     s = n / 128.0
-    return disc_phantom(n, seed, semi_px=(56.0 * s, 44.0 * s), radius_px=(6.0 * s, 12.0 * s))
+    return disc_phantom(n, seed, n_inserts=8 if n >= 64 else 3, semi_px=(56.0 * s, 44.0 * s),
+                        radius_px=(6.0 * s, 12.0 * s), margin=2.0 * min(1.0, s))
 
 
 def clinical_phantom(seed: int, n: int = 512, pixel_mm: float = 1.0) -> dict:

@@ -1,0 +1,59 @@
+"""CPU-side checks of the C ABI: the library loads and exports every function
+declared in include/recon.h; host-only entry points (defaults, model tables)
+agree with the oracle's tables.  No GPU compute is called here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def rc():
+    from paper_2308_01290_gb300 import build_lib
+    build_lib.build()
+    from paper_2308_01290_gb300 import recon
+    return recon
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "recon.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(recon_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_match_header(rc):
+    decl = declared_functions()
+    assert len(decl) >= 20
+    for name in decl:
+        assert hasattr(rc.lib, name), name
+    assert set(decl) == set(rc.EXPORTS)
+
+
+def test_struct_sizes_match_c_layout(rc):
+    import ctypes as C
+    out = (C.c_int64 * 4)()
+    assert rc.lib.recon_abi_sizes(out) == 0
+    assert tuple(out) == (C.sizeof(rc.Geometry), C.sizeof(rc.Spectrum), C.sizeof(rc.Params), C.sizeof(rc.Stats))
+    p = rc.default_params()
+    assert p.iters == 50 and p.precision == 1 and abs(p.lambda_ - 1e-2) < 1e-15
+
+
+def test_model_tables_match_oracle(rc):
+    from oracle import model
+    from synthetic import phantoms as ph
+    for kind in ("small", "clinical"):
+        acq = ph.acquisition(kind, n=128)
+        p = rc.default_params(low=acq.low, high=acq.high)
+        t = rc.model_tables(p)
+        tab = model.Tables(acq.low, acq.high)
+        ref = np.concatenate([tab.a.ravel(), tab.b.ravel(), tab.P, tab.psi, [tab.r], tab.c_f, [tab.c_rho],
+                              [tab.a_w], [model.S_MM]])
+        assert np.allclose(t, ref, rtol=1e-12, atol=0), (kind, t - ref)
+
+
+def test_strerror(rc):
+    assert rc.lib.recon_strerror(-1) == b"invalid argument"
+    assert rc.lib.recon_strerror(0) == b"ok"
