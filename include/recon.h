@@ -237,6 +237,27 @@ int recon_debug_scalars(recon_ctx* ctx, int32_t slice, double* out);
  * each launch of each of the library's kernels). */
 int64_t recon_kernel_launches(recon_ctx* ctx);
 
+/* Kernel families of the solver, for recon_profile*: 0 threshold + rhs,
+ * 1 FFT rows forward, 2 FFT columns (spectral divide), 3 FFT rows inverse,
+ * 4 synthesis, 5 PCG start, 6 PCG matvec, 7 PCG update, 8-10 the three FFT
+ * passes of the PCG preconditioner, 11 other. */
+#define RECON_KF_COUNT 12
+
+/* Time the launches of the kernel families whose bit is set in mask with
+ * CUDA events on the handle's stream (0 = off).  Algorithmic bytes and launch
+ * counts are always accounted. */
+int recon_profile(recon_ctx* ctx, uint32_t mask);
+
+/* Since the previous read (or creation): per family the summed event time in
+ * ms (families not timed: 0), launches, and algorithmic bytes (the bytes each
+ * launch must read and write in HBM: interior elements of its inputs and
+ * outputs, counted per processed tile / row group / column group).  Arrays of
+ * RECON_KF_COUNT entries, each may be NULL.  Synchronises the stream. */
+int recon_profile_read(recon_ctx* ctx, double* ms, int64_t* launches, uint64_t* bytes);
+
+/* Name of kernel family f. */
+const char* recon_profile_name(int32_t family);
+
 /* sizeof of recon_geometry, recon_spectrum, recon_params, recon_stats as
  * compiled into the library (for bindings to check their layouts). */
 int recon_abi_sizes(int64_t* out4);

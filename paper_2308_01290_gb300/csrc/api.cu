@@ -398,6 +398,32 @@ int recon_debug_scalars(recon_ctx* h, int32_t slice, double* out) {
 
 int64_t recon_kernel_launches(recon_ctx* h) { return h ? h->c.launches : -1; }
 
+int recon_profile(recon_ctx* h, uint32_t mask) {
+    if (!h) return RECON_EINVAL;
+    h->c.prof_mask = mask;
+    return RECON_OK;
+}
+
+int recon_profile_read(recon_ctx* h, double* ms, int64_t* launches, uint64_t* bytes) {
+    if (!h) return RECON_EINVAL;
+    long long l[KF_COUNT];
+    unsigned long long b[KF_COUNT];
+    int rc = solver_profile_read(h->c, ms, l, b);
+    if (rc) return rc;
+    for (int f = 0; f < KF_COUNT; ++f) {
+        if (launches) launches[f] = l[f];
+        if (bytes) bytes[f] = b[f];
+    }
+    return RECON_OK;
+}
+
+const char* recon_profile_name(int32_t f) {
+    static const char* names[KF_COUNT] = {"thr_rhs",     "fft_rows_fwd",  "fft_cols",     "fft_rows_inv",
+                                          "synth",       "pcg_start",     "pcg_matvec",   "pcg_update",
+                                          "pcg_pre_rows_fwd", "pcg_pre_cols", "pcg_pre_rows_inv", "other"};
+    return (f >= 0 && f < KF_COUNT) ? names[f] : "?";
+}
+
 int recon_abi_sizes(int64_t* out4) {
     if (!out4) return RECON_EINVAL;
     out4[0] = sizeof(recon_geometry);

@@ -74,6 +74,23 @@ struct ItemList {
     unsigned int* counters;   // one per slice (returned to zero after use)
 };
 
+// Kernel families for timing and algorithmic-byte accounting.
+enum KFam {
+    KF_THR_RHS = 0,
+    KF_ROWS_FWD,
+    KF_COLS,
+    KF_ROWS_INV,
+    KF_SYNTH,
+    KF_CG_INIT,
+    KF_CG_MATVEC,
+    KF_CG_UPDATE,
+    KF_ROWS_FWD_PRE,
+    KF_COLS_PRE,
+    KF_ROWS_INV_PRE,
+    KF_OTHER,
+    KF_COUNT
+};
+
 constexpr int kMaxPartials = 12;
 constexpr int kTile = 32;        // stencil tiles are kTile x kTile pixels
 constexpr int kStencilThreads = 256;

@@ -55,6 +55,14 @@ struct Ctx {
     int* d_cg_pending = nullptr;
     int* h_cg_pending = nullptr; // pinned
 
+    // accounting: algorithmic bytes per kernel family (device counters) and
+    // optional CUDA-event timing of the families in prof_mask
+    unsigned long long* d_acct = nullptr;
+    unsigned prof_mask = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+    long long fam_launches[KF_COUNT] = {};
+
     DevItemList tiles, rows, cols;
     bool has_data = false;
     int cg_parity = 0;
@@ -71,6 +79,7 @@ int solver_iterate(Ctx& c, bool stats);        // one iteration of Algorithm 1
 int solver_op(Ctx& c, int op);
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int on_device);
 int solver_read_state(Ctx& c, std::vector<SliceState>& out);
+int solver_profile_read(Ctx& c, double* ms, long long* launches, unsigned long long* bytes);
 
 // Input stage (ct.cu), float device buffers.
 int ct_project(const recon_geometry& g, int n, const float* img, float* sino, cudaStream_t st, long long* launches);
@@ -78,6 +87,16 @@ int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img
                    long long* launches);
 int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,
            long long* launches);
+
+// Records CUDA events around the launches of one kernel family when that
+// family is selected in Ctx::prof_mask.
+struct FamTimer {
+    Ctx& c;
+    int fam;
+    cudaEvent_t b = nullptr, e = nullptr;
+    FamTimer(Ctx& ctx, int f);
+    ~FamTimer();
+};
 
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);

@@ -14,6 +14,7 @@
 //               normalised to 1 at mean(a^2)
 //   k_next_beta beta <- kappa beta, beta~ = tau beta
 // Sums for reductions are FP64 in a fixed order (deterministic).
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -26,7 +27,19 @@ template <typename T>
 struct Ptrs {
     T* f[kNumFields];
     cplx<T>* s[kNumSpectra];
+    unsigned long long* acct;   // algorithmic bytes per kernel family
 };
+
+// Adds the algorithmic bytes of one processed item to its family's counter.
+__device__ __forceinline__ void account(unsigned long long* acct, int fam, long long bytes) {
+    if (threadIdx.x == 0) atomicAdd(acct + fam, (unsigned long long)bytes);
+}
+
+__device__ __forceinline__ long long tile_px(const SliceGeom& g, const Item& it) {
+    const int w = g.nx - it.a < kTile ? g.nx - it.a : kTile;
+    const int h = g.ny - it.b < kTile ? g.ny - it.b : kTile;
+    return (long long)w * h;
+}
 
 struct FftJobs {
     int n;
@@ -127,6 +140,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_thr_rhs(ItemList L, const S
         if (!st.active) continue;
         const SliceGeom g = G[it.slice];
         const SliceConst c = C[it.slice];
+        account(P.acct, KF_THR_RHS, tile_px(g, it) * 10 * (long long)sizeof(T));
         for (int q = threadIdx.x; q < (kTile + 2) * (kTile + 2); q += blockDim.x) {
             const int ly = q / (kTile + 2), lx = q - ly * (kTile + 2);
             const int gy = wrap(it.b - 1 + ly, g.ny), gx = wrap(it.a - 1 + lx, g.nx);
@@ -254,6 +268,11 @@ __global__ void __launch_bounds__(kFftThreads) k_rows_fwd(ItemList L, const Slic
         if (job_skip(st, J.coef[job])) continue;
         const SliceGeom g = G[it.slice];
         const int N = g.nx, pair0 = it.a, np = it.b;
+        {
+            const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
+            account(P.acct, MODE ? KF_ROWS_FWD_PRE : KF_ROWS_FWD,
+                    (long long)rows * ((MODE ? 2 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
+        }
         fill_twiddles(tw, N);
         const T* in = P.f[J.in[job]];
         const T* a2 = P.f[RECON_F_A2];
@@ -305,6 +324,7 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeo
         if (job_skip(st, J.coef[job])) continue;
         const SliceGeom g = G[it.slice];
         const int N = g.ny, col0 = it.a, nc = it.b, ld = N + 1;
+        account(P.acct, J.coef[job] == 3 ? KF_COLS_PRE : KF_COLS, (long long)nc * N * 4 * (long long)sizeof(T));
         fill_twiddles(tw, N);
         cplx<T>* sp = P.s[J.spec[job]];
         for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
@@ -353,6 +373,11 @@ __global__ void __launch_bounds__(kFftThreads) k_rows_inv(ItemList L, const Slic
         if (job_skip(st, J.coef[job])) continue;
         const SliceGeom g = G[it.slice];
         const int N = g.nx, pair0 = it.a, np = it.b;
+        {
+            const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
+            account(P.acct, MODE ? KF_ROWS_INV_PRE : KF_ROWS_INV,
+                    (long long)rows * ((MODE ? 3 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
+        }
         fill_twiddles(tw, N);
         const cplx<T>* sp = P.s[J.spec[job]];
         for (int q = threadIdx.x; q < np * N; q += blockDim.x) {
@@ -422,6 +447,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
         if (!S[it.slice].active) continue;
         const SliceGeom g = G[it.slice];
         const SliceConst c = C[it.slice];
+        account(P.acct, KF_SYNTH, tile_px(g, it) * 7 * (long long)sizeof(T));
         double acc[2] = {0.0, 0.0};
         for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
             const int x = it.a + (q & (kTile - 1)), y = it.b + q / kTile;
@@ -487,6 +513,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const S
         const SliceState st = S[it.slice];
         if (!st.active) continue;
         const SliceGeom g = G[it.slice];
+        account(P.acct, KF_CG_INIT, tile_px(g, it) * 4 * (long long)sizeof(T));
         const T* z = P.f[RECON_F_Z];
         load_halo<T>(sm, g, it, [&](long long d) { return z[d]; });
         __syncthreads();
@@ -532,6 +559,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_matvec(ItemList L, const
         const SliceState st = S[it.slice];
         if (cg_skip(st)) continue;
         const SliceGeom g = G[it.slice];
+        account(P.acct, KF_CG_MATVEC, tile_px(g, it) * 5 * (long long)sizeof(T));
         const bool first = st.cg_it == 0;
         const T bc = T(st.betacg);
         load_halo<T>(sm, g, it, [&](long long d) { return first ? yv[d] : yv[d] + bc * pold[d]; });
@@ -570,6 +598,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_update(ItemList L, const
         const SliceState st = S[it.slice];
         if (cg_skip(st)) continue;
         const SliceGeom g = G[it.slice];
+        account(P.acct, KF_CG_UPDATE, tile_px(g, it) * 6 * (long long)sizeof(T));
         const T al = T(st.alpha);
         double acc[1] = {0.0};
         for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
@@ -674,6 +703,7 @@ Ptrs<T> ptrs(Ctx& c) {
     Ptrs<T> p;
     for (int i = 0; i < kNumFields; ++i) p.f[i] = static_cast<T*>(c.field[i]);
     for (int i = 0; i < kNumSpectra; ++i) p.s[i] = static_cast<cplx<T>*>(c.spec[i]);
+    p.acct = c.d_acct;
     return p;
 }
 
@@ -695,18 +725,25 @@ int fft_solve(Ctx& c, const FftJobs& J, int mode) {
     const int smem = fft_smem_bytes<T>(c);
     const int buf = kRowBudget + 64;
     if (mode == 0) {
+        FamTimer t(c, KF_ROWS_FWD);
         k_rows_fwd<T, 0><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
                                                                                        c.d_state, P, J, buf);
     } else {
+        FamTimer t(c, KF_ROWS_FWD_PRE);
         k_rows_fwd<T, 1><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
                                                                                        c.d_state, P, J, buf);
     }
-    k_cols<T><<<grid_for(c, c.cols.n * J.n), kFftThreads, smem, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
-                                                                           c.d_state, P, J, buf);
+    {
+        FamTimer t(c, mode ? KF_COLS_PRE : KF_COLS);
+        k_cols<T><<<grid_for(c, c.cols.n * J.n), kFftThreads, smem, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
+                                                                               c.d_state, P, J, buf);
+    }
     if (mode == 0) {
+        FamTimer t(c, KF_ROWS_INV);
         k_rows_inv<T, 0><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
                                                                                        c.d_state, P, J, buf);
     } else {
+        FamTimer t(c, KF_ROWS_INV_PRE);
         k_rows_inv<T, 1><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
                                                                                        c.d_state, P, J, buf);
     }
@@ -739,6 +776,7 @@ FftJobs jobs1(int in, int spec, int out, int coef) {
 template <typename T>
 int op_thr_rhs(Ctx& c, bool stats) {
     const Ptrs<T> P = ptrs<T>(c);
+    FamTimer t(c, KF_THR_RHS);
     if (stats)
         k_thr_rhs<T, true><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
                                                                                      c.d_const, c.d_state, P);
@@ -769,6 +807,7 @@ int op_solve_f(Ctx& c) {
 
 template <typename T>
 int op_synth(Ctx& c) {
+    FamTimer t(c, KF_SYNTH);
     k_synth<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                         c.d_state, ptrs<T>(c));
     c.launches += 1;
@@ -780,6 +819,7 @@ template <typename T>
 int op_solve_z(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
     RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream));
+    FamTimer t0(c, KF_CG_INIT);
     k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                           c.d_state, P, c.d_cg_pending);
     c.launches += 1;
@@ -790,10 +830,16 @@ int op_solve_z(Ctx& c) {
     for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
     int par = c.cg_parity;
     for (int it = 0; it < cap; ++it) {
-        k_cg_matvec<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
-                                                                                c.d_state, P, par);
-        k_cg_update<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(
-            c.tiles.view(), c.d_geom, c.d_const, c.d_state, P, par, c.d_cg_pending);
+        {
+            FamTimer t(c, KF_CG_MATVEC);
+            k_cg_matvec<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
+                                                                                    c.d_state, P, par);
+        }
+        {
+            FamTimer t(c, KF_CG_UPDATE);
+            k_cg_update<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(
+                c.tiles.view(), c.d_geom, c.d_const, c.d_state, P, par, c.d_cg_pending);
+        }
         c.launches += 2;
         if ((rc = fft_solve<T>(c, pre, 1))) return rc;
         par ^= 1;
@@ -986,6 +1032,8 @@ int solver_setup(Ctx& c) {
     for (int i = 0; i < 2; ++i)
         if ((rc = alloc_dev(c, (void**)&c.d_stage[i], sizeof(float) * c.ext_elems))) return rc;
     if ((rc = alloc_dev(c, (void**)&c.d_cg_pending, sizeof(int)))) return rc;
+    if ((rc = alloc_dev(c, (void**)&c.d_acct, sizeof(unsigned long long) * KF_COUNT))) return rc;
+    RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
     RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, sizeof(int)));
     if (c.precision == 1) return set_fft_smem<float>(c);
     return set_fft_smem<double>(c);
@@ -1005,6 +1053,53 @@ int solver_op(Ctx& c, int op) { return c.precision == 1 ? op_t<float>(c, op) : o
 
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int /*on_device*/) {
     return c.precision == 1 ? extract_t<float>(c, Z, rhoe, f1, f2) : extract_t<double>(c, Z, rhoe, f1, f2);
+}
+
+FamTimer::FamTimer(Ctx& ctx, int f) : c(ctx), fam(f) {
+    c.fam_launches[f] += 1;
+    if (!(c.prof_mask & (1u << f))) return;
+    for (cudaEvent_t* ev : {&b, &e}) {
+        if (!c.ev_pool.empty()) {
+            *ev = c.ev_pool.back();
+            c.ev_pool.pop_back();
+        } else if (cudaEventCreate(ev) != cudaSuccess) {
+            *ev = nullptr;
+        }
+    }
+    if (b && e) cudaEventRecord(b, c.stream);
+}
+
+FamTimer::~FamTimer() {
+    if (b && e) {
+        cudaEventRecord(e, c.stream);
+        c.ev_used.push_back({fam, {b, e}});
+    } else {
+        if (b) c.ev_pool.push_back(b);
+        if (e) c.ev_pool.push_back(e);
+    }
+}
+
+int solver_profile_read(Ctx& c, double* ms, long long* launches, unsigned long long* bytes) {
+    RECON_CUDA(cudaStreamSynchronize(c.stream));
+    for (int f = 0; f < KF_COUNT; ++f) {
+        if (ms) ms[f] = 0.0;
+        if (launches) launches[f] = c.fam_launches[f];
+        c.fam_launches[f] = 0;
+    }
+    for (auto& u : c.ev_used) {
+        float t = 0.f;
+        RECON_CUDA(cudaEventElapsedTime(&t, u.second.first, u.second.second));
+        if (ms) ms[u.first] += t;
+        c.ev_pool.push_back(u.second.first);
+        c.ev_pool.push_back(u.second.second);
+    }
+    c.ev_used.clear();
+    std::vector<unsigned long long> h(KF_COUNT);
+    RECON_CUDA(cudaMemcpy(h.data(), c.d_acct, sizeof(unsigned long long) * KF_COUNT, cudaMemcpyDeviceToHost));
+    RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
+    if (bytes)
+        for (int f = 0; f < KF_COUNT; ++f) bytes[f] = h[f];
+    return RECON_OK;
 }
 
 int solver_read_state(Ctx& c, std::vector<SliceState>& out) {

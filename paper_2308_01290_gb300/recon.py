@@ -86,6 +86,9 @@ def _load():
         "recon_debug_scalars": (I, [VP, C.c_int32, P(D)]),
         "recon_kernel_launches": (C.c_int64, [VP]),
         "recon_abi_sizes": (I, [P(C.c_int64)]),
+        "recon_profile": (I, [VP, C.c_uint32]),
+        "recon_profile_read": (I, [VP, P(D), P(C.c_int64), P(C.c_uint64)]),
+        "recon_profile_name": (C.c_char_p, [C.c_int32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -110,7 +113,8 @@ EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_
            "recon_sync", "recon_destroy", "recon_solve", "recon_strerror", "recon_last_error", "recon_project",
            "recon_backproject", "recon_fbp", "recon_simulate", "recon_model_tables", "recon_debug_field",
            "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches",
-           "recon_abi_sizes")
+           "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name")
+KF_COUNT = 12
 
 
 def _check(rc, what):
@@ -277,6 +281,17 @@ class Solver:
         _check(lib.recon_debug_scalars(self.h, int(slice_), out), "recon_debug_scalars")
         return dict(beta=out[0], beta_t=out[1], k=int(out[2]), abar2=out[3], cg_iters=int(out[4]),
                     cg_rel_residual=out[5])
+
+    def profile(self, mask):
+        _check(lib.recon_profile(self.h, int(mask)), "recon_profile")
+
+    def profile_read(self):
+        """{family name: (ms, launches, algorithmic bytes)} since the last read."""
+        ms = (C.c_double * KF_COUNT)()
+        la = (C.c_int64 * KF_COUNT)()
+        by = (C.c_uint64 * KF_COUNT)()
+        _check(lib.recon_profile_read(self.h, ms, la, by), "recon_profile_read")
+        return {lib.recon_profile_name(f).decode(): (ms[f], la[f], by[f]) for f in range(KF_COUNT)}
 
     def launches(self):
         return int(lib.recon_kernel_launches(self.h))
