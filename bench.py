@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=1)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline leg")
+    ap.add_argument("--profile", action="store_true", help="print the per-kernel-family breakdown to stderr")
     return ap.parse_args()
 
 
@@ -111,6 +112,42 @@ def make_scans(rc, torch, slices, seed):
         hi_parts.append(hi)
     torch.cuda.synchronize()
     return torch.cat(lo_parts), torch.cat(hi_parts)
+
+
+# ---------------------------------------------------------------------------
+# roofline denominators and ncu traffic
+# ---------------------------------------------------------------------------
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    except (OSError, KeyError, ValueError):
+        return dict(hbm_gbs=6800.0, source="fallback")
+
+
+def read_traffic(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
+    None when none exists or the kernel source changed since it was taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2308_01290_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(src)):
+        with open(os.path.join(src, name), "rb") as f:
+            h.update(f.read())
+    e = d.get(kernel)
+    if not e or e.get("source_sha256") != h.hexdigest():
+        return None
+    # the capture's traffic scaled to this launch's algorithmic size
+    return e["dram_bytes_per_launch"] * alg_bytes_per_launch / e["algorithmic_bytes_per_launch"]
 
 
 # ---------------------------------------------------------------------------
@@ -274,6 +311,23 @@ def main():
     for _ in range(args.warmup):
         step()
     barrier()
+    # profiling pass (untimed): event-time every kernel family once
+    solver.profile((1 << rc.KF_COUNT) - 1)
+    solver.profile_read()
+    step()
+    prof = solver.profile_read()
+    dominant = max(prof, key=lambda k: prof[k][0])
+    dom_id = list(prof).index(dominant)
+    if args.profile and rank == 0:
+        tot = sum(v[0] for v in prof.values())
+        for k, (t, n, b) in sorted(prof.items(), key=lambda kv: -kv[1][0]):
+            if n:
+                print(f"  {k:18s} {t:9.2f} ms {100 * t / tot:5.1f}%  {n:6d} launches  "
+                      f"{b / 1e9:8.2f} GB  {b / 1e9 / (t / 1e3) if t else 0:8.1f} GB/s", file=sys.stderr)
+    # timed region: events only around the dominant family's launches
+    solver.profile(1 << dom_id)
+    solver.profile_read()
+    barrier()
     clocks = ClockSampler(local)
     clocks.start()
     l0 = solver.launches()
@@ -288,6 +342,15 @@ def main():
     clk = clocks.stop()
     ms = t_start.elapsed_time(t_end)
     launches = (solver.launches() - l0) // args.steps
+    dom_ms, dom_launches, dom_bytes = solver.profile_read()[dominant]
+    solver.profile(0)
+    peaks = read_peaks()
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9 if dom_ms > 0 else 0.0
+    roofline = dict(kernel=dominant, bound="hbm", achieved=achieved, peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=achieved / peaks["hbm_gbs"], peak_source=peaks["source"],
+                    traffic=read_traffic(dominant, dom_bytes / max(dom_launches, 1)),
+                    algorithmic_bytes_per_launch=dom_bytes / max(dom_launches, 1),
+                    launch_ms=dom_ms / max(dom_launches, 1), share_of_step=dom_ms / ms if ms else None)
     if world > 1:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -360,7 +423,7 @@ def main():
                     vs_baseline=None, dtype="f32" if args.precision == 1 else "f64", data="synthetic",
                     config=dict(workload=name, slices=len(slices), iters=iters, precision=args.precision,
                                 l2="working set > L2 (no flush needed)"),
-                    e2e=e2e, gpu_launches=int(launches), clocks=clk, roofline=None, cpu_baseline=cpu, **extra)
+                    e2e=e2e, gpu_launches=int(launches), clocks=clk, roofline=roofline, cpu_baseline=cpu, **extra)
         print(json.dumps(line), flush=True)
     solver.close()
     if world > 1:

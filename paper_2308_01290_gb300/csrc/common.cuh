@@ -30,6 +30,10 @@ struct SliceGeom {
     long long off;       // element offset of the slice in every real field pool
     long long coff;      // element offset of the slice in every spectrum pool
     long long ext_off;   // element offset of the slice in unpadded caller buffers
+    unsigned plan_x, plan_y;   // FFT plans (radix sequences) along x and y
+    long long twx, twy;        // offsets of the twiddle tables exp(-2 pi i t/N) in the twiddle pool
+    long long symx, symy;      // offsets of the tables 4 sin^2(pi t/N) in the symbol pool
+    int rows_per_item, cols_per_item;
 };
 
 // Model constants and parameters of one slice (FP64, read-only on device).
@@ -92,10 +96,22 @@ enum KFam {
 };
 
 constexpr int kMaxPartials = 12;
-constexpr int kTile = 32;        // stencil tiles are kTile x kTile pixels
+constexpr int kTileW = 64;       // tiles are kTileW pixels wide; their height is TileDim<T>::TH
+constexpr int kTileHFloat = 32;
+constexpr int kTileHDouble = 16;
 constexpr int kStencilThreads = 256;
 constexpr int kFftThreads = 256;
-constexpr int kRowBudget = 2048; // complex elements per FFT buffer (rows and columns)
+// complex elements one FFT block transforms at a time (rows or columns)
+template <typename T>
+struct FftBudget;
+template <>
+struct FftBudget<float> {
+    static constexpr int E = 4096;
+};
+template <>
+struct FftBudget<double> {
+    static constexpr int E = 2048;
+};
 
 __device__ __forceinline__ int wrap(int i, int n) {
     i %= n;
@@ -125,34 +141,40 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh /* NV * 32
 }
 
 // Store the partials of one item; returns true (in thread 0 only) when this
-// item is the last of its slice to finish, in which case all partials of the
-// slice are visible and `tot` holds their in-order sum.
+// item is the last of its slice to finish, in which case `tot` holds the sum
+// of all partials of the slice in a fixed order (deterministic).  The final
+// sum is taken by the whole block: each thread adds a strided subset of the
+// partials (read through L2), then a block reduction in fixed order.
 template <int NV>
 __device__ __forceinline__ bool item_reduce(const ItemList& L, int item, int slice, const double (&v)[NV],
-                                            double (&tot)[NV]) {
-    __shared__ bool s_last;
+                                            double (&tot)[NV], double* sh /* NV * 32 */) {
+    __shared__ int s_last;
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int q = 0; q < NV; ++q) L.partials[(size_t)item * kMaxPartials + q] = v[q];
         __threadfence();
         const unsigned prev = atomicAdd(&L.counters[slice], 1u);
-        s_last = (prev == (unsigned)L.cnt[slice] - 1u);
-        if (s_last) {
-            __threadfence();
-            const int lo = L.lo[slice], n = L.cnt[slice];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) tot[q] = 0.0;
-            for (int i = 0; i < n; ++i) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) tot[q] += ((volatile double*)L.partials)[(size_t)(lo + i) * kMaxPartials + q];
-            }
-            L.counters[slice] = 0u;
-        }
+        s_last = (prev == (unsigned)L.cnt[slice] - 1u) ? 1 : 0;
     }
     __syncthreads();
-    const bool last = s_last;
-    __syncthreads();
-    return last && threadIdx.x == 0;
+    const int last = s_last;
+    if (!last) return false;
+    __threadfence();
+    const int lo = L.lo[slice], n = L.cnt[slice];
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(L.partials + (size_t)(lo + i) * kMaxPartials + q);
+    }
+    block_sum<NV>(acc, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) tot[q] = acc[q];
+        L.counters[slice] = 0u;
+    }
+    return threadIdx.x == 0;
 }
 
 }  // namespace recon

@@ -130,76 +130,96 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
 // plane) and Ram-Lak ramp h(0) = 1/(4 ds^2), h(odd m) = -1/(pi m ds)^2,
 // q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view).
 __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ sino, float* __restrict__ q) {
-    extern __shared__ float wrow[];
-    const int sv = blockIdx.x;   // slice * n_views + view
-    if (sv >= n * g.n_views) return;
+    extern __shared__ float smem_f[];
     const int nb = g.n_bins;
+    float* wrow = smem_f;          // weighted row, zero-padded by nb on both sides
+    float* hodd = smem_f + 3 * nb; // ds h(m) for odd m = 2t + 1
+    const int sv = blockIdx.x;     // slice * n_views + view
+    if (sv >= n * g.n_views) return;
     const double ds = g.bin_mm * g.sid_mm / g.sdd_mm;
     const float* src = sino + (long long)sv * nb;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        const double s = ((double)b - 0.5 * (nb - 1)) * ds;
-        wrow[b] = (float)((double)src[b] * g.sid_mm / sqrt(g.sid_mm * g.sid_mm + s * s));
+    for (int b = threadIdx.x; b < 3 * nb; b += blockDim.x) {
+        const int k = b - nb;
+        float v = 0.f;
+        if (k >= 0 && k < nb) {
+            const double s = ((double)k - 0.5 * (nb - 1)) * ds;
+            v = (float)((double)src[k] * g.sid_mm / sqrt(g.sid_mm * g.sid_mm + s * s));
+        }
+        wrow[b] = v;
+    }
+    for (int t = threadIdx.x; t < (nb + 1) / 2; t += blockDim.x) {
+        const double m = 2.0 * t + 1.0;
+        hodd[t] = (float)(-1.0 / (M_PI * M_PI * ds * m * m));   // ds * (-1/(pi m ds)^2)
     }
     __syncthreads();
-    const float h0 = (float)(0.25 / ds);                    // ds * 1/(4 ds^2)
-    const float hodd = (float)(-1.0 / (M_PI * M_PI * ds));  // ds * (-1/(pi^2 ds^2)) / m^2
+    const float h0 = (float)(0.25 / ds);   // ds * 1/(4 ds^2)
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         float acc = 0.f;
-        // odd offsets m = b - k, both signs
-        for (int m = 1; m < nb; m += 2) {
-            const float hm = hodd / ((float)m * (float)m);
-            float pair = 0.f;
-            if (b - m >= 0) pair += wrow[b - m];
-            if (b + m < nb) pair += wrow[b + m];
-            acc = fmaf(hm, pair, acc);
-        }
-        q[(long long)sv * nb + b] = fmaf(h0, wrow[b], acc);
+        const float* c = wrow + nb + b;
+        // odd offsets m = 2t + 1 on both sides (zero padding outside the row)
+        for (int t = 0; 2 * t + 1 < nb; ++t) acc = fmaf(hodd[t], c[-(2 * t + 1)] + c[2 * t + 1], acc);
+        q[(long long)sv * nb + b] = fmaf(h0, c[0], acc);
     }
 }
 
 // FBP step 2: pixel-driven backprojection of the filtered rows with weight
 // 1/U^2, U = (sid - x cos t - y sin t) / sid, detector coordinate at the
 // isocentre s' = sid (-x sin t + y cos t) / (U sid), linear interpolation,
-// times (arc / n_views) / 2 for a full scan.
-__global__ void k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q, float* __restrict__ img) {
+// times (arc / n_views) / 2 for a full scan.  A block covers a 16 x 32 pixel
+// tile (each thread two pixels 16 rows apart) so that, for one view, the
+// tile's samples fall in a narrow range of bins.
+constexpr int kBpTx = 16, kBpTy = 16, kBpRows = 2;
+
+__global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q,
+                                                                  float* __restrict__ img) {
     extern __shared__ float trig[];   // cos, sin per view
-    for (int v = threadIdx.x; v < g.n_views; v += blockDim.x) {
+    for (int v = threadIdx.x + threadIdx.y * kBpTx; v < g.n_views; v += kBpTx * kBpTy) {
         double s, c;
         sincos(g.start_rad + g.arc_rad * (double)v / (double)g.n_views, &s, &c);
         trig[2 * v] = (float)c;
         trig[2 * v + 1] = (float)s;
     }
     __syncthreads();
-    const long long npx = (long long)g.nx * g.ny;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= npx * n) return;
-    const int sl = (int)(tid / npx);
-    const int pix = (int)(tid - (long long)sl * npx);
-    const int j = pix / g.nx, i = pix - j * g.nx;
-    const float x = (float)(((double)i - 0.5 * (g.nx - 1)) * g.pixel_mm);
-    const float y = (float)(((double)j - 0.5 * (g.ny - 1)) * g.pixel_mm);
+    const int sl = blockIdx.z;
+    const int i = blockIdx.x * kBpTx + threadIdx.x;
+    const int j0 = blockIdx.y * (kBpTy * kBpRows) + threadIdx.y;
     const float sid = (float)g.sid_mm;
     const float inv_ds = (float)(g.sdd_mm / (g.bin_mm * g.sid_mm));
     const float bc = 0.5f * (g.n_bins - 1);
+    const float x = (float)(((double)i - 0.5 * (g.nx - 1)) * g.pixel_mm);
+    float y[kBpRows], acc[kBpRows];
+#pragma unroll
+    for (int r = 0; r < kBpRows; ++r) {
+        y[r] = (float)(((double)(j0 + r * kBpTy) - 0.5 * (g.ny - 1)) * g.pixel_mm);
+        acc[r] = 0.f;
+    }
     const float* qs = q + (long long)sl * g.n_views * g.n_bins;
-    float acc = 0.f;
     for (int v = 0; v < g.n_views; ++v) {
         const float c = trig[2 * v], s = trig[2 * v + 1];
-        const float L = sid - (x * c + y * s);
-        const float invL = 1.f / L;
-        const float sp = sid * (y * c - x * s) * invL;
-        const float bf = fmaf(sp, inv_ds, bc);
-        const float fl = floorf(bf);
-        const int b0 = (int)fl;
-        const float w1 = bf - fl;
         const float* row = qs + (long long)v * g.n_bins;
-        float val = 0.f;
-        if (b0 >= 0 && b0 < g.n_bins) val += (1.f - w1) * __ldg(row + b0);
-        if (b0 + 1 >= 0 && b0 + 1 < g.n_bins) val += w1 * __ldg(row + b0 + 1);
-        const float U = L / sid;
-        acc += val / (U * U);
+#pragma unroll
+        for (int r = 0; r < kBpRows; ++r) {
+            const float L = sid - (x * c + y[r] * s);
+            const float invL = __frcp_rn(L);
+            const float bf = fmaf(sid * (y[r] * c - x * s) * invL, inv_ds, bc);
+            const float fl = floorf(bf);
+            const int b0 = (int)fl;
+            const float w1 = bf - fl;
+            float val = 0.f;
+            if (b0 >= 0 && b0 < g.n_bins) val += (1.f - w1) * __ldg(row + b0);
+            if (b0 + 1 >= 0 && b0 + 1 < g.n_bins) val += w1 * __ldg(row + b0 + 1);
+            // 1/U^2 = (sid / L)^2
+            const float su = sid * invL;
+            acc[r] = fmaf(val, su * su, acc[r]);
+        }
     }
-    img[tid] = acc * (float)(0.5 * g.arc_rad / g.n_views);
+    if (i >= g.nx) return;
+    const float scale = (float)(0.5 * g.arc_rad / g.n_views);
+#pragma unroll
+    for (int r = 0; r < kBpRows; ++r) {
+        const int j = j0 + r * kBpTy;
+        if (j < g.ny) img[(long long)sl * g.nx * g.ny + (long long)j * g.nx + i] = acc[r] * scale;
+    }
 }
 
 // rho_e z with z = (Z / Z_w)^m (the photoelectric line-integral map)
@@ -271,14 +291,15 @@ int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float*
            long long* launches) {
     int rc = check_geom(g);
     if (rc) return rc;
-    if (g.n_views * 2 * sizeof(float) > 96 * 1024 || g.n_bins * sizeof(float) > 96 * 1024) {
+    if (g.n_views * 2 * sizeof(float) > 48 * 1024 || (3.5 * g.n_bins + 1) * sizeof(float) > 48 * 1024 ||
+        n > 65535) {
         set_error("too many views or bins");
         return RECON_EINVAL;
     }
-    k_fbp_filter<<<n * g.n_views, 256, g.n_bins * sizeof(float), st>>>(g, n, sino, scratch);
-    const long long total = (long long)n * g.nx * g.ny;
-    k_fbp_backproject<<<(unsigned)((total + 255) / 256), 256, 2 * g.n_views * sizeof(float), st>>>(g, n, scratch,
-                                                                                                   img);
+    k_fbp_filter<<<n * g.n_views, 256, (3 * g.n_bins + (g.n_bins + 1) / 2) * sizeof(float), st>>>(g, n, sino,
+                                                                                                   scratch);
+    const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy * kBpRows - 1) / (kBpTy * kBpRows), n);
+    k_fbp_backproject<<<grid, dim3(kBpTx, kBpTy), 2 * g.n_views * sizeof(float), st>>>(g, n, scratch, img);
     if (launches) *launches += 2;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;

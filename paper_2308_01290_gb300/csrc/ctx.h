@@ -52,6 +52,8 @@ struct Ctx {
     float* d_stage[2] = {};      // unpadded float staging (inputs / outputs)
     float* d_sino[2] = {};       // sinogram staging when inputs are sinograms
     float* d_filt = nullptr;     // filtered sinogram scratch (one slice)
+    void* d_tw = nullptr;        // FFT twiddle tables (map precision)
+    void* d_sym = nullptr;       // |F dx|^2 symbol tables 4 sin^2(pi t/N) (map precision)
     int* d_cg_pending = nullptr;
     int* h_cg_pending = nullptr; // pinned
 

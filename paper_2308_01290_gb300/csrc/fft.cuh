@@ -1,52 +1,49 @@
 // Shared-memory mixed-radix (2, 3, 4, 5, 7, 8) Stockham FFT for a batch of
 // sequences of the same length N held in shared memory.
 //
-// Stage s with radix R and current sub-transform size Ns (product of the
+// Stage with radix R and current sub-transform size Ns (product of the
 // radices already applied, starting at 1): for butterfly j in [0, N/R),
-// k = j mod Ns, read in[j + r N/R] (r < R), multiply by w^(r k N/(Ns R)) with
+// k = j mod Ns, read x[j + r N/R] (r < R), multiply by w^(r k N/(Ns R)) with
 // w = exp(-+2 pi i / N), take an R-point DFT, and write
-// out[(j / Ns) Ns R + k + r Ns].  The result is in natural order after the
-// last stage (Stockham autosort; no bit reversal).
+// x'[(j / Ns) Ns R + k + r Ns].  After the last stage the result is in
+// natural order (Stockham autosort).  Stages ping-pong between two shared
+// buffers, one butterfly per thread at a time.  Element i of a sequence lives
+// at slot i + i/8 (one pad slot every 8) so that the stride-R accesses of
+// the early stages do not pile up in one shared-memory bank.
 #pragma once
 #include "common.cuh"
 
 namespace recon {
 
-struct FftPlan {
-    int n, ns;
-    int radix[24];
-};
-
-__device__ __forceinline__ FftPlan make_plan(int n) {
-    FftPlan p;
-    p.n = n;
-    p.ns = 0;
+// Radices of the stages, 4 bits each from the low end; the stage count in
+// bits 28..31.  Powers of two first (8, then 4, then 2), then 3, 5, 7.
+__host__ __device__ inline unsigned fft_plan_code(int n) {
+    unsigned code = 0;
+    int ns = 0;
     int m = n;
-    while (m % 8 == 0) { p.radix[p.ns++] = 8; m /= 8; }
-    while (m % 4 == 0) { p.radix[p.ns++] = 4; m /= 4; }
-    while (m % 2 == 0) { p.radix[p.ns++] = 2; m /= 2; }
-    while (m % 3 == 0) { p.radix[p.ns++] = 3; m /= 3; }
-    while (m % 5 == 0) { p.radix[p.ns++] = 5; m /= 5; }
-    while (m % 7 == 0) { p.radix[p.ns++] = 7; m /= 7; }
-    return p;
+    auto push = [&](int r) {
+        code |= (unsigned)r << (4 * ns);
+        ++ns;
+    };
+    while (m % 8 == 0) { push(8); m /= 8; }
+    while (m % 4 == 0) { push(4); m /= 4; }
+    while (m % 2 == 0) { push(2); m /= 2; }
+    while (m % 3 == 0) { push(3); m /= 3; }
+    while (m % 5 == 0) { push(5); m /= 5; }
+    while (m % 7 == 0) { push(7); m /= 7; }
+    return code | ((unsigned)ns << 28);
 }
 
-template <typename T>
-__device__ __forceinline__ void sincospi_t(T x, T* s, T* c);
-template <>
-__device__ __forceinline__ void sincospi_t<float>(float x, float* s, float* c) { sincospif(x, s, c); }
-template <>
-__device__ __forceinline__ void sincospi_t<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+// slots a padded sequence of n elements occupies
+__host__ __device__ inline int padded_len(int n) { return n + (n >> 3) + 1; }
 
-// tw[t] = exp(-2 pi i t / n), t < n (forward roots).
-template <typename T>
-__device__ __forceinline__ void fill_twiddles(cplx<T>* tw, int n) {
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        T s, c;
-        // angle 2 t / n in units of pi; reduce to keep the argument small
-        sincospi_t<T>(T(2) * T(t) / T(n), &s, &c);
-        tw[t] = {c, -s};
-    }
+// n / d for 0 <= n < 2^24 using a float reciprocal and one correction.
+__device__ __forceinline__ int fdiv(int n, int d, float inv_d) {
+    int q = (int)((float)n * inv_d);
+    q -= (q * d > n) ? 1 : 0;
+    q += ((q + 1) * d <= n) ? 1 : 0;
+    return q;
 }
 
 // multiply by -i (forward) or +i (inverse)
@@ -98,20 +95,41 @@ __device__ __forceinline__ void dft8(cplx<T>* v, int dir) {
     }
 }
 
-// Direct R-point DFT for odd radices 3, 5, 7.
+// Direct R-point DFT for the odd radices 3, 5, 7 (constants cos, sin of
+// 2 pi m / R from a small table).
 template <typename T, int R>
 __device__ __forceinline__ void dft_odd(cplx<T>* v, int dir) {
+    // cos(2 pi m / R), sin(2 pi m / R) for m < R
+    constexpr double c3[3] = {1.0, -0.5, -0.5};
+    constexpr double s3[3] = {0.0, 0.86602540378443864676, -0.86602540378443864676};
+    constexpr double c5[5] = {1.0, 0.30901699437494742410, -0.80901699437494742410, -0.80901699437494742410,
+                              0.30901699437494742410};
+    constexpr double s5[5] = {0.0, 0.95105651629515357212, 0.58778525229247312917, -0.58778525229247312917,
+                              -0.95105651629515357212};
+    constexpr double c7[7] = {1.0,
+                              0.62348980185873353053,
+                              -0.22252093395631440429,
+                              -0.90096886790241912624,
+                              -0.90096886790241912624,
+                              -0.22252093395631440429,
+                              0.62348980185873353053};
+    constexpr double s7[7] = {0.0,
+                              0.78183148246802980871,
+                              0.97492791218182360702,
+                              0.43388373911755812048,
+                              -0.43388373911755812048,
+                              -0.97492791218182360702,
+                              -0.78183148246802980871};
     cplx<T> out[R];
-    T cs[R], sn[R];
-#pragma unroll
-    for (int m = 0; m < R; ++m) sincospi_t<T>(T(2 * m) / T(R), &sn[m], &cs[m]);
 #pragma unroll
     for (int k = 0; k < R; ++k) {
         cplx<T> acc = v[0];
 #pragma unroll
         for (int n = 1; n < R; ++n) {
             const int m = (n * k) % R;
-            const T c = cs[m], s = dir < 0 ? -sn[m] : sn[m];
+            const T c = T(R == 3 ? c3[m] : (R == 5 ? c5[m] : c7[m]));
+            const T sv = T(R == 3 ? s3[m] : (R == 5 ? s5[m] : s7[m]));
+            const T s = dir < 0 ? -sv : sv;
             acc.x += v[n].x * c - v[n].y * s;
             acc.y += v[n].x * s + v[n].y * c;
         }
@@ -122,49 +140,70 @@ __device__ __forceinline__ void dft_odd(cplx<T>* v, int dir) {
 }
 
 template <typename T, int R>
+__device__ __forceinline__ void dft(cplx<T>* v, int dir) {
+    if (R == 2) dft2(v);
+    else if (R == 4) dft4(v, dir);
+    else if (R == 8) dft8(v, dir);
+    else dft_odd<T, R>(v, dir);
+}
+
+// Integer n / d and n % d for the index maps of a stage: shifts when d is a
+// power of two, else a float reciprocal with one correction (n < 2^24).
+struct DivMod {
+    int d, shift;
+    float inv;
+    __device__ __forceinline__ explicit DivMod(int dd) : d(dd), shift(-1), inv(1.0f / (float)dd) {
+        if ((dd & (dd - 1)) == 0) shift = __ffs(dd) - 1;
+    }
+    __device__ __forceinline__ int div(int n) const { return shift >= 0 ? (n >> shift) : fdiv(n, d, inv); }
+};
+
+// One stage from buffer `in` to buffer `out` (sequence b at +b*ld, padded
+// indexing), one butterfly per thread at a time.
+template <typename T, int R>
 __device__ __forceinline__ void fft_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int N, int Ns,
-                                          int batch, int ld, const cplx<T>* tw, int dir) {
+                                          int batch, int ld, const cplx<T>* __restrict__ tw, int dir) {
     const int nbf = N / R;
+    const int total = batch * nbf;
     const int step = N / (Ns * R);
-    for (int t = threadIdx.x; t < batch * nbf; t += blockDim.x) {
-        const int bidx = t / nbf, j = t - bidx * nbf;
-        const cplx<T>* src = in + (size_t)bidx * ld;
-        cplx<T>* dst = out + (size_t)bidx * ld;
-        const int k = j % Ns;
+    const DivMod dn(nbf), ds(Ns);
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int b = dn.div(t), j = t - b * nbf;
+        const int jn = ds.div(j), k = j - jn * Ns;
+        const cplx<T>* src = in + b * ld;
         cplx<T> v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = src[j + r * nbf];
+        for (int r = 0; r < R; ++r) v[r] = src[pad8(j + r * nbf)];
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                cplx<T> w = tw[(r * k * step) % N];
+                cplx<T> w = tw[r * k * step];
                 if (dir > 0) w.y = -w.y;
                 v[r] = cmul(v[r], w);
             }
         }
-        if (R == 2) dft2(v);
-        else if (R == 4) dft4(v, dir);
-        else if (R == 8) dft8(v, dir);
-        else if (R == 3) dft_odd<T, 3>(v, dir);
-        else if (R == 5) dft_odd<T, 5>(v, dir);
-        else dft_odd<T, 7>(v, dir);
-        const int idxD = (j / Ns) * Ns * R + k;
+        dft<T, R>(v, dir);
+        cplx<T>* dst = out + b * ld;
+        const int idxD = jn * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[idxD + r * Ns] = v[r];
+        for (int r = 0; r < R; ++r) dst[pad8(idxD + r * Ns)] = v[r];
     }
 }
 
-// Transform `batch` sequences of length N (sequence b at a + b*ld) in place
-// semantics: returns the buffer (a or b) holding the result.  dir = -1
-// forward (exp(-i ...)), +1 inverse, unnormalised.  Synchronises the block.
+// Transform `batch` sequences of length N (dir -1 forward, +1 inverse,
+// unnormalised), ping-ponging between buffers a and b; returns the buffer
+// holding the result.  `plan` from fft_plan_code(N); tw[t] = exp(-2 pi i t/N)
+// in global memory.  The caller synchronises before (data ready); the
+// function synchronises after every stage.
 template <typename T>
-__device__ cplx<T>* fft_batch(cplx<T>* a, cplx<T>* b, int N, int batch, int ld, const cplx<T>* tw, int dir) {
-    const FftPlan pl = make_plan(N);
+__device__ __forceinline__ cplx<T>* fft_batch(cplx<T>* a, cplx<T>* b, int N, unsigned plan, int batch, int ld,
+                                              const cplx<T>* tw, int dir) {
+    const int ns = (int)(plan >> 28);
     int Ns = 1;
     cplx<T>* in = a;
     cplx<T>* out = b;
-    for (int s = 0; s < pl.ns; ++s) {
-        const int R = pl.radix[s];
+    for (int s = 0; s < ns; ++s) {
+        const int R = (int)((plan >> (4 * s)) & 15u);
         switch (R) {
             case 8: fft_stage<T, 8>(in, out, N, Ns, batch, ld, tw, dir); break;
             case 4: fft_stage<T, 4>(in, out, N, Ns, batch, ld, tw, dir); break;

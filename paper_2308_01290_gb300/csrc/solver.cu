@@ -28,6 +28,7 @@ struct Ptrs {
     T* f[kNumFields];
     cplx<T>* s[kNumSpectra];
     unsigned long long* acct;   // algorithmic bytes per kernel family
+    const T* sym;               // symbol tables 4 sin^2(pi t / N)
 };
 
 // Adds the algorithmic bytes of one processed item to its family's counter.
@@ -35,9 +36,22 @@ __device__ __forceinline__ void account(unsigned long long* acct, int fam, long 
     if (threadIdx.x == 0) atomicAdd(acct + fam, (unsigned long long)bytes);
 }
 
+template <typename T>
+struct TileH;
+template <>
+struct TileH<float> {
+    static constexpr int v = kTileHFloat;
+};
+template <>
+struct TileH<double> {
+    static constexpr int v = kTileHDouble;
+};
+
+template <typename T>
 __device__ __forceinline__ long long tile_px(const SliceGeom& g, const Item& it) {
-    const int w = g.nx - it.a < kTile ? g.nx - it.a : kTile;
-    const int h = g.ny - it.b < kTile ? g.ny - it.b : kTile;
+    constexpr int TH = TileH<T>::v;
+    const int w = g.nx - it.a < kTileW ? g.nx - it.a : kTileW;
+    const int h = g.ny - it.b < TH ? g.ny - it.b : TH;
     return (long long)w * h;
 }
 
@@ -64,6 +78,20 @@ __device__ __forceinline__ float sub_rn<float>(float a, float b) { return __fsub
 template <>
 __device__ __forceinline__ double sub_rn<double>(double a, double b) { return __dsub_rn(a, b); }
 
+// a*b - c*d with the product c*d split exactly (FMA two-product), so the
+// difference of two nearly equal products keeps its precision.
+template <typename T>
+__device__ __forceinline__ T diff_of_products(T a, T b, T c, T d) {
+    const T cd = c * d;
+    const T err = fma(c, d, -cd);
+    return fma(a, b, -cd) - err;
+}
+
+// Jacobi scaling of the Z^m preconditioner: sqrt(num / (a2 + b4)), with
+// sqrt(num) passed in.
+__device__ __forceinline__ float dscale(float sqrt_num, float a2, float b4) { return sqrt_num * rsqrtf(a2 + b4); }
+__device__ __forceinline__ double dscale(double sqrt_num, double a2, double b4) { return sqrt_num / sqrt(a2 + b4); }
+
 template <typename T>
 __device__ __forceinline__ T thr_of(const SliceState& st);
 template <>
@@ -82,8 +110,8 @@ __global__ void k_load(ItemList L, const SliceGeom* G, const SliceConst* C, cons
         const Item it = L.items[w];
         const SliceGeom g = G[it.slice];
         const double s = C[it.slice].inv_S;
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int x = it.a + (q & (kTile - 1)), y = it.b + q / kTile;
+        for (int q = threadIdx.x; q < kTileW * TileH<T>::v; q += blockDim.x) {
+            const int x = it.a + (q & (kTileW - 1)), y = it.b + q / kTileW;
             if (x >= g.nx || y >= g.ny) continue;
             const long long e = g.ext_off + (long long)y * g.nx + x;
             const long long d = g.off + (long long)y * g.pitch + x;
@@ -99,8 +127,8 @@ __global__ void k_init(ItemList L, const SliceGeom* G, const SliceConst* C, Ptrs
         const Item it = L.items[w];
         const SliceGeom g = G[it.slice];
         const SliceConst c = C[it.slice];
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int x = it.a + (q & (kTile - 1)), y = it.b + q / kTile;
+        for (int q = threadIdx.x; q < kTileW * TileH<T>::v; q += blockDim.x) {
+            const int x = it.a + (q & (kTileW - 1)), y = it.b + q / kTileW;
             if (x >= g.nx || y >= g.ny) continue;
             const long long d = g.off + (long long)y * g.pitch + x;
             const double uL = P.f[RECON_F_MUL][d], uH = P.f[RECON_F_MUH][d];
@@ -125,87 +153,208 @@ __global__ void k_init(ItemList L, const SliceGeom* G, const SliceConst* C, Ptrs
 }
 
 // --------------------------------------------------------------------------
+// tiles in shared memory: kTileW x TH pixels plus a one-pixel halo; the
+// interior starts at a 16-byte boundary (column OFF) so rows move as 16-byte
+// vectors; left halo at column OFF - 1, right halo at OFF + kTileW.
+// --------------------------------------------------------------------------
+
+template <typename T>
+struct TileDim {
+    static constexpr int VN = 16 / (int)sizeof(T);   // elements per 16-byte vector
+    static constexpr int OFF = VN;
+    static constexpr int TH = TileH<T>::v;
+    static constexpr int SW = OFF + kTileW + VN;     // row stride
+};
+
+template <typename T>
+struct alignas(16) Pack {
+    T v[TileDim<T>::VN];
+};
+
+template <typename T, int NM>
+struct Vals {
+    T v[NM];
+};
+template <typename T, int NM>
+struct PVals {
+    Pack<T> p[NM];
+};
+
+// Copy a small struct into shared memory (whole block), no sync.
+template <typename S>
+__device__ __forceinline__ void stage_struct(S* dst, const S* src) {
+    static_assert(sizeof(S) % 4 == 0, "");
+    for (int i = threadIdx.x; i < (int)(sizeof(S) / 4); i += blockDim.x)
+        reinterpret_cast<int*>(dst)[i] = __ldg(reinterpret_cast<const int*>(src) + i);
+}
+
+// Load NM maps of one tile with halo.  vect(d) gives the NM 16-byte packs at
+// element offset d (16-byte aligned), scal(d) the NM scalars at d.
+template <typename T, int NM, typename FS, typename FV>
+__device__ __forceinline__ void load_tile(T (*sm)[TileDim<T>::TH + 2][TileDim<T>::SW], const SliceGeom& g, int tx0,
+                                          int ty0, FS scal, FV vect) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH;
+    if (tx0 + kTileW <= g.nx) {
+        constexpr int VR = kTileW / VN;
+        for (int q = threadIdx.x; q < (TH + 2) * VR; q += blockDim.x) {
+            const int ly = q / VR, lx = (q - ly * VR) * VN;
+            const int gy = wrap(ty0 - 1 + ly, g.ny);
+            const PVals<T, NM> pv = vect(g.off + (long long)gy * g.pitch + tx0 + lx);
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                *reinterpret_cast<Pack<T>*>(&sm[m][ly][OFF + lx]) = pv.p[m];
+        }
+        for (int q = threadIdx.x; q < 2 * (TH + 2); q += blockDim.x) {
+            const int ly = q >> 1, side = q & 1;
+            const int gy = wrap(ty0 - 1 + ly, g.ny);
+            const int gx = side ? wrap(tx0 + kTileW, g.nx) : wrap(tx0 - 1, g.nx);
+            const Vals<T, NM> sv = scal(g.off + (long long)gy * g.pitch + gx);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) sm[m][ly][side ? OFF + kTileW : OFF - 1] = sv.v[m];
+        }
+    } else {
+        for (int q = threadIdx.x; q < (TH + 2) * (kTileW + 2); q += blockDim.x) {
+            const int ly = q / (kTileW + 2), lx = q - ly * (kTileW + 2);
+            const int gy = wrap(ty0 - 1 + ly, g.ny), gx = wrap(tx0 - 1 + lx, g.nx);
+            const Vals<T, NM> sv = scal(g.off + (long long)gy * g.pitch + gx);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) sm[m][ly][OFF - 1 + lx] = sv.v[m];
+        }
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ Pack<T> ldv(const T* p, long long d) {
+    return *reinterpret_cast<const Pack<T>*>(p + d);
+}
+template <typename T>
+__device__ __forceinline__ void stv(T* p, long long d, const Pack<T>& v) {
+    *reinterpret_cast<Pack<T>*>(p + d) = v;
+}
+
+// --------------------------------------------------------------------------
 // K1: hard threshold (eq. sol_hv) + right-hand sides
 // --------------------------------------------------------------------------
 
 template <typename T, bool STATS>
 __global__ void __launch_bounds__(kStencilThreads) k_thr_rhs(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                              SliceState* S, Ptrs<T> P) {
-    __shared__ T sm[4][kTile + 2][kTile + 2];
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
+    __shared__ __align__(16) T sm[4][TileDim<T>::TH + 2][SW];
     __shared__ double red[9 * 32];
-    const int maps[4] = {RECON_F_F1, RECON_F_F2, RECON_F_RHO, RECON_F_Z};
+    __shared__ SliceGeom s_g;
+    __shared__ SliceConst s_c;
+    __shared__ SliceState s_st;
+    const T* f1p = P.f[RECON_F_F1];
+    const T* f2p = P.f[RECON_F_F2];
+    const T* rhp = P.f[RECON_F_RHO];
+    const T* zp = P.f[RECON_F_Z];
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
-        const SliceState st = S[it.slice];
-        if (!st.active) continue;
-        const SliceGeom g = G[it.slice];
-        const SliceConst c = C[it.slice];
-        account(P.acct, KF_THR_RHS, tile_px(g, it) * 10 * (long long)sizeof(T));
-        for (int q = threadIdx.x; q < (kTile + 2) * (kTile + 2); q += blockDim.x) {
-            const int ly = q / (kTile + 2), lx = q - ly * (kTile + 2);
-            const int gy = wrap(it.b - 1 + ly, g.ny), gx = wrap(it.a - 1 + lx, g.nx);
-            const long long d = g.off + (long long)gy * g.pitch + gx;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) sm[m][ly][lx] = P.f[maps[m]][d];
-        }
+        if (!__ldg(&S[it.slice].active)) continue;
+        stage_struct(&s_g, G + it.slice);
+        stage_struct(&s_c, C + it.slice);
+        stage_struct(&s_st, S + it.slice);
         __syncthreads();
-        const T thr = thr_of<T>(st);
-        const T beta = T(st.beta), beta_t = T(st.beta_t);
+        const SliceGeom& g = s_g;
+        account(P.acct, KF_THR_RHS, tile_px<T>(g, it) * 10 * (long long)sizeof(T));
+        load_tile<T, 4>(
+            sm, g, it.a, it.b,
+            [&](long long d) { return Vals<T, 4>{{f1p[d], f2p[d], rhp[d], zp[d]}}; },
+            [&](long long d) { return PVals<T, 4>{{ldv(f1p, d), ldv(f2p, d), ldv(rhp, d), ldv(zp, d)}}; });
+        __syncthreads();
+        const SliceConst& c = s_c;
+        const T thr = thr_of<T>(s_st);
+        const T beta = T(s_st.beta), beta_t = T(s_st.beta_t);
+        const bool full = it.a + kTileW <= g.nx;
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int lx = q & (kTile - 1), ly = q / kTile;
-            const int x = it.a + lx, y = it.b + ly;
-            if (x >= g.nx || y >= g.ny) continue;
-            T div[4];
+        constexpr int VR = kTileW / VN;
+        for (int q = threadIdx.x; q < TileDim<T>::TH * VR; q += blockDim.x) {
+            const int ly = q / VR, lx0 = (q - ly * VR) * VN;
+            const int y = it.b + ly;
+            if (y >= g.ny) continue;
+            const long long d0 = g.off + (long long)y * g.pitch + it.a + lx0;
+            Pack<T> uL, uH;
+            if (full) {
+                uL = ldv(P.f[RECON_F_MUL], d0);
+                uH = ldv(P.f[RECON_F_MUH], d0);
+            } else {
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const T gc = sm[m][ly + 1][lx + 1];
-                const T dx = sub_rn(sm[m][ly + 1][lx + 2], gc);
-                const T dy = sub_rn(sm[m][ly + 2][lx + 1], gc);
-                const T dxl = sub_rn(gc, sm[m][ly + 1][lx]);
-                const T dyl = sub_rn(sm[m][ly + 2][lx], sm[m][ly + 1][lx]);
-                const T dxu = sub_rn(sm[m][ly][lx + 2], sm[m][ly][lx + 1]);
-                const T dyu = sub_rn(gc, sm[m][ly][lx + 1]);
-                const bool k0 = keep_grad(dx, dy, thr);
-                const bool kl = keep_grad(dxl, dyl, thr);
-                const bool ku = keep_grad(dxu, dyu, thr);
-                const T h0 = k0 ? dx : T(0), v0 = k0 ? dy : T(0);
-                const T hl = kl ? dxl : T(0), vu = ku ? dyu : T(0);
-                div[m] = (hl - h0) + (vu - v0);
-                if (STATS) {
-                    if (!k0) acc[4] += (double)dx * dx + (double)dy * dy;
-                    acc[5 + m] += k0 ? 1.0 : 0.0;
+                for (int e = 0; e < VN; ++e) {
+                    const bool in = it.a + lx0 + e < g.nx;
+                    uL.v[e] = in ? P.f[RECON_F_MUL][d0 + e] : T(0);
+                    uH.v[e] = in ? P.f[RECON_F_MUH][d0 + e] : T(0);
                 }
             }
-            const long long d = g.off + (long long)y * g.pitch + x;
-            const T f1 = sm[0][ly + 1][lx + 1], f2 = sm[1][ly + 1][lx + 1];
-            const T rho = sm[2][ly + 1][lx + 1], z = sm[3][ly + 1][lx + 1];
-            const T uL = P.f[RECON_F_MUL][d], uH = P.f[RECON_F_MUH][d];
-            const T M1 = rho * (T(c.P1) * z + T(c.psi1));
-            const T M2 = rho * (T(c.P2) * z + T(c.psi2));
-            const T base1 = T(c.a00) * uL + T(c.a01) * uH + T(c.b00) * M1 + T(c.b01) * M2;
-            const T base2 = T(c.a10) * uL + T(c.a11) * uH + T(c.b10) * M1 + T(c.b11) * M2;
-            P.f[RECON_F_RHS_F1][d] = base1 - T(c.c12) * f2 + beta * div[0];
-            P.f[RECON_F_RHS_F2][d] = (c.order ? base2 : base2 - T(c.c12) * f1) + beta * div[1];
-            P.f[RECON_F_DIV_RHO][d] = beta_t * div[2];
-            P.f[RECON_F_DIV_Z][d] = beta_t * div[3];
-            if (STATS) {
-                const double dL = c.a00 * (double)f1 + c.a10 * (double)f2 - (double)uL;
-                const double dH = c.a01 * (double)f1 + c.a11 * (double)f2 - (double)uH;
-                const double m1 = c.b00 * (double)f1 + c.b10 * (double)f2;
-                const double m2 = c.b01 * (double)f1 + c.b11 * (double)f2;
-                const double e1 = (double)rho * (c.P1 * (double)z + c.psi1) - m1;
-                const double e2 = (double)rho * (c.P2 * (double)z + c.psi2) - m2;
-                acc[0] += dL * dL;
-                acc[1] += dH * dH;
-                acc[2] += e1 * e1;
-                acc[3] += e2 * e2;
+            Pack<T> o0, o1, o2, o3;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const int lx = OFF + lx0 + e;   // column of this pixel in sm
+                const int ry = ly + 1;
+                const bool in = full || (it.a + lx0 + e < g.nx);
+                T div[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const T gc = sm[m][ry][lx];
+                    const T dx = sub_rn(sm[m][ry][lx + 1], gc);
+                    const T dy = sub_rn(sm[m][ry + 1][lx], gc);
+                    const T dxl = sub_rn(gc, sm[m][ry][lx - 1]);
+                    const T dyl = sub_rn(sm[m][ry + 1][lx - 1], sm[m][ry][lx - 1]);
+                    const T dxu = sub_rn(sm[m][ry - 1][lx + 1], sm[m][ry - 1][lx]);
+                    const T dyu = sub_rn(gc, sm[m][ry - 1][lx]);
+                    const bool k0 = keep_grad(dx, dy, thr);
+                    const bool kl = keep_grad(dxl, dyl, thr);
+                    const bool ku = keep_grad(dxu, dyu, thr);
+                    const T h0 = k0 ? dx : T(0), v0 = k0 ? dy : T(0);
+                    const T hl = kl ? dxl : T(0), vu = ku ? dyu : T(0);
+                    div[m] = (hl - h0) + (vu - v0);
+                    if (STATS && in) {
+                        if (!k0) acc[4] += (double)dx * dx + (double)dy * dy;
+                        acc[5 + m] += k0 ? 1.0 : 0.0;
+                    }
+                }
+                const T f1 = sm[0][ry][lx], f2 = sm[1][ry][lx], rho = sm[2][ry][lx], z = sm[3][ry][lx];
+                const T M1 = rho * (T(c.P1) * z + T(c.psi1));
+                const T M2 = rho * (T(c.P2) * z + T(c.psi2));
+                const T base1 = T(c.a00) * uL.v[e] + T(c.a01) * uH.v[e] + T(c.b00) * M1 + T(c.b01) * M2;
+                const T base2 = T(c.a10) * uL.v[e] + T(c.a11) * uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2;
+                o0.v[e] = base1 - T(c.c12) * f2 + beta * div[0];
+                o1.v[e] = (c.order ? base2 : base2 - T(c.c12) * f1) + beta * div[1];
+                o2.v[e] = beta_t * div[2];
+                o3.v[e] = beta_t * div[3];
+                if (STATS && in) {
+                    const double dL = c.a00 * (double)f1 + c.a10 * (double)f2 - (double)uL.v[e];
+                    const double dH = c.a01 * (double)f1 + c.a11 * (double)f2 - (double)uH.v[e];
+                    const double m1 = c.b00 * (double)f1 + c.b10 * (double)f2;
+                    const double m2 = c.b01 * (double)f1 + c.b11 * (double)f2;
+                    const double e1 = (double)rho * (c.P1 * (double)z + c.psi1) - m1;
+                    const double e2 = (double)rho * (c.P2 * (double)z + c.psi2) - m2;
+                    acc[0] += dL * dL;
+                    acc[1] += dH * dH;
+                    acc[2] += e1 * e1;
+                    acc[3] += e2 * e2;
+                }
+            }
+            if (full) {
+                stv(P.f[RECON_F_RHS_F1], d0, o0);
+                stv(P.f[RECON_F_RHS_F2], d0, o1);
+                stv(P.f[RECON_F_DIV_RHO], d0, o2);
+                stv(P.f[RECON_F_DIV_Z], d0, o3);
+            } else {
+#pragma unroll
+                for (int e = 0; e < VN; ++e) {
+                    if (it.a + lx0 + e >= g.nx) continue;
+                    P.f[RECON_F_RHS_F1][d0 + e] = o0.v[e];
+                    P.f[RECON_F_RHS_F2][d0 + e] = o1.v[e];
+                    P.f[RECON_F_DIV_RHO][d0 + e] = o2.v[e];
+                    P.f[RECON_F_DIV_Z][d0 + e] = o3.v[e];
+                }
             }
         }
         if (STATS) {
             block_sum<9>(acc, red);
             double tot[9];
-            if (item_reduce<9>(L, w, it.slice, acc, tot)) {
+            if (item_reduce<9>(L, w, it.slice, acc, tot, red)) {
                 SliceState& so = S[it.slice];
                 for (int q = 0; q < 5; ++q) so.stat[q] = tot[q];
                 for (int m = 0; m < 4; ++m) so.nnz[m] = (long long)(tot[5 + m] + 0.5);
@@ -220,11 +369,11 @@ template <typename T>
 __global__ void k_gs_fix(ItemList L, const SliceGeom* G, const SliceConst* C, const SliceState* S, Ptrs<T> P) {
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
-        if (!S[it.slice].active) continue;
+        if (!__ldg(&S[it.slice].active)) continue;
         const SliceGeom g = G[it.slice];
         const T c12 = T(C[it.slice].c12);
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int x = it.a + (q & (kTile - 1)), y = it.b + q / kTile;
+        for (int q = threadIdx.x; q < kTileW * TileH<T>::v; q += blockDim.x) {
+            const int x = it.a + (q & (kTileW - 1)), y = it.b + q / kTileW;
             if (x >= g.nx || y >= g.ny) continue;
             const long long d = g.off + (long long)y * g.pitch + x;
             P.f[RECON_F_RHS_F2][d] -= c12 * P.f[RECON_F_F1][d];
@@ -237,120 +386,117 @@ __global__ void k_gs_fix(ItemList L, const SliceGeom* G, const SliceConst* C, co
 // columns (FFT, divide by c + beta K, inverse FFT), rows (C2R).
 // --------------------------------------------------------------------------
 
-template <typename T>
-__device__ __forceinline__ void solve_coef(int kind, const SliceConst& c, const SliceState& st, double& cc,
-                                           double& bb) {
-    switch (kind) {
-        case 0: cc = c.c_f1; bb = st.beta; break;
-        case 1: cc = c.c_f2; bb = st.beta; break;
-        case 2: cc = 1.0; bb = st.beta_t; break;
-        default: cc = st.abar2; bb = st.beta_t; break;
-    }
-}
-
-__device__ __forceinline__ bool job_skip(const SliceState& st, int kind) {
-    return !st.active || (kind == 3 && st.cg_done);
-}
-
 // MODE 0: input is a field.  MODE 1: input is D^-1/2-scaled CG residual.
+// Item: rows 2*it.a .. of one slice, it.b pairs; two real rows per complex FFT.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kFftThreads) k_rows_fwd(ItemList L, const SliceGeom* G, const SliceState* S,
-                                                           Ptrs<T> P, FftJobs J, int buf_elems) {
+                                                           Ptrs<T> P, FftJobs J, const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* bufB = bufA + buf_elems;
-    cplx<T>* tw = bufB + buf_elems;
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf2 = buf + half;
     const int total = L.n_items * J.n;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int job = w / L.n_items, item = w - job * L.n_items;
         const Item it = L.items[item];
-        const SliceState st = S[it.slice];
-        if (job_skip(st, J.coef[job])) continue;
+        const int kind = J.coef[job];
+        if (!__ldg(&S[it.slice].active) || (kind == 3 && __ldg(&S[it.slice].cg_done))) continue;
         const SliceGeom g = G[it.slice];
-        const int N = g.nx, pair0 = it.a, np = it.b;
-        {
-            const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
-            account(P.acct, MODE ? KF_ROWS_FWD_PRE : KF_ROWS_FWD,
-                    (long long)rows * ((MODE ? 2 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
-        }
-        fill_twiddles(tw, N);
+        const int N = g.nx, pair0 = it.a, np = it.b, ld = padded_len(N);
+        const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
+        account(P.acct, MODE ? KF_ROWS_FWD_PRE : KF_ROWS_FWD,
+                (long long)rows * ((MODE ? 2 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
         const T* in = P.f[J.in[job]];
         const T* a2 = P.f[RECON_F_A2];
-        const T num = T(st.abar2 + 4.0 * st.beta_t), b4 = T(4.0 * st.beta_t);
-        for (int q = threadIdx.x; q < np * N; q += blockDim.x) {
-            const int b = q / N, n = q - b * N;
+        T rnum = T(0), b4 = T(0);
+        if (MODE == 1) {
+            rnum = T(sqrt(__ldg(&S[it.slice].abar2) + 4.0 * __ldg(&S[it.slice].beta_t)));
+            b4 = T(4.0 * __ldg(&S[it.slice].beta_t));
+        }
+        for (int b = 0; b < np; ++b) {
             const int row = 2 * (pair0 + b);
-            const long long d0 = g.off + (long long)row * g.pitch + n;
-            T v0 = in[d0], v1 = T(0);
             const bool has1 = row + 1 < g.ny;
-            if (has1) v1 = in[d0 + g.pitch];
-            if (MODE == 1) {
-                v0 *= sqrt(num / (a2[d0] + b4));
-                if (has1) v1 *= sqrt(num / (a2[d0 + g.pitch] + b4));
+            const long long d0 = g.off + (long long)row * g.pitch;
+            for (int n = threadIdx.x; n < N; n += blockDim.x) {
+                T v0 = in[d0 + n], v1 = has1 ? in[d0 + g.pitch + n] : T(0);
+                if (MODE == 1) {
+                    v0 *= dscale(rnum, a2[d0 + n], b4);
+                    if (has1) v1 *= dscale(rnum, a2[d0 + g.pitch + n], b4);
+                }
+                buf[b * ld + pad8(n)] = {v0, v1};
             }
-            bufA[b * N + n] = {v0, v1};
         }
         __syncthreads();
-        const cplx<T>* res = fft_batch<T>(bufA, bufB, N, np, N, tw, -1);
+        const cplx<T>* res = fft_batch<T>(buf, buf2, N, g.plan_x, np, ld, twpool + g.twx, -1);
         cplx<T>* sp = P.s[J.spec[job]];
-        for (int q = threadIdx.x; q < np * g.nh; q += blockDim.x) {
-            const int b = q / g.nh, k = q - b * g.nh;
+        for (int b = 0; b < np; ++b) {
             const int row = 2 * (pair0 + b);
-            const cplx<T> zk = res[b * N + k];
-            const cplx<T> zc = res[b * N + (k == 0 ? 0 : N - k)];
-            // A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)
-            const cplx<T> A = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
-            const cplx<T> B = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
-            const long long e = g.coff + (long long)row * g.cpitch + k;
-            sp[e] = A;
-            if (row + 1 < g.ny) sp[e + g.cpitch] = B;
+            const long long e0 = g.coff + (long long)row * g.cpitch;
+            for (int k = threadIdx.x; k < g.nh; k += blockDim.x) {
+                const cplx<T> zk = res[b * ld + pad8(k)];
+                const cplx<T> zc = res[b * ld + pad8(k == 0 ? 0 : N - k)];
+                // A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)
+                sp[e0 + k] = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
+                if (row + 1 < g.ny) sp[e0 + g.cpitch + k] = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
+            }
         }
         __syncthreads();
     }
 }
 
+// Item: spectrum columns it.a .. it.a + it.b - 1 of one slice: FFT along y,
+// divide by (c + beta K) n_x n_y, inverse FFT along y.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeom* G, const SliceConst* C,
-                                                       const SliceState* S, Ptrs<T> P, FftJobs J, int buf_elems) {
+                                                       const SliceState* S, Ptrs<T> P, FftJobs J,
+                                                       const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* bufB = bufA + buf_elems;
-    cplx<T>* tw = bufB + buf_elems;
+    cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf1 = buf0 + half;
     const int total = L.n_items * J.n;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int job = w / L.n_items, item = w - job * L.n_items;
         const Item it = L.items[item];
-        const SliceState st = S[it.slice];
-        if (job_skip(st, J.coef[job])) continue;
+        const int kind = J.coef[job];
+        const SliceState* st = S + it.slice;
+        if (!__ldg(&st->active) || (kind == 3 && __ldg(&st->cg_done))) continue;
         const SliceGeom g = G[it.slice];
-        const int N = g.ny, col0 = it.a, nc = it.b, ld = N + 1;
-        account(P.acct, J.coef[job] == 3 ? KF_COLS_PRE : KF_COLS, (long long)nc * N * 4 * (long long)sizeof(T));
-        fill_twiddles(tw, N);
+        const int N = g.ny, col0 = it.a, nc = it.b, ld = padded_len(N) | 1;
+        account(P.acct, kind == 3 ? KF_COLS_PRE : KF_COLS, (long long)nc * N * 4 * (long long)sizeof(T));
         cplx<T>* sp = P.s[J.spec[job]];
         for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
             const int y = q / nc, cc = q - y * nc;
-            bufA[cc * ld + y] = sp[g.coff + (long long)y * g.cpitch + col0 + cc];
+            buf0[cc * ld + pad8(y)] = sp[g.coff + (long long)y * g.cpitch + col0 + cc];
         }
         __syncthreads();
-        cplx<T>* res = fft_batch<T>(bufA, bufB, N, nc, ld, tw, -1);
+        const cplx<T>* tw = twpool + g.twy;
         double cst, bet;
-        solve_coef<T>(J.coef[job], C[it.slice], st, cst, bet);
-        const T inv_n = T(1.0 / ((double)g.nx * (double)g.ny));
-        for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
-            const int cc = q / N, ky = q - cc * N;
-            T sx = sin(T(M_PI) * T(col0 + cc) / T(g.nx));
-            T sy = sin(T(M_PI) * T(ky) / T(N));
-            const T den = T(cst) + T(bet) * (T(4) * sx * sx + T(4) * sy * sy);
-            const T sc = inv_n / den;
-            cplx<T> v = res[cc * ld + ky];
-            res[cc * ld + ky] = {v.x * sc, v.y * sc};
+        switch (kind) {
+            case 0: cst = C[it.slice].c_f1; bet = __ldg(&st->beta); break;
+            case 1: cst = C[it.slice].c_f2; bet = __ldg(&st->beta); break;
+            case 2: cst = 1.0; bet = __ldg(&st->beta_t); break;
+            default: cst = __ldg(&st->abar2); bet = __ldg(&st->beta_t); break;
         }
-        __syncthreads();
-        cplx<T>* other = (res == bufA) ? bufB : bufA;
-        const cplx<T>* out = fft_batch<T>(res, other, N, nc, ld, tw, +1);
+        const T inv_n = T(1.0 / ((double)g.nx * (double)g.ny));
+        const T* symx = P.sym + g.symx;
+        const T* symy = P.sym + g.symy;
+        // forward FFT along y, spectral divide, inverse FFT along y (one
+        // inlined transform, run twice)
+        cplx<T>* buf = buf0;
+        for (int pass = 0; pass < 2; ++pass) {
+            buf = fft_batch<T>(buf, buf == buf0 ? buf1 : buf0, N, g.plan_y, nc, ld, tw, pass ? +1 : -1);
+            if (pass) break;
+            for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
+                const int cc = q / N, ky = q - cc * N;
+                // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
+                const T sc = inv_n / (T(cst) + T(bet) * (symx[col0 + cc] + symy[ky]));
+                cplx<T> v = buf[cc * ld + pad8(ky)];
+                buf[cc * ld + pad8(ky)] = {v.x * sc, v.y * sc};
+            }
+            __syncthreads();
+        }
         for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
             const int y = q / nc, cc = q - y * nc;
-            sp[g.coff + (long long)y * g.cpitch + col0 + cc] = out[cc * ld + y];
+            sp[g.coff + (long long)y * g.cpitch + col0 + cc] = buf[cc * ld + pad8(y)];
         }
         __syncthreads();
     }
@@ -359,72 +505,78 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeo
 // MODE 0: write the field.  MODE 1: y = D^-1/2 x into CG_Y and reduce r.y.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kFftThreads) k_rows_inv(ItemList L, const SliceGeom* G, SliceState* S, Ptrs<T> P,
-                                                           FftJobs J, int buf_elems) {
+                                                           FftJobs J, const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<T>* bufA = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* bufB = bufA + buf_elems;
-    cplx<T>* tw = bufB + buf_elems;
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf2 = buf + half;
     __shared__ double red[32];
     const int total = L.n_items * J.n;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int job = w / L.n_items, item = w - job * L.n_items;
         const Item it = L.items[item];
-        const SliceState st = S[it.slice];
-        if (job_skip(st, J.coef[job])) continue;
+        const int kind = J.coef[job];
+        if (!__ldg(&S[it.slice].active) || (kind == 3 && __ldg(&S[it.slice].cg_done))) continue;
         const SliceGeom g = G[it.slice];
-        const int N = g.nx, pair0 = it.a, np = it.b;
-        {
-            const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
-            account(P.acct, MODE ? KF_ROWS_INV_PRE : KF_ROWS_INV,
-                    (long long)rows * ((MODE ? 3 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
-        }
-        fill_twiddles(tw, N);
+        const int N = g.nx, pair0 = it.a, np = it.b, ld = padded_len(N);
+        const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
+        account(P.acct, MODE ? KF_ROWS_INV_PRE : KF_ROWS_INV,
+                (long long)rows * ((MODE ? 3 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
         const cplx<T>* sp = P.s[J.spec[job]];
-        for (int q = threadIdx.x; q < np * N; q += blockDim.x) {
-            const int b = q / N, n = q - b * N;
+        for (int b = 0; b < np; ++b) {
             const int row = 2 * (pair0 + b);
-            const bool herm = n >= g.nh;
-            const int k = herm ? N - n : n;
-            const long long e = g.coff + (long long)row * g.cpitch + k;
-            cplx<T> A = sp[e], B = {T(0), T(0)};
-            if (row + 1 < g.ny) B = sp[e + g.cpitch];
-            if (herm) {
-                A.y = -A.y;
-                B.y = -B.y;
+            const bool has1 = row + 1 < g.ny;
+            const long long e0 = g.coff + (long long)row * g.cpitch;
+            for (int n = threadIdx.x; n < N; n += blockDim.x) {
+                const bool herm = n >= g.nh;
+                const int k = herm ? N - n : n;
+                cplx<T> A = sp[e0 + k], B = {T(0), T(0)};
+                if (has1) B = sp[e0 + g.cpitch + k];
+                if (herm) {
+                    A.y = -A.y;
+                    B.y = -B.y;
+                }
+                buf[b * ld + pad8(n)] = {A.x - B.y, A.y + B.x};
             }
-            bufA[b * N + n] = {A.x - B.y, A.y + B.x};
         }
         __syncthreads();
-        const cplx<T>* res = fft_batch<T>(bufA, bufB, N, np, N, tw, +1);
+        const cplx<T>* res = fft_batch<T>(buf, buf2, N, g.plan_x, np, ld, twpool + g.twx, +1);
         T* out = P.f[J.out[job]];
         double acc[1] = {0.0};
+        T accT = T(0);
         const T* a2 = P.f[RECON_F_A2];
         const T* r = P.f[RECON_F_CG_R];
-        const T num = T(st.abar2 + 4.0 * st.beta_t), b4 = T(4.0 * st.beta_t);
-        for (int q = threadIdx.x; q < np * N; q += blockDim.x) {
-            const int b = q / N, n = q - b * N;
+        T rnum = T(0), b4 = T(0);
+        if (MODE == 1) {
+            rnum = T(sqrt(__ldg(&S[it.slice].abar2) + 4.0 * __ldg(&S[it.slice].beta_t)));
+            b4 = T(4.0 * __ldg(&S[it.slice].beta_t));
+        }
+        for (int b = 0; b < np; ++b) {
             const int row = 2 * (pair0 + b);
-            const long long d0 = g.off + (long long)row * g.pitch + n;
-            const cplx<T> v = res[b * N + n];
-            if (MODE == 0) {
-                out[d0] = v.x;
-                if (row + 1 < g.ny) out[d0 + g.pitch] = v.y;
-            } else {
-                const T y0 = v.x * sqrt(num / (a2[d0] + b4));
-                out[d0] = y0;
-                acc[0] += (double)y0 * (double)r[d0];
-                if (row + 1 < g.ny) {
-                    const long long d1 = d0 + g.pitch;
-                    const T y1 = v.y * sqrt(num / (a2[d1] + b4));
-                    out[d1] = y1;
-                    acc[0] += (double)y1 * (double)r[d1];
+            const bool has1 = row + 1 < g.ny;
+            const long long d0 = g.off + (long long)row * g.pitch;
+            for (int n = threadIdx.x; n < N; n += blockDim.x) {
+                const cplx<T> v = res[b * ld + pad8(n)];
+                if (MODE == 0) {
+                    out[d0 + n] = v.x;
+                    if (has1) out[d0 + g.pitch + n] = v.y;
+                } else {
+                    const T y0 = v.x * dscale(rnum, a2[d0 + n], b4);
+                    out[d0 + n] = y0;
+                    accT = fma(y0, r[d0 + n], accT);
+                    if (has1) {
+                        const long long d1 = d0 + g.pitch + n;
+                        const T y1 = v.y * dscale(rnum, a2[d1], b4);
+                        out[d1] = y1;
+                        accT = fma(y1, r[d1], accT);
+                    }
                 }
             }
         }
         if (MODE == 1) {
+            acc[0] = (double)accT;
             block_sum<1>(acc, red);
             double tot[1];
-            if (item_reduce<1>(L, item, it.slice, acc, tot)) {
+            if (item_reduce<1>(L, item, it.slice, acc, tot, red)) {
                 SliceState& so = S[it.slice];
                 so.betacg = (so.cg_it == 0) ? 0.0 : tot[0] / so.ry;
                 so.ry = tot[0];
@@ -438,39 +590,92 @@ __global__ void __launch_bounds__(kFftThreads) k_rows_inv(ItemList L, const Slic
 // synthesis at E1/E2 from the new f, rho_e rhs, Z^m normal equations
 // --------------------------------------------------------------------------
 
+// Visit the pixels of a tile VN at a time: fn(d0, e_count, full) with d0 the
+// element offset of the first pixel of the vector; `full` when all VN lie
+// inside the image.
+template <typename T, typename F>
+__device__ __forceinline__ void for_tile_vectors(const SliceGeom& g, const Item& it, F fn) {
+    constexpr int VN = TileDim<T>::VN, VR = kTileW / VN;
+    for (int q = threadIdx.x; q < TileDim<T>::TH * VR; q += blockDim.x) {
+        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
+        const int y = it.b + ly, x0 = it.a + lx0;
+        if (y >= g.ny || x0 >= g.nx) continue;
+        const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
+        fn(g.off + (long long)y * g.pitch + x0, cnt, ly, lx0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ Pack<T> ldv_n(const T* p, long long d, int cnt) {
+    if (cnt == TileDim<T>::VN) return ldv(p, d);
+    Pack<T> r;
+#pragma unroll
+    for (int e = 0; e < TileDim<T>::VN; ++e) r.v[e] = e < cnt ? p[d + e] : T(0);
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ void stv_n(T* p, long long d, const Pack<T>& v, int cnt) {
+    if (cnt == TileDim<T>::VN) {
+        stv(p, d, v);
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < TileDim<T>::VN; ++e)
+        if (e < cnt) p[d + e] = v.v[e];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                            SliceState* S, Ptrs<T> P) {
+    constexpr int VN = TileDim<T>::VN;
     __shared__ double red[2 * 32];
+    __shared__ SliceGeom s_g;
+    __shared__ SliceConst s_c;
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
-        if (!S[it.slice].active) continue;
-        const SliceGeom g = G[it.slice];
-        const SliceConst c = C[it.slice];
-        account(P.acct, KF_SYNTH, tile_px(g, it) * 7 * (long long)sizeof(T));
+        if (!__ldg(&S[it.slice].active)) continue;
+        stage_struct(&s_g, G + it.slice);
+        stage_struct(&s_c, C + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        const SliceConst& c = s_c;
+        account(P.acct, KF_SYNTH, tile_px<T>(g, it) * 7 * (long long)sizeof(T));
         double acc[2] = {0.0, 0.0};
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int x = it.a + (q & (kTile - 1)), y = it.b + q / kTile;
-            if (x >= g.nx || y >= g.ny) continue;
-            const long long d = g.off + (long long)y * g.pitch + x;
-            const double f1 = P.f[RECON_F_F1][d], f2 = P.f[RECON_F_F2][d];
-            const double m1 = c.b00 * f1 + c.b10 * f2;
-            const double m2 = c.b01 * f1 + c.b11 * f2;
-            const double rho_cf = (m1 * c.r - m2) / c.c_rho;
-            const double a = (m1 * c.P2 - m2 * c.P1) / c.a_w;
-            const double b = (m2 * c.psi1 - m1 * c.psi2) / c.a_w;
-            const T rr = T(rho_cf) + P.f[RECON_F_DIV_RHO][d];
-            const T a2 = T(a * a);
-            const T rz = T(a * b) + P.f[RECON_F_DIV_Z][d];
-            P.f[RECON_F_RHS_RHO][d] = rr;
-            P.f[RECON_F_A2][d] = a2;
-            P.f[RECON_F_RHS_Z][d] = rz;
-            acc[0] += (double)a2;
-            acc[1] += (double)rz * (double)rz;
-        }
+        T acc0 = T(0), acc1 = T(0);
+        const T b00 = T(c.b00), b10 = T(c.b10), b01 = T(c.b01), b11 = T(c.b11);
+        const T rr_ = T(c.r), inv_crho = T(1.0 / c.c_rho), inv_aw = T(1.0 / c.a_w);
+        const T P1 = T(c.P1), P2 = T(c.P2), psi1 = T(c.psi1), psi2 = T(c.psi2);
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
+            const Pack<T> f1 = ldv_n(P.f[RECON_F_F1], d, cnt), f2 = ldv_n(P.f[RECON_F_F2], d, cnt);
+            const Pack<T> dr = ldv_n(P.f[RECON_F_DIV_RHO], d, cnt), dz = ldv_n(P.f[RECON_F_DIV_Z], d, cnt);
+            Pack<T> orr, oa2, orz;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                // eq. mac_E1/E2 from the new fractions, then eq. rho_e and
+                // eq. Z_m (normalised); the two nearly cancelling products of
+                // a and b are formed with an exact split of one of them
+                const T m1 = b00 * f1.v[e] + b10 * f2.v[e];
+                const T m2 = b01 * f1.v[e] + b11 * f2.v[e];
+                const T rho_cf = (m1 * rr_ - m2) * inv_crho;
+                const T a = diff_of_products(m1, P2, m2, P1) * inv_aw;
+                const T b = diff_of_products(m2, psi1, m1, psi2) * inv_aw;
+                orr.v[e] = rho_cf + dr.v[e];
+                oa2.v[e] = a * a;
+                orz.v[e] = a * b + dz.v[e];
+                if (e < cnt) {
+                    acc0 += oa2.v[e];
+                    acc1 = fma(orz.v[e], orz.v[e], acc1);
+                }
+            }
+            stv_n(P.f[RECON_F_RHS_RHO], d, orr, cnt);
+            stv_n(P.f[RECON_F_A2], d, oa2, cnt);
+            stv_n(P.f[RECON_F_RHS_Z], d, orz, cnt);
+        });
+        acc[0] = (double)acc0;
+        acc[1] = (double)acc1;
         block_sum<2>(acc, red);
         double tot[2];
-        if (item_reduce<2>(L, w, it.slice, acc, tot)) {
+        if (item_reduce<2>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
             so.abar2 = tot[0] / ((double)g.nx * (double)g.ny);
             so.bb = tot[1];
@@ -483,55 +688,49 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
 // PCG for [diag(a^2) + beta~ L] z = rhs
 // --------------------------------------------------------------------------
 
-// stencil tile of a vector with its 4-neighbour halo (periodic)
-template <typename T, typename F>
-__device__ __forceinline__ void load_halo(T (*sm)[kTile + 2], const SliceGeom& g, const Item& it, F value) {
-    for (int q = threadIdx.x; q < (kTile + 2) * (kTile + 2); q += blockDim.x) {
-        const int ly = q / (kTile + 2), lx = q - ly * (kTile + 2);
-        const bool corner = (ly == 0 || ly == kTile + 1) && (lx == 0 || lx == kTile + 1);
-        if (corner) continue;
-        const int gy = wrap(it.b - 1 + ly, g.ny), gx = wrap(it.a - 1 + lx, g.nx);
-        sm[ly][lx] = value(g.off + (long long)gy * g.pitch + gx);
-    }
-}
-
 template <typename T>
-__device__ __forceinline__ T lap5(const T (*sm)[kTile + 2], int ly, int lx) {
-    const T c = sm[ly + 1][lx + 1];
-    return (T(4) * c - sm[ly + 1][lx] - sm[ly + 1][lx + 2]) - (sm[ly][lx + 1] + sm[ly + 2][lx + 1]);
+__device__ __forceinline__ T lap5(const T (*sm)[TileDim<T>::SW], int ry, int cx) {
+    const T c = sm[ry][cx];
+    return (T(4) * c - sm[ry][cx - 1] - sm[ry][cx + 1]) - (sm[ry - 1][cx] + sm[ry + 1][cx]);
 }
-
-__device__ __forceinline__ bool cg_skip(const SliceState& st) { return !st.active || st.cg_done; }
 
 template <typename T>
 __global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                              SliceState* S, Ptrs<T> P, int* pending) {
-    __shared__ T sm[kTile + 2][kTile + 2];
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
+    __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
     __shared__ double red[32];
+    __shared__ SliceGeom s_g;
+    const T* z = P.f[RECON_F_Z];
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
-        const SliceState st = S[it.slice];
-        if (!st.active) continue;
-        const SliceGeom g = G[it.slice];
-        account(P.acct, KF_CG_INIT, tile_px(g, it) * 4 * (long long)sizeof(T));
-        const T* z = P.f[RECON_F_Z];
-        load_halo<T>(sm, g, it, [&](long long d) { return z[d]; });
+        if (!__ldg(&S[it.slice].active)) continue;
+        stage_struct(&s_g, G + it.slice);
         __syncthreads();
-        const T bt = T(st.beta_t);
+        const SliceGeom& g = s_g;
+        account(P.acct, KF_CG_INIT, tile_px<T>(g, it) * 4 * (long long)sizeof(T));
+        load_tile<T, 1>(
+            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{z[d]}}; },
+            [&](long long d) { return PVals<T, 1>{{ldv(z, d)}}; });
+        __syncthreads();
+        const T bt = T(__ldg(&S[it.slice].beta_t));
         double acc[1] = {0.0};
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int lx = q & (kTile - 1), ly = q / kTile;
-            const int x = it.a + lx, y = it.b + ly;
-            if (x >= g.nx || y >= g.ny) continue;
-            const long long d = g.off + (long long)y * g.pitch + x;
-            const T Mz = P.f[RECON_F_A2][d] * sm[ly + 1][lx + 1] + bt * lap5<T>(sm, ly, lx);
-            const T r = P.f[RECON_F_RHS_Z][d] - Mz;
-            P.f[RECON_F_CG_R][d] = r;
-            acc[0] += (double)r * (double)r;
-        }
+        T accT = T(0);
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
+            const Pack<T> a2 = ldv_n(P.f[RECON_F_A2], d, cnt), rz = ldv_n(P.f[RECON_F_RHS_Z], d, cnt);
+            Pack<T> r;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const T Mz = a2.v[e] * sm[0][ly + 1][OFF + lx0 + e] + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e);
+                r.v[e] = rz.v[e] - Mz;
+                if (e < cnt) accT = fma(r.v[e], r.v[e], accT);
+            }
+            stv_n(P.f[RECON_F_CG_R], d, r, cnt);
+        });
+        acc[0] = (double)accT;
         block_sum<1>(acc, red);
         double tot[1];
-        if (item_reduce<1>(L, w, it.slice, acc, tot)) {
+        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
             const double tol2 = C[it.slice].cg_tol * C[it.slice].cg_tol;
             so.rr = tot[0];
@@ -549,37 +748,57 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const S
 template <typename T>
 __global__ void __launch_bounds__(kStencilThreads) k_cg_matvec(ItemList L, const SliceGeom* G, SliceState* S,
                                                                Ptrs<T> P, int par) {
-    __shared__ T sm[kTile + 2][kTile + 2];
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
+    __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
     __shared__ double red[32];
+    __shared__ SliceGeom s_g;
     const T* pold = P.f[par ? RECON_F_CG_P1 : RECON_F_CG_P0];
     T* pnew = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
     const T* yv = P.f[RECON_F_CG_Y];
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
-        const SliceState st = S[it.slice];
-        if (cg_skip(st)) continue;
-        const SliceGeom g = G[it.slice];
-        account(P.acct, KF_CG_MATVEC, tile_px(g, it) * 5 * (long long)sizeof(T));
-        const bool first = st.cg_it == 0;
-        const T bc = T(st.betacg);
-        load_halo<T>(sm, g, it, [&](long long d) { return first ? yv[d] : yv[d] + bc * pold[d]; });
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
         __syncthreads();
-        const T bt = T(st.beta_t);
+        const SliceGeom& g = s_g;
+        account(P.acct, KF_CG_MATVEC, tile_px<T>(g, it) * 5 * (long long)sizeof(T));
+        const bool first = __ldg(&sp->cg_it) == 0;
+        const T bc = first ? T(0) : T(__ldg(&sp->betacg));
+        // p = y + beta_cg p_old (p = y on the first step)
+        load_tile<T, 1>(
+            sm, g, it.a, it.b,
+            [&](long long d) { return Vals<T, 1>{{first ? yv[d] : yv[d] + bc * pold[d]}}; },
+            [&](long long d) {
+                Pack<T> y = ldv(yv, d);
+                if (!first) {
+                    const Pack<T> po = ldv(pold, d);
+#pragma unroll
+                    for (int e = 0; e < VN; ++e) y.v[e] += bc * po.v[e];
+                }
+                return PVals<T, 1>{{y}};
+            });
+        __syncthreads();
+        const T bt = T(__ldg(&sp->beta_t));
         double acc[1] = {0.0};
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int lx = q & (kTile - 1), ly = q / kTile;
-            const int x = it.a + lx, y = it.b + ly;
-            if (x >= g.nx || y >= g.ny) continue;
-            const long long d = g.off + (long long)y * g.pitch + x;
-            const T p = sm[ly + 1][lx + 1];
-            const T qv = P.f[RECON_F_A2][d] * p + bt * lap5<T>(sm, ly, lx);
-            pnew[d] = p;
-            P.f[RECON_F_CG_Q][d] = qv;
-            acc[0] += (double)p * (double)qv;
-        }
+        T accT = T(0);
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
+            const Pack<T> a2 = ldv_n(P.f[RECON_F_A2], d, cnt);
+            Pack<T> pv, qv;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const T p = sm[0][ly + 1][OFF + lx0 + e];
+                pv.v[e] = p;
+                qv.v[e] = a2.v[e] * p + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e);
+                if (e < cnt) accT = fma(p, qv.v[e], accT);
+            }
+            stv_n(pnew, d, pv, cnt);
+            stv_n(P.f[RECON_F_CG_Q], d, qv, cnt);
+        });
+        acc[0] = (double)accT;
         block_sum<1>(acc, red);
         double tot[1];
-        if (item_reduce<1>(L, w, it.slice, acc, tot)) {
+        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
             so.pq = tot[0];
             so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
@@ -591,28 +810,37 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_matvec(ItemList L, const
 template <typename T>
 __global__ void __launch_bounds__(kStencilThreads) k_cg_update(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                                SliceState* S, Ptrs<T> P, int par, int* pending) {
+    constexpr int VN = TileDim<T>::VN;
     __shared__ double red[32];
+    __shared__ SliceGeom s_g;
     const T* p = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
-        const SliceState st = S[it.slice];
-        if (cg_skip(st)) continue;
-        const SliceGeom g = G[it.slice];
-        account(P.acct, KF_CG_UPDATE, tile_px(g, it) * 6 * (long long)sizeof(T));
-        const T al = T(st.alpha);
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        account(P.acct, KF_CG_UPDATE, tile_px<T>(g, it) * 6 * (long long)sizeof(T));
+        const T al = T(__ldg(&sp->alpha));
         double acc[1] = {0.0};
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int x = it.a + (q & (kTile - 1)), y = it.b + q / kTile;
-            if (x >= g.nx || y >= g.ny) continue;
-            const long long d = g.off + (long long)y * g.pitch + x;
-            P.f[RECON_F_Z][d] += al * p[d];
-            const T r = P.f[RECON_F_CG_R][d] - al * P.f[RECON_F_CG_Q][d];
-            P.f[RECON_F_CG_R][d] = r;
-            acc[0] += (double)r * (double)r;
-        }
+        T accT = T(0);
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
+            Pack<T> z = ldv_n(P.f[RECON_F_Z], d, cnt), r = ldv_n(P.f[RECON_F_CG_R], d, cnt);
+            const Pack<T> pv = ldv_n(p, d, cnt), q = ldv_n(P.f[RECON_F_CG_Q], d, cnt);
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                z.v[e] += al * pv.v[e];
+                r.v[e] -= al * q.v[e];
+                if (e < cnt) accT = fma(r.v[e], r.v[e], accT);
+            }
+            stv_n(P.f[RECON_F_Z], d, z, cnt);
+            stv_n(P.f[RECON_F_CG_R], d, r, cnt);
+        });
+        acc[0] = (double)accT;
         block_sum<1>(acc, red);
         double tot[1];
-        if (item_reduce<1>(L, w, it.slice, acc, tot)) {
+        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
             const SliceConst& c = C[it.slice];
             so.rr = tot[0];
@@ -676,8 +904,8 @@ __global__ void k_extract(ItemList L, const SliceGeom* G, Ptrs<T> P, float* Z, f
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
         const SliceGeom g = G[it.slice];
-        for (int q = threadIdx.x; q < kTile * kTile; q += blockDim.x) {
-            const int x = it.a + (q & (kTile - 1)), y = it.b + q / kTile;
+        for (int q = threadIdx.x; q < kTileW * TileH<T>::v; q += blockDim.x) {
+            const int x = it.a + (q & (kTileW - 1)), y = it.b + q / kTileW;
             if (x >= g.nx || y >= g.ny) continue;
             const long long d = g.off + (long long)y * g.pitch + x;
             const long long e = g.ext_off + (long long)y * g.nx + x;
@@ -704,6 +932,7 @@ Ptrs<T> ptrs(Ctx& c) {
     for (int i = 0; i < kNumFields; ++i) p.f[i] = static_cast<T*>(c.field[i]);
     for (int i = 0; i < kNumSpectra; ++i) p.s[i] = static_cast<cplx<T>*>(c.spec[i]);
     p.acct = c.d_acct;
+    p.sym = static_cast<const T*>(c.d_sym);
     return p;
 }
 
@@ -714,38 +943,49 @@ int grid_for(const Ctx& c, int work) {
 
 template <typename T>
 int fft_smem_bytes(const Ctx& c) {
-    const int buf = kRowBudget + 64;
-    const int tw = c.max_nx > c.max_ny ? c.max_nx : c.max_ny;
-    return (2 * buf + tw) * (int)sizeof(cplx<T>);
+    int slots = 0;
+    for (const SliceGeom& g : c.sg) {
+        const int r = g.rows_per_item * padded_len(g.nx);
+        const int q = g.cols_per_item * (padded_len(g.ny) | 1);
+        slots = r > slots ? r : slots;
+        slots = q > slots ? q : slots;
+    }
+    return 2 * slots * (int)sizeof(cplx<T>);
+}
+
+template <typename T>
+int fft_half_slots(const Ctx& c) {
+    return fft_smem_bytes<T>(c) / (2 * (int)sizeof(cplx<T>));
 }
 
 template <typename T>
 int fft_solve(Ctx& c, const FftJobs& J, int mode) {
     const Ptrs<T> P = ptrs<T>(c);
     const int smem = fft_smem_bytes<T>(c);
-    const int buf = kRowBudget + 64;
+    const cplx<T>* buf = static_cast<const cplx<T>*>(c.d_tw);
+    const int half = fft_half_slots<T>(c);
     if (mode == 0) {
         FamTimer t(c, KF_ROWS_FWD);
         k_rows_fwd<T, 0><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf);
+                                                                                       c.d_state, P, J, buf, half);
     } else {
         FamTimer t(c, KF_ROWS_FWD_PRE);
         k_rows_fwd<T, 1><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf);
+                                                                                       c.d_state, P, J, buf, half);
     }
     {
         FamTimer t(c, mode ? KF_COLS_PRE : KF_COLS);
         k_cols<T><<<grid_for(c, c.cols.n * J.n), kFftThreads, smem, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
-                                                                               c.d_state, P, J, buf);
+                                                                               c.d_state, P, J, buf, half);
     }
     if (mode == 0) {
         FamTimer t(c, KF_ROWS_INV);
         k_rows_inv<T, 0><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf);
+                                                                                       c.d_state, P, J, buf, half);
     } else {
         FamTimer t(c, KF_ROWS_INV_PRE);
         k_rows_inv<T, 1><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf);
+                                                                                       c.d_state, P, J, buf, half);
     }
     c.launches += 3;
     RECON_CUDA(cudaGetLastError());
@@ -819,9 +1059,11 @@ template <typename T>
 int op_solve_z(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
     RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream));
-    FamTimer t0(c, KF_CG_INIT);
-    k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
-                                                                          c.d_state, P, c.d_cg_pending);
+    {
+        FamTimer t0(c, KF_CG_INIT);
+        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+                                                                              c.d_state, P, c.d_cg_pending);
+    }
     c.launches += 1;
     const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 3);
     int rc = fft_solve<T>(c, pre, 1);
@@ -978,25 +1220,69 @@ int solver_setup(Ctx& c) {
     c.tiles.h_lo.assign(c.n, 0); c.tiles.h_cnt.assign(c.n, 0);
     c.rows.h_lo.assign(c.n, 0); c.rows.h_cnt.assign(c.n, 0);
     c.cols.h_lo.assign(c.n, 0); c.cols.h_cnt.assign(c.n, 0);
+    const int budget = c.precision == 1 ? FftBudget<float>::E : FftBudget<double>::E;
     for (int s = 0; s < c.n; ++s) {
-        const SliceGeom& g = c.sg[s];
+        SliceGeom& g = c.sg[s];
         c.tiles.h_lo[s] = (int)c.tiles.h_items.size();
-        for (int ty = 0; ty < g.ny; ty += kTile)
-            for (int tx = 0; tx < g.nx; tx += kTile) c.tiles.h_items.push_back(Item{s, tx, ty, 0});
+        const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
+        for (int ty = 0; ty < g.ny; ty += th)
+            for (int tx = 0; tx < g.nx; tx += kTileW) c.tiles.h_items.push_back(Item{s, tx, ty, 0});
         c.tiles.h_cnt[s] = (int)c.tiles.h_items.size() - c.tiles.h_lo[s];
         c.rows.h_lo[s] = (int)c.rows.h_items.size();
         const int npairs = (g.ny + 1) / 2;
-        int per = kRowBudget / g.nx;
+        int per = budget / g.nx;
         if (per < 1) per = 1;
+        if (per > npairs) per = npairs;
+        g.rows_per_item = per;
         for (int p0 = 0; p0 < npairs; p0 += per)
             c.rows.h_items.push_back(Item{s, p0, (npairs - p0 < per ? npairs - p0 : per), 0});
         c.rows.h_cnt[s] = (int)c.rows.h_items.size() - c.rows.h_lo[s];
         c.cols.h_lo[s] = (int)c.cols.h_items.size();
-        int pc = kRowBudget / g.ny;
+        int pc = budget / g.ny;
         if (pc > 16) pc = 16;
         if (pc < 1) pc = 1;
+        if (pc > g.nh) pc = g.nh;
+        g.cols_per_item = pc;
         for (int c0 = 0; c0 < g.nh; c0 += pc) c.cols.h_items.push_back(Item{s, c0, (g.nh - c0 < pc ? g.nh - c0 : pc), 0});
         c.cols.h_cnt[s] = (int)c.cols.h_items.size() - c.cols.h_lo[s];
+        g.plan_x = fft_plan_code(g.nx);
+        g.plan_y = fft_plan_code(g.ny);
+    }
+    // twiddle tables exp(-2 pi i t / N), one per distinct N
+    {
+        std::vector<double> tw, sym;
+        std::vector<std::pair<int, std::pair<long long, long long>>> have;
+        auto table = [&](int n) -> std::pair<long long, long long> {
+            for (auto& h : have)
+                if (h.first == n) return h.second;
+            const long long off = (long long)tw.size() / 2, soff = (long long)sym.size();
+            for (int t = 0; t < n; ++t) {
+                const double a = 2.0 * M_PI * (double)t / (double)n;
+                tw.push_back(std::cos(a));
+                tw.push_back(-std::sin(a));
+                const double sn = std::sin(M_PI * (double)t / (double)n);
+                sym.push_back(4.0 * sn * sn);
+            }
+            have.push_back({n, {off, soff}});
+            return {off, soff};
+        };
+        for (SliceGeom& g : c.sg) {
+            const auto tx = table(g.nx), ty = table(g.ny);
+            g.twx = tx.first;
+            g.symx = tx.second;
+            g.twy = ty.first;
+            g.symy = ty.second;
+        }
+        if ((rc = alloc_dev(c, &c.d_tw, c.elem * tw.size()))) return rc;
+        if ((rc = alloc_dev(c, &c.d_sym, c.elem * sym.size()))) return rc;
+        if (c.precision == 1) {
+            std::vector<float> f(tw.begin(), tw.end()), fs(sym.begin(), sym.end());
+            RECON_CUDA(cudaMemcpy(c.d_tw, f.data(), sizeof(float) * f.size(), cudaMemcpyHostToDevice));
+            RECON_CUDA(cudaMemcpy(c.d_sym, fs.data(), sizeof(float) * fs.size(), cudaMemcpyHostToDevice));
+        } else {
+            RECON_CUDA(cudaMemcpy(c.d_tw, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice));
+            RECON_CUDA(cudaMemcpy(c.d_sym, sym.data(), sizeof(double) * sym.size(), cudaMemcpyHostToDevice));
+        }
     }
     if ((rc = upload_list(c, c.tiles)) || (rc = upload_list(c, c.rows)) || (rc = upload_list(c, c.cols))) return rc;
     // constants
