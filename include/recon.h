@@ -92,6 +92,8 @@ typedef struct recon_params {
     double cg_tol;                   /* relative residual of the Z^m PCG */
     double z_clip_max;               /* initial Z^m clipped to Z <= z_clip_max */
     double rho_air;                  /* initial Z^m set to water where rho_e < rho_air */
+    int32_t pcg_kernel;              /* 0: batched kernels; 1: cluster-resident Z^m solve where a slice fits */
+    int32_t reserved;
 } recon_params;
 
 /* Per-slice statistics of the last iteration run by recon_step.  The
@@ -114,7 +116,7 @@ typedef struct recon_ctx recon_ctx;
 /* Fill p with the library defaults: mono 60/90 keV arms, E1/E2 = 50/200 keV,
  * bone-like (13, 1.7) and water (7.45, 1.0) bases, lambda 1e-2,
  * beta0 = 2 lambda, beta_max 1e5, tau 1, iters 50, precision 1, order 0,
- * cg_max_iters 64, cg_tol 1e-6, z_clip_max 30, rho_air 0.1. */
+ * cg_max_iters 64, cg_tol 1e-6, z_clip_max 30, rho_air 0.1, pcg_kernel 0. */
 int recon_default_params(recon_params* p);
 
 /* Create a handle for one slice (recon_init) or a batch of n slices of
@@ -240,8 +242,9 @@ int64_t recon_kernel_launches(recon_ctx* ctx);
 /* Kernel families of the solver, for recon_profile*: 0 threshold + rhs,
  * 1 FFT rows forward, 2 FFT columns (spectral divide), 3 FFT rows inverse,
  * 4 synthesis, 5 PCG start, 6 PCG matvec, 7 PCG update, 8-10 the three FFT
- * passes of the PCG preconditioner, 11 other. */
-#define RECON_KF_COUNT 12
+ * passes of the PCG preconditioner, 11 the cluster-resident PCG (whole Z^m
+ * solve of a slice per thread-block cluster), 12 other. */
+#define RECON_KF_COUNT 13
 
 /* Time the launches of the kernel families whose bit is set in mask with
  * CUDA events on the handle's stream (0 = off).  Algorithmic bytes and launch

@@ -26,7 +26,8 @@ bool seven_smooth(int n) {
 int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
-        (p.order != 0 && p.order != 1) || !(p.e1_kev > 0) || !(p.e2_kev > 0) || p.e1_kev == p.e2_kev) {
+        (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 1) || !(p.e1_kev > 0) ||
+        !(p.e2_kev > 0) || p.e1_kev == p.e2_kev) {
         set_error("invalid recon_params");
         return RECON_EINVAL;
     }
@@ -117,8 +118,9 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
         int rc = check_geometry(geoms[s]);
         if (!rc) rc = check_params(params[s]);
         if (rc) return rc;
-        if (params[s].precision != params[0].precision || params[s].order != params[0].order) {
-            set_error("all slices of a batch need the same precision and order");
+        if (params[s].precision != params[0].precision || params[s].order != params[0].order ||
+            params[s].pcg_kernel != params[0].pcg_kernel) {
+            set_error("all slices of a batch need the same precision, order and pcg_kernel");
             return RECON_EINVAL;
         }
         if ((geoms[s].n_views > 0) != (geoms[0].n_views > 0)) {
@@ -135,6 +137,7 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
     c.geo.assign(geoms, geoms + n);
     c.prm.assign(params, params + n);
     c.sino_input = geoms[0].n_views > 0;
+    c.use_cluster = params[0].pcg_kernel == 1;
     int rc = solver_setup(c);
     if (!rc && c.sino_input) {
         c.sino_off.resize(n);
@@ -418,9 +421,10 @@ int recon_profile_read(recon_ctx* h, double* ms, int64_t* launches, uint64_t* by
 }
 
 const char* recon_profile_name(int32_t f) {
-    static const char* names[KF_COUNT] = {"thr_rhs",     "fft_rows_fwd",  "fft_cols",     "fft_rows_inv",
-                                          "synth",       "pcg_start",     "pcg_matvec",   "pcg_update",
-                                          "pcg_pre_rows_fwd", "pcg_pre_cols", "pcg_pre_rows_inv", "other"};
+    static const char* names[KF_COUNT] = {"thr_rhs",          "fft_rows_fwd", "fft_cols",         "fft_rows_inv",
+                                          "synth",            "pcg_start",    "pcg_matvec",       "pcg_update",
+                                          "pcg_pre_rows_fwd", "pcg_pre_cols", "pcg_pre_rows_inv", "pcg_cluster",
+                                          "other"};
     return (f >= 0 && f < KF_COUNT) ? names[f] : "?";
 }
 

@@ -34,6 +34,7 @@ struct SliceGeom {
     long long twx, twy;        // offsets of the twiddle tables exp(-2 pi i t/N) in the twiddle pool
     long long symx, symy;      // offsets of the tables 4 sin^2(pi t/N) in the symbol pool
     int rows_per_item, cols_per_item;
+    int cluster;               // 1: the Z^m solve of this slice runs in the cluster kernel
 };
 
 // Model constants and parameters of one slice (FP64, read-only on device).
@@ -91,6 +92,7 @@ enum KFam {
     KF_ROWS_FWD_PRE,
     KF_COLS_PRE,
     KF_ROWS_INV_PRE,
+    KF_PCG_CLUSTER,
     KF_OTHER,
     KF_COUNT
 };
@@ -112,6 +114,14 @@ template <>
 struct FftBudget<double> {
     static constexpr int E = 2048;
 };
+
+// Copy a small struct into shared memory (whole block), no sync.
+template <typename S>
+__device__ __forceinline__ void stage_struct(S* dst, const S* src) {
+    static_assert(sizeof(S) % 4 == 0, "");
+    for (int i = threadIdx.x; i < (int)(sizeof(S) / 4); i += blockDim.x)
+        reinterpret_cast<int*>(dst)[i] = __ldg(reinterpret_cast<const int*>(src) + i);
+}
 
 __device__ __forceinline__ int wrap(int i, int n) {
     i %= n;

@@ -65,6 +65,14 @@ struct Ctx {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     long long fam_launches[KF_COUNT] = {};
 
+    // cluster-resident PCG
+    std::vector<int> cl_slices;
+    int* d_cl_slices = nullptr;
+    int* d_cl_queue = nullptr;
+    int cl_smem_x = 0, cl_smem_s = 0, cl_max_clusters = 0;
+    size_t cl_bytes = 0;
+    bool use_cluster = true;
+
     DevItemList tiles, rows, cols;
     bool has_data = false;
     int cg_parity = 0;

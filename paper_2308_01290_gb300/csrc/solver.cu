@@ -20,6 +20,7 @@
 
 #include "ctx.h"
 #include "fft.cuh"
+#include "pcg_cluster.h"
 
 namespace recon {
 
@@ -180,13 +181,6 @@ struct PVals {
     Pack<T> p[NM];
 };
 
-// Copy a small struct into shared memory (whole block), no sync.
-template <typename S>
-__device__ __forceinline__ void stage_struct(S* dst, const S* src) {
-    static_assert(sizeof(S) % 4 == 0, "");
-    for (int i = threadIdx.x; i < (int)(sizeof(S) / 4); i += blockDim.x)
-        reinterpret_cast<int*>(dst)[i] = __ldg(reinterpret_cast<const int*>(src) + i);
-}
 
 // Load NM maps of one tile with halo.  vect(d) gives the NM 16-byte packs at
 // element offset d (16-byte aligned), scal(d) the NM scalars at d.
@@ -704,7 +698,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const S
     const T* z = P.f[RECON_F_Z];
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
-        if (!__ldg(&S[it.slice].active)) continue;
+        if (!__ldg(&S[it.slice].active) || __ldg(&G[it.slice].cluster)) continue;
         stage_struct(&s_g, G + it.slice);
         __syncthreads();
         const SliceGeom& g = s_g;
@@ -1058,6 +1052,11 @@ int op_synth(Ctx& c) {
 template <typename T>
 int op_solve_z(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
+    int rc;
+    if (!c.cl_slices.empty()) {
+        if ((rc = pcg_cluster_run(c))) return rc;
+        if ((int)c.cl_slices.size() == c.n) return RECON_OK;
+    }
     RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream));
     {
         FamTimer t0(c, KF_CG_INIT);
@@ -1066,7 +1065,7 @@ int op_solve_z(Ctx& c) {
     }
     c.launches += 1;
     const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 3);
-    int rc = fft_solve<T>(c, pre, 1);
+    rc = fft_solve<T>(c, pre, 1);
     if (rc) return rc;
     int cap = 0;
     for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
@@ -1321,6 +1320,8 @@ int solver_setup(Ctx& c) {
     if ((rc = alloc_dev(c, (void**)&c.d_acct, sizeof(unsigned long long) * KF_COUNT))) return rc;
     RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
     RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, sizeof(int)));
+    if ((rc = pcg_cluster_setup(c))) return rc;
+    RECON_CUDA(cudaMemcpy(c.d_geom, c.sg.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
     if (c.precision == 1) return set_fft_smem<float>(c);
     return set_fft_smem<double>(c);
 }

@@ -43,7 +43,8 @@ class Params(C.Structure):
                 ("basis_z", C.c_double * 2), ("basis_rhoe", C.c_double * 2), ("lambda_", C.c_double),
                 ("beta0", C.c_double), ("beta_max", C.c_double), ("tau", C.c_double), ("kappa", C.c_double),
                 ("iters", C.c_int32), ("precision", C.c_int32), ("order", C.c_int32), ("cg_max_iters", C.c_int32),
-                ("cg_tol", C.c_double), ("z_clip_max", C.c_double), ("rho_air", C.c_double)]
+                ("cg_tol", C.c_double), ("z_clip_max", C.c_double), ("rho_air", C.c_double),
+                ("pcg_kernel", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -114,7 +115,7 @@ EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_
            "recon_backproject", "recon_fbp", "recon_simulate", "recon_model_tables", "recon_debug_field",
            "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches",
            "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name")
-KF_COUNT = 12
+KF_COUNT = 13
 
 
 def _check(rc, what):

@@ -170,3 +170,50 @@ def test_invalid_sizes_rejected(rc):
     s = rc.Solver(rc.geometry(8, 8), p)
     with pytest.raises(rc.ReconError):
         s.step(1)      # before set_data
+
+
+@pytest.mark.parametrize("shape", [(128, 128), (96, 160), (100, 70)])
+def test_cluster_pcg_matches_batched_pcg(rc, shape):
+    """The cluster-resident Z^m solve (one slice per thread-block cluster) and
+    the batched kernels solve the same normal equations: both reach the PCG
+    tolerance and agree with the oracle's exact solution."""
+    from oracle import alg1
+    nx, ny = shape
+    acq = ph.acquisition("small")
+    P = ph.small_phantom(21, n=max(nx, ny))
+    Z, rho = P["Z"][:ny, :nx], P["rhoe"][:ny, :nx]
+    L = (model.mu_mm(rho, Z, 60.0) + 4e-4 * ph.normal_field((ny, nx), 22)).astype(np.float32)
+    H = (model.mu_mm(rho, Z, 90.0) + 4e-4 * ph.normal_field((ny, nx), 23)).astype(np.float32)
+    out = {}
+    for path in (1, 0):
+        p = rc.default_params(low=acq.low, high=acq.high, iters=50, pcg_kernel=path)
+        s = rc.Solver(rc.geometry(nx, ny), p)
+        s.set_data(L, H)
+        s.step(3)
+        s.op("THRESH_RHS")
+        s.op("SOLVE_F")
+        s.op("SYNTH")
+        a2, rz, bt = s.read("A2"), s.read("RHS_Z"), s.scalars()["beta_t"]
+        s.op("SOLVE_Z")
+        z = s.read("Z")
+        res = np.linalg.norm(a2 * z + bt * alg1.laplacian(z) - rz) / np.linalg.norm(rz)
+        assert res < 3e-5, (path, res)
+        zx = alg1.z_solve(a2, rz, bt)
+        assert np.abs(z - zx).max() <= 1e-3 * np.abs(zx).max(), path
+        out[path] = z
+    assert np.abs(out[0] - out[1]).max() <= 2e-3 * np.abs(out[1]).max()
+
+
+def test_cluster_full_solve_matches_oracle(rc, small_case):
+    """Whole 128^2 solve with the cluster-resident Z^m solve (the default run
+    uses the batched kernels): within the final-map tolerance."""
+    c = small_case
+    acq = c["acq"]
+    p = rc.default_params(low=acq.low, high=acq.high, iters=acq.iters, pcg_kernel=1)
+    s = rc.Solver(rc.geometry(acq.nx, acq.ny), p)
+    s.set_data(c["muL"].astype(np.float32), c["muH"].astype(np.float32))
+    s.step(acq.iters)
+    Z, rho, _, _ = [x[0] for x in s.get_host()]
+    body = c["P"]["rhoe"] >= 0.1
+    r = report("cluster-pcg", Z, rho, c["ref"], body)
+    assert r["mean_dZ"] <= 0.01 and r["mean_drho"] <= 1e-3
