@@ -172,6 +172,24 @@ int recon_backproject(const recon_geometry* geom, int32_t n, const float* sino, 
 /* Flat-detector fan-beam FBP of a full scan (cosine weight, Ram-Lak ramp,
  * 1/U^2 weighted pixel-driven backprojection). */
 int recon_fbp(const recon_geometry* geom, int32_t n, const float* sino, float* img, void* stream);
+/* recon_fbp without any device allocation, for callers that cannot allocate
+ * device memory when they call: for example a real-time reconstruction loop
+ * that forbids allocation once it has started, or a service that reserves all
+ * of its device memory up front and hands the library only its own buffers.
+ * (The paper has no counterpart: this is an interface of the library.)
+ * Same arguments, kernels and result as recon_fbp.  The filtered sinograms
+ * go to a fixed scratch array inside the library of RECON_FBP_NOALLOC_MAX
+ * floats (8 MiB), which every GPU that loads the library holds until the
+ * process exits; calls with n * n_views * n_bins above that return
+ * RECON_EINVAL.  The first call on a device looks up the array's device
+ * address (with that device current), so make that first call before any
+ * stream capture.  Every call shares the one array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Each call overwrites every scratch value it
+ * reads, so nothing has to be cleared between calls. */
+#define RECON_FBP_NOALLOC_MAX (2 * 1024 * 1024)
+int recon_fbp_noalloc(const recon_geometry* geom, int32_t n, const float* sino, float* img, void* stream);
+
 /* Synthetic scan: -log sinograms of both arms of params for truth maps Z and
  * rho_e (images, device).  noise: NULL (noiseless) or 2 * n * n_views *
  * n_bins standard normal deviates (low arm first) used as the Gaussian

@@ -14,6 +14,7 @@
 // Per-ray set-up is FP64; the marching is FP32 with the fractional index
 // evaluated as start + i * slope from FP64-rounded start and slope.
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "ctx.h"
@@ -337,6 +338,46 @@ extern "C" int recon_fbp(const recon_geometry* geom, int32_t n, const float* sin
     int rc = ct_fbp(*geom, n, sino, img, scratch, (cudaStream_t)stream, nullptr);
     cudaFreeAsync(scratch, (cudaStream_t)stream);
     return rc;
+}
+
+// Scratch of recon_fbp_noalloc: the filtered sinograms of one call.  In host
+// code this name stands for the symbol, not a device address; the address is
+// looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) float g_fbp_noalloc_scratch[RECON_FBP_NOALLOC_MAX];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+}  // namespace
+
+extern "C" int recon_fbp_noalloc(const recon_geometry* geom, int32_t n, const float* sino, float* img, void* stream) {
+    if (!geom || n < 1 || !img || !sino) {
+        set_error("recon_fbp_noalloc: bad arguments");
+        return RECON_EINVAL;
+    }
+    const long long need = (long long)n * geom->n_views * geom->n_bins;
+    if (geom->n_views < 1 || geom->n_bins < 1 || need > (long long)RECON_FBP_NOALLOC_MAX) {
+        set_error("recon_fbp_noalloc: n * n_views * n_bins exceeds RECON_FBP_NOALLOC_MAX floats of scratch");
+        return RECON_EINVAL;
+    }
+    int dev = 0;
+    RECON_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("recon_fbp_noalloc: device index out of range");
+        return RECON_EINVAL;
+    }
+    float* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            RECON_CUDA(cudaGetSymbolAddress(&p, g_fbp_noalloc_scratch));
+            g_noalloc_ptr[dev] = static_cast<float*>(p);
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    return ct_fbp(*geom, n, sino, img, scratch, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" int recon_simulate(const recon_geometry* geom, const recon_params* params, int32_t n, const float* Z,

@@ -79,6 +79,7 @@ def _load():
         "recon_project": (I, [P(Geometry), C.c_int32, VP, VP, VP]),
         "recon_backproject": (I, [P(Geometry), C.c_int32, VP, VP, VP]),
         "recon_fbp": (I, [P(Geometry), C.c_int32, VP, VP, VP]),
+        "recon_fbp_noalloc": (I, [P(Geometry), C.c_int32, VP, VP, VP]),
         "recon_simulate": (I, [P(Geometry), P(Params), C.c_int32, VP, VP, VP, D, VP, VP, VP]),
         "recon_model_tables": (I, [P(Params), P(D)]),
         "recon_debug_field": (I, [VP, C.c_int32, C.c_int32, P(VP), P(C.c_int32), P(C.c_int32)]),
@@ -112,7 +113,7 @@ def _check_layout():
 _check_layout()
 EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_data", "recon_step", "recon_get",
            "recon_sync", "recon_destroy", "recon_solve", "recon_strerror", "recon_last_error", "recon_project",
-           "recon_backproject", "recon_fbp", "recon_simulate", "recon_model_tables", "recon_debug_field",
+           "recon_backproject", "recon_fbp", "recon_fbp_noalloc", "recon_simulate", "recon_model_tables", "recon_debug_field",
            "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches",
            "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name")
 KF_COUNT = 13
@@ -319,6 +320,14 @@ def backproject(geom, n, sino, img, stream=None):
 
 def fbp(geom, n, sino, img, stream=None):
     _check(lib.recon_fbp(C.byref(geom), int(n), _ptr(sino), _ptr(img), stream), "recon_fbp")
+
+
+FBP_NOALLOC_MAX = 2 * 1024 * 1024
+
+
+def fbp_noalloc(geom, n, sino, img, stream=None):
+    """recon_fbp_noalloc: FBP with the library's fixed scratch (no allocation)."""
+    _check(lib.recon_fbp_noalloc(C.byref(geom), int(n), _ptr(sino), _ptr(img), stream), "recon_fbp_noalloc")
 
 
 def simulate(geom, params, n, Z, rhoe, noise, i0, sino_low, sino_high, stream=None):
