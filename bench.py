@@ -39,7 +39,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["mine", "reference"], default="mine")
-    ap.add_argument("--workload", choices=["volume", "clinical", "uneven", "small"], default="volume")
+    ap.add_argument("--workload", choices=["volume", "clinical", "uneven", "small", "serving"], default="volume")
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (slices/s)")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving leg of the default line")
     ap.add_argument("--slices", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--precision", type=int, default=1)
@@ -148,6 +150,69 @@ def read_traffic(kernel, alg_bytes_per_launch):
         return None
     # the capture's traffic scaled to this launch's algorithmic size
     return e["dram_bytes_per_launch"] * alg_bytes_per_launch / e["algorithmic_bytes_per_launch"]
+
+
+# ---------------------------------------------------------------------------
+# serving workload: Poisson arrivals into the continuous-batching engine
+# ---------------------------------------------------------------------------
+
+def serving_run(rc, torch, rate, n_req, seed, budget_bytes=150e9, steps_per_poll=4):
+    """Requests of 256^2..512^2 slices (own seed, I0 log-uniform in [2e4, 2e5],
+    50..150 iterations) arrive as a Poisson process of ``rate`` slices/s;
+    returns latency percentiles (arrival -> result on the host) and
+    throughput."""
+    from synthetic import phantoms as ph
+    rng = np.random.default_rng(seed)
+    sizes = ph.uneven_sizes(seed, n_req)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+    reqs = []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    for k, n in enumerate(sizes):
+        acq = ph.acquisition("uneven", n=n, i0=float(np.exp(rng.uniform(np.log(2e4), np.log(2e5)))),
+                             iters=int(rng.integers(50, 151)))
+        P = ph.small_phantom(seed + 1 + k, n=n)
+        g = rc.geometry_from_acq(acq)
+        p = rc.default_params(low=acq.low, high=acq.high, iters=acq.iters)
+        nr = acq.n_views * acq.n_bins
+        lo = torch.empty(nr, device="cuda")
+        hi = torch.empty(nr, device="cuda")
+        rc.simulate(g, p, 1, torch.from_numpy(P["Z"].astype(np.float32)).cuda(),
+                    torch.from_numpy(P["rhoe"].astype(np.float32)).cuda(),
+                    torch.randn(2 * nr, device="cuda", generator=gen), acq.i0, lo, hi)
+        reqs.append((g, p, lo.cpu().numpy(), hi.cpu().numpy(), acq.iters))
+    torch.cuda.synchronize()
+    srv = rc.Server(max_slots=n_req, max_nx=512, max_ny=512, max_views=720, max_bins=736,
+                    hbm_budget_bytes=budget_bytes)
+    t0 = time.perf_counter()
+    nxt = 0
+    tickets = {}
+    lat = []
+    done = 0
+    iters_done = 0
+    while done < n_req:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now:
+            g, p, lo, hi, it = reqs[nxt]
+            tickets[srv.submit(g, p, lo, hi)] = (nxt, it)
+            nxt += 1
+        active = srv.step(steps_per_poll)
+        t_now = time.perf_counter() - t0
+        for t in list(tickets):
+            r = srv.poll(t)
+            if r is not None:
+                k, it = tickets.pop(t)
+                lat.append(1000.0 * (t_now - arrivals[k]))
+                iters_done += it
+                done += 1
+        if active == 0 and not tickets and nxt < n_req:
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+    total = time.perf_counter() - t0
+    srv.close()
+    lat = np.array(lat)
+    return dict(rate_slices_per_s=rate, requests=n_req, p50_ms=float(np.percentile(lat, 50)),
+                p99_ms=float(np.percentile(lat, 99)), throughput_slice_iters_per_s=iters_done / total,
+                wall_s=total, budget_gb=budget_bytes / 1e9)
 
 
 # ---------------------------------------------------------------------------
@@ -288,6 +353,18 @@ def main():
     build_lib.build()
     from paper_2308_01290_gb300 import recon as rc
 
+    if args.workload == "serving":
+        r = serving_run(rc, torch, args.rate, args.slices or 64, 9000 + rank)
+        if rank == 0:
+            line = dict(metric=METRIC, value=r["throughput_slice_iters_per_s"], unit="slice-iters/s", n_gpus=world,
+                        steps=1, warmup=0, ms_per_step=1000.0 * r["wall_s"], higher_is_better=True, scaling="weak",
+                        vs_baseline=None, dtype="f32", data="synthetic",
+                        config=dict(workload=f"serving: Poisson arrivals at {args.rate:g} slices/s, 256^2..512^2, "
+                                             "I0 2e4..2e5, 50..150 iterations, 150 GB budget",
+                                    requests=r["requests"]),
+                        latency_ms=dict(p50=r["p50_ms"], p99=r["p99_ms"]))
+            print(json.dumps(line), flush=True)
+        return 0
     slices, iters, name = workload(args, rank)
     sino_lo, sino_hi = make_scans(rc, torch, slices, seed=4242 + rank)
     geoms = [rc.geometry_from_acq(acq) for _, _, acq in slices]
@@ -411,6 +488,8 @@ def main():
                                    sample=f"one {g0.nx}x{g0.ny} slice, {it64} iterations, precision FP64, "
                                           "one slice per launch sequence")
         s64.close()
+    if rank == 0 and not args.no_serving and args.workload == "volume":
+        extra["serving"] = serving_run(rc, torch, args.rate, 48, 9000)
     cpu = None
     if rank == 0 and not args.no_cpu:
         r = oracle_sample(slices, 3 if slices[0][0].shape[1] >= 512 else 10)

@@ -161,6 +161,57 @@ int recon_solve(const float* lowE, const float* highE, const recon_geometry* geo
 const char* recon_strerror(int code);
 const char* recon_last_error(void);
 
+/* ---- serving: continuous batching of independent slice solves ----
+ *
+ * A server holds max_slots solve slots on the device, each sized for images
+ * up to max_nx x max_ny (and sinograms up to max_views x max_bins).
+ * recon_submit queues a request (its host inputs are copied, so the caller's
+ * buffers are free on return).  recon_server_step admits queued requests into
+ * free slots while the summed device footprint of the in-flight solves stays
+ * within hbm_budget_bytes, loads them (FBP for sinogram requests), runs
+ * n_iters iterations of Algorithm 1 on every active slot in the same kernel
+ * launches (each slot at its own iteration count and parameters), and
+ * retires slots that have done their params.iters iterations, copying Z and
+ * rho_e to host memory.  recon_poll hands a finished result over.  A slot's
+ * result is bit-identical to the same request solved alone.  Not
+ * thread-safe: one thread drives a server. */
+typedef struct recon_server recon_server;
+
+typedef struct recon_server_config {
+    int32_t max_slots;          /* concurrent solves */
+    int32_t max_nx, max_ny;     /* largest image a slot holds */
+    int32_t max_views, max_bins;/* largest sinogram a slot holds (0: image requests only) */
+    int32_t precision;          /* as recon_params.precision; every request must match */
+    double hbm_budget_bytes;    /* admission budget of the in-flight solves; <= 0: slots only */
+} recon_server_config;
+
+typedef struct recon_request {
+    recon_geometry geom;        /* n_views = 0: images; else -log sinograms */
+    recon_params params;
+    const float* low;           /* host, copied by recon_submit */
+    const float* high;
+} recon_request;
+
+typedef struct recon_result {
+    int32_t status;             /* RECON_OK or the error of the solve */
+    int32_t iters;              /* iterations run */
+    double queue_ms;            /* submit -> admitted to a slot */
+    double latency_ms;          /* submit -> result on the host */
+} recon_result;
+
+int recon_server_create(const recon_server_config* cfg, void* stream, recon_server** out);
+/* Errors: EINVAL (size above the slot capacity, precision mismatch,
+ * size not 7-smooth), EBUDGET (footprint alone above the budget). */
+int recon_submit(recon_server* srv, const recon_request* req, uint64_t* ticket);
+/* *n_active (may be NULL): active slots after the step. */
+int recon_server_step(recon_server* srv, int32_t n_iters, int32_t* n_active);
+/* 1 and the result (Z, rho_e host buffers of ny*nx floats, may be NULL) when
+ * done, 0 while queued or running; EINVAL for an unknown ticket. */
+int recon_poll(recon_server* srv, uint64_t ticket, float* Z, float* rhoe, recon_result* res);
+/* out4: queued, active, finished-not-polled, in-flight footprint bytes. */
+int recon_server_stats(recon_server* srv, int64_t* out4);
+void recon_server_destroy(recon_server* srv);
+
 /* ---- fan-beam input stage (n slices of the same geometry, device buffers,
  * queued on stream) ---- */
 

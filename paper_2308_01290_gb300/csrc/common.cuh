@@ -103,6 +103,7 @@ constexpr int kTileHFloat = 32;
 constexpr int kTileHDouble = 16;
 constexpr int kStencilThreads = 256;
 constexpr int kFftThreads = 256;
+constexpr int kFftMinBlocks = 3;   // resident blocks per SM the FFT kernels are compiled for
 // complex elements one FFT block transforms at a time (rows or columns)
 template <typename T>
 struct FftBudget;

@@ -74,6 +74,12 @@ struct Ctx {
     bool use_cluster = true;
 
     DevItemList tiles, rows, cols;
+    DevItemList tmp_tiles;       // per-slot operations of the serving engine
+    std::vector<SliceConst> hconst;
+    // serving mode: every slot laid out at capacity; lists hold the active slots
+    bool server_mode = false;
+    int cap_nx = 0, cap_ny = 0;
+    std::vector<std::pair<int, std::pair<long long, long long>>> tw_index;   // N -> (twiddle, symbol) offsets
     bool has_data = false;
     int cg_parity = 0;
     long long launches = 0;
@@ -90,6 +96,11 @@ int solver_op(Ctx& c, int op);
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int on_device);
 int solver_read_state(Ctx& c, std::vector<SliceState>& out);
 int solver_profile_read(Ctx& c, double* ms, long long* launches, unsigned long long* bytes);
+// serving engine (slots of a capacity-sized handle)
+int solver_configure_slot(Ctx& c, int s, const recon_geometry& g, const recon_params& p);
+int solver_rebuild_lists(Ctx& c, const std::vector<int>& active);
+int solver_init_slots(Ctx& c, const std::vector<int>& slots, const float* lo, const float* hi);
+int solver_extract_slots(Ctx& c, const std::vector<int>& slots, float* Z, float* rhoe);
 
 // Input stage (ct.cu), float device buffers.
 int ct_project(const recon_geometry& g, int n, const float* img, float* sino, cudaStream_t st, long long* launches);

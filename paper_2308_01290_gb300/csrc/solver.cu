@@ -383,7 +383,7 @@ __global__ void k_gs_fix(ItemList L, const SliceGeom* G, const SliceConst* C, co
 // MODE 0: input is a field.  MODE 1: input is D^-1/2-scaled CG residual.
 // Item: rows 2*it.a .. of one slice, it.b pairs; two real rows per complex FFT.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFftThreads) k_rows_fwd(ItemList L, const SliceGeom* G, const SliceState* S,
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_fwd(ItemList L, const SliceGeom* G, const SliceState* S,
                                                            Ptrs<T> P, FftJobs J, const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -406,17 +406,41 @@ __global__ void __launch_bounds__(kFftThreads) k_rows_fwd(ItemList L, const Slic
             rnum = T(sqrt(__ldg(&S[it.slice].abar2) + 4.0 * __ldg(&S[it.slice].beta_t)));
             b4 = T(4.0 * __ldg(&S[it.slice].beta_t));
         }
-        for (int b = 0; b < np; ++b) {
-            const int row = 2 * (pair0 + b);
-            const bool has1 = row + 1 < g.ny;
-            const long long d0 = g.off + (long long)row * g.pitch;
-            for (int n = threadIdx.x; n < N; n += blockDim.x) {
-                T v0 = in[d0 + n], v1 = has1 ? in[d0 + g.pitch + n] : T(0);
-                if (MODE == 1) {
-                    v0 *= dscale(rnum, a2[d0 + n], b4);
-                    if (has1) v1 *= dscale(rnum, a2[d0 + g.pitch + n], b4);
+        {
+            // four elements per thread per round, loads issued before use
+            const DivMod dN(N);
+            const int total_q = np * N;
+            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
+                T v0[4], v1[4], w0[4], w1[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    v0[u] = v1[u] = w0[u] = w1[u] = T(0);
+                    if (q < total_q) {
+                        const int b = dN.div(q), n = q - b * N;
+                        const int row = 2 * (pair0 + b);
+                        const long long d0 = g.off + (long long)row * g.pitch + n;
+                        v0[u] = in[d0];
+                        if (MODE == 1) w0[u] = a2[d0];
+                        if (row + 1 < g.ny) {
+                            v1[u] = in[d0 + g.pitch];
+                            if (MODE == 1) w1[u] = a2[d0 + g.pitch];
+                        }
+                    }
                 }
-                buf[b * ld + pad8(n)] = {v0, v1};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int b = dN.div(q), n = q - b * N;
+                        T a = v0[u], c = v1[u];
+                        if (MODE == 1) {
+                            a *= dscale(rnum, w0[u], b4);
+                            c *= dscale(rnum, w1[u], b4);
+                        }
+                        buf[b * ld + pad8(n)] = {a, c};
+                    }
+                }
             }
         }
         __syncthreads();
@@ -440,7 +464,7 @@ __global__ void __launch_bounds__(kFftThreads) k_rows_fwd(ItemList L, const Slic
 // Item: spectrum columns it.a .. it.a + it.b - 1 of one slice: FFT along y,
 // divide by (c + beta K) n_x n_y, inverse FFT along y.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeom* G, const SliceConst* C,
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                        const SliceState* S, Ptrs<T> P, FftJobs J,
                                                        const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -457,9 +481,28 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeo
         const int N = g.ny, col0 = it.a, nc = it.b, ld = padded_len(N) | 1;
         account(P.acct, kind == 3 ? KF_COLS_PRE : KF_COLS, (long long)nc * N * 4 * (long long)sizeof(T));
         cplx<T>* sp = P.s[J.spec[job]];
-        for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
-            const int y = q / nc, cc = q - y * nc;
-            buf0[cc * ld + pad8(y)] = sp[g.coff + (long long)y * g.cpitch + col0 + cc];
+        {
+            const DivMod dc(nc);
+            const int total_q = nc * N;
+            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
+                cplx<T> v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int y = dc.div(q), cc = q - y * nc;
+                        v[u] = sp[g.coff + (long long)y * g.cpitch + col0 + cc];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int y = dc.div(q), cc = q - y * nc;
+                        buf0[cc * ld + pad8(y)] = v[u];
+                    }
+                }
+            }
         }
         __syncthreads();
         const cplx<T>* tw = twpool + g.twy;
@@ -479,8 +522,9 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeo
         for (int pass = 0; pass < 2; ++pass) {
             buf = fft_batch<T>(buf, buf == buf0 ? buf1 : buf0, N, g.plan_y, nc, ld, tw, pass ? +1 : -1);
             if (pass) break;
+            const DivMod dN(N);
             for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
-                const int cc = q / N, ky = q - cc * N;
+                const int cc = dN.div(q), ky = q - cc * N;
                 // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
                 const T sc = inv_n / (T(cst) + T(bet) * (symx[col0 + cc] + symy[ky]));
                 cplx<T> v = buf[cc * ld + pad8(ky)];
@@ -488,9 +532,12 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeo
             }
             __syncthreads();
         }
-        for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
-            const int y = q / nc, cc = q - y * nc;
-            sp[g.coff + (long long)y * g.cpitch + col0 + cc] = buf[cc * ld + pad8(y)];
+        {
+            const DivMod dc(nc);
+            for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
+                const int y = dc.div(q), cc = q - y * nc;
+                sp[g.coff + (long long)y * g.cpitch + col0 + cc] = buf[cc * ld + pad8(y)];
+            }
         }
         __syncthreads();
     }
@@ -498,7 +545,7 @@ __global__ void __launch_bounds__(kFftThreads) k_cols(ItemList L, const SliceGeo
 
 // MODE 0: write the field.  MODE 1: y = D^-1/2 x into CG_Y and reduce r.y.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFftThreads) k_rows_inv(ItemList L, const SliceGeom* G, SliceState* S, Ptrs<T> P,
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_inv(ItemList L, const SliceGeom* G, SliceState* S, Ptrs<T> P,
                                                            FftJobs J, const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -516,20 +563,37 @@ __global__ void __launch_bounds__(kFftThreads) k_rows_inv(ItemList L, const Slic
         account(P.acct, MODE ? KF_ROWS_INV_PRE : KF_ROWS_INV,
                 (long long)rows * ((MODE ? 3 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
         const cplx<T>* sp = P.s[J.spec[job]];
-        for (int b = 0; b < np; ++b) {
-            const int row = 2 * (pair0 + b);
-            const bool has1 = row + 1 < g.ny;
-            const long long e0 = g.coff + (long long)row * g.cpitch;
-            for (int n = threadIdx.x; n < N; n += blockDim.x) {
-                const bool herm = n >= g.nh;
-                const int k = herm ? N - n : n;
-                cplx<T> A = sp[e0 + k], B = {T(0), T(0)};
-                if (has1) B = sp[e0 + g.cpitch + k];
-                if (herm) {
-                    A.y = -A.y;
-                    B.y = -B.y;
+        {
+            const DivMod dN(N);
+            const int total_q = np * N;
+            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
+                cplx<T> A[4], B[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    A[u] = B[u] = {T(0), T(0)};
+                    if (q < total_q) {
+                        const int b = dN.div(q), n = q - b * N;
+                        const int row = 2 * (pair0 + b);
+                        const int k = n >= g.nh ? N - n : n;
+                        const long long e0 = g.coff + (long long)row * g.cpitch + k;
+                        A[u] = sp[e0];
+                        if (row + 1 < g.ny) B[u] = sp[e0 + g.cpitch];
+                    }
                 }
-                buf[b * ld + pad8(n)] = {A.x - B.y, A.y + B.x};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int b = dN.div(q), n = q - b * N;
+                        cplx<T> a = A[u], c = B[u];
+                        if (n >= g.nh) {   // Hermitian half of each real row
+                            a.y = -a.y;
+                            c.y = -c.y;
+                        }
+                        buf[b * ld + pad8(n)] = {a.x - c.y, a.y + c.x};
+                    }
+                }
             }
         }
         __syncthreads();
@@ -544,24 +608,49 @@ __global__ void __launch_bounds__(kFftThreads) k_rows_inv(ItemList L, const Slic
             rnum = T(sqrt(__ldg(&S[it.slice].abar2) + 4.0 * __ldg(&S[it.slice].beta_t)));
             b4 = T(4.0 * __ldg(&S[it.slice].beta_t));
         }
-        for (int b = 0; b < np; ++b) {
-            const int row = 2 * (pair0 + b);
-            const bool has1 = row + 1 < g.ny;
-            const long long d0 = g.off + (long long)row * g.pitch;
-            for (int n = threadIdx.x; n < N; n += blockDim.x) {
-                const cplx<T> v = res[b * ld + pad8(n)];
-                if (MODE == 0) {
-                    out[d0 + n] = v.x;
-                    if (has1) out[d0 + g.pitch + n] = v.y;
-                } else {
-                    const T y0 = v.x * dscale(rnum, a2[d0 + n], b4);
-                    out[d0 + n] = y0;
-                    accT = fma(y0, r[d0 + n], accT);
-                    if (has1) {
-                        const long long d1 = d0 + g.pitch + n;
-                        const T y1 = v.y * dscale(rnum, a2[d1], b4);
-                        out[d1] = y1;
-                        accT = fma(y1, r[d1], accT);
+        {
+            const DivMod dN(N);
+            const int total_q = np * N;
+            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
+                T wa[4], wb[4], ra[4], rb[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    wa[u] = wb[u] = ra[u] = rb[u] = T(0);
+                    if (MODE == 1 && q < total_q) {
+                        const int b = dN.div(q), n = q - b * N;
+                        const int row = 2 * (pair0 + b);
+                        const long long d0 = g.off + (long long)row * g.pitch + n;
+                        wa[u] = a2[d0];
+                        ra[u] = r[d0];
+                        if (row + 1 < g.ny) {
+                            wb[u] = a2[d0 + g.pitch];
+                            rb[u] = r[d0 + g.pitch];
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int b = dN.div(q), n = q - b * N;
+                        const int row = 2 * (pair0 + b);
+                        const bool has1 = row + 1 < g.ny;
+                        const long long d0 = g.off + (long long)row * g.pitch + n;
+                        const cplx<T> v = res[b * ld + pad8(n)];
+                        if (MODE == 0) {
+                            out[d0] = v.x;
+                            if (has1) out[d0 + g.pitch] = v.y;
+                        } else {
+                            const T y0 = v.x * dscale(rnum, wa[u], b4);
+                            out[d0] = y0;
+                            accT = fma(y0, ra[u], accT);
+                            if (has1) {
+                                const T y1 = v.y * dscale(rnum, wb[u], b4);
+                                out[d0 + g.pitch] = y1;
+                                accT = fma(y1, rb[u], accT);
+                            }
+                        }
                     }
                 }
             }
@@ -986,9 +1075,28 @@ int fft_solve(Ctx& c, const FftJobs& J, int mode) {
     return RECON_OK;
 }
 
+int fft_item_slots(int nx, int ny, int budget);
+
 template <typename T>
 int set_fft_smem(Ctx& c) {
-    const int smem = fft_smem_bytes<T>(c);
+    int smem = fft_smem_bytes<T>(c);
+    if (c.server_mode) {
+        // a slot may later hold any 7-smooth size up to the capacity
+        std::vector<int> sz;
+        const int top = c.cap_nx > c.cap_ny ? c.cap_nx : c.cap_ny;
+        for (int n = 1; n <= top; ++n) {
+            int m = n;
+            for (int f : {2, 3, 5, 7})
+                while (m % f == 0) m /= f;
+            if (m == 1) sz.push_back(n);
+        }
+        for (int nx : sz)
+            for (int ny : sz)
+                if (nx <= c.cap_nx && ny <= c.cap_ny) {
+                    const int b = 2 * fft_item_slots(nx, ny, FftBudget<T>::E) * (int)sizeof(cplx<T>);
+                    smem = b > smem ? b : smem;
+                }
+    }
     RECON_CUDA(cudaFuncSetAttribute(k_rows_fwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     RECON_CUDA(cudaFuncSetAttribute(k_rows_fwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     RECON_CUDA(cudaFuncSetAttribute(k_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -1158,6 +1266,59 @@ int op_t(Ctx& c, int op) {
     }
 }
 
+SliceConst slice_const(const recon_params& p, const Tables& t) {
+    SliceConst k{};
+    k.a00 = t.a[0][0]; k.a01 = t.a[0][1]; k.a10 = t.a[1][0]; k.a11 = t.a[1][1];
+    k.b00 = t.b[0][0]; k.b01 = t.b[0][1]; k.b10 = t.b[1][0]; k.b11 = t.b[1][1];
+    k.P1 = t.P[0]; k.P2 = t.P[1]; k.psi1 = t.psi[0]; k.psi2 = t.psi[1];
+    k.r = t.r; k.c_f1 = t.c_f[0]; k.c_f2 = t.c_f[1]; k.c12 = t.c12; k.c_rho = t.c_rho; k.a_w = t.a_w;
+    k.det = t.det; k.inv_S = 1.0 / t.S; k.zclip_hi = t.zclip_hi; k.rho_air = p.rho_air;
+    k.lambda = p.lambda; k.beta0 = p.beta0; k.tau = p.tau;
+    k.kappa = p.kappa > 0 ? p.kappa : (p.iters > 0 ? std::pow(p.beta_max / p.beta0, 1.0 / p.iters) : 1.0);
+    k.cg_tol = p.cg_tol; k.iters = p.iters; k.order = p.order; k.cg_max = p.cg_max_iters;
+    return k;
+}
+
+// Work-item lists of one slice (tiles, row-pair groups, column groups) and
+// its FFT batching, appended to the three lists.
+// Row pairs per row-FFT item and columns per column-FFT item of an nx x ny
+// slice, sized so one item's transforms fill about `budget` complex slots.
+int rows_per_item(int nx, int ny, int budget) {
+    const int npairs = (ny + 1) / 2;
+    int per = budget / nx;
+    if (per < 1) per = 1;
+    return per > npairs ? npairs : per;
+}
+
+int cols_per_item(int nx, int ny, int budget) {
+    int pc = budget / ny;
+    if (pc > 16) pc = 16;
+    if (pc < 1) pc = 1;
+    return pc > nx / 2 + 1 ? nx / 2 + 1 : pc;
+}
+
+// Complex slots of one FFT buffer for an nx x ny slice.
+int fft_item_slots(int nx, int ny, int budget) {
+    const int r = rows_per_item(nx, ny, budget) * padded_len(nx);
+    const int q = cols_per_item(nx, ny, budget) * (padded_len(ny) | 1);
+    return r > q ? r : q;
+}
+
+void slice_items(Ctx& c, int s, std::vector<Item>& tiles, std::vector<Item>& rows, std::vector<Item>& cols) {
+    SliceGeom& g = c.sg[s];
+    const int budget = c.precision == 1 ? FftBudget<float>::E : FftBudget<double>::E;
+    const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
+    for (int ty = 0; ty < g.ny; ty += th)
+        for (int tx = 0; tx < g.nx; tx += kTileW) tiles.push_back(Item{s, tx, ty, 0});
+    const int npairs = (g.ny + 1) / 2;
+    const int per = rows_per_item(g.nx, g.ny, budget);
+    g.rows_per_item = per;
+    for (int p0 = 0; p0 < npairs; p0 += per) rows.push_back(Item{s, p0, (npairs - p0 < per ? npairs - p0 : per), 0});
+    const int pc = cols_per_item(g.nx, g.ny, budget);
+    g.cols_per_item = pc;
+    for (int c0 = 0; c0 < g.nh; c0 += pc) cols.push_back(Item{s, c0, (g.nh - c0 < pc ? g.nh - c0 : pc), 0});
+}
+
 int alloc_dev(Ctx& c, void** p, size_t bytes) {
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMalloc(p, bytes);
@@ -1216,34 +1377,21 @@ int solver_setup(Ctx& c) {
     c.spec_elems = coff;
     c.ext_elems = ext;
     // item lists
-    c.tiles.h_lo.assign(c.n, 0); c.tiles.h_cnt.assign(c.n, 0);
-    c.rows.h_lo.assign(c.n, 0); c.rows.h_cnt.assign(c.n, 0);
-    c.cols.h_lo.assign(c.n, 0); c.cols.h_cnt.assign(c.n, 0);
-    const int budget = c.precision == 1 ? FftBudget<float>::E : FftBudget<double>::E;
+    for (DevItemList* L : {&c.tiles, &c.rows, &c.cols}) {
+        L->h_lo.assign(c.n, 0);
+        L->h_cnt.assign(c.n, 0);
+        L->h_items.clear();
+    }
     for (int s = 0; s < c.n; ++s) {
         SliceGeom& g = c.sg[s];
-        c.tiles.h_lo[s] = (int)c.tiles.h_items.size();
-        const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
-        for (int ty = 0; ty < g.ny; ty += th)
-            for (int tx = 0; tx < g.nx; tx += kTileW) c.tiles.h_items.push_back(Item{s, tx, ty, 0});
-        c.tiles.h_cnt[s] = (int)c.tiles.h_items.size() - c.tiles.h_lo[s];
-        c.rows.h_lo[s] = (int)c.rows.h_items.size();
-        const int npairs = (g.ny + 1) / 2;
-        int per = budget / g.nx;
-        if (per < 1) per = 1;
-        if (per > npairs) per = npairs;
-        g.rows_per_item = per;
-        for (int p0 = 0; p0 < npairs; p0 += per)
-            c.rows.h_items.push_back(Item{s, p0, (npairs - p0 < per ? npairs - p0 : per), 0});
-        c.rows.h_cnt[s] = (int)c.rows.h_items.size() - c.rows.h_lo[s];
-        c.cols.h_lo[s] = (int)c.cols.h_items.size();
-        int pc = budget / g.ny;
-        if (pc > 16) pc = 16;
-        if (pc < 1) pc = 1;
-        if (pc > g.nh) pc = g.nh;
-        g.cols_per_item = pc;
-        for (int c0 = 0; c0 < g.nh; c0 += pc) c.cols.h_items.push_back(Item{s, c0, (g.nh - c0 < pc ? g.nh - c0 : pc), 0});
-        c.cols.h_cnt[s] = (int)c.cols.h_items.size() - c.cols.h_lo[s];
+        const size_t t0 = c.tiles.h_items.size(), r0 = c.rows.h_items.size(), c0 = c.cols.h_items.size();
+        slice_items(c, s, c.tiles.h_items, c.rows.h_items, c.cols.h_items);
+        c.tiles.h_lo[s] = (int)t0;
+        c.tiles.h_cnt[s] = (int)(c.tiles.h_items.size() - t0);
+        c.rows.h_lo[s] = (int)r0;
+        c.rows.h_cnt[s] = (int)(c.rows.h_items.size() - r0);
+        c.cols.h_lo[s] = (int)c0;
+        c.cols.h_cnt[s] = (int)(c.cols.h_items.size() - c0);
         g.plan_x = fft_plan_code(g.nx);
         g.plan_y = fft_plan_code(g.ny);
     }
@@ -1265,6 +1413,15 @@ int solver_setup(Ctx& c) {
             have.push_back({n, {off, soff}});
             return {off, soff};
         };
+        if (c.server_mode) {
+            const int top = c.cap_nx > c.cap_ny ? c.cap_nx : c.cap_ny;
+            for (int n = 1; n <= top; ++n) {
+                int m = n;
+                for (int f : {2, 3, 5, 7})
+                    while (m % f == 0) m /= f;
+                if (m == 1) table(n);
+            }
+        }
         for (SliceGeom& g : c.sg) {
             const auto tx = table(g.nx), ty = table(g.ny);
             g.twx = tx.first;
@@ -1272,6 +1429,7 @@ int solver_setup(Ctx& c) {
             g.twy = ty.first;
             g.symy = ty.second;
         }
+        c.tw_index = have;
         if ((rc = alloc_dev(c, &c.d_tw, c.elem * tw.size()))) return rc;
         if ((rc = alloc_dev(c, &c.d_sym, c.elem * sym.size()))) return rc;
         if (c.precision == 1) {
@@ -1284,22 +1442,19 @@ int solver_setup(Ctx& c) {
         }
     }
     if ((rc = upload_list(c, c.tiles)) || (rc = upload_list(c, c.rows)) || (rc = upload_list(c, c.cols))) return rc;
+    if (c.server_mode) {
+        c.tmp_tiles.h_items = c.tiles.h_items;
+        c.tmp_tiles.h_lo = c.tiles.h_lo;
+        c.tmp_tiles.h_cnt = c.tiles.h_cnt;
+        if ((rc = upload_list(c, c.tmp_tiles))) return rc;
+    }
     // constants
-    std::vector<SliceConst> hc(c.n);
+    std::vector<SliceConst>& hc = c.hconst;
+    hc.assign(c.n, SliceConst{});
     c.tab.resize(c.n);
     for (int s = 0; s < c.n; ++s) {
-        const recon_params& p = c.prm[s];
-        const Tables t = make_tables(p);
-        c.tab[s] = t;
-        SliceConst& k = hc[s];
-        k.a00 = t.a[0][0]; k.a01 = t.a[0][1]; k.a10 = t.a[1][0]; k.a11 = t.a[1][1];
-        k.b00 = t.b[0][0]; k.b01 = t.b[0][1]; k.b10 = t.b[1][0]; k.b11 = t.b[1][1];
-        k.P1 = t.P[0]; k.P2 = t.P[1]; k.psi1 = t.psi[0]; k.psi2 = t.psi[1];
-        k.r = t.r; k.c_f1 = t.c_f[0]; k.c_f2 = t.c_f[1]; k.c12 = t.c12; k.c_rho = t.c_rho; k.a_w = t.a_w;
-        k.det = t.det; k.inv_S = 1.0 / t.S; k.zclip_hi = t.zclip_hi; k.rho_air = p.rho_air;
-        k.lambda = p.lambda; k.beta0 = p.beta0; k.tau = p.tau;
-        k.kappa = p.kappa > 0 ? p.kappa : (p.iters > 0 ? std::pow(p.beta_max / p.beta0, 1.0 / p.iters) : 1.0);
-        k.cg_tol = p.cg_tol; k.iters = p.iters; k.order = p.order; k.cg_max = p.cg_max_iters;
+        c.tab[s] = make_tables(c.prm[s]);
+        hc[s] = slice_const(c.prm[s], c.tab[s]);
     }
     if ((rc = alloc_dev(c, (void**)&c.d_geom, sizeof(SliceGeom) * c.n))) return rc;
     if ((rc = alloc_dev(c, (void**)&c.d_const, sizeof(SliceConst) * c.n))) return rc;
@@ -1320,7 +1475,7 @@ int solver_setup(Ctx& c) {
     if ((rc = alloc_dev(c, (void**)&c.d_acct, sizeof(unsigned long long) * KF_COUNT))) return rc;
     RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
     RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, sizeof(int)));
-    if ((rc = pcg_cluster_setup(c))) return rc;
+    if (!c.server_mode && (rc = pcg_cluster_setup(c))) return rc;
     RECON_CUDA(cudaMemcpy(c.d_geom, c.sg.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
     if (c.precision == 1) return set_fft_smem<float>(c);
     return set_fft_smem<double>(c);
@@ -1340,6 +1495,148 @@ int solver_op(Ctx& c, int op) { return c.precision == 1 ? op_t<float>(c, op) : o
 
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int /*on_device*/) {
     return c.precision == 1 ? extract_t<float>(c, Z, rhoe, f1, f2) : extract_t<double>(c, Z, rhoe, f1, f2);
+}
+
+__global__ void k_reset_slots(const int* slots, int n, const SliceConst* C, SliceState* S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = slots[i];
+    const SliceConst& c = C[s];
+    SliceState st = {};
+    st.beta = c.beta0;
+    st.beta_t = c.tau * c.beta0;
+    st.thr_d = c.lambda / c.beta0;
+    st.thr_f = (float)st.thr_d;
+    st.active = c.iters > 0;
+    st.cg_done = 1;
+    S[s] = st;
+}
+
+namespace {
+// Copy host item vectors into a device list allocated at capacity.
+int fill_list(Ctx& c, DevItemList& L) {
+    L.n = (int)L.h_items.size();
+    if (L.n)
+        RECON_CUDA(cudaMemcpyAsync(L.items, L.h_items.data(), sizeof(Item) * L.h_items.size(), cudaMemcpyHostToDevice,
+                                   c.stream));
+    RECON_CUDA(cudaMemcpyAsync(L.lo, L.h_lo.data(), sizeof(int) * c.n, cudaMemcpyHostToDevice, c.stream));
+    RECON_CUDA(cudaMemcpyAsync(L.cnt, L.h_cnt.data(), sizeof(int) * c.n, cudaMemcpyHostToDevice, c.stream));
+    RECON_CUDA(cudaStreamSynchronize(c.stream));   // host vectors may change right after
+    return RECON_OK;
+}
+
+void lists_for(Ctx& c, const std::vector<int>& slots, DevItemList* tiles, DevItemList* rows, DevItemList* cols) {
+    std::vector<Item> dr, dc;
+    for (DevItemList* L : {tiles, rows, cols}) {
+        if (!L) continue;
+        L->h_items.clear();
+        L->h_lo.assign(c.n, 0);
+        L->h_cnt.assign(c.n, 0);
+    }
+    for (int s : slots) {
+        const size_t t0 = tiles->h_items.size();
+        const size_t r0 = rows ? rows->h_items.size() : 0, c0 = cols ? cols->h_items.size() : 0;
+        slice_items(c, s, tiles->h_items, rows ? rows->h_items : dr, cols ? cols->h_items : dc);
+        tiles->h_lo[s] = (int)t0;
+        tiles->h_cnt[s] = (int)(tiles->h_items.size() - t0);
+        if (rows) {
+            rows->h_lo[s] = (int)r0;
+            rows->h_cnt[s] = (int)(rows->h_items.size() - r0);
+        }
+        if (cols) {
+            cols->h_lo[s] = (int)c0;
+            cols->h_cnt[s] = (int)(cols->h_items.size() - c0);
+        }
+    }
+}
+}  // namespace
+
+int solver_configure_slot(Ctx& c, int s, const recon_geometry& geo, const recon_params& p) {
+    if (!c.server_mode || s < 0 || s >= c.n) return RECON_EINVAL;
+    if (geo.nx > c.cap_nx || geo.ny > c.cap_ny || p.precision != c.precision) {
+        set_error("request exceeds the slot capacity or precision of the server");
+        return RECON_EINVAL;
+    }
+    c.geo[s] = geo;
+    c.prm[s] = p;
+    SliceGeom& g = c.sg[s];
+    g.nx = geo.nx;
+    g.ny = geo.ny;
+    g.nh = g.nx / 2 + 1;
+    g.plan_x = fft_plan_code(g.nx);
+    g.plan_y = fft_plan_code(g.ny);
+    for (auto& h : c.tw_index) {
+        if (h.first == g.nx) {
+            g.twx = h.second.first;
+            g.symx = h.second.second;
+        }
+        if (h.first == g.ny) {
+            g.twy = h.second.first;
+            g.symy = h.second.second;
+        }
+    }
+    std::vector<Item> a, b, d;
+    slice_items(c, s, a, b, d);   // sets rows_per_item / cols_per_item
+    c.tab[s] = make_tables(p);
+    c.hconst[s] = slice_const(p, c.tab[s]);
+    RECON_CUDA(cudaMemcpyAsync(c.d_geom + s, &c.sg[s], sizeof(SliceGeom), cudaMemcpyHostToDevice, c.stream));
+    RECON_CUDA(cudaMemcpyAsync(c.d_const + s, &c.hconst[s], sizeof(SliceConst), cudaMemcpyHostToDevice, c.stream));
+    RECON_CUDA(cudaStreamSynchronize(c.stream));
+    return RECON_OK;
+}
+
+int solver_rebuild_lists(Ctx& c, const std::vector<int>& active) {
+    lists_for(c, active, &c.tiles, &c.rows, &c.cols);
+    int rc;
+    if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+    return RECON_OK;
+}
+
+int solver_init_slots(Ctx& c, const std::vector<int>& slots, const float* lo, const float* hi) {
+    if (slots.empty()) return RECON_OK;
+    lists_for(c, slots, &c.tmp_tiles, nullptr, nullptr);
+    int rc;
+    if ((rc = fill_list(c, c.tmp_tiles))) return rc;
+    // the slot list itself rides in the tmp list's counter buffer (one int per slot)
+    RECON_CUDA(cudaMemcpyAsync(c.tmp_tiles.counters, slots.data(), sizeof(int) * slots.size(), cudaMemcpyHostToDevice,
+                               c.stream));
+    k_reset_slots<<<((int)slots.size() + 127) / 128, 128, 0, c.stream>>>(
+        reinterpret_cast<const int*>(c.tmp_tiles.counters), (int)slots.size(), c.d_const, c.d_state);
+    RECON_CUDA(cudaMemsetAsync(c.tmp_tiles.counters, 0, sizeof(unsigned) * c.n, c.stream));
+    const ItemList L = c.tmp_tiles.view();
+    const int grid = grid_for(c, L.n_items);
+    if (c.precision == 1) {
+        k_load<float><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, c.d_const, lo, hi,
+                                                             static_cast<float*>(c.field[RECON_F_MUL]),
+                                                             static_cast<float*>(c.field[RECON_F_MUH]));
+        k_init<float><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, c.d_const, ptrs<float>(c));
+    } else {
+        k_load<double><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, c.d_const, lo, hi,
+                                                              static_cast<double*>(c.field[RECON_F_MUL]),
+                                                              static_cast<double*>(c.field[RECON_F_MUH]));
+        k_init<double><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, c.d_const, ptrs<double>(c));
+    }
+    c.launches += 3;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
+int solver_extract_slots(Ctx& c, const std::vector<int>& slots, float* Z, float* rhoe) {
+    if (slots.empty()) return RECON_OK;
+    lists_for(c, slots, &c.tmp_tiles, nullptr, nullptr);
+    int rc;
+    if ((rc = fill_list(c, c.tmp_tiles))) return rc;
+    const ItemList L = c.tmp_tiles.view();
+    const int grid = grid_for(c, L.n_items);
+    if (c.precision == 1)
+        k_extract<float><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, ptrs<float>(c), Z, rhoe, nullptr,
+                                                                 nullptr, water_z(), z_exponent());
+    else
+        k_extract<double><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, ptrs<double>(c), Z, rhoe, nullptr,
+                                                                  nullptr, water_z(), z_exponent());
+    c.launches += 1;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
 }
 
 FamTimer::FamTimer(Ctx& ctx, int f) : c(ctx), fam(f) {

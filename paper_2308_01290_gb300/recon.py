@@ -54,6 +54,19 @@ class Stats(C.Structure):
                 ("cg_rel_residual", C.c_double)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("max_nx", C.c_int32), ("max_ny", C.c_int32), ("max_views", C.c_int32),
+                ("max_bins", C.c_int32), ("precision", C.c_int32), ("hbm_budget_bytes", C.c_double)]
+
+
+class Request(C.Structure):
+    _fields_ = [("geom", Geometry), ("params", Params), ("low", C.c_void_p), ("high", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("queue_ms", C.c_double), ("latency_ms", C.c_double)]
+
+
 class ReconError(RuntimeError):
     pass
 
@@ -88,6 +101,12 @@ def _load():
         "recon_debug_scalars": (I, [VP, C.c_int32, P(D)]),
         "recon_kernel_launches": (C.c_int64, [VP]),
         "recon_abi_sizes": (I, [P(C.c_int64)]),
+        "recon_server_create": (I, [P(ServerConfig), VP, P(VP)]),
+        "recon_submit": (I, [VP, P(Request), P(C.c_uint64)]),
+        "recon_server_step": (I, [VP, C.c_int32, P(C.c_int32)]),
+        "recon_poll": (I, [VP, C.c_uint64, VP, VP, P(Result)]),
+        "recon_server_stats": (I, [VP, P(C.c_int64)]),
+        "recon_server_destroy": (None, [VP]),
         "recon_profile": (I, [VP, C.c_uint32]),
         "recon_profile_read": (I, [VP, P(D), P(C.c_int64), P(C.c_uint64)]),
         "recon_profile_name": (C.c_char_p, [C.c_int32]),
@@ -115,7 +134,8 @@ EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_
            "recon_sync", "recon_destroy", "recon_solve", "recon_strerror", "recon_last_error", "recon_project",
            "recon_backproject", "recon_fbp", "recon_fbp_noalloc", "recon_simulate", "recon_model_tables", "recon_debug_field",
            "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches",
-           "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name")
+           "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name", "recon_server_create",
+           "recon_submit", "recon_server_step", "recon_poll", "recon_server_stats", "recon_server_destroy")
 KF_COUNT = 13
 
 
@@ -333,3 +353,63 @@ def fbp_noalloc(geom, n, sino, img, stream=None):
 def simulate(geom, params, n, Z, rhoe, noise, i0, sino_low, sino_high, stream=None):
     _check(lib.recon_simulate(C.byref(geom), C.byref(params), int(n), _ptr(Z), _ptr(rhoe), _ptr(noise), float(i0),
                               _ptr(sino_low), _ptr(sino_high), stream), "recon_simulate")
+
+
+# --------------------------------------------------------------------------
+# serving engine
+# --------------------------------------------------------------------------
+
+class Server:
+    """recon_server: continuous batching of independent slice solves."""
+
+    def __init__(self, max_slots, max_nx, max_ny, max_views=0, max_bins=0, precision=1, hbm_budget_bytes=0.0,
+                 stream=None):
+        cfg = ServerConfig(int(max_slots), int(max_nx), int(max_ny), int(max_views), int(max_bins), int(precision),
+                           float(hbm_budget_bytes))
+        h = C.c_void_p()
+        _check(lib.recon_server_create(C.byref(cfg), stream, C.byref(h)), "recon_server_create")
+        self.h = h
+        self.shapes = {}
+
+    def close(self):
+        if self.h:
+            lib.recon_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, geom, params, low, high):
+        low = np.ascontiguousarray(low, np.float32)
+        high = np.ascontiguousarray(high, np.float32)
+        req = Request(geom, params, low.ctypes.data, high.ctypes.data)
+        t = C.c_uint64()
+        _check(lib.recon_submit(self.h, C.byref(req), C.byref(t)), "recon_submit")
+        self.shapes[t.value] = (geom.ny, geom.nx)
+        return t.value
+
+    def step(self, n_iters=1):
+        n = C.c_int32()
+        _check(lib.recon_server_step(self.h, int(n_iters), C.byref(n)), "recon_server_step")
+        return n.value
+
+    def poll(self, ticket):
+        """None while pending, else (Z, rho_e, Result)."""
+        ny, nx = self.shapes[ticket]
+        Z = np.empty((ny, nx), np.float32)
+        R = np.empty((ny, nx), np.float32)
+        res = Result()
+        rc = _check(lib.recon_poll(self.h, C.c_uint64(ticket), Z.ctypes.data, R.ctypes.data, C.byref(res)),
+                    "recon_poll")
+        if rc == 0:
+            return None
+        del self.shapes[ticket]
+        return Z, R, res
+
+    def stats(self):
+        out = (C.c_int64 * 4)()
+        _check(lib.recon_server_stats(self.h, out), "recon_server_stats")
+        return dict(queued=out[0], active=out[1], finished=out[2], footprint=out[3])
