@@ -310,10 +310,13 @@ int64_t recon_kernel_launches(recon_ctx* ctx);
 
 /* Kernel families of the solver, for recon_profile*: 0 threshold + rhs,
  * 1 FFT rows forward, 2 FFT columns (spectral divide), 3 FFT rows inverse,
- * 4 synthesis, 5 PCG start, 6 PCG matvec, 7 PCG update, 8-10 the three FFT
- * passes of the PCG preconditioner, 11 the cluster-resident PCG (whole Z^m
- * solve of a slice per thread-block cluster), 12 other. */
-#define RECON_KF_COUNT 13
+ * 4 synthesis, 5 PCG start (r = b - M z), and the three passes of a PCG
+ * step: 6 update of z and r, convergence test and forward row transforms of
+ * D^-1/2 r; 7 column transforms with the preconditioner's divide and r.y;
+ * 8 inverse row transforms, new search direction p and q = M p.  9 the
+ * cluster-resident PCG (whole Z^m solve of a slice per thread-block
+ * cluster), 10 other. */
+#define RECON_KF_COUNT 11
 
 /* Time the launches of the kernel families whose bit is set in mask with
  * CUDA events on the handle's stream (0 = off).  Algorithmic bytes and launch

@@ -421,10 +421,9 @@ int recon_profile_read(recon_ctx* h, double* ms, int64_t* launches, uint64_t* by
 }
 
 const char* recon_profile_name(int32_t f) {
-    static const char* names[KF_COUNT] = {"thr_rhs",          "fft_rows_fwd", "fft_cols",         "fft_rows_inv",
-                                          "synth",            "pcg_start",    "pcg_matvec",       "pcg_update",
-                                          "pcg_pre_rows_fwd", "pcg_pre_cols", "pcg_pre_rows_inv", "pcg_cluster",
-                                          "other"};
+    static const char* names[KF_COUNT] = {"thr_rhs",   "fft_rows_fwd", "fft_cols", "fft_rows_inv",
+                                          "synth",     "pcg_start",    "pcg_fwd",  "pcg_cols",
+                                          "pcg_inv",   "pcg_cluster",  "other"};
     return (f >= 0 && f < KF_COUNT) ? names[f] : "?";
 }
 

@@ -87,11 +87,9 @@ enum KFam {
     KF_ROWS_INV,
     KF_SYNTH,
     KF_CG_INIT,
-    KF_CG_MATVEC,
-    KF_CG_UPDATE,
-    KF_ROWS_FWD_PRE,
+    KF_PCG_FWD,
     KF_COLS_PRE,
-    KF_ROWS_INV_PRE,
+    KF_PCG_INV,
     KF_PCG_CLUSTER,
     KF_OTHER,
     KF_COUNT

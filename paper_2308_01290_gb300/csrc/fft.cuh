@@ -221,4 +221,160 @@ __device__ __forceinline__ cplx<T>* fft_batch(cplx<T>* a, cplx<T>* b, int N, uns
     return in;
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time power-of-two transforms.  Same Stockham stages as above (8s
+// first, then one 4 or 2), but every index map is a shift or a mask, the
+// padded shared-memory offsets of a butterfly's R legs are immediates, and
+// a stage's source or destination may be a functor that reads or writes HBM
+// directly, so the first and last stages of an item need no separate copy
+// through shared memory.
+// ---------------------------------------------------------------------------
+
+__host__ __device__ constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n >> 1); }
+__host__ __device__ constexpr bool is_pow2c(int n) { return n > 0 && (n & (n - 1)) == 0; }
+
+// Leading dimension (complex slots) of one column sequence of length N in
+// the column pass.  Power-of-two N >= 64 takes padded_len(N) + 1, which is
+// 2 mod 16 slots: the eight columns of a column-fastest access then fall in
+// distinct banks.  Other N take the odd length padded_len(N) | 1.
+__host__ __device__ inline int col_ld(int n) {
+    return (is_pow2c(n) && n >= 64) ? padded_len(n) + 1 : (padded_len(n) | 1);
+}
+
+template <int N>
+struct P2Plan {
+    static constexpr int L = ilog2c(N);
+    static constexpr int N8 = L / 3;                      // radix-8 stages
+    static constexpr int REM = L - 3 * N8;                // 0, 1 (radix 2) or 2 (radix 4)
+    static constexpr int S = N8 + (REM ? 1 : 0);          // stage count
+    __host__ __device__ static constexpr int radix(int s) { return s < N8 ? 8 : (REM == 2 ? 4 : 2); }
+    __host__ __device__ static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
+};
+
+// Sources and destinations of a stage provide load_legs<R, NBF>(b, j, v)
+// (v[r] = element j + r NBF of sequence b) and store_legs<R, NS>(b, idx0, v)
+// (element idx0 + r NS of sequence b = v[r]).
+
+// Shared-memory sequence set: sequence b at p + b * ld, padded indexing.
+// With the radix-8-first plans NBF and NS are 1 or multiples of 8 (and with
+// NS = 1, idx0 is a multiple of R, R | 8), so the padded offsets of the legs
+// are immediates.
+template <typename T>
+struct SmemSeq {
+    cplx<T>* p;
+    int ld;
+    template <int R, int NBF>
+    __device__ __forceinline__ void load_legs(int b, int j, cplx<T>* v) const {
+        const cplx<T>* s = p + b * ld;
+        if constexpr (NBF % 8 == 0) {
+            const int o = pad8(j);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s[o + r * (NBF + NBF / 8)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[r] = s[pad8(j + r * NBF)];
+        }
+    }
+    template <int R, int NS>
+    __device__ __forceinline__ void store_legs(int b, int idx0, const cplx<T>* v) const {
+        cplx<T>* s = p + b * ld;
+        if constexpr (NS == 1) {
+            const int o = pad8(idx0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[o + r] = v[r];
+        } else if constexpr (NS % 8 == 0) {
+            const int o = pad8(idx0);
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[o + r * (NS + NS / 8)] = v[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) s[pad8(idx0 + r * NS)] = v[r];
+        }
+    }
+};
+
+// Element-wise functor source f(b, idx) -> cplx and destination f(b, idx, v).
+template <typename T, class F>
+struct FnLoad {
+    F f;
+    template <int R, int NBF>
+    __device__ __forceinline__ void load_legs(int b, int j, cplx<T>* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = f(b, j + r * NBF);
+    }
+};
+template <typename T, class F>
+struct FnStore {
+    F f;
+    template <int R, int NS>
+    __device__ __forceinline__ void store_legs(int b, int idx0, const cplx<T>* v) const {
+#pragma unroll
+        for (int r = 0; r < R; ++r) f(b, idx0 + r * NS, v[r]);
+    }
+};
+template <typename T, class F>
+__device__ __forceinline__ FnLoad<T, F> fn_load(F f) {
+    return FnLoad<T, F>{f};
+}
+template <typename T, class F>
+__device__ __forceinline__ FnStore<T, F> fn_store(F f) {
+    return FnStore<T, F>{f};
+}
+
+// v * w (DIR < 0) or v * conj(w) (DIR > 0)
+template <typename T, int DIR>
+__device__ __forceinline__ cplx<T> cmul_dir(cplx<T> v, cplx<T> w) {
+    if constexpr (DIR < 0) return {v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x};
+    else return {v.x * w.x + v.y * w.y, v.y * w.x - v.x * w.y};
+}
+
+// Stage s of the length-N plan over `batch` sequences.  Tasks map to
+// (sequence b, butterfly j) with j fastest, or with b fastest over CB slots
+// (BFAST: tasks with b >= batch idle), which keeps a column-fastest HBM
+// access coalesced.
+template <typename T, int N, int STAGE, int DIR, bool BFAST, int CB, class SRC, class DST>
+__device__ __forceinline__ void p2_stage(int batch, const cplx<T>* __restrict__ tw, const SRC& src, const DST& dst) {
+    constexpr int R = P2Plan<N>::radix(STAGE);
+    constexpr int NS = P2Plan<N>::ns(STAGE);
+    constexpr int NBF = N / R;
+    constexpr int STEP = N / (NS * R);
+    const int total = BFAST ? CB * NBF : batch * NBF;
+#pragma unroll 1
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        int b, j;
+        if constexpr (BFAST) {
+            b = t & (CB - 1);
+            j = t >> ilog2c(CB);
+            if (b >= batch) continue;
+        } else {
+            j = t & (NBF - 1);
+            b = t >> ilog2c(NBF);
+        }
+        cplx<T> v[R];
+        src.template load_legs<R, NBF>(b, j, v);
+        const int k = j & (NS - 1);
+        if constexpr (NS > 1) {
+            const int ks = k * STEP;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul_dir<T, DIR>(v[r], tw[r * ks]);
+        }
+        dft<T, R>(v, DIR);
+        dst.template store_legs<R, NS>(b, (j >> ilog2c(NS)) * NS * R + k, v);
+    }
+}
+
+// Stages FIRST..LAST between the shared buffers a and b (ping-pong, stage
+// FIRST reads a), j-fastest; a synchronisation after each stage.  Returns
+// the buffer holding the result.
+template <typename T, int N, int DIR, int FIRST, int LAST>
+__device__ __forceinline__ cplx<T>* p2_smem_stages(cplx<T>* a, cplx<T>* b, int ld, int batch, const cplx<T>* tw) {
+    if constexpr (FIRST > LAST) {
+        return a;
+    } else {
+        p2_stage<T, N, FIRST, DIR, false, 1>(batch, tw, SmemSeq<T>{a, ld}, SmemSeq<T>{b, ld});
+        __syncthreads();
+        return p2_smem_stages<T, N, DIR, FIRST + 1, LAST>(b, a, ld, batch, tw);
+    }
+}
+
 }  // namespace recon

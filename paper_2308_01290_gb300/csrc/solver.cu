@@ -16,6 +16,7 @@
 // Sums for reductions are FP64 in a fixed order (deterministic).
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "ctx.h"
@@ -378,11 +379,74 @@ __global__ void k_gs_fix(ItemList L, const SliceGeom* G, const SliceConst* C, co
 // --------------------------------------------------------------------------
 // FFT-diagonalised solve: rows (R2C, two real rows per complex FFT),
 // columns (FFT, divide by c + beta K, inverse FFT), rows (C2R).
+//
+// Power-of-two sizes (FP32) take compile-time transforms whose first stage
+// reads HBM and whose last stage writes it; other 7-smooth sizes take the
+// runtime mixed-radix transform with a load phase and a store phase.
 // --------------------------------------------------------------------------
 
-// MODE 0: input is a field.  MODE 1: input is D^-1/2-scaled CG residual.
+__device__ __forceinline__ bool p2_fast(int n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
+
+// Runs the statements with `constexpr int NN` set to n (one of p2_fast).
+#define RECON_P2_DISPATCH(n, ...)                \
+    switch (n) {                                 \
+        case 64: {                               \
+            constexpr int NN = 64;               \
+            __VA_ARGS__;                         \
+        } break;                                 \
+        case 128: {                              \
+            constexpr int NN = 128;              \
+            __VA_ARGS__;                         \
+        } break;                                 \
+        case 256: {                              \
+            constexpr int NN = 256;              \
+            __VA_ARGS__;                         \
+        } break;                                 \
+        case 512: {                              \
+            constexpr int NN = 512;              \
+            __VA_ARGS__;                         \
+        } break;                                 \
+        default: {                               \
+            constexpr int NN = 1024;             \
+            __VA_ARGS__;                         \
+        } break;                                 \
+    }
+
+// Split the transforms of np row pairs (natural order in `res`) into the two
+// half spectra of each pair: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
+template <typename T>
+__device__ __forceinline__ void rows_to_half_spectra(const cplx<T>* res, int ld, int N, int nh, int np, int rows,
+                                                     cplx<T>* spr, int cpitch) {
+    const DivMod dh(nh);
+    for (int q = threadIdx.x; q < np * nh; q += blockDim.x) {
+        const int b = dh.div(q), k = q - b * nh;
+        const cplx<T> zk = res[b * ld + pad8(k)];
+        const cplx<T> zc = res[b * ld + pad8(k == 0 ? 0 : N - k)];
+        const long long e0 = (long long)(2 * b) * cpitch + k;
+        spr[e0] = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
+        if (2 * b + 1 < rows) spr[e0 + cpitch] = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
+    }
+}
+
+// Element n of the complex sequence A + iB whose inverse transform gives the
+// real rows of the half spectra ra (real part) and rb (imaginary part; null
+// for none); the upper half follows from Hermitian symmetry.
+template <typename T>
+__device__ __forceinline__ cplx<T> row_pair_from_half_spectra(const cplx<T>* ra, const cplx<T>* rb, int N, int nh,
+                                                             int n) {
+    const bool upper = n >= nh;
+    const int k = upper ? N - n : n;
+    cplx<T> a = ra[k], c = {T(0), T(0)};
+    if (rb) c = rb[k];
+    if (upper) {
+        a.y = -a.y;
+        c.y = -c.y;
+    }
+    return {a.x - c.y, a.y + c.x};
+}
+
 // Item: rows 2*it.a .. of one slice, it.b pairs; two real rows per complex FFT.
-template <typename T, int MODE>
+template <typename T>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_fwd(ItemList L, const SliceGeom* G, const SliceState* S,
                                                            Ptrs<T> P, FftJobs J, const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -392,84 +456,106 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_fwd(ItemLis
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int job = w / L.n_items, item = w - job * L.n_items;
         const Item it = L.items[item];
-        const int kind = J.coef[job];
-        if (!__ldg(&S[it.slice].active) || (kind == 3 && __ldg(&S[it.slice].cg_done))) continue;
+        if (!__ldg(&S[it.slice].active)) continue;
         const SliceGeom g = G[it.slice];
         const int N = g.nx, pair0 = it.a, np = it.b, ld = padded_len(N);
         const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
-        account(P.acct, MODE ? KF_ROWS_FWD_PRE : KF_ROWS_FWD,
-                (long long)rows * ((MODE ? 2 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
-        const T* in = P.f[J.in[job]];
-        const T* a2 = P.f[RECON_F_A2];
-        T rnum = T(0), b4 = T(0);
-        if (MODE == 1) {
-            rnum = T(sqrt(__ldg(&S[it.slice].abar2) + 4.0 * __ldg(&S[it.slice].beta_t)));
-            b4 = T(4.0 * __ldg(&S[it.slice].beta_t));
-        }
-        {
+        account(P.acct, KF_ROWS_FWD, (long long)rows * (N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
+        const T* inr = P.f[J.in[job]] + g.off + (long long)(2 * pair0) * g.pitch;
+        const cplx<T>* tw = twpool + g.twx;
+        const cplx<T>* res;
+        auto elem = [&](int b, int n) -> cplx<T> {
+            const long long d = (long long)(2 * b) * g.pitch + n;
+            return {inr[d], 2 * b + 1 < rows ? inr[d + g.pitch] : T(0)};
+        };
+        bool fast = false;
+        if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
+        if (fast) {
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+                              __syncthreads();
+                              res = p2_smem_stages<T, NN, -1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np, tw));
+        } else {
             // four elements per thread per round, loads issued before use
             const DivMod dN(N);
             const int total_q = np * N;
             for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
-                T v0[4], v1[4], w0[4], w1[4];
+                cplx<T> v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int q = q0 + u * blockDim.x;
-                    v0[u] = v1[u] = w0[u] = w1[u] = T(0);
                     if (q < total_q) {
-                        const int b = dN.div(q), n = q - b * N;
-                        const int row = 2 * (pair0 + b);
-                        const long long d0 = g.off + (long long)row * g.pitch + n;
-                        v0[u] = in[d0];
-                        if (MODE == 1) w0[u] = a2[d0];
-                        if (row + 1 < g.ny) {
-                            v1[u] = in[d0 + g.pitch];
-                            if (MODE == 1) w1[u] = a2[d0 + g.pitch];
-                        }
+                        const int b = dN.div(q);
+                        v[u] = elem(b, q - b * N);
                     }
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int q = q0 + u * blockDim.x;
                     if (q < total_q) {
-                        const int b = dN.div(q), n = q - b * N;
-                        T a = v0[u], c = v1[u];
-                        if (MODE == 1) {
-                            a *= dscale(rnum, w0[u], b4);
-                            c *= dscale(rnum, w1[u], b4);
-                        }
-                        buf[b * ld + pad8(n)] = {a, c};
+                        const int b = dN.div(q);
+                        buf[b * ld + pad8(q - b * N)] = v[u];
                     }
                 }
             }
+            __syncthreads();
+            res = fft_batch<T>(buf, buf2, N, g.plan_x, np, ld, tw, -1);
         }
-        __syncthreads();
-        const cplx<T>* res = fft_batch<T>(buf, buf2, N, g.plan_x, np, ld, twpool + g.twx, -1);
-        cplx<T>* sp = P.s[J.spec[job]];
-        for (int b = 0; b < np; ++b) {
-            const int row = 2 * (pair0 + b);
-            const long long e0 = g.coff + (long long)row * g.cpitch;
-            for (int k = threadIdx.x; k < g.nh; k += blockDim.x) {
-                const cplx<T> zk = res[b * ld + pad8(k)];
-                const cplx<T> zc = res[b * ld + pad8(k == 0 ? 0 : N - k)];
-                // A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i)
-                sp[e0 + k] = {T(0.5) * (zk.x + zc.x), T(0.5) * (zk.y - zc.y)};
-                if (row + 1 < g.ny) sp[e0 + g.cpitch + k] = {T(0.5) * (zk.y + zc.y), T(-0.5) * (zk.x - zc.x)};
-            }
-        }
+        rows_to_half_spectra(res, ld, N, g.nh, np, rows,
+                             P.s[J.spec[job]] + g.coff + (long long)(2 * pair0) * g.cpitch, g.cpitch);
         __syncthreads();
     }
 }
 
-// Item: spectrum columns it.a .. it.a + it.b - 1 of one slice: FFT along y,
-// divide by (c + beta K) n_x n_y, inverse FFT along y.
+// Column item, power-of-two N: forward transform along y (first stage read
+// straight from the spectrum, column-fastest), the spectral divide folded into
+// the last forward stage, inverse transform with the last stage written
+// straight back.  With RY, adds sum_k w_kx |X_k|^2 / (n m_k) over the item to
+// `acc` (the item's share of u.(m(F))^-1 u by Parseval; w = 1 on the columns
+// kx = 0 and kx = nx/2, which stand for themselves, 2 on the others, which
+// also stand for their conjugate partners outside the half spectrum).
+template <typename T, int N, bool RY>
+__device__ __forceinline__ void cols_item_p2(cplx<T>* spc, int cpitch, int nc, int col0, int nx, cplx<T>* buf0,
+                                             cplx<T>* buf1, const cplx<T>* tw, const T* symx, const T* symy, T cst,
+                                             T bet, T inv_n, T& acc) {
+    constexpr int S = P2Plan<N>::S;
+    constexpr int E = FftBudget<T>::E / N;
+    constexpr int CB = E > 16 ? 16 : (E < 1 ? 1 : E);
+    const int ld = col_ld(N);
+    auto gload = [&](int b, int y) -> cplx<T> { return spc[(long long)y * cpitch + b]; };
+    p2_stage<T, N, 0, -1, true, CB>(nc, tw, fn_load<T>(gload), SmemSeq<T>{buf0, ld});
+    __syncthreads();
+    cplx<T>* cur = p2_smem_stages<T, N, -1, 1, S - 2>(buf0, buf1, ld, nc, tw);
+    cplx<T>* oth = cur == buf0 ? buf1 : buf0;
+    // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
+    auto divide = [&](int b, int ky, cplx<T> v) {
+        const T sc = inv_n / (cst + bet * (symx[col0 + b] + symy[ky]));
+        if (RY) {
+            const int kx = col0 + b;
+            const T wgt = (kx == 0 || 2 * kx == nx) ? T(1) : T(2);
+            acc = fma(wgt * sc, v.x * v.x + v.y * v.y, acc);
+        }
+        oth[b * ld + pad8(ky)] = {v.x * sc, v.y * sc};
+    };
+    p2_stage<T, N, S - 1, -1, false, 1>(nc, tw, SmemSeq<T>{cur, ld}, fn_store<T>(divide));
+    __syncthreads();
+    cur = p2_smem_stages<T, N, +1, 0, S - 2>(oth, cur, ld, nc, tw);
+    auto gstore = [&](int b, int y, cplx<T> v) { spc[(long long)y * cpitch + b] = v; };
+    p2_stage<T, N, S - 1, +1, true, CB>(nc, tw, SmemSeq<T>{cur, ld}, fn_store<T>(gstore));
+    __syncthreads();
+}
+
+// Column pass.  Kinds 0, 1, 2 divide by c_f1 + beta K, c_f2 + beta K,
+// 1 + beta~ K (the f1, f2 and rho_e solves); kind 3 divides by
+// abar^2 + beta~ K (the PCG preconditioner) and also reduces r.y of the PCG
+// step over the slice, which sets beta_cg = (r.y)/(r.y)_old.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L, const SliceGeom* G, const SliceConst* C,
-                                                       const SliceState* S, Ptrs<T> P, FftJobs J,
+                                                       SliceState* S, Ptrs<T> P, FftJobs J,
                                                        const cplx<T>* twpool, int half) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf1 = buf0 + half;
+    __shared__ double red[32];
     const int total = L.n_items * J.n;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int job = w / L.n_items, item = w - job * L.n_items;
@@ -478,33 +564,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
         const SliceState* st = S + it.slice;
         if (!__ldg(&st->active) || (kind == 3 && __ldg(&st->cg_done))) continue;
         const SliceGeom g = G[it.slice];
-        const int N = g.ny, col0 = it.a, nc = it.b, ld = padded_len(N) | 1;
+        const int N = g.ny, col0 = it.a, nc = it.b, ld = col_ld(N);
         account(P.acct, kind == 3 ? KF_COLS_PRE : KF_COLS, (long long)nc * N * 4 * (long long)sizeof(T));
         cplx<T>* sp = P.s[J.spec[job]];
-        {
-            const DivMod dc(nc);
-            const int total_q = nc * N;
-            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
-                cplx<T> v[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u * blockDim.x;
-                    if (q < total_q) {
-                        const int y = dc.div(q), cc = q - y * nc;
-                        v[u] = sp[g.coff + (long long)y * g.cpitch + col0 + cc];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u * blockDim.x;
-                    if (q < total_q) {
-                        const int y = dc.div(q), cc = q - y * nc;
-                        buf0[cc * ld + pad8(y)] = v[u];
-                    }
-                }
-            }
-        }
-        __syncthreads();
         const cplx<T>* tw = twpool + g.twy;
         double cst, bet;
         switch (kind) {
@@ -516,147 +578,75 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
         const T inv_n = T(1.0 / ((double)g.nx * (double)g.ny));
         const T* symx = P.sym + g.symx;
         const T* symy = P.sym + g.symy;
-        // forward FFT along y, spectral divide, inverse FFT along y (one
-        // inlined transform, run twice)
-        cplx<T>* buf = buf0;
-        for (int pass = 0; pass < 2; ++pass) {
-            buf = fft_batch<T>(buf, buf == buf0 ? buf1 : buf0, N, g.plan_y, nc, ld, tw, pass ? +1 : -1);
-            if (pass) break;
-            const DivMod dN(N);
-            for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
-                const int cc = dN.div(q), ky = q - cc * N;
-                // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
-                const T sc = inv_n / (T(cst) + T(bet) * (symx[col0 + cc] + symy[ky]));
-                cplx<T> v = buf[cc * ld + pad8(ky)];
-                buf[cc * ld + pad8(ky)] = {v.x * sc, v.y * sc};
+        T accT = T(0);
+        bool fast = false;
+        if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
+        if (fast) {
+            cplx<T>* spc = sp + g.coff + col0;
+            if (kind == 3) {
+                RECON_P2_DISPATCH(N, cols_item_p2<T, NN, true>(spc, g.cpitch, nc, col0, g.nx, buf0, buf1, tw, symx,
+                                                               symy, T(cst), T(bet), inv_n, accT));
+            } else {
+                RECON_P2_DISPATCH(N, cols_item_p2<T, NN, false>(spc, g.cpitch, nc, col0, g.nx, buf0, buf1, tw, symx,
+                                                                symy, T(cst), T(bet), inv_n, accT));
+            }
+        } else {
+            {
+                const DivMod dc(nc);
+                const int total_q = nc * N;
+                for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
+                    cplx<T> v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u * blockDim.x;
+                        if (q < total_q) {
+                            const int y = dc.div(q), cc = q - y * nc;
+                            v[u] = sp[g.coff + (long long)y * g.cpitch + col0 + cc];
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int q = q0 + u * blockDim.x;
+                        if (q < total_q) {
+                            const int y = dc.div(q), cc = q - y * nc;
+                            buf0[cc * ld + pad8(y)] = v[u];
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // forward FFT along y, spectral divide, inverse FFT along y (one
+            // inlined transform, run twice)
+            cplx<T>* buf = buf0;
+            for (int pass = 0; pass < 2; ++pass) {
+                buf = fft_batch<T>(buf, buf == buf0 ? buf1 : buf0, N, g.plan_y, nc, ld, tw, pass ? +1 : -1);
+                if (pass) break;
+                const DivMod dN(N);
+                for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
+                    const int cc = dN.div(q), ky = q - cc * N;
+                    // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
+                    const T sc = inv_n / (T(cst) + T(bet) * (symx[col0 + cc] + symy[ky]));
+                    cplx<T> v = buf[cc * ld + pad8(ky)];
+                    if (kind == 3) {
+                        const int kx = col0 + cc;
+                        const T wgt = (kx == 0 || 2 * kx == g.nx) ? T(1) : T(2);
+                        accT = fma(wgt * sc, v.x * v.x + v.y * v.y, accT);
+                    }
+                    buf[cc * ld + pad8(ky)] = {v.x * sc, v.y * sc};
+                }
+                __syncthreads();
+            }
+            {
+                const DivMod dc(nc);
+                for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
+                    const int y = dc.div(q), cc = q - y * nc;
+                    sp[g.coff + (long long)y * g.cpitch + col0 + cc] = buf[cc * ld + pad8(y)];
+                }
             }
             __syncthreads();
         }
-        {
-            const DivMod dc(nc);
-            for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
-                const int y = dc.div(q), cc = q - y * nc;
-                sp[g.coff + (long long)y * g.cpitch + col0 + cc] = buf[cc * ld + pad8(y)];
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// MODE 0: write the field.  MODE 1: y = D^-1/2 x into CG_Y and reduce r.y.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_inv(ItemList L, const SliceGeom* G, SliceState* S, Ptrs<T> P,
-                                                           FftJobs J, const cplx<T>* twpool, int half) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
-    cplx<T>* buf2 = buf + half;
-    __shared__ double red[32];
-    const int total = L.n_items * J.n;
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
-        const int job = w / L.n_items, item = w - job * L.n_items;
-        const Item it = L.items[item];
-        const int kind = J.coef[job];
-        if (!__ldg(&S[it.slice].active) || (kind == 3 && __ldg(&S[it.slice].cg_done))) continue;
-        const SliceGeom g = G[it.slice];
-        const int N = g.nx, pair0 = it.a, np = it.b, ld = padded_len(N);
-        const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
-        account(P.acct, MODE ? KF_ROWS_INV_PRE : KF_ROWS_INV,
-                (long long)rows * ((MODE ? 3 : 1) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
-        const cplx<T>* sp = P.s[J.spec[job]];
-        {
-            const DivMod dN(N);
-            const int total_q = np * N;
-            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
-                cplx<T> A[4], B[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u * blockDim.x;
-                    A[u] = B[u] = {T(0), T(0)};
-                    if (q < total_q) {
-                        const int b = dN.div(q), n = q - b * N;
-                        const int row = 2 * (pair0 + b);
-                        const int k = n >= g.nh ? N - n : n;
-                        const long long e0 = g.coff + (long long)row * g.cpitch + k;
-                        A[u] = sp[e0];
-                        if (row + 1 < g.ny) B[u] = sp[e0 + g.cpitch];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u * blockDim.x;
-                    if (q < total_q) {
-                        const int b = dN.div(q), n = q - b * N;
-                        cplx<T> a = A[u], c = B[u];
-                        if (n >= g.nh) {   // Hermitian half of each real row
-                            a.y = -a.y;
-                            c.y = -c.y;
-                        }
-                        buf[b * ld + pad8(n)] = {a.x - c.y, a.y + c.x};
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        const cplx<T>* res = fft_batch<T>(buf, buf2, N, g.plan_x, np, ld, twpool + g.twx, +1);
-        T* out = P.f[J.out[job]];
-        double acc[1] = {0.0};
-        T accT = T(0);
-        const T* a2 = P.f[RECON_F_A2];
-        const T* r = P.f[RECON_F_CG_R];
-        T rnum = T(0), b4 = T(0);
-        if (MODE == 1) {
-            rnum = T(sqrt(__ldg(&S[it.slice].abar2) + 4.0 * __ldg(&S[it.slice].beta_t)));
-            b4 = T(4.0 * __ldg(&S[it.slice].beta_t));
-        }
-        {
-            const DivMod dN(N);
-            const int total_q = np * N;
-            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
-                T wa[4], wb[4], ra[4], rb[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u * blockDim.x;
-                    wa[u] = wb[u] = ra[u] = rb[u] = T(0);
-                    if (MODE == 1 && q < total_q) {
-                        const int b = dN.div(q), n = q - b * N;
-                        const int row = 2 * (pair0 + b);
-                        const long long d0 = g.off + (long long)row * g.pitch + n;
-                        wa[u] = a2[d0];
-                        ra[u] = r[d0];
-                        if (row + 1 < g.ny) {
-                            wb[u] = a2[d0 + g.pitch];
-                            rb[u] = r[d0 + g.pitch];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int q = q0 + u * blockDim.x;
-                    if (q < total_q) {
-                        const int b = dN.div(q), n = q - b * N;
-                        const int row = 2 * (pair0 + b);
-                        const bool has1 = row + 1 < g.ny;
-                        const long long d0 = g.off + (long long)row * g.pitch + n;
-                        const cplx<T> v = res[b * ld + pad8(n)];
-                        if (MODE == 0) {
-                            out[d0] = v.x;
-                            if (has1) out[d0 + g.pitch] = v.y;
-                        } else {
-                            const T y0 = v.x * dscale(rnum, wa[u], b4);
-                            out[d0] = y0;
-                            accT = fma(y0, ra[u], accT);
-                            if (has1) {
-                                const T y1 = v.y * dscale(rnum, wb[u], b4);
-                                out[d0 + g.pitch] = y1;
-                                accT = fma(y1, rb[u], accT);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        if (MODE == 1) {
-            acc[0] = (double)accT;
+        if (kind == 3) {
+            double acc[1] = {(double)accT};
             block_sum<1>(acc, red);
             double tot[1];
             if (item_reduce<1>(L, item, it.slice, acc, tot, red)) {
@@ -664,6 +654,373 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_inv(ItemLis
                 so.betacg = (so.cg_it == 0) ? 0.0 : tot[0] / so.ry;
                 so.ry = tot[0];
             }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_inv(ItemList L, const SliceGeom* G, const SliceState* S,
+                                                           Ptrs<T> P, FftJobs J, const cplx<T>* twpool, int half) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf2 = buf + half;
+    const int total = L.n_items * J.n;
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int job = w / L.n_items, item = w - job * L.n_items;
+        const Item it = L.items[item];
+        if (!__ldg(&S[it.slice].active)) continue;
+        const SliceGeom g = G[it.slice];
+        const int N = g.nx, pair0 = it.a, np = it.b, ld = padded_len(N);
+        const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
+        account(P.acct, KF_ROWS_INV, (long long)rows * (N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
+        const cplx<T>* spr = P.s[J.spec[job]] + g.coff + (long long)(2 * pair0) * g.cpitch;
+        T* outr = P.f[J.out[job]] + g.off + (long long)(2 * pair0) * g.pitch;
+        const cplx<T>* tw = twpool + g.twx;
+        auto elem = [&](int b, int n) -> cplx<T> {
+            const cplx<T>* ra = spr + (long long)(2 * b) * g.cpitch;
+            return row_pair_from_half_spectra<T>(ra, 2 * b + 1 < rows ? ra + g.cpitch : nullptr, N, g.nh, n);
+        };
+        auto put = [&](int b, int n, cplx<T> v) {
+            const long long d = (long long)(2 * b) * g.pitch + n;
+            outr[d] = v.x;
+            if (2 * b + 1 < rows) outr[d + g.pitch] = v.y;
+        };
+        bool fast = false;
+        if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
+        if (fast) {
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np, tw, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+                              __syncthreads();
+                              cplx<T>* cur = p2_smem_stages<T, NN, +1, 1, P2Plan<NN>::S - 2>(buf, buf2, ld, np, tw);
+                              p2_stage<T, NN, P2Plan<NN>::S - 1, +1, false, 1>(np, tw, SmemSeq<T>{cur, ld},
+                                                                              fn_store<T>(put)));
+        } else {
+            const DivMod dN(N);
+            const int total_q = np * N;
+            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
+                cplx<T> v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int b = dN.div(q);
+                        v[u] = elem(b, q - b * N);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int b = dN.div(q);
+                        buf[b * ld + pad8(q - b * N)] = v[u];
+                    }
+                }
+            }
+            __syncthreads();
+            const cplx<T>* res = fft_batch<T>(buf, buf2, N, g.plan_x, np, ld, tw, +1);
+            for (int q = threadIdx.x; q < total_q; q += blockDim.x) {
+                const int b = dN.div(q), n = q - b * N;
+                put(b, n, res[b * ld + pad8(n)]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------------
+// PCG of the Z^m step (Alg. 1): M z = ab + beta~ div(h, v) with
+// M = diag(a^2) + beta~ (dx'dx + dy'dy), preconditioner
+// D^-1/2 (abar^2 + beta~ L)^-1 D^-1/2, D = diag((a^2 + 4 beta~)/(abar^2 + 4 beta~)).
+// A step takes three passes over row-pair items and column items:
+//   k_pcg_fwd  z += alpha p, r -= alpha q, r.r and the convergence test;
+//              u = D^-1/2 r; row transforms of u -> half spectrum
+//   k_cols     column transforms, r.y = u.(abar^2 + beta~ L)^-1 u taken in
+//              the spectral domain, divide, inverse columns -> beta_cg
+//   k_pcg_inv  inverse row transforms -> x = (abar^2 + beta~ L)^-1 u on the
+//              item's rows and the rows just above and below it;
+//              p = D^-1/2 x + beta_cg p_old; q = M p; p.q -> alpha
+// --------------------------------------------------------------------------
+
+// Stage-0 source of the forward row transform of a PCG step: element n of
+// rows 2b and 2b+1 of the item gets z += alpha p and r -= alpha q (UPD), adds
+// r^2 to `acc`, and enters the transform as u = D^-1/2 r.  The loads of four
+// legs are issued before any store.
+template <typename T, bool UPD>
+struct PcgFwdLoad {
+    T* z;
+    T* r;
+    const T* p;
+    const T* q;
+    const T* a2;
+    int pitch, rows;
+    T al, rnum, b4;
+    T& acc;
+
+    __device__ __forceinline__ cplx<T> one(int b, int n) const {
+        T u[2] = {T(0), T(0)};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && 2 * b + 1 >= rows) break;
+            const long long d = (long long)(2 * b + h) * pitch + n;
+            T rv = r[d];
+            const T w = a2[d];
+            if (UPD) {
+                z[d] = fma(al, p[d], z[d]);
+                rv = fma(-al, q[d], rv);
+                r[d] = rv;
+                acc = fma(rv, rv, acc);
+            }
+            u[h] = rv * dscale(rnum, w, b4);
+        }
+        return {u[0], u[1]};
+    }
+
+    template <int R, int NBF>
+    __device__ __forceinline__ void load_legs(int b, int j, cplx<T>* v) const {
+        constexpr int G4 = R < 4 ? R : 4;
+        const long long d0 = (long long)(2 * b) * pitch + j;
+        const bool has1 = 2 * b + 1 < rows;
+#pragma unroll
+        for (int g0 = 0; g0 < R; g0 += G4) {
+            T rv[2][G4], wv[2][G4], zv[2][G4], pv[2][G4], qv[2][G4];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int u = 0; u < G4; ++u) {
+                    const long long d = d0 + h * pitch + (g0 + u) * NBF;
+                    const bool ok = h == 0 || has1;
+                    rv[h][u] = ok ? r[d] : T(0);
+                    wv[h][u] = ok ? a2[d] : T(0);
+                    if (UPD) {
+                        zv[h][u] = ok ? z[d] : T(0);
+                        pv[h][u] = ok ? p[d] : T(0);
+                        qv[h][u] = ok ? q[d] : T(0);
+                    }
+                }
+#pragma unroll
+            for (int u = 0; u < G4; ++u) {
+                T uo[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    T rn = rv[h][u];
+                    if (UPD && (h == 0 || has1)) {
+                        const long long d = d0 + h * pitch + (g0 + u) * NBF;
+                        z[d] = fma(al, pv[h][u], zv[h][u]);
+                        rn = fma(-al, qv[h][u], rn);
+                        r[d] = rn;
+                        acc = fma(rn, rn, acc);
+                    }
+                    uo[h] = (h == 0 || has1) ? rn * dscale(rnum, wv[h][u], b4) : T(0);
+                }
+                v[g0 + u] = {uo[0], uo[1]};
+            }
+        }
+    }
+};
+
+// UPD = false: the first step of the solve (r from k_cg_init, no update).
+template <typename T, bool UPD>
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_fwd(ItemList L, const SliceGeom* G,
+                                                                        const SliceConst* C, SliceState* S, Ptrs<T> P,
+                                                                        const cplx<T>* twpool, int half, int par,
+                                                                        int* pending) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf2 = buf + half;
+    __shared__ double red[32];
+    for (int item = blockIdx.x; item < L.n_items; item += gridDim.x) {
+        const Item it = L.items[item];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        const SliceGeom g = G[it.slice];
+        const int N = g.nx, np = it.b, ld = padded_len(N), r0 = 2 * it.a;
+        const int rows = (g.ny - r0 < 2 * np) ? g.ny - r0 : 2 * np;
+        account(P.acct, KF_PCG_FWD,
+                (long long)rows * ((UPD ? 7 : 2) * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
+        const long long d0 = g.off + (long long)r0 * g.pitch;
+        T acc = T(0);
+        const PcgFwdLoad<T, UPD> src{P.f[RECON_F_Z] + d0,
+                                     P.f[RECON_F_CG_R] + d0,
+                                     P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1] + d0,
+                                     P.f[RECON_F_CG_Q] + d0,
+                                     P.f[RECON_F_A2] + d0,
+                                     g.pitch,
+                                     rows,
+                                     UPD ? T(__ldg(&sp->alpha)) : T(0),
+                                     T(sqrt(__ldg(&sp->abar2) + 4.0 * __ldg(&sp->beta_t))),
+                                     T(4.0 * __ldg(&sp->beta_t)),
+                                     acc};
+        const cplx<T>* tw = twpool + g.twx;
+        const cplx<T>* res;
+        bool fast = false;
+        if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
+        if (fast) {
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw, src, SmemSeq<T>{buf, ld});
+                              __syncthreads();
+                              res = p2_smem_stages<T, NN, -1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np, tw));
+        } else {
+            const DivMod dN(N);
+            for (int q = threadIdx.x; q < np * N; q += blockDim.x) {
+                const int b = dN.div(q), n = q - b * N;
+                buf[b * ld + pad8(n)] = src.one(b, n);
+            }
+            __syncthreads();
+            res = fft_batch<T>(buf, buf2, N, g.plan_x, np, ld, tw, -1);
+        }
+        rows_to_half_spectra(res, ld, N, g.nh, np, rows, P.s[0] + g.coff + (long long)r0 * g.cpitch, g.cpitch);
+        if (UPD) {
+            double a[1] = {(double)acc};
+            block_sum<1>(a, red);
+            double tot[1];
+            if (item_reduce<1>(L, item, it.slice, a, tot, red)) {
+                SliceState& so = S[it.slice];
+                const SliceConst& c = C[it.slice];
+                so.rr = tot[0];
+                so.cg_it += 1;
+                const bool conv = !(tot[0] > c.cg_tol * c.cg_tol * so.bb);
+                if (conv || so.cg_it >= c.cg_max) {
+                    so.cg_done = 1;
+                    atomicSub(pending, 1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Relative row i in [-1, rows] of a k_pcg_inv item -> (sequence, component):
+// rows 0 .. rows-1 are pairs 0 .. np-1; row -1 (above) and row `rows`
+// (below) form sequence np.
+__device__ __forceinline__ int pcg_row_slot(int i, int rows, int np, int ld) {
+    int b, comp;
+    if (i < 0) {
+        b = np;
+        comp = 0;
+    } else if (i >= rows) {
+        b = np;
+        comp = 1;
+    } else {
+        b = i >> 1;
+        comp = i & 1;
+    }
+    return 2 * b * ld + comp;   // in scalars; add 2 * pad8(n)
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList L, const SliceGeom* G, SliceState* S,
+                                                                        Ptrs<T> P, const cplx<T>* twpool, int half,
+                                                                        int par) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
+    cplx<T>* buf2 = buf + half;
+    __shared__ double red[32];
+    const T* pold = P.f[par ? RECON_F_CG_P1 : RECON_F_CG_P0];
+    T* pnew = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
+    const T* a2 = P.f[RECON_F_A2];
+    T* qo = P.f[RECON_F_CG_Q];
+    for (int item = blockIdx.x; item < L.n_items; item += gridDim.x) {
+        const Item it = L.items[item];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        const SliceGeom g = G[it.slice];
+        const int N = g.nx, np = it.b, ld = padded_len(N), r0 = 2 * it.a;
+        const int rows = (g.ny - r0 < 2 * np) ? g.ny - r0 : 2 * np;
+        const int up = wrap(r0 - 1, g.ny), dn = wrap(r0 + rows, g.ny);
+        account(P.acct, KF_PCG_INV,
+                (long long)rows * (4 * N * (long long)sizeof(T) + g.nh * 2 * (long long)sizeof(T)));
+        const cplx<T>* s0 = P.s[0] + g.coff;
+        auto elem = [&](int b, int n) -> cplx<T> {
+            const cplx<T>* ra;
+            const cplx<T>* rb;
+            if (b < np) {
+                ra = s0 + (long long)(r0 + 2 * b) * g.cpitch;
+                rb = 2 * b + 1 < rows ? ra + g.cpitch : nullptr;
+            } else {
+                ra = s0 + (long long)up * g.cpitch;
+                rb = s0 + (long long)dn * g.cpitch;
+            }
+            return row_pair_from_half_spectra<T>(ra, rb, N, g.nh, n);
+        };
+        const cplx<T>* tw = twpool + g.twx;
+        cplx<T>* res;
+        bool fast = false;
+        if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
+        if (fast) {
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np + 1, tw, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+                              __syncthreads();
+                              res = p2_smem_stages<T, NN, +1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np + 1, tw));
+        } else {
+            const DivMod dN(N);
+            for (int q = threadIdx.x; q < (np + 1) * N; q += blockDim.x) {
+                const int b = dN.div(q), n = q - b * N;
+                buf[b * ld + pad8(n)] = elem(b, n);
+            }
+            __syncthreads();
+            res = fft_batch<T>(buf, buf2, N, g.plan_x, np + 1, ld, tw, +1);
+        }
+        T* rx = reinterpret_cast<T*>(res);
+        T* a2s = reinterpret_cast<T*>(res == buf ? buf2 : buf);   // a^2 of the interior rows
+        const bool first = __ldg(&sp->cg_it) == 0;
+        const T bc = first ? T(0) : T(__ldg(&sp->betacg));
+        const T rnum = T(sqrt(__ldg(&sp->abar2) + 4.0 * __ldg(&sp->beta_t)));
+        const T b4 = T(4.0 * __ldg(&sp->beta_t));
+        const T bt = T(__ldg(&sp->beta_t));
+        const DivMod dN(N);
+        // p = D^-1/2 x + beta_cg p_old on rows -1 .. rows, in place; four
+        // elements per thread per round, loads issued before use
+        {
+            const int total_q = (rows + 2) * N;
+            for (int q0 = threadIdx.x; q0 < total_q; q0 += 4 * blockDim.x) {
+                T wv[4], pv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    wv[u] = pv[u] = T(0);
+                    if (q < total_q) {
+                        const int i = dN.div(q) - 1, n = q - (i + 1) * N;
+                        const int grow = i < 0 ? up : (i >= rows ? dn : r0 + i);
+                        const long long d = g.off + (long long)grow * g.pitch + n;
+                        wv[u] = a2[d];
+                        if (!first) pv[u] = pold[d];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * blockDim.x;
+                    if (q < total_q) {
+                        const int i = dN.div(q) - 1, n = q - (i + 1) * N;
+                        T* px = rx + pcg_row_slot(i, rows, np, ld) + 2 * pad8(n);
+                        *px = fma(bc, pv[u], *px * dscale(rnum, wv[u], b4));
+                        if (i >= 0 && i < rows) a2s[i * N + n] = wv[u];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // q = a^2 p + beta~ (4p - p_left - p_right - p_up - p_down), p.q
+        T acc = T(0);
+        for (int q = threadIdx.x; q < rows * N; q += blockDim.x) {
+            const int i = dN.div(q), n = q - i * N;
+            const T* row = rx + pcg_row_slot(i, rows, np, ld);
+            const T c = row[2 * pad8(n)];
+            const T l = row[2 * pad8(n == 0 ? N - 1 : n - 1)];
+            const T rr = row[2 * pad8(n == N - 1 ? 0 : n + 1)];
+            const T u = rx[pcg_row_slot(i - 1, rows, np, ld) + 2 * pad8(n)];
+            const T dw = rx[pcg_row_slot(i + 1, rows, np, ld) + 2 * pad8(n)];
+            const T lp = (T(4) * c - l - rr) - (u + dw);
+            const T qq = a2s[i * N + n] * c + bt * lp;
+            const long long d = g.off + (long long)(r0 + i) * g.pitch + n;
+            pnew[d] = c;
+            qo[d] = qq;
+            acc = fma(c, qq, acc);
+        }
+        double a[1] = {(double)acc};
+        block_sum<1>(a, red);
+        double tot[1];
+        if (item_reduce<1>(L, item, it.slice, a, tot, red)) {
+            SliceState& so = S[it.slice];
+            so.pq = tot[0];
+            so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
         }
         __syncthreads();
     }
@@ -828,116 +1185,6 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const S
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kStencilThreads) k_cg_matvec(ItemList L, const SliceGeom* G, SliceState* S,
-                                                               Ptrs<T> P, int par) {
-    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
-    __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
-    __shared__ double red[32];
-    __shared__ SliceGeom s_g;
-    const T* pold = P.f[par ? RECON_F_CG_P1 : RECON_F_CG_P0];
-    T* pnew = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
-    const T* yv = P.f[RECON_F_CG_Y];
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
-        const SliceState* sp = S + it.slice;
-        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
-        stage_struct(&s_g, G + it.slice);
-        __syncthreads();
-        const SliceGeom& g = s_g;
-        account(P.acct, KF_CG_MATVEC, tile_px<T>(g, it) * 5 * (long long)sizeof(T));
-        const bool first = __ldg(&sp->cg_it) == 0;
-        const T bc = first ? T(0) : T(__ldg(&sp->betacg));
-        // p = y + beta_cg p_old (p = y on the first step)
-        load_tile<T, 1>(
-            sm, g, it.a, it.b,
-            [&](long long d) { return Vals<T, 1>{{first ? yv[d] : yv[d] + bc * pold[d]}}; },
-            [&](long long d) {
-                Pack<T> y = ldv(yv, d);
-                if (!first) {
-                    const Pack<T> po = ldv(pold, d);
-#pragma unroll
-                    for (int e = 0; e < VN; ++e) y.v[e] += bc * po.v[e];
-                }
-                return PVals<T, 1>{{y}};
-            });
-        __syncthreads();
-        const T bt = T(__ldg(&sp->beta_t));
-        double acc[1] = {0.0};
-        T accT = T(0);
-        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
-            const Pack<T> a2 = ldv_n(P.f[RECON_F_A2], d, cnt);
-            Pack<T> pv, qv;
-#pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                const T p = sm[0][ly + 1][OFF + lx0 + e];
-                pv.v[e] = p;
-                qv.v[e] = a2.v[e] * p + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e);
-                if (e < cnt) accT = fma(p, qv.v[e], accT);
-            }
-            stv_n(pnew, d, pv, cnt);
-            stv_n(P.f[RECON_F_CG_Q], d, qv, cnt);
-        });
-        acc[0] = (double)accT;
-        block_sum<1>(acc, red);
-        double tot[1];
-        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
-            SliceState& so = S[it.slice];
-            so.pq = tot[0];
-            so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
-        }
-        __syncthreads();
-    }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kStencilThreads) k_cg_update(ItemList L, const SliceGeom* G, const SliceConst* C,
-                                                               SliceState* S, Ptrs<T> P, int par, int* pending) {
-    constexpr int VN = TileDim<T>::VN;
-    __shared__ double red[32];
-    __shared__ SliceGeom s_g;
-    const T* p = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
-        const SliceState* sp = S + it.slice;
-        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
-        stage_struct(&s_g, G + it.slice);
-        __syncthreads();
-        const SliceGeom& g = s_g;
-        account(P.acct, KF_CG_UPDATE, tile_px<T>(g, it) * 6 * (long long)sizeof(T));
-        const T al = T(__ldg(&sp->alpha));
-        double acc[1] = {0.0};
-        T accT = T(0);
-        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
-            Pack<T> z = ldv_n(P.f[RECON_F_Z], d, cnt), r = ldv_n(P.f[RECON_F_CG_R], d, cnt);
-            const Pack<T> pv = ldv_n(p, d, cnt), q = ldv_n(P.f[RECON_F_CG_Q], d, cnt);
-#pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                z.v[e] += al * pv.v[e];
-                r.v[e] -= al * q.v[e];
-                if (e < cnt) accT = fma(r.v[e], r.v[e], accT);
-            }
-            stv_n(P.f[RECON_F_Z], d, z, cnt);
-            stv_n(P.f[RECON_F_CG_R], d, r, cnt);
-        });
-        acc[0] = (double)accT;
-        block_sum<1>(acc, red);
-        double tot[1];
-        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
-            SliceState& so = S[it.slice];
-            const SliceConst& c = C[it.slice];
-            so.rr = tot[0];
-            so.cg_it += 1;
-            const bool conv = !(tot[0] > c.cg_tol * c.cg_tol * so.bb);
-            if (conv || so.cg_it >= c.cg_max) {
-                so.cg_done = 1;
-                atomicSub(pending, 1);
-            }
-        }
-        __syncthreads();
-    }
-}
-
 __global__ void k_next_beta(int n, const SliceConst* C, SliceState* S) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -1028,8 +1275,8 @@ template <typename T>
 int fft_smem_bytes(const Ctx& c) {
     int slots = 0;
     for (const SliceGeom& g : c.sg) {
-        const int r = g.rows_per_item * padded_len(g.nx);
-        const int q = g.cols_per_item * (padded_len(g.ny) | 1);
+        const int r = (g.rows_per_item + 1) * padded_len(g.nx);
+        const int q = g.cols_per_item * col_ld(g.ny);
         slots = r > slots ? r : slots;
         slots = q > slots ? q : slots;
     }
@@ -1042,33 +1289,25 @@ int fft_half_slots(const Ctx& c) {
 }
 
 template <typename T>
-int fft_solve(Ctx& c, const FftJobs& J, int mode) {
+int fft_solve(Ctx& c, const FftJobs& J) {
     const Ptrs<T> P = ptrs<T>(c);
     const int smem = fft_smem_bytes<T>(c);
-    const cplx<T>* buf = static_cast<const cplx<T>*>(c.d_tw);
+    const cplx<T>* tw = static_cast<const cplx<T>*>(c.d_tw);
     const int half = fft_half_slots<T>(c);
-    if (mode == 0) {
+    {
         FamTimer t(c, KF_ROWS_FWD);
-        k_rows_fwd<T, 0><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf, half);
-    } else {
-        FamTimer t(c, KF_ROWS_FWD_PRE);
-        k_rows_fwd<T, 1><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf, half);
+        k_rows_fwd<T><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
+                                                                                    c.d_state, P, J, tw, half);
     }
     {
-        FamTimer t(c, mode ? KF_COLS_PRE : KF_COLS);
+        FamTimer t(c, KF_COLS);
         k_cols<T><<<grid_for(c, c.cols.n * J.n), kFftThreads, smem, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
-                                                                               c.d_state, P, J, buf, half);
+                                                                               c.d_state, P, J, tw, half);
     }
-    if (mode == 0) {
+    {
         FamTimer t(c, KF_ROWS_INV);
-        k_rows_inv<T, 0><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf, half);
-    } else {
-        FamTimer t(c, KF_ROWS_INV_PRE);
-        k_rows_inv<T, 1><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
-                                                                                       c.d_state, P, J, buf, half);
+        k_rows_inv<T><<<grid_for(c, c.rows.n * J.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom,
+                                                                                    c.d_state, P, J, tw, half);
     }
     c.launches += 3;
     RECON_CUDA(cudaGetLastError());
@@ -1097,11 +1336,12 @@ int set_fft_smem(Ctx& c) {
                     smem = b > smem ? b : smem;
                 }
     }
-    RECON_CUDA(cudaFuncSetAttribute(k_rows_fwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    RECON_CUDA(cudaFuncSetAttribute(k_rows_fwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RECON_CUDA(cudaFuncSetAttribute(k_rows_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     RECON_CUDA(cudaFuncSetAttribute(k_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    RECON_CUDA(cudaFuncSetAttribute(k_rows_inv<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    RECON_CUDA(cudaFuncSetAttribute(k_rows_inv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RECON_CUDA(cudaFuncSetAttribute(k_rows_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RECON_CUDA(cudaFuncSetAttribute(k_pcg_fwd<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RECON_CUDA(cudaFuncSetAttribute(k_pcg_fwd<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    RECON_CUDA(cudaFuncSetAttribute(k_pcg_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     return RECON_OK;
 }
 
@@ -1138,13 +1378,13 @@ int op_solve_f(Ctx& c) {
         J.n = 2;
         J.in[0] = RECON_F_RHS_F1; J.spec[0] = 0; J.out[0] = RECON_F_F1; J.coef[0] = 0;
         J.in[1] = RECON_F_RHS_F2; J.spec[1] = 1; J.out[1] = RECON_F_F2; J.coef[1] = 1;
-        return fft_solve<T>(c, J, 0);
+        return fft_solve<T>(c, J);
     }
-    if ((rc = fft_solve<T>(c, jobs1(RECON_F_RHS_F1, 0, RECON_F_F1, 0), 0))) return rc;
+    if ((rc = fft_solve<T>(c, jobs1(RECON_F_RHS_F1, 0, RECON_F_F1, 0)))) return rc;
     k_gs_fix<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                          c.d_state, ptrs<T>(c));
     c.launches += 1;
-    return fft_solve<T>(c, jobs1(RECON_F_RHS_F2, 1, RECON_F_F2, 1), 0);
+    return fft_solve<T>(c, jobs1(RECON_F_RHS_F2, 1, RECON_F_F2, 1));
 }
 
 template <typename T>
@@ -1172,25 +1412,37 @@ int op_solve_z(Ctx& c) {
                                                                               c.d_state, P, c.d_cg_pending);
     }
     c.launches += 1;
+    const int smem = fft_smem_bytes<T>(c);
+    const cplx<T>* tw = static_cast<const cplx<T>*>(c.d_tw);
+    const int half = fft_half_slots<T>(c);
     const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 3);
-    rc = fft_solve<T>(c, pre, 1);
-    if (rc) return rc;
+    int par = c.cg_parity;
+    {
+        FamTimer t(c, KF_PCG_FWD);
+        k_pcg_fwd<T, false><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
+            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending);
+    }
+    c.launches += 1;
     int cap = 0;
     for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
-    int par = c.cg_parity;
     for (int it = 0; it < cap; ++it) {
         {
-            FamTimer t(c, KF_CG_MATVEC);
-            k_cg_matvec<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
-                                                                                    c.d_state, P, par);
+            FamTimer t(c, KF_COLS_PRE);
+            k_cols<T><<<grid_for(c, c.cols.n), kFftThreads, smem, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
+                                                                              c.d_state, P, pre, tw, half);
         }
         {
-            FamTimer t(c, KF_CG_UPDATE);
-            k_cg_update<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(
-                c.tiles.view(), c.d_geom, c.d_const, c.d_state, P, par, c.d_cg_pending);
+            FamTimer t(c, KF_PCG_INV);
+            k_pcg_inv<T><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom, c.d_state,
+                                                                                P, tw, half, par);
         }
-        c.launches += 2;
-        if ((rc = fft_solve<T>(c, pre, 1))) return rc;
+        {
+            FamTimer t(c, KF_PCG_FWD);
+            k_pcg_fwd<T, true><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
+                c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending);
+        }
+        c.launches += 3;
+        RECON_CUDA(cudaGetLastError());
         par ^= 1;
         if ((it & 3) == 3 || it == cap - 1) {
             RECON_CUDA(cudaMemcpyAsync(c.h_cg_pending, c.d_cg_pending, sizeof(int), cudaMemcpyDeviceToHost,
@@ -1218,7 +1470,7 @@ int iterate_t(Ctx& c, bool stats) {
     if ((rc = op_thr_rhs<T>(c, stats))) return rc;
     if ((rc = op_solve_f<T>(c))) return rc;
     if ((rc = op_synth<T>(c))) return rc;
-    if ((rc = fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2), 0))) return rc;
+    if ((rc = fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2)))) return rc;
     if ((rc = op_solve_z<T>(c))) return rc;
     return op_next_beta<T>(c);
 }
@@ -1259,7 +1511,7 @@ int op_t(Ctx& c, int op) {
         case RECON_OP_THRESH_RHS: return op_thr_rhs<T>(c, false);
         case RECON_OP_SOLVE_F: return op_solve_f<T>(c);
         case RECON_OP_SYNTH: return op_synth<T>(c);
-        case RECON_OP_SOLVE_RHO: return fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2), 0);
+        case RECON_OP_SOLVE_RHO: return fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2));
         case RECON_OP_SOLVE_Z: return op_solve_z<T>(c);
         case RECON_OP_NEXT_BETA: return op_next_beta<T>(c);
         default: set_error("unknown operator"); return RECON_EINVAL;
@@ -1285,7 +1537,7 @@ SliceConst slice_const(const recon_params& p, const Tables& t) {
 // slice, sized so one item's transforms fill about `budget` complex slots.
 int rows_per_item(int nx, int ny, int budget) {
     const int npairs = (ny + 1) / 2;
-    int per = budget / nx;
+    int per = budget / nx - 1;   // k_pcg_inv transforms one more pair (the halo rows)
     if (per < 1) per = 1;
     return per > npairs ? npairs : per;
 }
@@ -1299,8 +1551,8 @@ int cols_per_item(int nx, int ny, int budget) {
 
 // Complex slots of one FFT buffer for an nx x ny slice.
 int fft_item_slots(int nx, int ny, int budget) {
-    const int r = rows_per_item(nx, ny, budget) * padded_len(nx);
-    const int q = cols_per_item(nx, ny, budget) * (padded_len(ny) | 1);
+    const int r = (rows_per_item(nx, ny, budget) + 1) * padded_len(nx);
+    const int q = cols_per_item(nx, ny, budget) * col_ld(ny);
     return r > q ? r : q;
 }
 

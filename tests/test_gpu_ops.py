@@ -204,7 +204,8 @@ def test_gauss_seidel_operator(rc):
     close(s.read("F2"), ref2, 1e-5)
 
 
-@pytest.mark.parametrize("shape", [(512, 512), (320, 384), (448, 256), (2048, 6), (5, 2048), (3, 3)])
+@pytest.mark.parametrize("shape", [(512, 512), (320, 384), (448, 256), (2048, 6), (5, 2048), (3, 3),
+                                   (64, 1024), (1024, 128), (256, 64), (128, 512), (64, 63), (256, 45)])
 def test_fft_solve_sizes(rc, shape):
     nx, ny = shape
     s, tab = make(rc, nx, ny)
