@@ -241,6 +241,12 @@ __host__ __device__ inline int col_ld(int n) {
     return (is_pow2c(n) && n >= 64) ? padded_len(n) + 1 : (padded_len(n) | 1);
 }
 
+// Stage plan of a power-of-two length N.  Stage s > 0 multiplies leg r of
+// butterfly k (k < ns) by w^r, w = exp(-+2 pi i k / (ns R)).  Its twiddles
+// sit in a stage-major table that follows the N-entry table exp(-2 pi i t/N)
+// in the twiddle pool: for each stage s > 0, blocks of ns entries holding w,
+// w^2 and w^4 (as far as they are below R), contiguous in k; the butterfly
+// forms w^3, w^5, w^6, w^7 as products of two of them.
 template <int N>
 struct P2Plan {
     static constexpr int L = ilog2c(N);
@@ -249,6 +255,11 @@ struct P2Plan {
     static constexpr int S = N8 + (REM ? 1 : 0);          // stage count
     __host__ __device__ static constexpr int radix(int s) { return s < N8 ? 8 : (REM == 2 ? 4 : 2); }
     __host__ __device__ static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
+    // stored powers per butterfly (w, w^2, w^4 below R)
+    __host__ __device__ static constexpr int powers(int s) { return radix(s) == 8 ? 3 : (radix(s) == 4 ? 2 : 1); }
+    __host__ __device__ static constexpr int tw_off(int s) {
+        return s <= 1 ? 0 : tw_off(s - 1) + powers(s - 1) * ns(s - 1);
+    }
 };
 
 // Sources and destinations of a stage provide load_legs<R, NBF>(b, j, v)
@@ -337,7 +348,6 @@ __device__ __forceinline__ void p2_stage(int batch, const cplx<T>* __restrict__ 
     constexpr int R = P2Plan<N>::radix(STAGE);
     constexpr int NS = P2Plan<N>::ns(STAGE);
     constexpr int NBF = N / R;
-    constexpr int STEP = N / (NS * R);
     const int total = BFAST ? CB * NBF : batch * NBF;
 #pragma unroll 1
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
@@ -354,9 +364,28 @@ __device__ __forceinline__ void p2_stage(int batch, const cplx<T>* __restrict__ 
         src.template load_legs<R, NBF>(b, j, v);
         const int k = j & (NS - 1);
         if constexpr (NS > 1) {
-            const int ks = k * STEP;
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul_dir<T, DIR>(v[r], tw[r * ks]);
+            const cplx<T>* t = tw + P2Plan<N>::tw_off(STAGE) + k;
+            const cplx<T> w1 = t[0];
+            if constexpr (R == 2) {
+                v[1] = cmul_dir<T, DIR>(v[1], w1);
+            } else {
+                const cplx<T> w2 = t[NS];
+                if constexpr (R == 4) {
+                    v[1] = cmul_dir<T, DIR>(v[1], w1);
+                    v[2] = cmul_dir<T, DIR>(v[2], w2);
+                    v[3] = cmul_dir<T, DIR>(v[3], cmul(w1, w2));
+                } else {
+                    const cplx<T> w4 = t[2 * NS];
+                    const cplx<T> w3 = cmul(w1, w2);
+                    v[1] = cmul_dir<T, DIR>(v[1], w1);
+                    v[2] = cmul_dir<T, DIR>(v[2], w2);
+                    v[3] = cmul_dir<T, DIR>(v[3], w3);
+                    v[4] = cmul_dir<T, DIR>(v[4], w4);
+                    v[5] = cmul_dir<T, DIR>(v[5], cmul(w1, w4));
+                    v[6] = cmul_dir<T, DIR>(v[6], cmul(w2, w4));
+                    v[7] = cmul_dir<T, DIR>(v[7], cmul(w3, w4));
+                }
+            }
         }
         dft<T, R>(v, DIR);
         dst.template store_legs<R, NS>(b, (j >> ilog2c(NS)) * NS * R + k, v);

@@ -471,9 +471,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_fwd(ItemLis
         bool fast = false;
         if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
         if (fast) {
-            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw + NN, fn_load<T>(elem), SmemSeq<T>{buf, ld});
                               __syncthreads();
-                              res = p2_smem_stages<T, NN, -1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np, tw));
+                              res = p2_smem_stages<T, NN, -1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np, tw + NN));
         } else {
             // four elements per thread per round, loads issued before use
             const DivMod dN(N);
@@ -522,9 +522,9 @@ __device__ __forceinline__ void cols_item_p2(cplx<T>* spc, int cpitch, int nc, i
     constexpr int CB = E > 16 ? 16 : (E < 1 ? 1 : E);
     const int ld = col_ld(N);
     auto gload = [&](int b, int y) -> cplx<T> { return spc[(long long)y * cpitch + b]; };
-    p2_stage<T, N, 0, -1, true, CB>(nc, tw, fn_load<T>(gload), SmemSeq<T>{buf0, ld});
+    p2_stage<T, N, 0, -1, true, CB>(nc, tw + N, fn_load<T>(gload), SmemSeq<T>{buf0, ld});
     __syncthreads();
-    cplx<T>* cur = p2_smem_stages<T, N, -1, 1, S - 2>(buf0, buf1, ld, nc, tw);
+    cplx<T>* cur = p2_smem_stages<T, N, -1, 1, S - 2>(buf0, buf1, ld, nc, tw + N);
     cplx<T>* oth = cur == buf0 ? buf1 : buf0;
     // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
     auto divide = [&](int b, int ky, cplx<T> v) {
@@ -536,11 +536,11 @@ __device__ __forceinline__ void cols_item_p2(cplx<T>* spc, int cpitch, int nc, i
         }
         oth[b * ld + pad8(ky)] = {v.x * sc, v.y * sc};
     };
-    p2_stage<T, N, S - 1, -1, false, 1>(nc, tw, SmemSeq<T>{cur, ld}, fn_store<T>(divide));
+    p2_stage<T, N, S - 1, -1, false, 1>(nc, tw + N, SmemSeq<T>{cur, ld}, fn_store<T>(divide));
     __syncthreads();
-    cur = p2_smem_stages<T, N, +1, 0, S - 2>(oth, cur, ld, nc, tw);
+    cur = p2_smem_stages<T, N, +1, 0, S - 2>(oth, cur, ld, nc, tw + N);
     auto gstore = [&](int b, int y, cplx<T> v) { spc[(long long)y * cpitch + b] = v; };
-    p2_stage<T, N, S - 1, +1, true, CB>(nc, tw, SmemSeq<T>{cur, ld}, fn_store<T>(gstore));
+    p2_stage<T, N, S - 1, +1, true, CB>(nc, tw + N, SmemSeq<T>{cur, ld}, fn_store<T>(gstore));
     __syncthreads();
 }
 
@@ -689,10 +689,10 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_inv(ItemLis
         bool fast = false;
         if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
         if (fast) {
-            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np, tw, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np, tw + NN, fn_load<T>(elem), SmemSeq<T>{buf, ld});
                               __syncthreads();
-                              cplx<T>* cur = p2_smem_stages<T, NN, +1, 1, P2Plan<NN>::S - 2>(buf, buf2, ld, np, tw);
-                              p2_stage<T, NN, P2Plan<NN>::S - 1, +1, false, 1>(np, tw, SmemSeq<T>{cur, ld},
+                              cplx<T>* cur = p2_smem_stages<T, NN, +1, 1, P2Plan<NN>::S - 2>(buf, buf2, ld, np, tw + NN);
+                              p2_stage<T, NN, P2Plan<NN>::S - 1, +1, false, 1>(np, tw + NN, SmemSeq<T>{cur, ld},
                                                                               fn_store<T>(put)));
         } else {
             const DivMod dN(N);
@@ -855,9 +855,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_fwd(ItemList
         bool fast = false;
         if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
         if (fast) {
-            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw, src, SmemSeq<T>{buf, ld});
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw + NN, src, SmemSeq<T>{buf, ld});
                               __syncthreads();
-                              res = p2_smem_stages<T, NN, -1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np, tw));
+                              res = p2_smem_stages<T, NN, -1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np, tw + NN));
         } else {
             const DivMod dN(N);
             for (int q = threadIdx.x; q < np * N; q += blockDim.x) {
@@ -906,6 +906,79 @@ __device__ __forceinline__ int pcg_row_slot(int i, int rows, int np, int ld) {
     return 2 * b * ld + comp;   // in scalars; add 2 * pad8(n)
 }
 
+// Tail of a k_pcg_inv item for a power-of-two row length N (FP32), four
+// pixels per task with 16-byte loads and stores: p = D^-1/2 x + beta_cg p_old
+// on rows -1 .. rows in place (x in `rx`, interleaved as the transforms left
+// it), a^2 of the item's rows staged in `a2s`, then q = M p on the item's
+// rows; returns this thread's share of p.q.
+template <int N>
+__device__ __forceinline__ float pcg_inv_tail_p2(float* rx, float* a2s, int ld, int np, int rows, int r0, int up,
+                                                 int dn, long long off, int pitch, const float* __restrict__ a2,
+                                                 const float* __restrict__ pold, float* __restrict__ pnew,
+                                                 float* __restrict__ qo, bool first, float bc, float rnum, float b4,
+                                                 float bt) {
+    constexpr int NV = N / 4, LNV = ilog2c(NV);
+    {
+        const int total = (rows + 2) * NV;
+        for (int t0 = threadIdx.x; t0 < total; t0 += 4 * blockDim.x) {
+            float4 wv[4], pv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * blockDim.x;
+                wv[u] = pv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t < total) {
+                    const int i = (t >> LNV) - 1, n0 = (t & (NV - 1)) * 4;
+                    const int grow = i < 0 ? up : (i >= rows ? dn : r0 + i);
+                    const long long d = off + (long long)grow * pitch + n0;
+                    wv[u] = *reinterpret_cast<const float4*>(a2 + d);
+                    if (!first) pv[u] = *reinterpret_cast<const float4*>(pold + d);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int t = t0 + u * blockDim.x;
+                if (t < total) {
+                    const int i = (t >> LNV) - 1, n0 = (t & (NV - 1)) * 4;
+                    float* px = rx + pcg_row_slot(i, rows, np, ld) + 2 * pad8(n0);   // n0 % 4 == 0: legs at +2e
+                    px[0] = fmaf(bc, pv[u].x, px[0] * dscale(rnum, wv[u].x, b4));
+                    px[2] = fmaf(bc, pv[u].y, px[2] * dscale(rnum, wv[u].y, b4));
+                    px[4] = fmaf(bc, pv[u].z, px[4] * dscale(rnum, wv[u].z, b4));
+                    px[6] = fmaf(bc, pv[u].w, px[6] * dscale(rnum, wv[u].w, b4));
+                    if (i >= 0 && i < rows) *reinterpret_cast<float4*>(a2s + i * N + n0) = wv[u];
+                }
+            }
+        }
+    }
+    __syncthreads();
+    float acc = 0.f;
+    const int total = rows * NV;
+    for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int i = t >> LNV, n0 = (t & (NV - 1)) * 4;
+        const float* row = rx + pcg_row_slot(i, rows, np, ld);
+        const float* rup = rx + pcg_row_slot(i - 1, rows, np, ld);
+        const float* rdn = rx + pcg_row_slot(i + 1, rows, np, ld);
+        const int o = 2 * pad8(n0);
+        const float c[4] = {row[o], row[o + 2], row[o + 4], row[o + 6]};
+        const float lf = row[2 * pad8(n0 == 0 ? N - 1 : n0 - 1)];
+        const float rt = row[2 * pad8(n0 + 4 == N ? 0 : n0 + 4)];
+        const float4 w4 = *reinterpret_cast<const float4*>(a2s + i * N + n0);
+        const float w[4] = {w4.x, w4.y, w4.z, w4.w};
+        float q[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float l = e == 0 ? lf : c[e - 1];
+            const float r = e == 3 ? rt : c[e + 1];
+            const float lp = (4.f * c[e] - l - r) - (rup[o + 2 * e] + rdn[o + 2 * e]);
+            q[e] = w[e] * c[e] + bt * lp;
+            acc = fmaf(c[e], q[e], acc);
+        }
+        const long long d = off + (long long)(r0 + i) * pitch + n0;
+        *reinterpret_cast<float4*>(pnew + d) = make_float4(c[0], c[1], c[2], c[3]);
+        *reinterpret_cast<float4*>(qo + d) = make_float4(q[0], q[1], q[2], q[3]);
+    }
+    return acc;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList L, const SliceGeom* G, SliceState* S,
                                                                         Ptrs<T> P, const cplx<T>* twpool, int half,
@@ -946,9 +1019,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
         bool fast = false;
         if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
         if (fast) {
-            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np + 1, tw, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np + 1, tw + NN, fn_load<T>(elem), SmemSeq<T>{buf, ld});
                               __syncthreads();
-                              res = p2_smem_stages<T, NN, +1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np + 1, tw));
+                              res = p2_smem_stages<T, NN, +1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np + 1, tw + NN));
         } else {
             const DivMod dN(N);
             for (int q = threadIdx.x; q < (np + 1) * N; q += blockDim.x) {
@@ -965,6 +1038,23 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
         const T rnum = T(sqrt(__ldg(&sp->abar2) + 4.0 * __ldg(&sp->beta_t)));
         const T b4 = T(4.0 * __ldg(&sp->beta_t));
         const T bt = T(__ldg(&sp->beta_t));
+        if constexpr (std::is_same<T, float>::value) {
+            if (fast) {
+                T acc = T(0);
+                RECON_P2_DISPATCH(N, acc = pcg_inv_tail_p2<NN>(rx, a2s, ld, np, rows, r0, up, dn, g.off, g.pitch, a2,
+                                                               pold, pnew, qo, first, bc, rnum, b4, bt));
+                double a[1] = {(double)acc};
+                block_sum<1>(a, red);
+                double tot[1];
+                if (item_reduce<1>(L, item, it.slice, a, tot, red)) {
+                    SliceState& so = S[it.slice];
+                    so.pq = tot[0];
+                    so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
+                }
+                __syncthreads();
+                continue;
+            }
+        }
         const DivMod dN(N);
         // p = D^-1/2 x + beta_cg p_old on rows -1 .. rows, in place; four
         // elements per thread per round, loads issued before use
@@ -1280,6 +1370,7 @@ int fft_smem_bytes(const Ctx& c) {
         slots = r > slots ? r : slots;
         slots = q > slots ? q : slots;
     }
+    slots = (slots + 1) & ~1;   // the second buffer starts on a 16-byte boundary
     return 2 * slots * (int)sizeof(cplx<T>);
 }
 
@@ -1332,7 +1423,7 @@ int set_fft_smem(Ctx& c) {
         for (int nx : sz)
             for (int ny : sz)
                 if (nx <= c.cap_nx && ny <= c.cap_ny) {
-                    const int b = 2 * fft_item_slots(nx, ny, FftBudget<T>::E) * (int)sizeof(cplx<T>);
+                    const int b = 2 * ((fft_item_slots(nx, ny, FftBudget<T>::E) + 1) & ~1) * (int)sizeof(cplx<T>);
                     smem = b > smem ? b : smem;
                 }
     }
@@ -1661,6 +1752,27 @@ int solver_setup(Ctx& c) {
                 tw.push_back(-std::sin(a));
                 const double sn = std::sin(M_PI * (double)t / (double)n);
                 sym.push_back(4.0 * sn * sn);
+            }
+            // compile-time power-of-two transforms: stage-major table after
+            // the N entries (layout of P2Plan in fft.cuh)
+            if (n >= 64 && n <= 1024 && (n & (n - 1)) == 0) {
+                int l = 0;
+                while ((1 << l) < n) ++l;
+                const int n8 = l / 3, rem = l - 3 * n8, stages = n8 + (rem ? 1 : 0);
+                int ns = 1;
+                for (int st = 0; st < stages; ++st) {
+                    const int R = st < n8 ? 8 : (rem == 2 ? 4 : 2);
+                    if (st > 0)
+                        for (int m : {1, 2, 4}) {
+                            if (m >= R) break;
+                            for (int k = 0; k < ns; ++k) {
+                                const double a = 2.0 * M_PI * (double)(m * k) / (double)(ns * R);
+                                tw.push_back(std::cos(a));
+                                tw.push_back(-std::sin(a));
+                            }
+                        }
+                    ns *= R;
+                }
             }
             have.push_back({n, {off, soff}});
             return {off, soff};
