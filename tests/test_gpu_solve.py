@@ -2,19 +2,15 @@
 the C ABI, on the 128^2 workload (disc phantom, mono 60/90 keV, 180 views,
 192 bins, Poisson noise at I0 = 1e5, 50 iterations).
 
-Final-map tolerances over the body (truth rho_e >= 0.1).  FP64 path: mean
-|dZ| <= 0.01 and mean |d rho_e| <= 1e-3.  FP32 path: median |dZ| <= 0.01,
-mean |dZ| <= 0.02, at most 1 % of the pixels with |dZ| > 0.1, mean
-|d rho_e| <= 1e-3.  The GPU's Z^m step is a PCG to a relative residual of
-1e-6 while the oracle solves it exactly.  In FP32, Z^m is ill-conditioned
-(the photoelectric share of mu is small, so a = m1 P2 - m2 P1 cancels) and
-L0 thresholding (eq. sol_hv) is discontinuous: a gradient within rounding
-of the threshold can fall on the other side, and at large beta~ the
-near-Poisson solves spread that change over the slice.  One-ulp
-perturbations of the inputs move the FP32 result's mean |dZ| between 9e-4
-and 6e-3 on the 64^2 smoke case while the FP64 oracle moves by 1e-6, so the
-FP32 bounds sit above that spread and far below the O(0.1-1) error of a
-broken operator; the operator tests check each step element by element."""
+Final-map tolerances over the body (truth rho_e >= 0.1), both precisions:
+mean |dZ| <= 0.01 and mean |d rho_e| <= 1e-3, with the 99.9th percentile,
+the median and the count of pixels with |dZ| > 0.1 reported.  The GPU's Z^m
+step is a PCG to a relative residual of 1e-6 while the oracle solves it
+exactly, and L0 thresholding (eq. sol_hv) is discontinuous: in FP32 a
+gradient within rounding of the threshold can fall on the other side, and at
+large beta~ the near-Poisson solves spread that change over the slice.  So
+the iterates are compared on these statistics, not element by element; the
+operator tests check each step element by element."""
 import numpy as np
 import pytest
 
@@ -47,7 +43,7 @@ def report(tag, Z, rho, ref, body):
     dZ = np.abs(Z - ref["Z"])
     dr = np.abs(rho - ref["rhoe"])
     out = dict(mean_dZ=float(dZ[body].mean()), median_dZ=float(np.median(dZ[body])),
-               frac_dZ_gt_01=float((dZ[body] > 0.1).mean()), mean_drho=float(dr[body].mean()),
+               n_dZ_gt_01=int((dZ[body] > 0.1).sum()), mean_drho=float(dr[body].mean()),
                p999_dZ=float(np.percentile(dZ[body], 99.9)), p999_drho=float(np.percentile(dr[body], 99.9)),
                mean_dZ_all=float(dZ.mean()), mean_drho_all=float(dr.mean()))
     print(tag, out)
@@ -55,10 +51,7 @@ def report(tag, Z, rho, ref, body):
 
 
 def parity_ok(r, precision=1):
-    if precision == 0:
-        return r["mean_dZ"] <= 0.01 and r["mean_drho"] <= 1e-3
-    return (r["median_dZ"] <= 0.01 and r["mean_dZ"] <= 0.02 and r["frac_dZ_gt_01"] <= 0.01
-            and r["mean_drho"] <= 1e-3)
+    return r["mean_dZ"] <= 0.01 and r["mean_drho"] <= 1e-3
 
 
 @pytest.mark.parametrize("precision", [1, 0])
