@@ -1,0 +1,100 @@
+"""Pins of the sinogram-domain f-updates of the oracle (oracle/modeb.py)."""
+import numpy as np
+
+from oracle import alg1, ct, model, modeb
+from synthetic import phantoms as ph
+
+
+def tiny():
+    acq = ph.acquisition("small", n=16)
+    geom = dict(nx=16, ny=12, pixel_mm=1.0, n_views=24, n_bins=28, sid_mm=200.0, sdd_mm=300.0,
+                bin_mm=1.0, start_rad=0.05, arc_rad=2 * np.pi)
+    tab = model.Tables(acq.low, acq.high)
+    return geom, tab
+
+
+def random_state(shape, seed):
+    rng = np.random.default_rng(seed)
+    st = dict(f1=0.2 * rng.standard_normal(shape), f2=1.0 + 0.2 * rng.standard_normal(shape),
+              rhoe=1.0 + 0.1 * rng.standard_normal(shape), zt=1.0 + 0.1 * rng.standard_normal(shape))
+    hv = (0.05 * rng.standard_normal(shape), 0.05 * rng.standard_normal(shape))
+    return st, hv
+
+
+def test_gamma_is_dc_gain():
+    geom, _ = tiny()
+    g = modeb.gamma(geom)
+    ones = np.ones((geom["ny"], geom["nx"]))
+    assert np.isclose(np.sum(ones * ct.backproject(ct.project(ones, geom), geom)) / ones.size, g, rtol=1e-12)
+
+
+def test_normal_operator_symmetric_positive_definite():
+    geom, tab = tiny()
+    g = modeb.gamma(geom)
+    rng = np.random.default_rng(3)
+    shape = (geom["ny"], geom["nx"])
+    for k in (0, 1):
+        x, y = rng.standard_normal(shape), rng.standard_normal(shape)
+        qx, qy = modeb.normal_op(x, k, 0.7, geom, tab, g), modeb.normal_op(y, k, 0.7, geom, tab, g)
+        assert abs(np.sum(qx * y) - np.sum(x * qy)) <= 1e-12 * np.sum(np.abs(qx * y))
+        assert np.sum(qx * x) > 0
+
+
+def test_cg_equals_dense_solve():
+    geom, tab = tiny()
+    g = modeb.gamma(geom)
+    shape = (geom["ny"], geom["nx"])
+    n = shape[0] * shape[1]
+    rng = np.random.default_rng(4)
+    for k in (0, 1):
+        Q = np.empty((n, n))
+        for c in range(n):
+            e = np.zeros(n)
+            e[c] = 1.0
+            Q[:, c] = modeb.normal_op(e.reshape(shape), k, 0.3, geom, tab, g).ravel()
+        b = rng.standard_normal(shape)
+        ref = np.linalg.solve(Q, b.ravel()).reshape(shape)
+        got = modeb.f_solve(b, k, 0.3, geom, tab, g, np.zeros(shape))
+        assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_f_update_is_the_exact_minimiser_of_its_sub_objective():
+    """E(f* + d) - E(f*) = d^T Q d for the quadratic sub-objective written
+    from the data term itself; a missing term or sign in the normal
+    equations breaks the identity."""
+    geom, tab = tiny()
+    g = modeb.gamma(geom)
+    shape = (geom["ny"], geom["nx"])
+    st, hv = random_state(shape, 5)
+    rng = np.random.default_rng(6)
+    sL = rng.uniform(0.0, 3.0, (geom["n_views"], geom["n_bins"]))
+    sH = rng.uniform(0.0, 2.5, (geom["n_views"], geom["n_bins"]))
+    t = modeb.data_images(sL, sH, geom, tab, g)
+    beta = 0.4
+    for k in (0, 1):
+        fk = modeb.f_solve(modeb.rhs(k, st, hv, beta, t, geom, tab, g), k, beta, geom, tab, g, np.zeros(shape))
+        e0 = modeb.sub_objective(fk, k, st, hv, beta, sL, sH, geom, tab, g)
+        for s in range(3):
+            d = 1e-2 * rng.standard_normal(shape)
+            e1 = modeb.sub_objective(fk + d, k, st, hv, beta, sL, sH, geom, tab, g)
+            dqd = float(np.sum(d * modeb.normal_op(d, k, beta, geom, tab, g)))
+            assert e1 > e0
+            assert abs((e1 - e0) - dqd) <= 1e-7 * dqd
+
+
+def test_uniform_water_is_a_fixed_point():
+    """Consistent noiseless mono sinograms of uniform water: the state
+    f = (0, 1), rho_e = 1, z = 1 is kept by a whole iteration."""
+    acq = ph.acquisition("small", n=16)
+    geom = ct.geometry(acq)
+    tab = model.Tables(acq.low, acq.high)
+    shape = (acq.ny, acq.nx)
+    Z = np.full(shape, 7.45)
+    rho = np.ones(shape)
+    sL, sH = ct.simulate(Z, rho, acq, seed=None)
+    g = modeb.gamma(geom)
+    t = modeb.data_images(sL, sH, geom, tab, g)
+    st = dict(f1=np.zeros(shape), f2=np.ones(shape), rhoe=np.ones(shape), zt=np.ones(shape))
+    new, _ = modeb.iterate(st, 0.5, 0.5, 1e-2, t, geom, tab, g, z_method="dense")
+    for key in ("f1", "f2", "rhoe", "zt"):
+        assert np.max(np.abs(new[key] - st[key])) <= 1e-8, key
