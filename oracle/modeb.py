@@ -26,11 +26,14 @@ whose normal equations are
           + sum_j b_kj (rho_e (P_j z + psi_j) - f_o b_oj) + beta (dx^T h + dy^T v),
 
 alpha_k = sum_i a_ki^2, c'_k = sum_j b_kj^2, t_k = A^T (sum_i a_ki s_i / S) / gamma.
-The oracle solves them by conjugate gradients to a relative residual of 1e-12
-(dense solve on tiny grids in the tests).  The solve starts from the FBP
-image pair as in the image-domain mode.
+The oracle solves them by conjugate gradients, preconditioned by the FFT
+solve (alpha_k + c'_k + beta K)^-1, to a relative residual of 1e-12 (dense
+solve on tiny grids in the tests).  A and A^T are applied as one sparse
+matrix per geometry holding the Joseph weights of oracle/ct.py.  The solve
+starts from the FBP image pair as in the image-domain mode.
 
-Pins (tests/test_oracle_modeb.py): the normal operator is symmetric positive
+Pins (tests/test_oracle_modeb.py): the sparse matrix reproduces ct.project
+and ct.backproject; the normal operator is symmetric positive
 definite (adjoint identity of A); the CG solve equals a dense solve of the
 same system and minimises the f_k sub-objective under random perturbations;
 a uniform material with consistent noiseless data is a fixed point of a
@@ -39,14 +42,42 @@ whole iteration.
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 
 from . import alg1, ct, model
+
+_matrices = {}
+
+
+def matrix(geom):
+    """A as a sparse (rays x pixels) matrix of the Joseph weights of
+    oracle/ct.py (repeated (ray, pixel) pairs summed), cached per geometry."""
+    key = tuple(sorted((k, float(v)) for k, v in geom.items()))
+    if key not in _matrices:
+        rows, cols, vals = [], [], []
+        for ray, pix, w in ct._joseph_samples(geom):
+            rows.append(ray)
+            cols.append(pix)
+            vals.append(w)
+        shape = (geom["n_views"] * geom["n_bins"], geom["nx"] * geom["ny"])
+        A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=shape)
+        A.sum_duplicates()
+        _matrices[key] = A
+    return _matrices[key]
+
+
+def project(x, geom):
+    return (matrix(geom) @ np.asarray(x, np.float64).ravel()).reshape(geom["n_views"], geom["n_bins"])
+
+
+def backproject(y, geom):
+    return (matrix(geom).T @ np.asarray(y, np.float64).ravel()).reshape(geom["ny"], geom["nx"])
 
 
 def gamma(geom):
     """||A 1||^2 / n_pixels (reading R17)."""
     ones = np.ones((geom["ny"], geom["nx"]))
-    p = ct.project(ones, geom)
+    p = project(ones, geom)
     return float(np.sum(p * p) / ones.size)
 
 
@@ -54,14 +85,21 @@ def data_images(sL, sH, geom, tab, g):
     """t_k = A^T (sum_i a_ki s_i / S) / gamma, k = 0, 1."""
     hL = np.asarray(sL, np.float64) / model.S_MM
     hH = np.asarray(sH, np.float64) / model.S_MM
-    return [ct.backproject(tab.a[k, 0] * hL + tab.a[k, 1] * hH, geom) / g for k in (0, 1)]
+    return [backproject(tab.a[k, 0] * hL + tab.a[k, 1] * hH, geom) / g for k in (0, 1)]
+
+
+def coefficients(k, tab):
+    """(alpha_k, c'_k, cross) of the f_k normal equations."""
+    alpha = tab.a[k, 0] ** 2 + tab.a[k, 1] ** 2
+    cp = tab.b[k, 0] ** 2 + tab.b[k, 1] ** 2
+    cross = tab.a[0, 0] * tab.a[1, 0] + tab.a[0, 1] * tab.a[1, 1]
+    return alpha, cp, cross
 
 
 def normal_op(x, k, beta, geom, tab, g):
     """[alpha_k A^T A / gamma + c'_k + beta (dx^T dx + dy^T dy)] x."""
-    alpha = tab.a[k, 0] ** 2 + tab.a[k, 1] ** 2
-    cp = tab.b[k, 0] ** 2 + tab.b[k, 1] ** 2
-    return alpha * ct.backproject(ct.project(x, geom), geom) / g + cp * x + beta * alg1.laplacian(x)
+    alpha, cp, _ = coefficients(k, tab)
+    return alpha * backproject(project(x, geom), geom) / g + cp * x + beta * alg1.laplacian(x)
 
 
 def rhs(k, st, hv, beta, t, geom, tab, g):
@@ -72,28 +110,33 @@ def rhs(k, st, hv, beta, t, geom, tab, g):
     M1, M2 = alg1.model_eval(st["rhoe"], st["zt"], tab)
     mod = tab.b[k, 0] * (M1 - fo * tab.b[o, 0]) + tab.b[k, 1] * (M2 - fo * tab.b[o, 1])
     h, v = hv
-    return t[k] - cross * ct.backproject(ct.project(fo, geom), geom) / g + mod + beta * alg1.adjoint_diff(h, v)
+    return t[k] - cross * backproject(project(fo, geom), geom) / g + mod + beta * alg1.adjoint_diff(h, v)
 
 
 def f_solve(b, k, beta, geom, tab, g, x0, tol=1e-12, max_iter=2000):
-    """Conjugate gradients on the f_k normal equations from x0."""
+    """Preconditioned conjugate gradients on the f_k normal equations from
+    x0, preconditioner (alpha_k + c'_k + beta K)^-1 by FFT, stopping at
+    ||r|| <= tol ||b||."""
+    alpha, cp, _ = coefficients(k, tab)
     x = np.array(x0, dtype=np.float64)
     r = b - normal_op(x, k, beta, geom, tab, g)
     bb = float(np.sum(b * b))
     if bb == 0.0:
         return np.zeros_like(x)
-    p = r.copy()
-    rr = float(np.sum(r * r))
+    y = alg1.fft_solve(r, alpha + cp, beta)
+    p = y.copy()
+    ry = float(np.sum(r * y))
     for _ in range(max_iter):
-        if rr <= tol * tol * bb:
+        if float(np.sum(r * r)) <= tol * tol * bb:
             break
         q = normal_op(p, k, beta, geom, tab, g)
-        a = rr / float(np.sum(p * q))
+        a = ry / float(np.sum(p * q))
         x += a * p
         r -= a * q
-        rr_new = float(np.sum(r * r))
-        p = r + (rr_new / rr) * p
-        rr = rr_new
+        y = alg1.fft_solve(r, alpha + cp, beta)
+        ry_new = float(np.sum(r * y))
+        p = y + (ry_new / ry) * p
+        ry = ry_new
     return x
 
 

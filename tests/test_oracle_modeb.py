@@ -21,6 +21,16 @@ def random_state(shape, seed):
     return st, hv
 
 
+def test_sparse_matrix_reproduces_projector():
+    geom, _ = tiny()
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((geom["ny"], geom["nx"]))
+    y = rng.standard_normal((geom["n_views"], geom["n_bins"]))
+    px, bx = ct.project(x, geom), ct.backproject(y, geom)
+    assert np.max(np.abs(modeb.project(x, geom) - px)) <= 1e-12 * np.max(np.abs(px))
+    assert np.max(np.abs(modeb.backproject(y, geom) - bx)) <= 1e-12 * np.max(np.abs(bx))
+
+
 def test_gamma_is_dc_gain():
     geom, _ = tiny()
     g = modeb.gamma(geom)
