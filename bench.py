@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", choices=["volume", "clinical", "uneven", "small", "serving"], default="volume")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (slices/s)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg of the default line")
+    ap.add_argument("--domain", choices=["image", "sino"], default="image",
+                    help="data terms on the FBP image pair (as printed) or on the sinograms through the projector")
     ap.add_argument("--slices", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--precision", type=int, default=1)
@@ -119,6 +121,9 @@ def make_scans(rc, torch, slices, seed):
 # ---------------------------------------------------------------------------
 # roofline denominators and ncu traffic
 # ---------------------------------------------------------------------------
+
+L2_BYTES = 129 * 1024 * 1024   # GB300 L2
+
 
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -273,15 +278,25 @@ class ClockSampler:
 # reference arm: the CPU FP64 oracle
 # ---------------------------------------------------------------------------
 
-def oracle_sample(slices, iters_sample):
+def oracle_sample(slices, iters_sample, domain="image"):
     """Time the oracle on one slice of the workload for a bounded number of
-    iterations (image-domain inputs made by the oracle's own model)."""
+    iterations (image-domain inputs made by the oracle's own model; with
+    domain "sino", noisy sinograms from the oracle's scan model and the
+    sinogram-domain f updates)."""
     from oracle import alg1, model
     from synthetic import phantoms as ph
     Z, rho, acq = slices[0]
     Z = np.asarray(Z, np.float64)
     rho = np.asarray(rho, np.float64)
     ny, nx = Z.shape
+    if domain == "sino":
+        from oracle import ct, modeb
+        sL, sH = ct.simulate(Z, rho, acq, seed=77)
+        tab = model.Tables(acq.low, acq.high)
+        t0 = time.perf_counter()
+        modeb.solve(sL, sH, ct.geometry(acq), tab, alg1.Params(iters=iters_sample))
+        dt = time.perf_counter() - t0
+        return dict(value=iters_sample / dt, seconds=dt, nx=nx, ny=ny, iters=iters_sample)
     E = [model.spectrum_bins(s) for s in (acq.low, acq.high)]
     mus = []
     for k, (Eb, wb) in enumerate(E):
@@ -312,10 +327,10 @@ def run_reference(args, rank, world):
     it = 3 if nx >= 512 else 10
     vals = []
     for _ in range(args.warmup):
-        oracle_sample(slices, 1)
+        oracle_sample(slices, 1, args.domain)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        vals.append(oracle_sample(slices, it)["value"])
+        vals.append(oracle_sample(slices, it, args.domain)["value"])
     dt = time.perf_counter() - t0
     value = float(np.mean(vals))
     cores = cpu_cores_used()
@@ -368,7 +383,8 @@ def main():
     slices, iters, name = workload(args, rank)
     sino_lo, sino_hi = make_scans(rc, torch, slices, seed=4242 + rank)
     geoms = [rc.geometry_from_acq(acq) for _, _, acq in slices]
-    params = [rc.default_params(low=acq.low, high=acq.high, iters=iters, precision=args.precision)
+    params = [rc.default_params(low=acq.low, high=acq.high, iters=iters, precision=args.precision,
+                                domain=1 if args.domain == "sino" else 0)
               for _, _, acq in slices]
     solver = rc.Solver(geoms, params)
     npx = sum(g.nx * g.ny for g in geoms)
@@ -408,16 +424,36 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     l0 = solver.launches()
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
+    # device working set: 18 maps and 3 half spectra per slice, plus the sinograms
+    elem = 4 if args.precision == 1 else 8
+    work_bytes = sum(elem * g.ny * (-(-g.nx // 32) * 32) * 18 + 2 * elem * g.ny * (-(-(g.nx // 2 + 1) // 16) * 16) * 3
+                     for g in geoms) + 4 * (sino_lo.numel() + sino_hi.numel())
+    flush = work_bytes < 2 * L2_BYTES
+    flush_buf = torch.empty(4 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if flush else None
     barrier()
-    t_start.record()
-    for _ in range(args.steps):
-        step()
-    t_end.record()
-    barrier()
+    if not flush:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record()
+        for _ in range(args.steps):
+            step()
+        t_end.record()
+        barrier()
+        ms = t_start.elapsed_time(t_end)
+    else:
+        # working set within L2: each step timed alone after overwriting a buffer 4x the L2
+        ms = 0.0
+        for _ in range(args.steps):
+            flush_buf.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            step()
+            b.record()
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        barrier()
     clk = clocks.stop()
-    ms = t_start.elapsed_time(t_end)
     launches = (solver.launches() - l0) // args.steps
     dom_ms, dom_launches, dom_bytes = solver.profile_read()[dominant]
     solver.profile(0)
@@ -465,7 +501,7 @@ def main():
                d2h_bytes_per_step=int(h_Z.numel() + h_R.numel()) * 4)
 
     extra = {}
-    if rank == 0 and not args.no_fp64:
+    if rank == 0 and not args.no_fp64 and args.domain == "image":
         # plain FP64 path: same algorithm in double, one slice at a time
         Zs, Rs, acq0 = slices[0]
         g0 = rc.geometry_from_acq(acq0)
@@ -492,16 +528,21 @@ def main():
         extra["serving"] = serving_run(rc, torch, args.rate, 48, 9000)
     cpu = None
     if rank == 0 and not args.no_cpu:
-        r = oracle_sample(slices, 3 if slices[0][0].shape[1] >= 512 else 10)
+        r = oracle_sample(slices, 3 if slices[0][0].shape[1] >= 512 else 10, args.domain)
         cpu = dict(value=r["value"], unit="slice-iters/s", cores=cpu_cores_used(), kind="oracle",
                    sample=f"one {r['nx']}x{r['ny']} slice of the workload, {r['iters']} iterations, "
-                          f"{r['seconds']:.1f} s, image-domain inputs from the oracle's model")
+                          f"{r['seconds']:.1f} s, " + ("noisy sinograms from the oracle's scan model, sinogram-domain "
+                                                       "f updates" if args.domain == "sino" else
+                                                       "image-domain inputs from the oracle's model"))
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="slice-iters/s", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak",
                     vs_baseline=None, dtype="f32" if args.precision == 1 else "f64", data="synthetic",
-                    config=dict(workload=name, slices=len(slices), iters=iters, precision=args.precision,
-                                l2="working set > L2 (no flush needed)"),
+                    config=dict(workload=name + (", sinogram-domain data terms" if args.domain == "sino" else ""),
+                                slices=len(slices), iters=iters, precision=args.precision,
+                                l2=(f"working set {work_bytes / 1e6:.0f} MB within 2x L2: L2 flushed ({4 * L2_BYTES >> 20} MiB write) "
+                                    "before each timed step" if flush else
+                                    f"working set {work_bytes / 1e9:.2f} GB > L2 (no flush needed)")),
                     e2e=e2e, gpu_launches=int(launches), clocks=clk, roofline=roofline, cpu_baseline=cpu, **extra)
         print(json.dumps(line), flush=True)
     solver.close()

@@ -93,8 +93,24 @@ typedef struct recon_params {
     double z_clip_max;               /* initial Z^m clipped to Z <= z_clip_max */
     double rho_air;                  /* initial Z^m set to water where rho_e < rho_air */
     int32_t pcg_kernel;              /* 0: batched kernels; 1: cluster-resident Z^m solve where a slice fits */
-    int32_t reserved;
+    int32_t domain;                  /* data terms of the arms: 0 on the image pair (Sec. II-B, as printed);
+                                        1 on the sinograms through the projector (below) */
 } recon_params;
+
+/* domain = 1 (sinogram-domain data terms).  The paper fits the reconstructed
+ * image pair; with sinograms s_L, s_H as data, the basis-fidelity terms of
+ * eq. obj_unconstraint become, per arm i,
+ *     (1/gamma) || A (f1 mu1(E_i) + f2 mu2(E_i)) - s_i / S ||^2,
+ * A the Joseph projector of recon_project, S the water electron density
+ * (mu in 1/mm = S mu_hat), gamma = ||A 1||^2 / (nx ny).  The model-
+ * consistency terms, the L0 relaxation and the rho_e and Z^m steps are
+ * unchanged; each f update solves its normal equations by conjugate
+ * gradients (warm start, cap cg_max_iters, relative residual cg_tol) with
+ * the FFT preconditioner (sum_i mu_k(E_i)^2 + sum_j b_kj^2 + beta K)^-1.
+ * Requires sinogram inputs (n_views > 0), the same geometry for every slice
+ * of a batch, precision 1 and order 0.  A^T adds with atomics, so results
+ * may differ in the last bits between runs.  The solve starts from the FBP
+ * image pair; recon_stats.fid_low/fid_high are 0 in this mode. */
 
 /* Per-slice statistics of the last iteration run by recon_step.  The
  * objective terms are those of eq. obj_unconstraint at the iterate the
@@ -116,7 +132,7 @@ typedef struct recon_ctx recon_ctx;
 /* Fill p with the library defaults: mono 60/90 keV arms, E1/E2 = 50/200 keV,
  * bone-like (13, 1.7) and water (7.45, 1.0) bases, lambda 1e-2,
  * beta0 = 2 lambda, beta_max 1e5, tau 1, iters 50, precision 1, order 0,
- * cg_max_iters 64, cg_tol 1e-6, z_clip_max 30, rho_air 0.1, pcg_kernel 0. */
+ * cg_max_iters 64, cg_tol 1e-6, z_clip_max 30, rho_air 0.1, pcg_kernel 0, domain 0. */
 int recon_default_params(recon_params* p);
 
 /* Create a handle for one slice (recon_init) or a batch of n slices of
@@ -315,8 +331,10 @@ int64_t recon_kernel_launches(recon_ctx* ctx);
  * D^-1/2 r; 7 column transforms with the preconditioner's divide and r.y;
  * 8 inverse row transforms, new search direction p and q = M p.  9 the
  * cluster-resident PCG (whole Z^m solve of a slice per thread-block
- * cluster), 10 other. */
-#define RECON_KF_COUNT 11
+ * cluster), 10 the CG of the sinogram-domain f updates (its pointwise,
+ * stencil and preconditioner column passes), 11 projector and backprojector
+ * inside the solve (domain 1), 12 other. */
+#define RECON_KF_COUNT 13
 
 /* Time the launches of the kernel families whose bit is set in mask with
  * CUDA events on the handle's stream (0 = off).  Algorithmic bytes and launch

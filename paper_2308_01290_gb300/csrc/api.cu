@@ -26,7 +26,8 @@ bool seven_smooth(int n) {
 int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
-        (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 1) || !(p.e1_kev > 0) ||
+        (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 1) ||
+        (p.domain != 0 && p.domain != 1) || (p.domain == 1 && (p.precision != 1 || p.order != 0)) || !(p.e1_kev > 0) ||
         !(p.e2_kev > 0) || p.e1_kev == p.e2_kev) {
         set_error("invalid recon_params");
         return RECON_EINVAL;
@@ -104,6 +105,8 @@ int recon_default_params(recon_params* p) {
     p->cg_tol = 1e-6;
     p->z_clip_max = 30.0;
     p->rho_air = 0.1;
+    p->pcg_kernel = 0;
+    p->domain = 0;
     return RECON_OK;
 }
 
@@ -119,13 +122,23 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
         if (!rc) rc = check_params(params[s]);
         if (rc) return rc;
         if (params[s].precision != params[0].precision || params[s].order != params[0].order ||
-            params[s].pcg_kernel != params[0].pcg_kernel) {
-            set_error("all slices of a batch need the same precision, order and pcg_kernel");
+            params[s].pcg_kernel != params[0].pcg_kernel || params[s].domain != params[0].domain) {
+            set_error("all slices of a batch need the same precision, order, pcg_kernel and domain");
             return RECON_EINVAL;
         }
         if ((geoms[s].n_views > 0) != (geoms[0].n_views > 0)) {
             set_error("all slices of a batch take images, or all take sinograms");
             return RECON_EINVAL;
+        }
+        if (params[0].domain == 1) {
+            const recon_geometry& a = geoms[s];
+            const recon_geometry& b = geoms[0];
+            if (a.n_views < 1 || a.nx != b.nx || a.ny != b.ny || a.n_views != b.n_views || a.n_bins != b.n_bins ||
+                a.pixel_mm != b.pixel_mm || a.sid_mm != b.sid_mm || a.sdd_mm != b.sdd_mm || a.bin_mm != b.bin_mm ||
+                a.start_rad != b.start_rad || a.arc_rad != b.arc_rad) {
+                set_error("domain 1 needs sinogram inputs and one geometry for every slice of the batch");
+                return RECON_EINVAL;
+            }
         }
     }
     recon_ctx* h = new (std::nothrow) recon_ctx();
@@ -161,6 +174,7 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
             else c.allocations.push_back(c.d_filt);
         }
     }
+    if (!rc && params[0].domain == 1) rc = solver_setup_sino(c);
     if (rc) {
         free_ctx(c);
         delete h;
@@ -204,6 +218,7 @@ int recon_set_data(recon_ctx* h, const float* low, const float* high, int on_dev
     }
     if ((rc = solver_load_images(c, lo, hi, 1))) return rc;
     if ((rc = solver_init_maps(c))) return rc;
+    if (c.domain == 1 && (rc = solver_modeb_data(c))) return rc;
     c.has_data = true;
     return RECON_OK;
 }
@@ -423,7 +438,8 @@ int recon_profile_read(recon_ctx* h, double* ms, int64_t* launches, uint64_t* by
 const char* recon_profile_name(int32_t f) {
     static const char* names[KF_COUNT] = {"thr_rhs",   "fft_rows_fwd", "fft_cols", "fft_rows_inv",
                                           "synth",     "pcg_start",    "pcg_fwd",  "pcg_cols",
-                                          "pcg_inv",   "pcg_cluster",  "other"};
+                                          "pcg_inv",   "pcg_cluster",  "fcg",      "project",
+                                          "other"};
     return (f >= 0 && f < KF_COUNT) ? names[f] : "?";
 }
 

@@ -46,7 +46,10 @@ struct SliceConst {
     double inv_S, zclip_hi, rho_air;
     double lambda, beta0, kappa, tau;
     double cg_tol;
-    int iters, order, cg_max, pad;
+    // sinogram-domain data terms (domain 1): alpha_k = sum_i a[k][i]^2,
+    // c'_k = sum_j b[k][j]^2, cross = sum_i a[0][i] a[1][i], 1/gamma
+    double fa0, fa1, fcp0, fcp1, fcross, inv_gamma;
+    int iters, order, cg_max, domain;
 };
 
 // Mutable per-slice state (device).
@@ -91,6 +94,8 @@ enum KFam {
     KF_COLS_PRE,
     KF_PCG_INV,
     KF_PCG_CLUSTER,
+    KF_FCG,
+    KF_PROJ,
     KF_OTHER,
     KF_COUNT
 };

@@ -60,7 +60,9 @@ __device__ __forceinline__ RaySetup ray_setup(const recon_geometry& g, int view,
 }
 
 // one thread per ray; sino[(slice * n_views + view) * n_bins + bin]
-__global__ void k_project(recon_geometry g, int n, const float* __restrict__ img, float* __restrict__ sino) {
+// Image slice sl at img + sl * stride, rows `pitch` elements apart.
+__global__ void k_project(recon_geometry g, int n, const float* __restrict__ img, long long pitch, long long stride,
+                          float* __restrict__ sino) {
     const long long nr = (long long)g.n_views * g.n_bins;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= nr * n) return;
@@ -68,7 +70,7 @@ __global__ void k_project(recon_geometry g, int n, const float* __restrict__ img
     const int ray = (int)(tid - (long long)sl * nr);
     const int view = ray / g.n_bins, bin = ray - view * g.n_bins;
     const RaySetup r = ray_setup(g, view, bin);
-    const float* im = img + (long long)sl * g.nx * g.ny;
+    const float* im = img + (long long)sl * stride;
     float acc = 0.f;
     if (r.xmajor) {
         for (int i = 0; i < g.nx; ++i) {
@@ -76,8 +78,8 @@ __global__ void k_project(recon_geometry g, int n, const float* __restrict__ img
             const float fl = floorf(jf);
             const int j0 = (int)fl;
             const float w1 = jf - fl;
-            if (j0 >= 0 && j0 < g.ny) acc += (1.f - w1) * __ldg(im + (long long)j0 * g.nx + i);
-            if (j0 + 1 >= 0 && j0 + 1 < g.ny) acc += w1 * __ldg(im + (long long)(j0 + 1) * g.nx + i);
+            if (j0 >= 0 && j0 < g.ny) acc += (1.f - w1) * __ldg(im + (long long)j0 * pitch + i);
+            if (j0 + 1 >= 0 && j0 + 1 < g.ny) acc += w1 * __ldg(im + (long long)(j0 + 1) * pitch + i);
         }
     } else {
         for (int j = 0; j < g.ny; ++j) {
@@ -85,7 +87,7 @@ __global__ void k_project(recon_geometry g, int n, const float* __restrict__ img
             const float fl = floorf(xf);
             const int i0 = (int)fl;
             const float w1 = xf - fl;
-            const float* row = im + (long long)j * g.nx;
+            const float* row = im + (long long)j * pitch;
             if (i0 >= 0 && i0 < g.nx) acc += (1.f - w1) * __ldg(row + i0);
             if (i0 + 1 >= 0 && i0 + 1 < g.nx) acc += w1 * __ldg(row + i0 + 1);
         }
@@ -94,7 +96,9 @@ __global__ void k_project(recon_geometry g, int n, const float* __restrict__ img
 }
 
 // exact transpose of k_project (same samples, scattered with atomics)
-__global__ void k_backproject(recon_geometry g, int n, const float* __restrict__ sino, float* img) {
+// Adds A^T sino into img (layout as k_project).
+__global__ void k_backproject(recon_geometry g, int n, const float* __restrict__ sino, float* img, long long pitch,
+                              long long stride) {
     const long long nr = (long long)g.n_views * g.n_bins;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= nr * n) return;
@@ -102,7 +106,7 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
     const int ray = (int)(tid - (long long)sl * nr);
     const int view = ray / g.n_bins, bin = ray - view * g.n_bins;
     const RaySetup r = ray_setup(g, view, bin);
-    float* im = img + (long long)sl * g.nx * g.ny;
+    float* im = img + (long long)sl * stride;
     const float v = sino[tid] * r.w;
     if (v == 0.f) return;
     if (r.xmajor) {
@@ -111,8 +115,8 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
             const float fl = floorf(jf);
             const int j0 = (int)fl;
             const float w1 = jf - fl;
-            if (j0 >= 0 && j0 < g.ny) atomicAdd(im + (long long)j0 * g.nx + i, (1.f - w1) * v);
-            if (j0 + 1 >= 0 && j0 + 1 < g.ny) atomicAdd(im + (long long)(j0 + 1) * g.nx + i, w1 * v);
+            if (j0 >= 0 && j0 < g.ny) atomicAdd(im + (long long)j0 * pitch + i, (1.f - w1) * v);
+            if (j0 + 1 >= 0 && j0 + 1 < g.ny) atomicAdd(im + (long long)(j0 + 1) * pitch + i, w1 * v);
         }
     } else {
         for (int j = 0; j < g.ny; ++j) {
@@ -120,7 +124,7 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
             const float fl = floorf(xf);
             const int i0 = (int)fl;
             const float w1 = xf - fl;
-            float* row = im + (long long)j * g.nx;
+            float* row = im + (long long)j * pitch;
             if (i0 >= 0 && i0 < g.nx) atomicAdd(row + i0, (1.f - w1) * v);
             if (i0 + 1 >= 0 && i0 + 1 < g.nx) atomicAdd(row + i0 + 1, w1 * v);
         }
@@ -269,8 +273,24 @@ int check_geom(const recon_geometry& g) {
 int ct_project(const recon_geometry& g, int n, const float* img, float* sino, cudaStream_t st, long long* launches) {
     int rc = check_geom(g);
     if (rc) return rc;
+    return ct_project_pitched(g, n, img, g.nx, (long long)g.nx * g.ny, sino, st, launches);
+}
+
+int ct_project_pitched(const recon_geometry& g, int n, const float* img, long long pitch, long long stride,
+                       float* sino, cudaStream_t st, long long* launches) {
     const long long total = (long long)n * g.n_views * g.n_bins;
-    k_project<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, img, sino);
+    if (total <= 0) return RECON_OK;
+    k_project<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, img, pitch, stride, sino);
+    if (launches) *launches += 1;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
+int ct_backproject_add(const recon_geometry& g, int n, const float* sino, float* img, long long pitch,
+                       long long stride, cudaStream_t st, long long* launches) {
+    const long long total = (long long)n * g.n_views * g.n_bins;
+    if (total <= 0) return RECON_OK;
+    k_backproject<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, sino, img, pitch, stride);
     if (launches) *launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
@@ -281,11 +301,7 @@ int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img
     int rc = check_geom(g);
     if (rc) return rc;
     RECON_CUDA(cudaMemsetAsync(img, 0, sizeof(float) * (size_t)n * g.nx * g.ny, st));
-    const long long total = (long long)n * g.n_views * g.n_bins;
-    k_backproject<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, sino, img);
-    if (launches) *launches += 1;
-    RECON_CUDA(cudaGetLastError());
-    return RECON_OK;
+    return ct_backproject_add(g, n, sino, img, g.nx, (long long)g.nx * g.ny, st, launches);
 }
 
 int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,

@@ -78,6 +78,10 @@ struct Ctx {
     std::vector<SliceConst> hconst;
     // serving mode: every slot laid out at capacity; lists hold the active slots
     bool server_mode = false;
+    // sinogram-domain data terms (domain 1)
+    int domain = 0;
+    double gamma = 0.0;             // ||A 1||^2 / (nx ny)
+    float* d_sino_tmp = nullptr;    // one sinogram per slice (A p)
     int cap_nx = 0, cap_ny = 0;
     std::vector<std::pair<int, std::pair<long long, long long>>> tw_index;   // N -> (twiddle, symbol) offsets
     bool has_data = false;
@@ -91,6 +95,8 @@ struct Ctx {
 int solver_setup(Ctx& c);                      // item lists, constants, scratch
 int solver_load_images(Ctx& c, const float* low, const float* high, int on_device);
 int solver_init_maps(Ctx& c);
+int solver_setup_sino(Ctx& c);                 // domain 1: gamma and the sinogram scratch
+int solver_modeb_data(Ctx& c);                 // domain 1: data images t_k from the sinograms
 int solver_iterate(Ctx& c, bool stats);        // one iteration of Algorithm 1
 int solver_op(Ctx& c, int op);
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int on_device);
@@ -104,6 +110,12 @@ int solver_extract_slots(Ctx& c, const std::vector<int>& slots, float* Z, float*
 
 // Input stage (ct.cu), float device buffers.
 int ct_project(const recon_geometry& g, int n, const float* img, float* sino, cudaStream_t st, long long* launches);
+// Variants on padded layouts: slice s at img + s * stride, rows pitch apart;
+// ct_backproject_add adds A^T sino into img (the caller clears it).
+int ct_project_pitched(const recon_geometry& g, int n, const float* img, long long pitch, long long stride,
+                       float* sino, cudaStream_t st, long long* launches);
+int ct_backproject_add(const recon_geometry& g, int n, const float* sino, float* img, long long pitch,
+                       long long stride, cudaStream_t st, long long* launches);
 int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img, cudaStream_t st,
                    long long* launches);
 int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,

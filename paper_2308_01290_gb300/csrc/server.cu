@@ -137,8 +137,9 @@ int recon_submit(recon_server* s, const recon_request* r, uint64_t* ticket) {
     }
     const recon_geometry& g = r->geom;
     if (g.nx < 1 || g.ny < 1 || g.nx > s->cfg.max_nx || g.ny > s->cfg.max_ny || !seven_smooth(g.nx) ||
-        !seven_smooth(g.ny) || r->params.precision != s->cfg.precision || r->params.order != 0) {
-        set_error("recon_submit: size above the slot capacity, not 7-smooth, or precision/order mismatch");
+        !seven_smooth(g.ny) || r->params.precision != s->cfg.precision || r->params.order != 0 ||
+        r->params.domain != 0) {
+        set_error("recon_submit: size above the slot capacity, not 7-smooth, precision/order mismatch, or domain 1");
         return RECON_EINVAL;
     }
     if (g.n_views > 0 && ((long long)g.n_views * g.n_bins > s->cap_sino || g.n_bins < 1)) {

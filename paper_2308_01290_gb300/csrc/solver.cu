@@ -269,16 +269,25 @@ __global__ void __launch_bounds__(kStencilThreads) k_thr_rhs(ItemList L, const S
             const int y = it.b + ly;
             if (y >= g.ny) continue;
             const long long d0 = g.off + (long long)y * g.pitch + it.a + lx0;
-            Pack<T> uL, uH;
+            // image domain: uL, uH = mu_hat(E_L), mu_hat(E_H).  Sinogram domain
+            // (domain 1): uL, uH = t_1, t_2 and G1, G2 = A^T A f1, A^T A f2
+            const bool sino = c.domain == 1;
+            Pack<T> uL, uH, G1, G2;
             if (full) {
                 uL = ldv(P.f[RECON_F_MUL], d0);
                 uH = ldv(P.f[RECON_F_MUH], d0);
+                if (sino) {
+                    G1 = ldv(P.f[RECON_F_A2], d0);
+                    G2 = ldv(P.f[RECON_F_RHS_Z], d0);
+                }
             } else {
 #pragma unroll
                 for (int e = 0; e < VN; ++e) {
                     const bool in = it.a + lx0 + e < g.nx;
                     uL.v[e] = in ? P.f[RECON_F_MUL][d0 + e] : T(0);
                     uH.v[e] = in ? P.f[RECON_F_MUH][d0 + e] : T(0);
+                    G1.v[e] = (in && sino) ? P.f[RECON_F_A2][d0 + e] : T(0);
+                    G2.v[e] = (in && sino) ? P.f[RECON_F_RHS_Z][d0 + e] : T(0);
                 }
             }
             Pack<T> o0, o1, o2, o3;
@@ -311,15 +320,22 @@ __global__ void __launch_bounds__(kStencilThreads) k_thr_rhs(ItemList L, const S
                 const T f1 = sm[0][ry][lx], f2 = sm[1][ry][lx], rho = sm[2][ry][lx], z = sm[3][ry][lx];
                 const T M1 = rho * (T(c.P1) * z + T(c.psi1));
                 const T M2 = rho * (T(c.P2) * z + T(c.psi2));
-                const T base1 = T(c.a00) * uL.v[e] + T(c.a01) * uH.v[e] + T(c.b00) * M1 + T(c.b01) * M2;
-                const T base2 = T(c.a10) * uL.v[e] + T(c.a11) * uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2;
-                o0.v[e] = base1 - T(c.c12) * f2 + beta * div[0];
-                o1.v[e] = (c.order ? base2 : base2 - T(c.c12) * f1) + beta * div[1];
+                if (!sino) {
+                    const T base1 = T(c.a00) * uL.v[e] + T(c.a01) * uH.v[e] + T(c.b00) * M1 + T(c.b01) * M2;
+                    const T base2 = T(c.a10) * uL.v[e] + T(c.a11) * uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2;
+                    o0.v[e] = base1 - T(c.c12) * f2 + beta * div[0];
+                    o1.v[e] = (c.order ? base2 : base2 - T(c.c12) * f1) + beta * div[1];
+                } else {
+                    // t_k - cross A^T A f_o / gamma + sum_j b_kj (M_j - f_o b_oj) + beta div
+                    const T ag = T(c.fcross * c.inv_gamma), bc = T(c.c12 - c.fcross);
+                    o0.v[e] = uL.v[e] + T(c.b00) * M1 + T(c.b01) * M2 - ag * G2.v[e] - bc * f2 + beta * div[0];
+                    o1.v[e] = uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2 - ag * G1.v[e] - bc * f1 + beta * div[1];
+                }
                 o2.v[e] = beta_t * div[2];
                 o3.v[e] = beta_t * div[3];
                 if (STATS && in) {
-                    const double dL = c.a00 * (double)f1 + c.a10 * (double)f2 - (double)uL.v[e];
-                    const double dH = c.a01 * (double)f1 + c.a11 * (double)f2 - (double)uH.v[e];
+                    const double dL = sino ? 0.0 : c.a00 * (double)f1 + c.a10 * (double)f2 - (double)uL.v[e];
+                    const double dH = sino ? 0.0 : c.a01 * (double)f1 + c.a11 * (double)f2 - (double)uH.v[e];
                     const double m1 = c.b00 * (double)f1 + c.b10 * (double)f2;
                     const double m2 = c.b01 * (double)f1 + c.b11 * (double)f2;
                     const double e1 = (double)rho * (c.P1 * (double)z + c.psi1) - m1;
@@ -456,7 +472,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_fwd(ItemLis
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int job = w / L.n_items, item = w - job * L.n_items;
         const Item it = L.items[item];
-        if (!__ldg(&S[it.slice].active)) continue;
+        if (!__ldg(&S[it.slice].active) || (J.coef[job] >= 3 && __ldg(&S[it.slice].cg_done))) continue;
         const SliceGeom g = G[it.slice];
         const int N = g.nx, pair0 = it.a, np = it.b, ld = padded_len(N);
         const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
@@ -562,10 +578,11 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
         const Item it = L.items[item];
         const int kind = J.coef[job];
         const SliceState* st = S + it.slice;
-        if (!__ldg(&st->active) || (kind == 3 && __ldg(&st->cg_done))) continue;
+        if (!__ldg(&st->active) || (kind >= 3 && __ldg(&st->cg_done))) continue;
         const SliceGeom g = G[it.slice];
         const int N = g.ny, col0 = it.a, nc = it.b, ld = col_ld(N);
-        account(P.acct, kind == 3 ? KF_COLS_PRE : KF_COLS, (long long)nc * N * 4 * (long long)sizeof(T));
+        account(P.acct, kind == 3 ? KF_COLS_PRE : (kind > 3 ? KF_FCG : KF_COLS),
+                (long long)nc * N * 4 * (long long)sizeof(T));
         cplx<T>* sp = P.s[J.spec[job]];
         const cplx<T>* tw = twpool + g.twy;
         double cst, bet;
@@ -573,7 +590,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
             case 0: cst = C[it.slice].c_f1; bet = __ldg(&st->beta); break;
             case 1: cst = C[it.slice].c_f2; bet = __ldg(&st->beta); break;
             case 2: cst = 1.0; bet = __ldg(&st->beta_t); break;
-            default: cst = __ldg(&st->abar2); bet = __ldg(&st->beta_t); break;
+            case 3: cst = __ldg(&st->abar2); bet = __ldg(&st->beta_t); break;
+            case 4: cst = C[it.slice].fa0 + C[it.slice].fcp0; bet = __ldg(&st->beta); break;
+            default: cst = C[it.slice].fa1 + C[it.slice].fcp1; bet = __ldg(&st->beta); break;
         }
         const T inv_n = T(1.0 / ((double)g.nx * (double)g.ny));
         const T* symx = P.sym + g.symx;
@@ -583,7 +602,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
         if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
         if (fast) {
             cplx<T>* spc = sp + g.coff + col0;
-            if (kind == 3) {
+            if (kind >= 3) {
                 RECON_P2_DISPATCH(N, cols_item_p2<T, NN, true>(spc, g.cpitch, nc, col0, g.nx, buf0, buf1, tw, symx,
                                                                symy, T(cst), T(bet), inv_n, accT));
             } else {
@@ -627,7 +646,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
                     // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
                     const T sc = inv_n / (T(cst) + T(bet) * (symx[col0 + cc] + symy[ky]));
                     cplx<T> v = buf[cc * ld + pad8(ky)];
-                    if (kind == 3) {
+                    if (kind >= 3) {
                         const int kx = col0 + cc;
                         const T wgt = (kx == 0 || 2 * kx == g.nx) ? T(1) : T(2);
                         accT = fma(wgt * sc, v.x * v.x + v.y * v.y, accT);
@@ -645,7 +664,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
             }
             __syncthreads();
         }
-        if (kind == 3) {
+        if (kind >= 3) {
             double acc[1] = {(double)accT};
             block_sum<1>(acc, red);
             double tot[1];
@@ -669,7 +688,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_inv(ItemLis
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int job = w / L.n_items, item = w - job * L.n_items;
         const Item it = L.items[item];
-        if (!__ldg(&S[it.slice].active)) continue;
+        if (!__ldg(&S[it.slice].active) || (J.coef[job] >= 3 && __ldg(&S[it.slice].cg_done))) continue;
         const SliceGeom g = G[it.slice];
         const int N = g.nx, pair0 = it.a, np = it.b, ld = padded_len(N);
         const int rows = (g.ny - 2 * pair0 < 2 * np) ? g.ny - 2 * pair0 : 2 * np;
@@ -1275,6 +1294,203 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const S
     }
 }
 
+// --------------------------------------------------------------------------
+// Sinogram-domain f updates (domain 1): conjugate gradients on
+//   [alpha_k A^T A / gamma + c'_k + beta L] f_k = rhs_k
+// preconditioned by (alpha_k + c'_k + beta K)^-1 applied by FFT (kinds 4, 5
+// of the column pass, which also reduces r.y).  Fields: x = f_k, r = CG_R,
+// y = CG_Y, p = CG_P0, q = CG_Q, A^T A p in CG_P1; A^T A f_k of the
+// iterate (formed for the right-hand sides) in A2 (k = 0) or RHS_Z (k = 1).
+// --------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ void fcg_coeffs(const SliceConst& c, int k, T& al, T& cp) {
+    al = T((k ? c.fa1 : c.fa0) * c.inv_gamma);
+    cp = T(k ? c.fcp1 : c.fcp0);
+}
+
+// r = rhs - (alpha/gamma A^T A x + c' x + beta L x); |rhs|^2, |r|^2; start of the solve
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads) k_fcg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
+                                                              SliceState* S, Ptrs<T> P, int k, int* pending) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
+    __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
+    __shared__ double red[2 * 32];
+    __shared__ SliceGeom s_g;
+    const T* x = P.f[k ? RECON_F_F2 : RECON_F_F1];
+    const T* gx = P.f[k ? RECON_F_RHS_Z : RECON_F_A2];
+    const T* rhs = P.f[k ? RECON_F_RHS_F2 : RECON_F_RHS_F1];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        if (!__ldg(&S[it.slice].active)) continue;
+        stage_struct(&s_g, G + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        account(P.acct, KF_FCG, tile_px<T>(g, it) * 4 * (long long)sizeof(T));
+        load_tile<T, 1>(
+            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{x[d]}}; },
+            [&](long long d) { return PVals<T, 1>{{ldv(x, d)}}; });
+        __syncthreads();
+        T al, cp;
+        fcg_coeffs<T>(C[it.slice], k, al, cp);
+        const T bt = T(__ldg(&S[it.slice].beta));
+        double acc[2] = {0.0, 0.0};
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
+            const Pack<T> gv = ldv_n(gx, d, cnt), b = ldv_n(rhs, d, cnt);
+            Pack<T> r;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const T xc = sm[0][ly + 1][OFF + lx0 + e];
+                r.v[e] = b.v[e] - (al * gv.v[e] + cp * xc + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e));
+                if (e < cnt) {
+                    acc[0] += (double)b.v[e] * b.v[e];
+                    acc[1] += (double)r.v[e] * r.v[e];
+                }
+            }
+            stv_n(P.f[RECON_F_CG_R], d, r, cnt);
+        });
+        block_sum<2>(acc, red);
+        double tot[2];
+        if (item_reduce<2>(L, w, it.slice, acc, tot, red)) {
+            SliceState& so = S[it.slice];
+            const double tol2 = C[it.slice].cg_tol * C[it.slice].cg_tol;
+            so.bb = tot[0];
+            so.rr = tot[1];
+            so.rr0 = tot[1];
+            so.cg_it = 0;
+            so.ry = 0.0;
+            so.betacg = 0.0;
+            so.cg_done = (tot[0] == 0.0 || !(tot[1] > tol2 * tot[0])) ? 1 : 0;
+            if (!so.cg_done) atomicAdd(pending, 1);
+        }
+        __syncthreads();
+    }
+}
+
+// p = y + beta_cg p (p = y on the first step)
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads) k_fcg_p(ItemList L, const SliceGeom* G, const SliceState* S,
+                                                           Ptrs<T> P) {
+    constexpr int VN = TileDim<T>::VN;
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        const SliceGeom g = G[it.slice];
+        account(P.acct, KF_FCG, tile_px<T>(g, it) * 3 * (long long)sizeof(T));
+        const bool first = __ldg(&sp->cg_it) == 0;
+        const T bc = first ? T(0) : T(__ldg(&sp->betacg));
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
+            const Pack<T> y = ldv_n(P.f[RECON_F_CG_Y], d, cnt);
+            Pack<T> p = first ? y : ldv_n(P.f[RECON_F_CG_P0], d, cnt);
+            if (!first) {
+#pragma unroll
+                for (int e = 0; e < VN; ++e) p.v[e] = fma(bc, p.v[e], y.v[e]);
+            }
+            stv_n(P.f[RECON_F_CG_P0], d, p, cnt);
+        });
+    }
+}
+
+// q = alpha/gamma A^T A p + c' p + beta L p, p.q -> alpha
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads) k_fcg_q(ItemList L, const SliceGeom* G, const SliceConst* C,
+                                                           SliceState* S, Ptrs<T> P, int k) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
+    __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
+    __shared__ double red[32];
+    __shared__ SliceGeom s_g;
+    const T* p = P.f[RECON_F_CG_P0];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        account(P.acct, KF_FCG, tile_px<T>(g, it) * 3 * (long long)sizeof(T));
+        load_tile<T, 1>(
+            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{p[d]}}; },
+            [&](long long d) { return PVals<T, 1>{{ldv(p, d)}}; });
+        __syncthreads();
+        T al, cp;
+        fcg_coeffs<T>(C[it.slice], k, al, cp);
+        const T bt = T(__ldg(&sp->beta));
+        T accT = T(0);
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
+            const Pack<T> ap = ldv_n(P.f[RECON_F_CG_P1], d, cnt);
+            Pack<T> q;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const T pc = sm[0][ly + 1][OFF + lx0 + e];
+                q.v[e] = al * ap.v[e] + cp * pc + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e);
+                if (e < cnt) accT = fma(pc, q.v[e], accT);
+            }
+            stv_n(P.f[RECON_F_CG_Q], d, q, cnt);
+        });
+        double acc[1] = {(double)accT};
+        block_sum<1>(acc, red);
+        double tot[1];
+        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
+            SliceState& so = S[it.slice];
+            so.pq = tot[0];
+            so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
+        }
+        __syncthreads();
+    }
+}
+
+// x += alpha p, r -= alpha q, r.r and the convergence test
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads) k_fcg_update(ItemList L, const SliceGeom* G, const SliceConst* C,
+                                                                SliceState* S, Ptrs<T> P, int k, int* pending) {
+    constexpr int VN = TileDim<T>::VN;
+    __shared__ double red[32];
+    T* x = P.f[k ? RECON_F_F2 : RECON_F_F1];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        const SliceGeom g = G[it.slice];
+        account(P.acct, KF_FCG, tile_px<T>(g, it) * 6 * (long long)sizeof(T));
+        const T al = T(__ldg(&sp->alpha));
+        T accT = T(0);
+        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
+            Pack<T> xv = ldv_n(x, d, cnt), r = ldv_n(P.f[RECON_F_CG_R], d, cnt);
+            const Pack<T> pv = ldv_n(P.f[RECON_F_CG_P0], d, cnt), q = ldv_n(P.f[RECON_F_CG_Q], d, cnt);
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                xv.v[e] = fma(al, pv.v[e], xv.v[e]);
+                r.v[e] = fma(-al, q.v[e], r.v[e]);
+                if (e < cnt) accT = fma(r.v[e], r.v[e], accT);
+            }
+            stv_n(x, d, xv, cnt);
+            stv_n(P.f[RECON_F_CG_R], d, r, cnt);
+        });
+        double acc[1] = {(double)accT};
+        block_sum<1>(acc, red);
+        double tot[1];
+        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
+            SliceState& so = S[it.slice];
+            const SliceConst& c = C[it.slice];
+            so.rr = tot[0];
+            so.cg_it += 1;
+            const bool conv = !(tot[0] > c.cg_tol * c.cg_tol * so.bb);
+            if (conv || so.cg_it >= c.cg_max) {
+                so.cg_done = 1;
+                atomicSub(pending, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// sinogram combination of the data images: out = (a_k0 s_L + a_k1 s_H) / (S gamma)
+__global__ void k_sino_combine(long long n, const float* sL, const float* sH, float wL, float wH, float* out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = wL * sL[i] + wH * sH[i];
+}
+
 __global__ void k_next_beta(int n, const SliceConst* C, SliceState* S) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
@@ -1547,6 +1763,90 @@ int op_solve_z(Ctx& c) {
     return RECON_OK;
 }
 
+// ---- sinogram-domain f updates (domain 1; FP32 fields) ----
+
+// Slice s of a field: all slices of a domain-1 handle share one geometry, so
+// they sit ny * pitch elements apart.
+template <typename T>
+T* field_base(Ctx& c, int f) {
+    return static_cast<T*>(c.field[f]) + c.sg[0].off;
+}
+
+// out (cleared) = A^T A x over all slices
+int gram_all(Ctx& c, const float* x, float* out) {
+    const recon_geometry& g = c.geo[0];
+    const long long pitch = c.sg[0].pitch, stride = (long long)c.sg[0].ny * pitch;
+    FamTimer t(c, KF_PROJ);
+    int rc;
+    if ((rc = ct_project_pitched(g, c.n, x, pitch, stride, c.d_sino_tmp, c.stream, &c.launches))) return rc;
+    RECON_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * stride * c.n, c.stream));
+    return ct_backproject_add(g, c.n, c.d_sino_tmp, out, pitch, stride, c.stream, &c.launches);
+}
+
+// A^T A f1 into A2 and A^T A f2 into RHS_Z (read by the right-hand sides
+// and by the starts of the two CG solves; the synthesis rewrites both)
+template <typename T>
+int op_modeb_gram(Ctx& c) {
+    if constexpr (std::is_same<T, float>::value) {
+        int rc;
+        if ((rc = gram_all(c, field_base<float>(c, RECON_F_F1), field_base<float>(c, RECON_F_A2)))) return rc;
+        return gram_all(c, field_base<float>(c, RECON_F_F2), field_base<float>(c, RECON_F_RHS_Z));
+    } else {
+        set_error("domain 1 needs precision 1");
+        return RECON_EINVAL;
+    }
+}
+
+template <typename T>
+int op_solve_f_sino(Ctx& c) {
+    if constexpr (!std::is_same<T, float>::value) {
+        set_error("domain 1 needs precision 1");
+        return RECON_EINVAL;
+    } else {
+        const Ptrs<T> P = ptrs<T>(c);
+        int cap = 0;
+        for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
+        int rc;
+        for (int k = 0; k < 2; ++k) {
+            const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 4 + k);
+            RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream));
+            {
+                FamTimer t(c, KF_FCG);
+                k_fcg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(
+                    c.tiles.view(), c.d_geom, c.d_const, c.d_state, P, k, c.d_cg_pending);
+            }
+            c.launches += 1;
+            if ((rc = fft_solve<T>(c, pre))) return rc;
+            for (int it = 0; it < cap; ++it) {
+                {
+                    FamTimer t(c, KF_FCG);
+                    k_fcg_p<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
+                                                                                        c.d_state, P);
+                }
+                if ((rc = gram_all(c, field_base<float>(c, RECON_F_CG_P0), field_base<float>(c, RECON_F_CG_P1))))
+                    return rc;
+                {
+                    FamTimer t(c, KF_FCG);
+                    k_fcg_q<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(
+                        c.tiles.view(), c.d_geom, c.d_const, c.d_state, P, k);
+                    k_fcg_update<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(
+                        c.tiles.view(), c.d_geom, c.d_const, c.d_state, P, k, c.d_cg_pending);
+                }
+                c.launches += 3;
+                RECON_CUDA(cudaGetLastError());
+                if ((rc = fft_solve<T>(c, pre))) return rc;
+                if ((it & 3) == 3 || it == cap - 1) {
+                    RECON_CUDA(cudaMemcpyAsync(c.h_cg_pending, c.d_cg_pending, sizeof(int), cudaMemcpyDeviceToHost,
+                                               c.stream));
+                    RECON_CUDA(cudaStreamSynchronize(c.stream));
+                    if (*c.h_cg_pending <= 0) break;
+                }
+            }
+        }
+        return RECON_OK;
+    }
+}
+
 template <typename T>
 int op_next_beta(Ctx& c) {
     k_next_beta<<<(c.n + 127) / 128, 128, 0, c.stream>>>(c.n, c.d_const, c.d_state);
@@ -1558,8 +1858,9 @@ int op_next_beta(Ctx& c) {
 template <typename T>
 int iterate_t(Ctx& c, bool stats) {
     int rc;
+    if (c.domain == 1 && (rc = op_modeb_gram<T>(c))) return rc;
     if ((rc = op_thr_rhs<T>(c, stats))) return rc;
-    if ((rc = op_solve_f<T>(c))) return rc;
+    if ((rc = c.domain == 1 ? op_solve_f_sino<T>(c) : op_solve_f<T>(c))) return rc;
     if ((rc = op_synth<T>(c))) return rc;
     if ((rc = fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2)))) return rc;
     if ((rc = op_solve_z<T>(c))) return rc;
@@ -1599,8 +1900,12 @@ template <typename T>
 int op_t(Ctx& c, int op) {
     switch (op) {
         case RECON_OP_INIT: return init_maps_t<T>(c);
-        case RECON_OP_THRESH_RHS: return op_thr_rhs<T>(c, false);
-        case RECON_OP_SOLVE_F: return op_solve_f<T>(c);
+        case RECON_OP_THRESH_RHS: {
+            int rc;
+            if (c.domain == 1 && (rc = op_modeb_gram<T>(c))) return rc;
+            return op_thr_rhs<T>(c, false);
+        }
+        case RECON_OP_SOLVE_F: return c.domain == 1 ? op_solve_f_sino<T>(c) : op_solve_f<T>(c);
         case RECON_OP_SYNTH: return op_synth<T>(c);
         case RECON_OP_SOLVE_RHO: return fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2));
         case RECON_OP_SOLVE_Z: return op_solve_z<T>(c);
@@ -1619,6 +1924,13 @@ SliceConst slice_const(const recon_params& p, const Tables& t) {
     k.lambda = p.lambda; k.beta0 = p.beta0; k.tau = p.tau;
     k.kappa = p.kappa > 0 ? p.kappa : (p.iters > 0 ? std::pow(p.beta_max / p.beta0, 1.0 / p.iters) : 1.0);
     k.cg_tol = p.cg_tol; k.iters = p.iters; k.order = p.order; k.cg_max = p.cg_max_iters;
+    k.domain = p.domain;
+    k.fa0 = t.a[0][0] * t.a[0][0] + t.a[0][1] * t.a[0][1];
+    k.fa1 = t.a[1][0] * t.a[1][0] + t.a[1][1] * t.a[1][1];
+    k.fcp0 = t.b[0][0] * t.b[0][0] + t.b[0][1] * t.b[0][1];
+    k.fcp1 = t.b[1][0] * t.b[1][0] + t.b[1][1] * t.b[1][1];
+    k.fcross = t.a[0][0] * t.a[1][0] + t.a[0][1] * t.a[1][1];
+    k.inv_gamma = 0.0;   // set once the geometry's gamma is known
     return k;
 }
 
@@ -1850,6 +2162,61 @@ int solver_load_images(Ctx& c, const float* lo, const float* hi, int /*on_device
 }
 
 int solver_init_maps(Ctx& c) { return c.precision == 1 ? init_maps_t<float>(c) : init_maps_t<double>(c); }
+
+int solver_setup_sino(Ctx& c) {
+    const recon_geometry& g = c.geo[0];
+    const long long nr = (long long)g.n_views * g.n_bins;
+    int rc;
+    if ((rc = alloc_dev(c, (void**)&c.d_sino_tmp, sizeof(float) * nr * c.n))) return rc;
+    // gamma = ||A 1||^2 / (nx ny)
+    float* ones = nullptr;
+    RECON_CUDA(cudaMalloc((void**)&ones, sizeof(float) * g.nx * g.ny));
+    std::vector<float> h(std::max<long long>(nr, (long long)g.nx * g.ny), 1.f);
+    cudaError_t e = cudaMemcpy(ones, h.data(), sizeof(float) * g.nx * g.ny, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        rc = ct_project_pitched(g, 1, ones, g.nx, (long long)g.nx * g.ny, c.d_sino_tmp, c.stream, &c.launches);
+        if (!rc) e = cudaStreamSynchronize(c.stream);
+        if (!rc && e == cudaSuccess) e = cudaMemcpy(h.data(), c.d_sino_tmp, sizeof(float) * nr, cudaMemcpyDeviceToHost);
+    }
+    cudaFree(ones);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "gamma of the projector");
+    double s2 = 0.0;
+    for (long long i = 0; i < nr; ++i) s2 += (double)h[i] * (double)h[i];
+    c.gamma = s2 / ((double)g.nx * (double)g.ny);
+    if (!(c.gamma > 0.0)) {
+        set_error("domain 1: the projector misses the image (gamma = 0)");
+        return RECON_EINVAL;
+    }
+    for (int s = 0; s < c.n; ++s) c.hconst[s].inv_gamma = 1.0 / c.gamma;
+    RECON_CUDA(cudaMemcpy(c.d_const, c.hconst.data(), sizeof(SliceConst) * c.n, cudaMemcpyHostToDevice));
+    c.domain = 1;
+    return RECON_OK;
+}
+
+int solver_modeb_data(Ctx& c) {
+    // t_k = A^T ((a_k0 s_L + a_k1 s_H) / (S gamma)) into MUL (k = 0) and MUH (k = 1);
+    // the initialisation has already used the FBP images held there
+    const recon_geometry& g = c.geo[0];
+    const long long nr = (long long)g.n_views * g.n_bins;
+    const long long pitch = c.sg[0].pitch, stride = (long long)c.sg[0].ny * pitch;
+    int rc;
+    for (int k = 0; k < 2; ++k) {
+        for (int s = 0; s < c.n; ++s) {
+            const SliceConst& q = c.hconst[s];
+            const double sc = q.inv_S * q.inv_gamma;
+            const float wL = (float)((k ? q.a10 : q.a00) * sc), wH = (float)((k ? q.a11 : q.a01) * sc);
+            k_sino_combine<<<(unsigned)((nr + 255) / 256), 256, 0, c.stream>>>(
+                nr, c.d_sino[0] + c.sino_off[s], c.d_sino[1] + c.sino_off[s], wL, wH, c.d_sino_tmp + nr * s);
+            c.launches += 1;
+        }
+        RECON_CUDA(cudaGetLastError());
+        float* out = field_base<float>(c, k ? RECON_F_MUH : RECON_F_MUL);
+        RECON_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * stride * c.n, c.stream));
+        if ((rc = ct_backproject_add(g, c.n, c.d_sino_tmp, out, pitch, stride, c.stream, &c.launches))) return rc;
+    }
+    return RECON_OK;
+}
 
 int solver_iterate(Ctx& c, bool stats) {
     return c.precision == 1 ? iterate_t<float>(c, stats) : iterate_t<double>(c, stats);

@@ -44,7 +44,7 @@ class Params(C.Structure):
                 ("beta0", C.c_double), ("beta_max", C.c_double), ("tau", C.c_double), ("kappa", C.c_double),
                 ("iters", C.c_int32), ("precision", C.c_int32), ("order", C.c_int32), ("cg_max_iters", C.c_int32),
                 ("cg_tol", C.c_double), ("z_clip_max", C.c_double), ("rho_air", C.c_double),
-                ("pcg_kernel", C.c_int32), ("reserved", C.c_int32)]
+                ("pcg_kernel", C.c_int32), ("domain", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -136,7 +136,7 @@ EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_
            "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches",
            "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name", "recon_server_create",
            "recon_submit", "recon_server_step", "recon_poll", "recon_server_stats", "recon_server_destroy")
-KF_COUNT = 11
+KF_COUNT = 13
 
 
 def _check(rc, what):

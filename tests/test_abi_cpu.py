@@ -57,3 +57,22 @@ def test_model_tables_match_oracle(rc):
 def test_strerror(rc):
     assert rc.lib.recon_strerror(-1) == b"invalid argument"
     assert rc.lib.recon_strerror(0) == b"ok"
+
+
+def test_sinogram_domain_rejects_unsupported_configurations(rc):
+    """Validation returns before any device work, so this runs without a GPU."""
+    from synthetic import phantoms as ph
+    acq = ph.acquisition("small", n=32)
+    sino = rc.geometry_from_acq(acq)
+    img = rc.geometry_from_acq(acq, image_input=True)
+    other = rc.geometry(acq.nx, acq.ny, acq.pixel_mm, acq.n_views + 2, acq.n_bins, acq.sid_mm, acq.sdd_mm,
+                        acq.bin_mm)
+    p = rc.default_params(low=acq.low, high=acq.high, domain=1)
+    bad = [([img], [p]),                                                   # image inputs
+           ([sino, other], [p, p]),                                        # two geometries
+           ([sino], [rc.default_params(domain=1, precision=0)]),           # FP64
+           ([sino], [rc.default_params(domain=1, order=1)]),               # Gauss-Seidel
+           ([sino], [rc.default_params(domain=2)])]
+    for geoms, params in bad:
+        with pytest.raises(rc.ReconError):
+            rc.Solver(geoms, params)
