@@ -320,6 +320,34 @@ int recon_debug_op(recon_ctx* ctx, int32_t op);
  * steps of the last solve, [5] final relative residual. */
 int recon_debug_scalars(recon_ctx* ctx, int32_t slice, double* out);
 
+/* Autotuner of the launch shapes.  mode 0: off (default; grid 8 x SMs and
+ * the built-in item sizes).  1: the next recon_set_data also times one
+ * stencil kernel and one FFT solve on scratch fields with grids of
+ * {4, 8, 16} x SMs and keeps the fastest; the arithmetic, and so every
+ * result, is unchanged.  2: as 1, and row items of {2048, 3072, 4096}
+ * complex slots (FP32), which regroups the per-item partial sums of the
+ * PCG reductions and so changes results in the last bits.  The choice holds
+ * for the handle. */
+int recon_set_autotune(recon_ctx* ctx, int32_t mode);
+
+/* The launch shape in use: out2[0] grid multiplier (grid = out2[0] x SMs),
+ * out2[1] complex slots of a row item (0: built-in). */
+int recon_tuning(recon_ctx* ctx, int32_t* out2);
+
+/* Run each following iteration of recon_step as one CUDA graph launch
+ * (on = 1) or as separate launches (0, the default).  The graph is captured
+ * on first use: the steps of Algorithm 1 up to the first PCG step of the
+ * Z^m solve, a conditional WHILE node whose body runs two PCG steps and then
+ * sets the loop condition on the device (continue while a slice has not
+ * converged and fewer than ceil(cg_max_iters / 2) bodies have run), and the
+ * beta update.  Results are bitwise those of the separate launches (PCG
+ * steps past a slice's convergence skip that slice).  The graph runs on a
+ * stream of the handle, ordered after earlier and before later work of the
+ * handle's stream; the iteration that fills recon_stats, and iterations
+ * while recon_profile is on, still run as separate launches.  Needs domain 0
+ * and pcg_kernel 0 (RECON_EINVAL otherwise). */
+int recon_set_graph(recon_ctx* ctx, int32_t on);
+
 /* Number of kernels this handle has launched since creation (counting
  * each launch of each of the library's kernels). */
 int64_t recon_kernel_launches(recon_ctx* ctx);

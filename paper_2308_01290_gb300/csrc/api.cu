@@ -60,6 +60,11 @@ int check_geometry(const recon_geometry& g) {
 }
 
 void free_ctx(Ctx& c) {
+    solver_free_graph(c);
+    if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
+    for (cudaEvent_t e : c.graph_ev)
+        if (e) cudaEventDestroy(e);
+    c.graph_stream = nullptr;
     for (void* p : c.allocations) cudaFree(p);
     c.allocations.clear();
     if (c.h_cg_pending) cudaFreeHost(c.h_cg_pending);
@@ -219,6 +224,7 @@ int recon_set_data(recon_ctx* h, const float* low, const float* high, int on_dev
     if ((rc = solver_load_images(c, lo, hi, 1))) return rc;
     if ((rc = solver_init_maps(c))) return rc;
     if (c.domain == 1 && (rc = solver_modeb_data(c))) return rc;
+    if (c.autotune && !c.tuned && (rc = solver_autotune(c))) return rc;
     c.has_data = true;
     return RECON_OK;
 }
@@ -303,6 +309,7 @@ int recon_sync(recon_ctx* h) {
 void recon_destroy(recon_ctx* h) {
     if (!h) return;
     cudaStreamSynchronize(h->c.stream);
+    if (h->c.graph_stream) cudaStreamSynchronize(h->c.graph_stream);
     free_ctx(h->c);
     delete h;
 }
@@ -414,7 +421,34 @@ int recon_debug_scalars(recon_ctx* h, int32_t slice, double* out) {
     return RECON_OK;
 }
 
-int64_t recon_kernel_launches(recon_ctx* h) { return h ? h->c.launches : -1; }
+int64_t recon_kernel_launches(recon_ctx* h) {
+    return h ? h->c.launches + solver_graph_loop_launches(h->c) : -1;
+}
+
+int recon_set_autotune(recon_ctx* h, int32_t mode) {
+    if (!h || mode < 0 || mode > 2) {
+        set_error("recon_set_autotune: bad arguments");
+        return RECON_EINVAL;
+    }
+    h->c.autotune = mode;
+    h->c.tuned = false;
+    return RECON_OK;
+}
+
+int recon_tuning(recon_ctx* h, int32_t* out2) {
+    if (!h || !out2) return RECON_EINVAL;
+    out2[0] = h->c.grid_mult;
+    out2[1] = h->c.row_budget;
+    return RECON_OK;
+}
+
+int recon_set_graph(recon_ctx* h, int32_t on) {
+    if (!h || (on != 0 && on != 1)) {
+        set_error("recon_set_graph: bad arguments");
+        return RECON_EINVAL;
+    }
+    return solver_set_graph(h->c, on == 1);
+}
 
 int recon_profile(recon_ctx* h, uint32_t mask) {
     if (!h) return RECON_EINVAL;

@@ -23,6 +23,7 @@ struct DevItemList {
     double* partials = nullptr;
     unsigned int* counters = nullptr;
     int n = 0;
+    int cap = 0;                 // items the device arrays hold
     ItemList view() const { return ItemList{items, n, lo, cnt, partials, counters}; }
 };
 
@@ -64,6 +65,7 @@ struct Ctx {
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
     long long fam_launches[KF_COUNT] = {};
+    unsigned long long host_acct[KF_COUNT] = {};   // algorithmic bytes of launches accounted on the host
 
     // cluster-resident PCG
     std::vector<int> cl_slices;
@@ -86,6 +88,21 @@ struct Ctx {
     std::vector<std::pair<int, std::pair<long long, long long>>> tw_index;   // N -> (twiddle, symbol) offsets
     bool has_data = false;
     int cg_parity = 0;
+    // one iteration captured as a CUDA graph (recon_set_graph): the Z^m PCG
+    // runs as a conditional WHILE node of two PCG steps per body
+    bool graph_on = false;
+    cudaStream_t graph_stream = nullptr;    // capture and launch stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaEvent_t graph_ev[2] = {nullptr, nullptr};
+    int* d_graph_body = nullptr;            // bodies run by the current loop
+    unsigned long long* d_graph_launches = nullptr;   // kernels run inside the loops
+    long long graph_static_launches = 0;
+    // launch shape and row-item size (autotuned on request, recon_set_autotune)
+    int grid_mult = 8;           // grid = grid_mult x SMs (grid-stride over items)
+    int row_budget = 0;          // complex slots of a row item; 0: the FFT budget
+    int autotune = 0;            // 0 off, 1 grid, 2 grid and row-item size
+    bool tuned = false;
     long long launches = 0;
     int sm_count = 152;
     std::vector<void*> allocations;
@@ -96,6 +113,10 @@ int solver_setup(Ctx& c);                      // item lists, constants, scratch
 int solver_load_images(Ctx& c, const float* low, const float* high, int on_device);
 int solver_init_maps(Ctx& c);
 int solver_setup_sino(Ctx& c);                 // domain 1: gamma and the sinogram scratch
+int solver_set_graph(Ctx& c, bool on);         // capture each iteration as one CUDA graph
+int solver_autotune(Ctx& c);                   // pick grid_mult (and row_budget) by timing
+void solver_free_graph(Ctx& c);
+long long solver_graph_loop_launches(Ctx& c);  // kernels run inside captured loops so far
 int solver_modeb_data(Ctx& c);                 // domain 1: data images t_k from the sinograms
 int solver_iterate(Ctx& c, bool stats);        // one iteration of Algorithm 1
 int solver_op(Ctx& c, int op);

@@ -1573,7 +1573,7 @@ Ptrs<T> ptrs(Ctx& c) {
 }
 
 int grid_for(const Ctx& c, int work) {
-    const int cap = c.sm_count * 8;
+    const int cap = c.sm_count * c.grid_mult;
     return work < cap ? (work > 0 ? work : 1) : cap;
 }
 
@@ -1772,11 +1772,15 @@ T* field_base(Ctx& c, int f) {
     return static_cast<T*>(c.field[f]) + c.sg[0].off;
 }
 
-// out (cleared) = A^T A x over all slices
+// out (cleared) = A^T A x over all slices.  Algorithmic HBM bytes: the image
+// read and the sinogram written by A, the sinogram read and the image added
+// to by A^T (the gathers themselves hit the L2-resident image).
 int gram_all(Ctx& c, const float* x, float* out) {
     const recon_geometry& g = c.geo[0];
     const long long pitch = c.sg[0].pitch, stride = (long long)c.sg[0].ny * pitch;
     FamTimer t(c, KF_PROJ);
+    c.host_acct[KF_PROJ] += 4ull * (unsigned long long)c.n *
+                            (3ull * g.nx * g.ny + 2ull * (unsigned long long)g.n_views * g.n_bins);
     int rc;
     if ((rc = ct_project_pitched(g, c.n, x, pitch, stride, c.d_sino_tmp, c.stream, &c.launches))) return rc;
     RECON_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * stride * c.n, c.stream));
@@ -1852,6 +1856,141 @@ int op_next_beta(Ctx& c) {
     k_next_beta<<<(c.n + 127) / 128, 128, 0, c.stream>>>(c.n, c.d_const, c.d_state);
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
+int alloc_dev(Ctx& c, void** p, size_t bytes);
+
+// ---- one iteration as a CUDA graph ----
+
+// Set the WHILE condition of the PCG loop before its first body.
+__global__ void k_pcg_loop_start(cudaGraphConditionalHandle h, const int* pending, int* body) {
+    *body = 0;
+    cudaGraphSetConditional(h, *pending > 0 ? 1u : 0u);
+}
+
+// End of a body (two PCG steps): run another while a slice has not
+// converged and fewer than `cap` bodies have run (bounded loop).
+__global__ void k_pcg_loop_cond(cudaGraphConditionalHandle h, const int* pending, int* body, int cap,
+                                unsigned long long* launches) {
+    const int b = *body + 1;
+    *body = b;
+    cudaGraphSetConditional(h, (*pending > 0 && b < cap) ? 1u : 0u);
+    atomicAdd(launches, 7ull);   // six PCG kernels and this one
+}
+
+template <typename T>
+int graph_build_t(Ctx& c) {
+    const Ptrs<T> P = ptrs<T>(c);
+    const int smem = fft_smem_bytes<T>(c), smem_c = smem;
+    const cplx<T>* tw = static_cast<const cplx<T>*>(c.d_tw);
+    const int half = fft_half_slots<T>(c), half_c = half;
+    const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 3);
+    int cap = 0;
+    for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
+    const int bodies = (cap + 1) / 2;
+    cudaStream_t user = c.stream;
+    c.stream = c.graph_stream;   // the op functions launch on c.stream
+    int rc = RECON_OK;
+    const long long l0 = c.launches;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t cond = nullptr;
+    auto fail = [&](cudaError_t e, const char* what) {
+        c.stream = user;
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(e, what);
+    };
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return fail(e, "cudaGraphCreate");
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
+    // 1. threshold + rhs, f and rho_e solves, synthesis, start of the PCG
+    e = cudaStreamBeginCaptureToGraph(c.stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(e, "capture (iteration head)");
+    if (!rc) rc = op_thr_rhs<T>(c, false);
+    if (!rc) rc = op_solve_f<T>(c);
+    if (!rc) rc = op_synth<T>(c);
+    if (!rc) rc = fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2));
+    if (!rc) {
+        cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream);
+        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+                                                                              c.d_state, P, c.d_cg_pending);
+        k_pcg_fwd<T, false><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
+            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, 0, c.d_cg_pending);
+        k_pcg_loop_start<<<1, 1, 0, c.stream>>>(h, c.d_cg_pending, c.d_graph_body);
+        c.launches += 3;
+    }
+    e = cudaStreamEndCapture(c.stream, &g);
+    if (rc) {
+        c.stream = user;
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(e, "capture end (iteration head)");
+    // leaves of the head become the dependencies of the loop
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn), leaves;
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (cudaGraphNode_t n : nodes) {
+        size_t nd = 0;
+        cudaGraphNodeGetDependentNodes(n, nullptr, nullptr, &nd);
+        if (nd == 0) leaves.push_back(n);
+    }
+    // 2. WHILE (pending && body < bodies): two PCG steps
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    e = cudaGraphAddNode(&cond, g, leaves.data(), nullptr, leaves.size(), &cp);
+    if (e != cudaSuccess) return fail(e, "cudaGraphAddNode (while)");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(e, "capture (PCG body)");
+    for (int par = 0; par < 2; ++par) {
+        k_cols<T><<<grid_for(c, c.cols.n), kFftThreads, smem_c, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
+                                                                            c.d_state, P, pre, tw, half_c);
+        k_pcg_inv<T><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom, c.d_state, P,
+                                                                            tw, half, par);
+        k_pcg_fwd<T, true><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
+            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending);
+    }
+    k_pcg_loop_cond<<<1, 1, 0, c.stream>>>(h, c.d_cg_pending, c.d_graph_body, bodies, c.d_graph_launches);
+    e = cudaStreamEndCapture(c.stream, &body);
+    if (e != cudaSuccess) return fail(e, "capture end (PCG body)");
+    // 3. beta schedule after the loop
+    e = cudaStreamBeginCaptureToGraph(c.stream, g, &cond, nullptr, 1, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(e, "capture (iteration tail)");
+    rc = op_next_beta<T>(c);
+    e = cudaStreamEndCapture(c.stream, &g);
+    c.stream = user;
+    if (rc) {
+        cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(e, "capture end (iteration tail)");
+    e = cudaGraphInstantiate(&c.graph_exec, g, 0);
+    if (e != cudaSuccess) return fail(e, "cudaGraphInstantiate");
+    c.graph = g;
+    c.graph_static_launches = c.launches - l0;
+    c.launches = l0;
+    return RECON_OK;
+}
+
+// One captured iteration on the graph stream, ordered after and before the
+// work of the handle's stream.
+template <typename T>
+int graph_iterate_t(Ctx& c) {
+    int rc;
+    if (!c.graph_exec && (rc = graph_build_t<T>(c))) return rc;
+    RECON_CUDA(cudaEventRecord(c.graph_ev[0], c.stream));
+    RECON_CUDA(cudaStreamWaitEvent(c.graph_stream, c.graph_ev[0], 0));
+    RECON_CUDA(cudaGraphLaunch(c.graph_exec, c.graph_stream));
+    RECON_CUDA(cudaEventRecord(c.graph_ev[1], c.graph_stream));
+    RECON_CUDA(cudaStreamWaitEvent(c.stream, c.graph_ev[1], 0));
+    c.launches += c.graph_static_launches;
     return RECON_OK;
 }
 
@@ -1966,7 +2105,7 @@ void slice_items(Ctx& c, int s, std::vector<Item>& tiles, std::vector<Item>& row
     for (int ty = 0; ty < g.ny; ty += th)
         for (int tx = 0; tx < g.nx; tx += kTileW) tiles.push_back(Item{s, tx, ty, 0});
     const int npairs = (g.ny + 1) / 2;
-    const int per = rows_per_item(g.nx, g.ny, budget);
+    const int per = rows_per_item(g.nx, g.ny, c.row_budget > 0 ? c.row_budget : budget);
     g.rows_per_item = per;
     for (int p0 = 0; p0 < npairs; p0 += per) rows.push_back(Item{s, p0, (npairs - p0 < per ? npairs - p0 : per), 0});
     const int pc = cols_per_item(g.nx, g.ny, budget);
@@ -1988,6 +2127,7 @@ int alloc_dev(Ctx& c, void** p, size_t bytes) {
 int upload_list(Ctx& c, DevItemList& L) {
     int rc;
     L.n = (int)L.h_items.size();
+    L.cap = L.n;
     if ((rc = alloc_dev(c, (void**)&L.items, sizeof(Item) * L.h_items.size()))) return rc;
     if ((rc = alloc_dev(c, (void**)&L.lo, sizeof(int) * c.n))) return rc;
     if ((rc = alloc_dev(c, (void**)&L.cnt, sizeof(int) * c.n))) return rc;
@@ -2218,35 +2358,77 @@ int solver_modeb_data(Ctx& c) {
     return RECON_OK;
 }
 
-int solver_iterate(Ctx& c, bool stats) {
-    return c.precision == 1 ? iterate_t<float>(c, stats) : iterate_t<double>(c, stats);
+// Time `reps` passes of one stencil kernel (k_cg_init) and one FFT solve
+// (CG_R -> CG_Y, the rho_e divide) on fields the solve state does not use
+// before the next iteration; returns the time in ms.
+template <typename T>
+int tune_time(Ctx& c, int reps, float* ms) {
+    const Ptrs<T> P = ptrs<T>(c);
+    cudaEvent_t a, b;
+    RECON_CUDA(cudaEventCreate(&a));
+    RECON_CUDA(cudaEventCreate(&b));
+    int rc = RECON_OK;
+    for (int r = -1; r < reps && !rc; ++r) {   // r = -1: warm-up
+        if (r == 0) cudaEventRecord(a, c.stream);
+        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+                                                                              c.d_state, P, c.d_cg_pending);
+        c.launches += 1;
+        rc = fft_solve<T>(c, jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 2));
+    }
+    cudaEventRecord(b, c.stream);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (!rc && e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    return e == cudaSuccess ? RECON_OK : cuda_fail(e, "autotune timing");
 }
 
-int solver_op(Ctx& c, int op) { return c.precision == 1 ? op_t<float>(c, op) : op_t<double>(c, op); }
-
-int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int /*on_device*/) {
-    return c.precision == 1 ? extract_t<float>(c, Z, rhoe, f1, f2) : extract_t<double>(c, Z, rhoe, f1, f2);
+void solver_free_graph(Ctx& c) {
+    if (c.graph_exec) cudaGraphExecDestroy(c.graph_exec);
+    if (c.graph) cudaGraphDestroy(c.graph);
+    c.graph_exec = nullptr;
+    c.graph = nullptr;
 }
 
-__global__ void k_reset_slots(const int* slots, int n, const SliceConst* C, SliceState* S) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int s = slots[i];
-    const SliceConst& c = C[s];
-    SliceState st = {};
-    st.beta = c.beta0;
-    st.beta_t = c.tau * c.beta0;
-    st.thr_d = c.lambda / c.beta0;
-    st.thr_f = (float)st.thr_d;
-    st.active = c.iters > 0;
-    st.cg_done = 1;
-    S[s] = st;
+int solver_set_graph(Ctx& c, bool on) {
+    if (on && (c.domain != 0 || c.use_cluster || c.server_mode)) {
+        set_error("graph capture needs domain 0, pcg_kernel 0 and a solve handle");
+        return RECON_EINVAL;
+    }
+    solver_free_graph(c);
+    if (on && !c.graph_stream) {
+        RECON_CUDA(cudaStreamCreateWithFlags(&c.graph_stream, cudaStreamNonBlocking));
+        RECON_CUDA(cudaEventCreateWithFlags(&c.graph_ev[0], cudaEventDisableTiming));
+        RECON_CUDA(cudaEventCreateWithFlags(&c.graph_ev[1], cudaEventDisableTiming));
+        int rc;
+        if ((rc = alloc_dev(c, (void**)&c.d_graph_body, sizeof(int)))) return rc;
+        if ((rc = alloc_dev(c, (void**)&c.d_graph_launches, sizeof(unsigned long long)))) return rc;
+        RECON_CUDA(cudaMemset(c.d_graph_launches, 0, sizeof(unsigned long long)));
+    }
+    c.graph_on = on;
+    return RECON_OK;
+}
+
+long long solver_graph_loop_launches(Ctx& c) {
+    if (!c.d_graph_launches) return 0;
+    unsigned long long v = 0;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess || cudaStreamSynchronize(c.graph_stream) != cudaSuccess ||
+        cudaMemcpy(&v, c.d_graph_launches, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return 0;
+    return (long long)v;
 }
 
 namespace {
 // Copy host item vectors into a device list allocated at capacity.
 int fill_list(Ctx& c, DevItemList& L) {
     L.n = (int)L.h_items.size();
+    if (L.n > L.cap) {   // more items than at setup (smaller row items): larger arrays
+        int rc;
+        if ((rc = alloc_dev(c, (void**)&L.items, sizeof(Item) * L.n))) return rc;
+        if ((rc = alloc_dev(c, (void**)&L.partials, sizeof(double) * kMaxPartials * L.n))) return rc;
+        L.cap = L.n;
+    }
     if (L.n)
         RECON_CUDA(cudaMemcpyAsync(L.items, L.h_items.data(), sizeof(Item) * L.h_items.size(), cudaMemcpyHostToDevice,
                                    c.stream));
@@ -2281,6 +2463,75 @@ void lists_for(Ctx& c, const std::vector<int>& slots, DevItemList* tiles, DevIte
     }
 }
 }  // namespace
+
+// Candidates: grid = {4, 8, 16} x SMs (the arithmetic is the same for all;
+// items and their partial sums do not change), and with autotune = 2 (FP32)
+// row items of {2048, 3072, 4096} complex slots, which regroups the per-item
+// partial sums of the PCG reductions (last-bit differences).  Best of three
+// timed passes each; the choice holds for the handle.
+int solver_autotune(Ctx& c) {
+    if (c.autotune == 0 || c.server_mode) return RECON_OK;
+    std::vector<int> all(c.n);
+    for (int s = 0; s < c.n; ++s) all[s] = s;
+    std::vector<int> budgets = {c.row_budget};
+    if (c.autotune == 2 && c.precision == 1) budgets = {2048, 3072, 4096};
+    float best = 1e30f;
+    int best_m = c.grid_mult, best_b = c.row_budget;
+    int rc;
+    for (int b : budgets) {
+        c.row_budget = b;
+        lists_for(c, all, &c.tiles, &c.rows, &c.cols);
+        if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+        if ((rc = c.precision == 1 ? set_fft_smem<float>(c) : set_fft_smem<double>(c))) return rc;
+        for (int m : {4, 8, 16}) {
+            c.grid_mult = m;
+            float ms = 0.f;
+            if ((rc = c.precision == 1 ? tune_time<float>(c, 3, &ms) : tune_time<double>(c, 3, &ms))) return rc;
+            if (ms < best) {
+                best = ms;
+                best_m = m;
+                best_b = b;
+            }
+        }
+    }
+    c.grid_mult = best_m;
+    c.row_budget = best_b;
+    lists_for(c, all, &c.tiles, &c.rows, &c.cols);
+    if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+    if ((rc = c.precision == 1 ? set_fft_smem<float>(c) : set_fft_smem<double>(c))) return rc;
+    c.tuned = true;
+    solver_free_graph(c);   // a captured graph holds the old launch shapes
+    return RECON_OK;
+}
+
+int solver_iterate(Ctx& c, bool stats) {
+    if (c.graph_on && !stats && c.prof_mask == 0)
+        return c.precision == 1 ? graph_iterate_t<float>(c) : graph_iterate_t<double>(c);
+    return c.precision == 1 ? iterate_t<float>(c, stats) : iterate_t<double>(c, stats);
+}
+
+int solver_op(Ctx& c, int op) { return c.precision == 1 ? op_t<float>(c, op) : op_t<double>(c, op); }
+
+int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int /*on_device*/) {
+    return c.precision == 1 ? extract_t<float>(c, Z, rhoe, f1, f2) : extract_t<double>(c, Z, rhoe, f1, f2);
+}
+
+__global__ void k_reset_slots(const int* slots, int n, const SliceConst* C, SliceState* S) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int s = slots[i];
+    const SliceConst& c = C[s];
+    SliceState st = {};
+    st.beta = c.beta0;
+    st.beta_t = c.tau * c.beta0;
+    st.thr_d = c.lambda / c.beta0;
+    st.thr_f = (float)st.thr_d;
+    st.active = c.iters > 0;
+    st.cg_done = 1;
+    S[s] = st;
+}
+
+
 
 int solver_configure_slot(Ctx& c, int s, const recon_geometry& geo, const recon_params& p) {
     if (!c.server_mode || s < 0 || s >= c.n) return RECON_EINVAL;
@@ -2413,7 +2664,8 @@ int solver_profile_read(Ctx& c, double* ms, long long* launches, unsigned long l
     RECON_CUDA(cudaMemcpy(h.data(), c.d_acct, sizeof(unsigned long long) * KF_COUNT, cudaMemcpyDeviceToHost));
     RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
     if (bytes)
-        for (int f = 0; f < KF_COUNT; ++f) bytes[f] = h[f];
+        for (int f = 0; f < KF_COUNT; ++f) bytes[f] = h[f] + c.host_acct[f];
+    for (int f = 0; f < KF_COUNT; ++f) c.host_acct[f] = 0;
     return RECON_OK;
 }
 

@@ -100,6 +100,9 @@ def _load():
         "recon_debug_io": (I, [VP, C.c_int32, C.c_int32, P(D), C.c_int32]),
         "recon_debug_scalars": (I, [VP, C.c_int32, P(D)]),
         "recon_kernel_launches": (C.c_int64, [VP]),
+        "recon_set_graph": (I, [VP, C.c_int32]),
+        "recon_set_autotune": (I, [VP, C.c_int32]),
+        "recon_tuning": (I, [VP, P(C.c_int32)]),
         "recon_abi_sizes": (I, [P(C.c_int64)]),
         "recon_server_create": (I, [P(ServerConfig), VP, P(VP)]),
         "recon_submit": (I, [VP, P(Request), P(C.c_uint64)]),
@@ -133,7 +136,8 @@ _check_layout()
 EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_data", "recon_step", "recon_get",
            "recon_sync", "recon_destroy", "recon_solve", "recon_strerror", "recon_last_error", "recon_project",
            "recon_backproject", "recon_fbp", "recon_fbp_noalloc", "recon_simulate", "recon_model_tables", "recon_debug_field",
-           "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches",
+           "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches", "recon_set_graph",
+           "recon_set_autotune", "recon_tuning",
            "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name", "recon_server_create",
            "recon_submit", "recon_server_step", "recon_poll", "recon_server_stats", "recon_server_destroy")
 KF_COUNT = 13
@@ -317,6 +321,20 @@ class Solver:
 
     def launches(self):
         return int(lib.recon_kernel_launches(self.h))
+
+    def set_graph(self, on=True):
+        """Run each following iteration as one CUDA graph launch (recon_set_graph)."""
+        _check(lib.recon_set_graph(self.h, 1 if on else 0), "recon_set_graph")
+
+    def set_autotune(self, mode=1):
+        """Tune the launch shapes at the next set_data (recon_set_autotune)."""
+        _check(lib.recon_set_autotune(self.h, int(mode)), "recon_set_autotune")
+
+    def tuning(self):
+        """(grid multiplier, row-item slots) in use (recon_tuning)."""
+        out = (C.c_int32 * 2)()
+        _check(lib.recon_tuning(self.h, out), "recon_tuning")
+        return int(out[0]), int(out[1])
 
 
 def solve(low, high, geom: Geometry, lam, beta, iters):

@@ -247,3 +247,57 @@ def test_cluster_full_solve_matches_oracle(rc, small_case):
     body = c["P"]["rhoe"] >= 0.1
     r = report("cluster-pcg", Z, rho, c["ref"], body)
     assert parity_ok(r), r
+
+
+def test_graph_iterations_equal_separate_launches(rc, small_case):
+    """Iterations run as one CUDA graph launch each (a conditional WHILE node
+    for the Z^m PCG) give bitwise the maps of separate launches."""
+    c = small_case
+    acq = c["acq"]
+    g = rc.geometry(acq.nx, acq.ny)
+    p = rc.default_params(low=acq.low, high=acq.high, iters=12)
+    lo = np.stack([c["muL"], 1.02 * c["muL"]]).astype(np.float32)
+    hi = np.stack([c["muH"], 1.02 * c["muH"]]).astype(np.float32)
+    out = []
+    for graph in (False, True):
+        s = rc.Solver([g, g], [p, p])
+        if graph:
+            s.set_graph(True)
+        s.set_data(lo, hi)
+        s.step(12)
+        out.append(s.get_host())
+        launches = s.launches()
+        s.close()
+        assert launches > 12 * 20, launches
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_keeps_results(rc, small_case):
+    """Autotune mode 1 picks a grid of {4, 8, 16} x SMs and leaves every
+    result bitwise as it was; mode 2 also picks a row-item size and stays
+    within the final-map tolerance of the untuned solve."""
+    c = small_case
+    acq = c["acq"]
+    g = rc.geometry(acq.nx, acq.ny)
+    p = rc.default_params(low=acq.low, high=acq.high, iters=10)
+    lo = np.stack([c["muL"], 0.98 * c["muL"]]).astype(np.float32)
+    hi = np.stack([c["muH"], 0.98 * c["muH"]]).astype(np.float32)
+    out, tunes = [], []
+    for mode in (0, 1, 2):
+        s = rc.Solver([g, g], [p, p])
+        s.set_autotune(mode)
+        s.set_data(lo, hi)
+        s.step(10)
+        out.append(s.get_host())
+        tunes.append(s.tuning())
+        s.close()
+    assert tunes[0] == (8, 0)
+    assert tunes[1][0] in (4, 8, 16) and tunes[1][1] == 0
+    assert tunes[2][0] in (4, 8, 16) and tunes[2][1] in (2048, 3072, 4096)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+    body = c["P"]["rhoe"] >= 0.1
+    for k in range(2):
+        assert np.abs(out[2][0][k] - out[0][0][k])[body].mean() <= 0.01
+        assert np.abs(out[2][1][k] - out[0][1][k])[body].mean() <= 1e-3
