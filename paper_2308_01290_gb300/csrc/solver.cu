@@ -189,21 +189,59 @@ template <typename T, int NM, typename FS, typename FV>
 __device__ __forceinline__ void load_tile(T (*sm)[TileDim<T>::TH + 2][TileDim<T>::SW], const SliceGeom& g, int tx0,
                                           int ty0, FS scal, FV vect) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH;
-    if (tx0 + kTileW <= g.nx) {
+    if (NM > 2 && tx0 + kTileW <= g.nx) {
+        // many maps: round by round (registers)
         constexpr int VR = kTileW / VN;
         for (int q = threadIdx.x; q < (TH + 2) * VR; q += blockDim.x) {
             const int ly = q / VR, lx = (q - ly * VR) * VN;
             const int gy = wrap(ty0 - 1 + ly, g.ny);
             const PVals<T, NM> pv = vect(g.off + (long long)gy * g.pitch + tx0 + lx);
 #pragma unroll
-            for (int m = 0; m < NM; ++m)
-                *reinterpret_cast<Pack<T>*>(&sm[m][ly][OFF + lx]) = pv.p[m];
+            for (int m = 0; m < NM; ++m) *reinterpret_cast<Pack<T>*>(&sm[m][ly][OFF + lx]) = pv.p[m];
         }
         for (int q = threadIdx.x; q < 2 * (TH + 2); q += blockDim.x) {
             const int ly = q >> 1, side = q & 1;
             const int gy = wrap(ty0 - 1 + ly, g.ny);
             const int gx = side ? wrap(tx0 + kTileW, g.nx) : wrap(tx0 - 1, g.nx);
             const Vals<T, NM> sv = scal(g.off + (long long)gy * g.pitch + gx);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) sm[m][ly][side ? OFF + kTileW : OFF - 1] = sv.v[m];
+        }
+    } else if (tx0 + kTileW <= g.nx) {
+        // every load of the tile (vector rounds and halo) is issued before
+        // the first store to shared memory; blockDim.x == kStencilThreads
+        constexpr int VR = kTileW / VN, NV = (TH + 2) * VR;
+        constexpr int RV = (NV + kStencilThreads - 1) / kStencilThreads;
+        PVals<T, NM> pv[RV];
+#pragma unroll
+        for (int u = 0; u < RV; ++u) {
+            const int q = threadIdx.x + u * kStencilThreads;
+            if (q < NV) {
+                const int ly = q / VR, lx = (q - ly * VR) * VN;
+                const int gy = wrap(ty0 - 1 + ly, g.ny);
+                pv[u] = vect(g.off + (long long)gy * g.pitch + tx0 + lx);
+            }
+        }
+        const int hq = threadIdx.x;
+        const bool halo = hq < 2 * (TH + 2);
+        Vals<T, NM> sv;
+        if (halo) {
+            const int ly = hq >> 1, side = hq & 1;
+            const int gy = wrap(ty0 - 1 + ly, g.ny);
+            const int gx = side ? wrap(tx0 + kTileW, g.nx) : wrap(tx0 - 1, g.nx);
+            sv = scal(g.off + (long long)gy * g.pitch + gx);
+        }
+#pragma unroll
+        for (int u = 0; u < RV; ++u) {
+            const int q = threadIdx.x + u * kStencilThreads;
+            if (q < NV) {
+                const int ly = q / VR, lx = (q - ly * VR) * VN;
+#pragma unroll
+                for (int m = 0; m < NM; ++m) *reinterpret_cast<Pack<T>*>(&sm[m][ly][OFF + lx]) = pv[u].p[m];
+            }
+        }
+        if (halo) {
+            const int ly = hq >> 1, side = hq & 1;
 #pragma unroll
             for (int m = 0; m < NM; ++m) sm[m][ly][side ? OFF + kTileW : OFF - 1] = sv.v[m];
         }
@@ -227,12 +265,73 @@ __device__ __forceinline__ void stv(T* p, long long d, const Pack<T>& v) {
     *reinterpret_cast<Pack<T>*>(p + d) = v;
 }
 
+// Visit the pixels of a tile VN at a time: fn(d0, e_count, full) with d0 the
+// element offset of the first pixel of the vector; `full` when all VN lie
+// inside the image.
+template <typename T, typename F>
+__device__ __forceinline__ void for_tile_vectors(const SliceGeom& g, const Item& it, F fn) {
+    constexpr int VN = TileDim<T>::VN, VR = kTileW / VN;
+    for (int q = threadIdx.x; q < TileDim<T>::TH * VR; q += blockDim.x) {
+        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
+        const int y = it.b + ly, x0 = it.a + lx0;
+        if (y >= g.ny || x0 >= g.nx) continue;
+        const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
+        fn(g.off + (long long)y * g.pitch + x0, cnt, ly, lx0);
+    }
+}
+
+// As for_tile_vectors, in two phases: load(d0, cnt) for every vector of the
+// thread first, then store(d0, cnt, ly, lx0, loaded) for each; the loads of
+// all rounds are in flight together.  blockDim.x == kStencilThreads.
+template <typename T, typename FL, typename FS>
+__device__ __forceinline__ void for_tile_vectors2(const SliceGeom& g, const Item& it, FL load, FS store) {
+    constexpr int VN = TileDim<T>::VN, VR = kTileW / VN, TOTAL = TileDim<T>::TH * VR;
+    constexpr int R = (TOTAL + kStencilThreads - 1) / kStencilThreads;
+    using V = decltype(load(0LL, 0));
+    V v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int q = threadIdx.x + u * kStencilThreads;
+        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
+        const int y = it.b + ly, x0 = it.a + lx0;
+        if (q < TOTAL && y < g.ny && x0 < g.nx)
+            v[u] = load(g.off + (long long)y * g.pitch + x0, g.nx - x0 < VN ? g.nx - x0 : VN);
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int q = threadIdx.x + u * kStencilThreads;
+        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
+        const int y = it.b + ly, x0 = it.a + lx0;
+        if (q < TOTAL && y < g.ny && x0 < g.nx)
+            store(g.off + (long long)y * g.pitch + x0, g.nx - x0 < VN ? g.nx - x0 : VN, ly, lx0, v[u]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ Pack<T> ldv_n(const T* p, long long d, int cnt) {
+    if (cnt == TileDim<T>::VN) return ldv(p, d);
+    Pack<T> r;
+#pragma unroll
+    for (int e = 0; e < TileDim<T>::VN; ++e) r.v[e] = e < cnt ? p[d + e] : T(0);
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ void stv_n(T* p, long long d, const Pack<T>& v, int cnt) {
+    if (cnt == TileDim<T>::VN) {
+        stv(p, d, v);
+        return;
+    }
+#pragma unroll
+    for (int e = 0; e < TileDim<T>::VN; ++e)
+        if (e < cnt) p[d + e] = v.v[e];
+}
+
 // --------------------------------------------------------------------------
 // K1: hard threshold (eq. sol_hv) + right-hand sides
 // --------------------------------------------------------------------------
 
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(kStencilThreads) k_thr_rhs(ItemList L, const SliceGeom* G, const SliceConst* C,
+__global__ void __launch_bounds__(kStencilThreads, 2) k_thr_rhs(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                              SliceState* S, Ptrs<T> P) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
     __shared__ __align__(16) T sm[4][TileDim<T>::TH + 2][SW];
@@ -261,41 +360,31 @@ __global__ void __launch_bounds__(kStencilThreads) k_thr_rhs(ItemList L, const S
         const SliceConst& c = s_c;
         const T thr = thr_of<T>(s_st);
         const T beta = T(s_st.beta), beta_t = T(s_st.beta_t);
-        const bool full = it.a + kTileW <= g.nx;
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-        constexpr int VR = kTileW / VN;
-        for (int q = threadIdx.x; q < TileDim<T>::TH * VR; q += blockDim.x) {
-            const int ly = q / VR, lx0 = (q - ly * VR) * VN;
-            const int y = it.b + ly;
-            if (y >= g.ny) continue;
-            const long long d0 = g.off + (long long)y * g.pitch + it.a + lx0;
-            // image domain: uL, uH = mu_hat(E_L), mu_hat(E_H).  Sinogram domain
-            // (domain 1): uL, uH = t_1, t_2 and G1, G2 = A^T A f1, A^T A f2
-            const bool sino = c.domain == 1;
+        // image domain: uL, uH = mu_hat(E_L), mu_hat(E_H).  Sinogram domain
+        // (domain 1): uL, uH = t_1, t_2 and G1, G2 = A^T A f1, A^T A f2
+        const bool sino = c.domain == 1;
+        struct In {
             Pack<T> uL, uH, G1, G2;
-            if (full) {
-                uL = ldv(P.f[RECON_F_MUL], d0);
-                uH = ldv(P.f[RECON_F_MUH], d0);
-                if (sino) {
-                    G1 = ldv(P.f[RECON_F_A2], d0);
-                    G2 = ldv(P.f[RECON_F_RHS_Z], d0);
-                }
-            } else {
-#pragma unroll
-                for (int e = 0; e < VN; ++e) {
-                    const bool in = it.a + lx0 + e < g.nx;
-                    uL.v[e] = in ? P.f[RECON_F_MUL][d0 + e] : T(0);
-                    uH.v[e] = in ? P.f[RECON_F_MUH][d0 + e] : T(0);
-                    G1.v[e] = (in && sino) ? P.f[RECON_F_A2][d0 + e] : T(0);
-                    G2.v[e] = (in && sino) ? P.f[RECON_F_RHS_Z][d0 + e] : T(0);
-                }
+        };
+        auto load = [&](long long d, int cnt) {
+            In x;
+            x.uL = ldv_n(P.f[RECON_F_MUL], d, cnt);
+            x.uH = ldv_n(P.f[RECON_F_MUH], d, cnt);
+            if (sino) {
+                x.G1 = ldv_n(P.f[RECON_F_A2], d, cnt);
+                x.G2 = ldv_n(P.f[RECON_F_RHS_Z], d, cnt);
             }
+            return x;
+        };
+        for_tile_vectors2<T>(g, it, load, [&](long long d0, int cnt, int ly, int lx0, const In& x) {
+            const Pack<T>&uL = x.uL, &uH = x.uH, &G1 = x.G1, &G2 = x.G2;
             Pack<T> o0, o1, o2, o3;
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 const int lx = OFF + lx0 + e;   // column of this pixel in sm
                 const int ry = ly + 1;
-                const bool in = full || (it.a + lx0 + e < g.nx);
+                const bool in = e < cnt;
                 T div[4];
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
@@ -346,22 +435,11 @@ __global__ void __launch_bounds__(kStencilThreads) k_thr_rhs(ItemList L, const S
                     acc[3] += e2 * e2;
                 }
             }
-            if (full) {
-                stv(P.f[RECON_F_RHS_F1], d0, o0);
-                stv(P.f[RECON_F_RHS_F2], d0, o1);
-                stv(P.f[RECON_F_DIV_RHO], d0, o2);
-                stv(P.f[RECON_F_DIV_Z], d0, o3);
-            } else {
-#pragma unroll
-                for (int e = 0; e < VN; ++e) {
-                    if (it.a + lx0 + e >= g.nx) continue;
-                    P.f[RECON_F_RHS_F1][d0 + e] = o0.v[e];
-                    P.f[RECON_F_RHS_F2][d0 + e] = o1.v[e];
-                    P.f[RECON_F_DIV_RHO][d0 + e] = o2.v[e];
-                    P.f[RECON_F_DIV_Z][d0 + e] = o3.v[e];
-                }
-            }
-        }
+            stv_n(P.f[RECON_F_RHS_F1], d0, o0, cnt);
+            stv_n(P.f[RECON_F_RHS_F2], d0, o1, cnt);
+            stv_n(P.f[RECON_F_DIV_RHO], d0, o2, cnt);
+            stv_n(P.f[RECON_F_DIV_Z], d0, o3, cnt);
+        });
         if (STATS) {
             block_sum<9>(acc, red);
             double tot[9];
@@ -567,13 +645,14 @@ __device__ __forceinline__ void cols_item_p2(cplx<T>* spc, int cpitch, int nc, i
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                        SliceState* S, Ptrs<T> P, FftJobs J,
-                                                       const cplx<T>* twpool, int half) {
+                                                       const cplx<T>* twpool, int half, int rev = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* buf0 = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf1 = buf0 + half;
     __shared__ double red[32];
     const int total = L.n_items * J.n;
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    for (int w0 = blockIdx.x; w0 < total; w0 += gridDim.x) {
+        const int w = rev ? total - 1 - w0 : w0;   // reversed order: see op_solve_z
         const int job = w / L.n_items, item = w - job * L.n_items;
         const Item it = L.items[item];
         const int kind = J.coef[job];
@@ -842,12 +921,13 @@ template <typename T, bool UPD>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_fwd(ItemList L, const SliceGeom* G,
                                                                         const SliceConst* C, SliceState* S, Ptrs<T> P,
                                                                         const cplx<T>* twpool, int half, int par,
-                                                                        int* pending) {
+                                                                        int* pending, int rev = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf2 = buf + half;
     __shared__ double red[32];
-    for (int item = blockIdx.x; item < L.n_items; item += gridDim.x) {
+    for (int w0 = blockIdx.x; w0 < L.n_items; w0 += gridDim.x) {
+        const int item = rev ? L.n_items - 1 - w0 : w0;
         const Item it = L.items[item];
         const SliceState* sp = S + it.slice;
         if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
@@ -1001,7 +1081,7 @@ __device__ __forceinline__ float pcg_inv_tail_p2(float* rx, float* a2s, int ld, 
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList L, const SliceGeom* G, SliceState* S,
                                                                         Ptrs<T> P, const cplx<T>* twpool, int half,
-                                                                        int par) {
+                                                                        int par, int rev = 0) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<T>* buf = reinterpret_cast<cplx<T>*>(smem_raw);
     cplx<T>* buf2 = buf + half;
@@ -1010,7 +1090,8 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
     T* pnew = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
     const T* a2 = P.f[RECON_F_A2];
     T* qo = P.f[RECON_F_CG_Q];
-    for (int item = blockIdx.x; item < L.n_items; item += gridDim.x) {
+    for (int w0 = blockIdx.x; w0 < L.n_items; w0 += gridDim.x) {
+        const int item = rev ? L.n_items - 1 - w0 : w0;
         const Item it = L.items[item];
         const SliceState* sp = S + it.slice;
         if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
@@ -1139,40 +1220,6 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
 // synthesis at E1/E2 from the new f, rho_e rhs, Z^m normal equations
 // --------------------------------------------------------------------------
 
-// Visit the pixels of a tile VN at a time: fn(d0, e_count, full) with d0 the
-// element offset of the first pixel of the vector; `full` when all VN lie
-// inside the image.
-template <typename T, typename F>
-__device__ __forceinline__ void for_tile_vectors(const SliceGeom& g, const Item& it, F fn) {
-    constexpr int VN = TileDim<T>::VN, VR = kTileW / VN;
-    for (int q = threadIdx.x; q < TileDim<T>::TH * VR; q += blockDim.x) {
-        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
-        const int y = it.b + ly, x0 = it.a + lx0;
-        if (y >= g.ny || x0 >= g.nx) continue;
-        const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
-        fn(g.off + (long long)y * g.pitch + x0, cnt, ly, lx0);
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ Pack<T> ldv_n(const T* p, long long d, int cnt) {
-    if (cnt == TileDim<T>::VN) return ldv(p, d);
-    Pack<T> r;
-#pragma unroll
-    for (int e = 0; e < TileDim<T>::VN; ++e) r.v[e] = e < cnt ? p[d + e] : T(0);
-    return r;
-}
-template <typename T>
-__device__ __forceinline__ void stv_n(T* p, long long d, const Pack<T>& v, int cnt) {
-    if (cnt == TileDim<T>::VN) {
-        stv(p, d, v);
-        return;
-    }
-#pragma unroll
-    for (int e = 0; e < TileDim<T>::VN; ++e)
-        if (e < cnt) p[d + e] = v.v[e];
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                            SliceState* S, Ptrs<T> P) {
@@ -1244,7 +1291,7 @@ __device__ __forceinline__ T lap5(const T (*sm)[TileDim<T>::SW], int ry, int cx)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
+__global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                              SliceState* S, Ptrs<T> P, int* pending) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
     __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
@@ -1265,8 +1312,14 @@ __global__ void __launch_bounds__(kStencilThreads) k_cg_init(ItemList L, const S
         const T bt = T(__ldg(&S[it.slice].beta_t));
         double acc[1] = {0.0};
         T accT = T(0);
-        for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
-            const Pack<T> a2 = ldv_n(P.f[RECON_F_A2], d, cnt), rz = ldv_n(P.f[RECON_F_RHS_Z], d, cnt);
+        struct In {
+            Pack<T> a2, rz;
+        };
+        auto load = [&](long long d, int cnt) {
+            return In{ldv_n(P.f[RECON_F_A2], d, cnt), ldv_n(P.f[RECON_F_RHS_Z], d, cnt)};
+        };
+        for_tile_vectors2<T>(g, it, load, [&](long long d, int cnt, int ly, int lx0, const In& x) {
+            const Pack<T>&a2 = x.a2, &rz = x.rz;
             Pack<T> r;
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
@@ -1724,10 +1777,16 @@ int op_solve_z(Ctx& c) {
     const int half = fft_half_slots<T>(c);
     const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 3);
     int par = c.cg_parity;
+    // Consecutive passes walk the items in opposite orders, so that each
+    // pass starts on the slices the previous one touched last, which are
+    // still in the L2 (the working set is many times the L2).  k_cg_init ran
+    // forward, so the first PCG pass runs backward.
+    int rev = 1;
     {
         FamTimer t(c, KF_PCG_FWD);
         k_pcg_fwd<T, false><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending);
+            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, rev);
+        rev ^= 1;
     }
     c.launches += 1;
     int cap = 0;
@@ -1736,17 +1795,20 @@ int op_solve_z(Ctx& c) {
         {
             FamTimer t(c, KF_COLS_PRE);
             k_cols<T><<<grid_for(c, c.cols.n), kFftThreads, smem, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
-                                                                              c.d_state, P, pre, tw, half);
+                                                                              c.d_state, P, pre, tw, half, rev);
+            rev ^= 1;
         }
         {
             FamTimer t(c, KF_PCG_INV);
             k_pcg_inv<T><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom, c.d_state,
-                                                                                P, tw, half, par);
+                                                                                P, tw, half, par, rev);
+            rev ^= 1;
         }
         {
             FamTimer t(c, KF_PCG_FWD);
             k_pcg_fwd<T, true><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-                c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending);
+                c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, rev);
+            rev ^= 1;
         }
         c.launches += 3;
         RECON_CUDA(cudaGetLastError());
@@ -1917,7 +1979,7 @@ int graph_build_t(Ctx& c) {
         k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                               c.d_state, P, c.d_cg_pending);
         k_pcg_fwd<T, false><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, 0, c.d_cg_pending);
+            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, 0, c.d_cg_pending, 1);
         k_pcg_loop_start<<<1, 1, 0, c.stream>>>(h, c.d_cg_pending, c.d_graph_body);
         c.launches += 3;
     }
@@ -1949,13 +2011,13 @@ int graph_build_t(Ctx& c) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return fail(e, "capture (PCG body)");
-    for (int par = 0; par < 2; ++par) {
+    for (int par = 0; par < 2; ++par) {   // six passes: directions alternate as in op_solve_z
         k_cols<T><<<grid_for(c, c.cols.n), kFftThreads, smem_c, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
-                                                                            c.d_state, P, pre, tw, half_c);
+                                                                            c.d_state, P, pre, tw, half_c, par);
         k_pcg_inv<T><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom, c.d_state, P,
-                                                                            tw, half, par);
+                                                                            tw, half, par, par ^ 1);
         k_pcg_fwd<T, true><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending);
+            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, par);
     }
     k_pcg_loop_cond<<<1, 1, 0, c.stream>>>(h, c.d_cg_pending, c.d_graph_body, bodies, c.d_graph_launches);
     e = cudaStreamEndCapture(c.stream, &body);
