@@ -331,7 +331,7 @@ __device__ __forceinline__ void stv_n(T* p, long long d, const Pack<T>& v, int c
 // --------------------------------------------------------------------------
 
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(kStencilThreads, 2) k_thr_rhs(ItemList L, const SliceGeom* G, const SliceConst* C,
+__global__ void __launch_bounds__(kStencilThreads, 3) k_thr_rhs(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                              SliceState* S, Ptrs<T> P) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
     __shared__ __align__(16) T sm[4][TileDim<T>::TH + 2][SW];
@@ -377,51 +377,52 @@ __global__ void __launch_bounds__(kStencilThreads, 2) k_thr_rhs(ItemList L, cons
             }
             return x;
         };
-        for_tile_vectors2<T>(g, it, load, [&](long long d0, int cnt, int ly, int lx0, const In& x) {
+        // thresholded divergence of map m at (ry, lx) of the tile (eq. sol_hv,
+        // periodic forward differences; the statistics of the kept gradient)
+        auto div_of = [&](int m, int ry, int lx, bool in) -> T {
+            const T gc = sm[m][ry][lx];
+            const T dx = sub_rn(sm[m][ry][lx + 1], gc);
+            const T dy = sub_rn(sm[m][ry + 1][lx], gc);
+            const T dxl = sub_rn(gc, sm[m][ry][lx - 1]);
+            const T dyl = sub_rn(sm[m][ry + 1][lx - 1], sm[m][ry][lx - 1]);
+            const T dxu = sub_rn(sm[m][ry - 1][lx + 1], sm[m][ry - 1][lx]);
+            const T dyu = sub_rn(gc, sm[m][ry - 1][lx]);
+            const bool k0 = keep_grad(dx, dy, thr);
+            const bool kl = keep_grad(dxl, dyl, thr);
+            const bool ku = keep_grad(dxu, dyu, thr);
+            const T h0 = k0 ? dx : T(0), v0 = k0 ? dy : T(0);
+            const T hl = kl ? dxl : T(0), vu = ku ? dyu : T(0);
+            if (STATS && in) {
+                if (!k0) acc[4] += (double)dx * dx + (double)dy * dy;
+                acc[5 + m] += k0 ? 1.0 : 0.0;
+            }
+            return (hl - h0) + (vu - v0);
+        };
+        // pass A: f1, f2 (thresholds, right-hand sides, data and model terms)
+        for_tile_vectors<T>(g, it, [&](long long d0, int cnt, int ly, int lx0) {
+            const In x = load(d0, cnt);
             const Pack<T>&uL = x.uL, &uH = x.uH, &G1 = x.G1, &G2 = x.G2;
-            Pack<T> o0, o1, o2, o3;
+            Pack<T> o0, o1;
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
                 const int lx = OFF + lx0 + e;   // column of this pixel in sm
                 const int ry = ly + 1;
                 const bool in = e < cnt;
-                T div[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const T gc = sm[m][ry][lx];
-                    const T dx = sub_rn(sm[m][ry][lx + 1], gc);
-                    const T dy = sub_rn(sm[m][ry + 1][lx], gc);
-                    const T dxl = sub_rn(gc, sm[m][ry][lx - 1]);
-                    const T dyl = sub_rn(sm[m][ry + 1][lx - 1], sm[m][ry][lx - 1]);
-                    const T dxu = sub_rn(sm[m][ry - 1][lx + 1], sm[m][ry - 1][lx]);
-                    const T dyu = sub_rn(gc, sm[m][ry - 1][lx]);
-                    const bool k0 = keep_grad(dx, dy, thr);
-                    const bool kl = keep_grad(dxl, dyl, thr);
-                    const bool ku = keep_grad(dxu, dyu, thr);
-                    const T h0 = k0 ? dx : T(0), v0 = k0 ? dy : T(0);
-                    const T hl = kl ? dxl : T(0), vu = ku ? dyu : T(0);
-                    div[m] = (hl - h0) + (vu - v0);
-                    if (STATS && in) {
-                        if (!k0) acc[4] += (double)dx * dx + (double)dy * dy;
-                        acc[5 + m] += k0 ? 1.0 : 0.0;
-                    }
-                }
+                const T div0 = div_of(0, ry, lx, in), div1 = div_of(1, ry, lx, in);
                 const T f1 = sm[0][ry][lx], f2 = sm[1][ry][lx], rho = sm[2][ry][lx], z = sm[3][ry][lx];
                 const T M1 = rho * (T(c.P1) * z + T(c.psi1));
                 const T M2 = rho * (T(c.P2) * z + T(c.psi2));
                 if (!sino) {
                     const T base1 = T(c.a00) * uL.v[e] + T(c.a01) * uH.v[e] + T(c.b00) * M1 + T(c.b01) * M2;
                     const T base2 = T(c.a10) * uL.v[e] + T(c.a11) * uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2;
-                    o0.v[e] = base1 - T(c.c12) * f2 + beta * div[0];
-                    o1.v[e] = (c.order ? base2 : base2 - T(c.c12) * f1) + beta * div[1];
+                    o0.v[e] = base1 - T(c.c12) * f2 + beta * div0;
+                    o1.v[e] = (c.order ? base2 : base2 - T(c.c12) * f1) + beta * div1;
                 } else {
                     // t_k - cross A^T A f_o / gamma + sum_j b_kj (M_j - f_o b_oj) + beta div
                     const T ag = T(c.fcross * c.inv_gamma), bc = T(c.c12 - c.fcross);
-                    o0.v[e] = uL.v[e] + T(c.b00) * M1 + T(c.b01) * M2 - ag * G2.v[e] - bc * f2 + beta * div[0];
-                    o1.v[e] = uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2 - ag * G1.v[e] - bc * f1 + beta * div[1];
+                    o0.v[e] = uL.v[e] + T(c.b00) * M1 + T(c.b01) * M2 - ag * G2.v[e] - bc * f2 + beta * div0;
+                    o1.v[e] = uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2 - ag * G1.v[e] - bc * f1 + beta * div1;
                 }
-                o2.v[e] = beta_t * div[2];
-                o3.v[e] = beta_t * div[3];
                 if (STATS && in) {
                     const double dL = sino ? 0.0 : c.a00 * (double)f1 + c.a10 * (double)f2 - (double)uL.v[e];
                     const double dH = sino ? 0.0 : c.a01 * (double)f1 + c.a11 * (double)f2 - (double)uH.v[e];
@@ -437,6 +438,17 @@ __global__ void __launch_bounds__(kStencilThreads, 2) k_thr_rhs(ItemList L, cons
             }
             stv_n(P.f[RECON_F_RHS_F1], d0, o0, cnt);
             stv_n(P.f[RECON_F_RHS_F2], d0, o1, cnt);
+        });
+        // pass B: rho_e, z (thresholds, beta~-weighted divergences), from shared memory only
+        for_tile_vectors<T>(g, it, [&](long long d0, int cnt, int ly, int lx0) {
+            Pack<T> o2, o3;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                const int lx = OFF + lx0 + e, ry = ly + 1;
+                const bool in = e < cnt;
+                o2.v[e] = beta_t * div_of(2, ry, lx, in);
+                o3.v[e] = beta_t * div_of(3, ry, lx, in);
+            }
             stv_n(P.f[RECON_F_DIV_RHO], d0, o2, cnt);
             stv_n(P.f[RECON_F_DIV_Z], d0, o3, cnt);
         });
