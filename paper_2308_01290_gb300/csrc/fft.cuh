@@ -241,22 +241,32 @@ __host__ __device__ inline int col_ld(int n) {
     return (is_pow2c(n) && n >= 64) ? padded_len(n) + 1 : (padded_len(n) | 1);
 }
 
-// Stage plan of a power-of-two length N.  Stage s > 0 multiplies leg r of
-// butterfly k (k < ns) by w^r, w = exp(-+2 pi i k / (ns R)).  Its twiddles
-// sit in a stage-major table that follows the N-entry table exp(-2 pi i t/N)
-// in the twiddle pool: for each stage s > 0, blocks of ns entries holding w,
-// w^2 and w^4 (as far as they are below R), contiguous in k; the butterfly
-// forms w^3, w^5, w^6, w^7 as products of two of them.
+__host__ __device__ constexpr int count_factor(int n, int f) { return (n > 0 && n % f == 0) ? 1 + count_factor(n / f, f) : 0; }
+
+// Stage plan of a compile-time length N = 2^a 3^b 5^c 7^d: radix-8 stages,
+// then one 4 or 2, then 3s, 5s, 7s (the order of fft_plan_code).  Stage
+// s > 0 multiplies leg r of butterfly k (k < ns) by w^r,
+// w = exp(-+2 pi i k / (ns R)).  Its twiddles sit in a stage-major table that
+// follows the N-entry table exp(-2 pi i t/N) in the twiddle pool: for each
+// stage s > 0, blocks of ns entries contiguous in k holding w, w^2 and w^4
+// as far as they are below R (R = 2, 4, 8; the butterfly forms w^3, w^5, w^6,
+// w^7 as products of two of them), or w .. w^(R-1) (R = 3, 5, 7).
 template <int N>
 struct P2Plan {
-    static constexpr int L = ilog2c(N);
+    static constexpr int L = count_factor(N, 2);
     static constexpr int N8 = L / 3;                      // radix-8 stages
     static constexpr int REM = L - 3 * N8;                // 0, 1 (radix 2) or 2 (radix 4)
-    static constexpr int S = N8 + (REM ? 1 : 0);          // stage count
-    __host__ __device__ static constexpr int radix(int s) { return s < N8 ? 8 : (REM == 2 ? 4 : 2); }
+    static constexpr int P2S = N8 + (REM ? 1 : 0);        // power-of-two stages
+    static constexpr int C3 = count_factor(N, 3), C5 = count_factor(N, 5), C7 = count_factor(N, 7);
+    static constexpr int S = P2S + C3 + C5 + C7;          // stage count
+    __host__ __device__ static constexpr int radix(int s) {
+        return s < N8 ? 8 : (s < P2S ? (REM == 2 ? 4 : 2) : (s < P2S + C3 ? 3 : (s < P2S + C3 + C5 ? 5 : 7)));
+    }
     __host__ __device__ static constexpr int ns(int s) { return s == 0 ? 1 : ns(s - 1) * radix(s - 1); }
-    // stored powers per butterfly (w, w^2, w^4 below R)
-    __host__ __device__ static constexpr int powers(int s) { return radix(s) == 8 ? 3 : (radix(s) == 4 ? 2 : 1); }
+    // stored powers per butterfly
+    __host__ __device__ static constexpr int powers(int s) {
+        return radix(s) == 8 ? 3 : (radix(s) == 4 ? 2 : (radix(s) == 2 ? 1 : radix(s) - 1));
+    }
     __host__ __device__ static constexpr int tw_off(int s) {
         return s <= 1 ? 0 : tw_off(s - 1) + powers(s - 1) * ns(s - 1);
     }
@@ -289,7 +299,7 @@ struct SmemSeq {
     template <int R, int NS>
     __device__ __forceinline__ void store_legs(int b, int idx0, const cplx<T>* v) const {
         cplx<T>* s = p + b * ld;
-        if constexpr (NS == 1) {
+        if constexpr (NS == 1 && 8 % R == 0) {
             const int o = pad8(idx0);
 #pragma unroll
             for (int r = 0; r < R; ++r) s[o + r] = v[r];
@@ -353,21 +363,25 @@ __device__ __forceinline__ void p2_stage(int batch, const cplx<T>* __restrict__ 
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
         int b, j;
         if constexpr (BFAST) {
-            b = t & (CB - 1);
-            j = t >> ilog2c(CB);
+            b = t % CB;
+            j = t / CB;
             if (b >= batch) continue;
         } else {
-            j = t & (NBF - 1);
-            b = t >> ilog2c(NBF);
+            j = t % NBF;
+            b = t / NBF;
         }
         cplx<T> v[R];
         src.template load_legs<R, NBF>(b, j, v);
-        const int k = j & (NS - 1);
+        const int k = j % NS;
         if constexpr (NS > 1) {
             const cplx<T>* t = tw + P2Plan<N>::tw_off(STAGE) + k;
             const cplx<T> w1 = t[0];
             if constexpr (R == 2) {
                 v[1] = cmul_dir<T, DIR>(v[1], w1);
+            } else if constexpr (R % 2 == 1) {
+                v[1] = cmul_dir<T, DIR>(v[1], w1);
+#pragma unroll
+                for (int r = 2; r < R; ++r) v[r] = cmul_dir<T, DIR>(v[r], t[(r - 1) * NS]);
             } else {
                 const cplx<T> w2 = t[NS];
                 if constexpr (R == 4) {
@@ -388,7 +402,7 @@ __device__ __forceinline__ void p2_stage(int batch, const cplx<T>* __restrict__ 
             }
         }
         dft<T, R>(v, DIR);
-        dst.template store_legs<R, NS>(b, (j >> ilog2c(NS)) * NS * R + k, v);
+        dst.template store_legs<R, NS>(b, (j / NS) * NS * R + k, v);
     }
 }
 

@@ -491,7 +491,11 @@ __global__ void k_gs_fix(ItemList L, const SliceGeom* G, const SliceConst* C, co
 // runtime mixed-radix transform with a load phase and a store phase.
 // --------------------------------------------------------------------------
 
-__device__ __forceinline__ bool p2_fast(int n) { return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024; }
+// Sizes with compile-time transforms: powers of two 64 .. 1024 and the
+// mixed sizes 320 (8 8 5), 384 (8 8 2 3), 448 (8 8 7).
+__device__ __forceinline__ bool p2_fast(int n) {
+    return n == 64 || n == 128 || n == 256 || n == 512 || n == 1024 || n == 320 || n == 384 || n == 448;
+}
 
 // Runs the statements with `constexpr int NN` set to n (one of p2_fast).
 #define RECON_P2_DISPATCH(n, ...)                \
@@ -510,6 +514,18 @@ __device__ __forceinline__ bool p2_fast(int n) { return n == 64 || n == 128 || n
         } break;                                 \
         case 512: {                              \
             constexpr int NN = 512;              \
+            __VA_ARGS__;                         \
+        } break;                                 \
+        case 320: {                              \
+            constexpr int NN = 320;              \
+            __VA_ARGS__;                         \
+        } break;                                 \
+        case 384: {                              \
+            constexpr int NN = 384;              \
+            __VA_ARGS__;                         \
+        } break;                                 \
+        case 448: {                              \
+            constexpr int NN = 448;              \
             __VA_ARGS__;                         \
         } break;                                 \
         default: {                               \
@@ -888,6 +904,7 @@ struct PcgFwdLoad {
     template <int R, int NBF>
     __device__ __forceinline__ void load_legs(int b, int j, cplx<T>* v) const {
         constexpr int G4 = R < 4 ? R : 4;
+        static_assert(R % G4 == 0, "first-stage radix of the row transforms is 2, 4 or 8");
         const long long d0 = (long long)(2 * b) * pitch + j;
         const bool has1 = 2 * b + 1 < rows;
 #pragma unroll
@@ -1028,7 +1045,7 @@ __device__ __forceinline__ float pcg_inv_tail_p2(float* rx, float* a2s, int ld, 
                                                  const float* __restrict__ pold, float* __restrict__ pnew,
                                                  float* __restrict__ qo, bool first, float bc, float rnum, float b4,
                                                  float bt) {
-    constexpr int NV = N / 4, LNV = ilog2c(NV);
+    constexpr int NV = N / 4;
     {
         const int total = (rows + 2) * NV;
         for (int t0 = threadIdx.x; t0 < total; t0 += 4 * blockDim.x) {
@@ -1038,7 +1055,7 @@ __device__ __forceinline__ float pcg_inv_tail_p2(float* rx, float* a2s, int ld, 
                 const int t = t0 + u * blockDim.x;
                 wv[u] = pv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (t < total) {
-                    const int i = (t >> LNV) - 1, n0 = (t & (NV - 1)) * 4;
+                    const int i = t / NV - 1, n0 = (t % NV) * 4;
                     const int grow = i < 0 ? up : (i >= rows ? dn : r0 + i);
                     const long long d = off + (long long)grow * pitch + n0;
                     wv[u] = *reinterpret_cast<const float4*>(a2 + d);
@@ -1049,7 +1066,7 @@ __device__ __forceinline__ float pcg_inv_tail_p2(float* rx, float* a2s, int ld, 
             for (int u = 0; u < 4; ++u) {
                 const int t = t0 + u * blockDim.x;
                 if (t < total) {
-                    const int i = (t >> LNV) - 1, n0 = (t & (NV - 1)) * 4;
+                    const int i = t / NV - 1, n0 = (t % NV) * 4;
                     float* px = rx + pcg_row_slot(i, rows, np, ld) + 2 * pad8(n0);   // n0 % 4 == 0: legs at +2e
                     px[0] = fmaf(bc, pv[u].x, px[0] * dscale(rnum, wv[u].x, b4));
                     px[2] = fmaf(bc, pv[u].y, px[2] * dscale(rnum, wv[u].y, b4));
@@ -1064,7 +1081,7 @@ __device__ __forceinline__ float pcg_inv_tail_p2(float* rx, float* a2s, int ld, 
     float acc = 0.f;
     const int total = rows * NV;
     for (int t = threadIdx.x; t < total; t += blockDim.x) {
-        const int i = t >> LNV, n0 = (t & (NV - 1)) * 4;
+        const int i = t / NV, n0 = (t % NV) * 4;
         const float* row = rx + pcg_row_slot(i, rows, np, ld);
         const float* rup = rx + pcg_row_slot(i - 1, rows, np, ld);
         const float* rdn = rx + pcg_row_slot(i + 1, rows, np, ld);
@@ -2279,24 +2296,36 @@ int solver_setup(Ctx& c) {
                 const double sn = std::sin(M_PI * (double)t / (double)n);
                 sym.push_back(4.0 * sn * sn);
             }
-            // compile-time power-of-two transforms: stage-major table after
-            // the N entries (layout of P2Plan in fft.cuh)
-            if (n >= 64 && n <= 1024 && (n & (n - 1)) == 0) {
-                int l = 0;
-                while ((1 << l) < n) ++l;
-                const int n8 = l / 3, rem = l - 3 * n8, stages = n8 + (rem ? 1 : 0);
+            // compile-time transforms: stage-major table after the N entries
+            // (layout of P2Plan in fft.cuh)
+            if ((n >= 64 && n <= 1024 && (n & (n - 1)) == 0) || n == 320 || n == 384 || n == 448) {
+                std::vector<int> radices;
+                int m2 = n, l = 0;
+                while (m2 % 2 == 0) { m2 /= 2; ++l; }
+                for (int i = 0; i < l / 3; ++i) radices.push_back(8);
+                if (l % 3) radices.push_back(l % 3 == 2 ? 4 : 2);
+                for (int f : {3, 5, 7})
+                    while (m2 % f == 0) {
+                        m2 /= f;
+                        radices.push_back(f);
+                    }
                 int ns = 1;
-                for (int st = 0; st < stages; ++st) {
-                    const int R = st < n8 ? 8 : (rem == 2 ? 4 : 2);
-                    if (st > 0)
-                        for (int m : {1, 2, 4}) {
-                            if (m >= R) break;
+                for (size_t st = 0; st < radices.size(); ++st) {
+                    const int R = radices[st];
+                    if (st > 0) {
+                        std::vector<int> pw;
+                        if (R % 2 == 1)
+                            for (int q = 1; q < R; ++q) pw.push_back(q);
+                        else
+                            for (int q : {1, 2, 4})
+                                if (q < R) pw.push_back(q);
+                        for (int q : pw)
                             for (int k = 0; k < ns; ++k) {
-                                const double a = 2.0 * M_PI * (double)(m * k) / (double)(ns * R);
+                                const double a = 2.0 * M_PI * (double)(q * k) / (double)(ns * R);
                                 tw.push_back(std::cos(a));
                                 tw.push_back(-std::sin(a));
                             }
-                        }
+                    }
                     ns *= R;
                 }
             }

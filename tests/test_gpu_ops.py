@@ -23,7 +23,7 @@ from synthetic import phantoms as ph
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [(64, 48, 1), (100, 70, 1), (63, 45, 1), (128, 128, 1), (1, 12, 1), (7, 1, 1), (512, 512, 4)]
+SIZES = [(64, 48, 1), (100, 70, 1), (63, 45, 1), (128, 128, 1), (1, 12, 1), (7, 1, 1), (512, 512, 4), (384, 320, 2)]
 LAM = 1e-2
 
 
@@ -205,7 +205,8 @@ def test_gauss_seidel_operator(rc):
 
 
 @pytest.mark.parametrize("shape", [(512, 512), (320, 384), (448, 256), (2048, 6), (5, 2048), (3, 3),
-                                   (64, 1024), (1024, 128), (256, 64), (128, 512), (64, 63), (256, 45)])
+                                   (64, 1024), (1024, 128), (256, 64), (128, 512), (64, 63), (256, 45),
+                                   (384, 448), (448, 320)])
 def test_fft_solve_sizes(rc, shape):
     nx, ny = shape
     s, tab = make(rc, nx, ny)
