@@ -1249,7 +1249,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
 // synthesis at E1/E2 from the new f, rho_e rhs, Z^m normal equations
 // --------------------------------------------------------------------------
 
-template <typename T>
+// REDUCE: also form mean(a^2) and ||rhs_z||^2 for the cluster-resident Z^m
+// solve; the batched PCG takes them from k_cg_init instead.
+template <typename T, bool REDUCE>
 __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                            SliceState* S, Ptrs<T> P) {
     constexpr int VN = TileDim<T>::VN;
@@ -1287,7 +1289,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
                 orr.v[e] = rho_cf + dr.v[e];
                 oa2.v[e] = a * a;
                 orz.v[e] = a * b + dz.v[e];
-                if (e < cnt) {
+                if (REDUCE && e < cnt) {
                     acc0 += oa2.v[e];
                     acc1 = fma(orz.v[e], orz.v[e], acc1);
                 }
@@ -1296,14 +1298,16 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
             stv_n(P.f[RECON_F_A2], d, oa2, cnt);
             stv_n(P.f[RECON_F_RHS_Z], d, orz, cnt);
         });
-        acc[0] = (double)acc0;
-        acc[1] = (double)acc1;
-        block_sum<2>(acc, red);
-        double tot[2];
-        if (item_reduce<2>(L, w, it.slice, acc, tot, red)) {
-            SliceState& so = S[it.slice];
-            so.abar2 = tot[0] / ((double)g.nx * (double)g.ny);
-            so.bb = tot[1];
+        if constexpr (REDUCE) {
+            acc[0] = (double)acc0;
+            acc[1] = (double)acc1;
+            block_sum<2>(acc, red);
+            double tot[2];
+            if (item_reduce<2>(L, w, it.slice, acc, tot, red)) {
+                SliceState& so = S[it.slice];
+                so.abar2 = tot[0] / ((double)g.nx * (double)g.ny);
+                so.bb = tot[1];
+            }
         }
         __syncthreads();
     }
@@ -1324,7 +1328,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
                                                              SliceState* S, Ptrs<T> P, int* pending) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
     __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
-    __shared__ double red[32];
+    __shared__ double red[3 * 32];
     __shared__ SliceGeom s_g;
     const T* z = P.f[RECON_F_Z];
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
@@ -1339,8 +1343,8 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
             [&](long long d) { return PVals<T, 1>{{ldv(z, d)}}; });
         __syncthreads();
         const T bt = T(__ldg(&S[it.slice].beta_t));
-        double acc[1] = {0.0};
-        T accT = T(0);
+        double acc[3] = {0.0, 0.0, 0.0};
+        T accT = T(0), acc_a2 = T(0), acc_b = T(0);
         struct In {
             Pack<T> a2, rz;
         };
@@ -1354,16 +1358,26 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
             for (int e = 0; e < VN; ++e) {
                 const T Mz = a2.v[e] * sm[0][ly + 1][OFF + lx0 + e] + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e);
                 r.v[e] = rz.v[e] - Mz;
-                if (e < cnt) accT = fma(r.v[e], r.v[e], accT);
+                if (e < cnt) {
+                    accT = fma(r.v[e], r.v[e], accT);
+                    acc_a2 += a2.v[e];
+                    acc_b = fma(rz.v[e], rz.v[e], acc_b);
+                }
             }
             stv_n(P.f[RECON_F_CG_R], d, r, cnt);
         });
         acc[0] = (double)accT;
-        block_sum<1>(acc, red);
-        double tot[1];
-        if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
+        acc[1] = (double)acc_a2;
+        acc[2] = (double)acc_b;
+        block_sum<3>(acc, red);
+        double tot[3];
+        if (item_reduce<3>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
             const double tol2 = C[it.slice].cg_tol * C[it.slice].cg_tol;
+            // mean(a^2) sets the preconditioner's diagonal, ||rhs||^2 the
+            // stopping test (of the a^2 and rhs this solve reads)
+            so.abar2 = tot[1] / ((double)g.nx * (double)g.ny);
+            so.bb = tot[2];
             so.rr = tot[0];
             so.rr0 = tot[0];
             so.cg_it = 0;
@@ -1779,8 +1793,12 @@ int op_solve_f(Ctx& c) {
 template <typename T>
 int op_synth(Ctx& c) {
     FamTimer t(c, KF_SYNTH);
-    k_synth<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
-                                                                        c.d_state, ptrs<T>(c));
+    if (!c.cl_slices.empty())
+        k_synth<T, true><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
+                                                                                  c.d_const, c.d_state, ptrs<T>(c));
+    else
+        k_synth<T, false><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
+                                                                                   c.d_const, c.d_state, ptrs<T>(c));
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;

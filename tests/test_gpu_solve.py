@@ -54,6 +54,19 @@ def parity_ok(r, precision=1):
     return r["mean_dZ"] <= 0.01 and r["mean_drho"] <= 1e-3
 
 
+def map_errors(tag, maps, ref, body):
+    """Error against the FP64 oracle of each final map over the body: mean,
+    99.9th percentile and maximum of |GPU - oracle|, and the oracle map's
+    mean magnitude for scale."""
+    out = {}
+    for name, got in maps.items():
+        d = np.abs(np.asarray(got, np.float64) - ref[name])[body]
+        out[name] = dict(mean=float(d.mean()), p999=float(np.percentile(d, 99.9)), max=float(d.max()),
+                         scale=float(np.abs(ref[name][body]).mean()))
+    print(tag, "per-map error", out)
+    return out
+
+
 @pytest.mark.parametrize("precision", [1, 0])
 def test_small_solve_matches_oracle(rc, small_case, precision):
     c = small_case
@@ -65,6 +78,8 @@ def test_small_solve_matches_oracle(rc, small_case, precision):
     Z, rho, f1, f2 = [x[0] for x in s.get_host()]
     body = c["P"]["rhoe"] >= 0.1
     r = report(f"precision={precision}", Z, rho, c["ref"], body)
+    m = map_errors(f"precision={precision}", dict(Z=Z, rhoe=rho, f1=f1, f2=f2), c["ref"], body)
+    assert all(np.isfinite(v["max"]) for v in m.values())
     assert parity_ok(r, precision), r
     sc = s.scalars()
     assert sc["k"] == acq.iters
