@@ -280,31 +280,53 @@ __device__ __forceinline__ void for_tile_vectors(const SliceGeom& g, const Item&
     }
 }
 
-// As for_tile_vectors, in two phases: load(d0, cnt) for every vector of the
-// thread first, then store(d0, cnt, ly, lx0, loaded) for each; the loads of
-// all rounds are in flight together.  blockDim.x == kStencilThreads.
+// Vectors of a tile, kStencilThreads threads: R rounds of one vector each.
+template <typename T>
+struct TileVec {
+    static constexpr int VN = TileDim<T>::VN, VR = kTileW / VN, TOTAL = TileDim<T>::TH * VR;
+    static constexpr int R = (TOTAL + kStencilThreads - 1) / kStencilThreads;
+};
+
+// First phase of a two-phase visit: load(d0, cnt) for every vector of the
+// thread, into v; nothing waits for the loads here.  blockDim.x ==
+// kStencilThreads.
+template <typename T, typename FL, typename V>
+__device__ __forceinline__ void tile_vec_load(const SliceGeom& g, const Item& it, FL load, V (&v)[TileVec<T>::R]) {
+    using TV = TileVec<T>;
+#pragma unroll
+    for (int u = 0; u < TV::R; ++u) {
+        const int q = threadIdx.x + u * kStencilThreads;
+        const int ly = q / TV::VR, lx0 = (q - ly * TV::VR) * TV::VN;
+        const int y = it.b + ly, x0 = it.a + lx0;
+        if (q < TV::TOTAL && y < g.ny && x0 < g.nx)
+            v[u] = load(g.off + (long long)y * g.pitch + x0, g.nx - x0 < TV::VN ? g.nx - x0 : TV::VN);
+    }
+}
+
+// Second phase: store(d0, cnt, ly, lx0, loaded) for each vector loaded by
+// tile_vec_load.
+template <typename T, typename FS, typename V>
+__device__ __forceinline__ void tile_vec_use(const SliceGeom& g, const Item& it, FS store,
+                                             const V (&v)[TileVec<T>::R]) {
+    using TV = TileVec<T>;
+#pragma unroll
+    for (int u = 0; u < TV::R; ++u) {
+        const int q = threadIdx.x + u * kStencilThreads;
+        const int ly = q / TV::VR, lx0 = (q - ly * TV::VR) * TV::VN;
+        const int y = it.b + ly, x0 = it.a + lx0;
+        if (q < TV::TOTAL && y < g.ny && x0 < g.nx)
+            store(g.off + (long long)y * g.pitch + x0, g.nx - x0 < TV::VN ? g.nx - x0 : TV::VN, ly, lx0, v[u]);
+    }
+}
+
+// As for_tile_vectors, in two phases: the loads of all rounds are in flight
+// together.
 template <typename T, typename FL, typename FS>
 __device__ __forceinline__ void for_tile_vectors2(const SliceGeom& g, const Item& it, FL load, FS store) {
-    constexpr int VN = TileDim<T>::VN, VR = kTileW / VN, TOTAL = TileDim<T>::TH * VR;
-    constexpr int R = (TOTAL + kStencilThreads - 1) / kStencilThreads;
     using V = decltype(load(0LL, 0));
-    V v[R];
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-        const int q = threadIdx.x + u * kStencilThreads;
-        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
-        const int y = it.b + ly, x0 = it.a + lx0;
-        if (q < TOTAL && y < g.ny && x0 < g.nx)
-            v[u] = load(g.off + (long long)y * g.pitch + x0, g.nx - x0 < VN ? g.nx - x0 : VN);
-    }
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-        const int q = threadIdx.x + u * kStencilThreads;
-        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
-        const int y = it.b + ly, x0 = it.a + lx0;
-        if (q < TOTAL && y < g.ny && x0 < g.nx)
-            store(g.off + (long long)y * g.pitch + x0, g.nx - x0 < VN ? g.nx - x0 : VN, ly, lx0, v[u]);
-    }
+    V v[TileVec<T>::R];
+    tile_vec_load<T>(g, it, load, v);
+    tile_vec_use<T>(g, it, store, v);
 }
 
 template <typename T>
@@ -1331,13 +1353,25 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
     __shared__ double red[3 * 32];
     __shared__ SliceGeom s_g;
     const T* z = P.f[RECON_F_Z];
+    struct In {
+        Pack<T> a2, rz;
+    };
+    auto load = [&](long long d, int cnt) {
+        return In{ldv_n(P.f[RECON_F_A2], d, cnt), ldv_n(P.f[RECON_F_RHS_Z], d, cnt)};
+    };
+    // the next item's descriptor is fetched while this one is processed
+    Item nxt = blockIdx.x < (unsigned)L.n_items ? L.items[blockIdx.x] : Item{};
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
+        const Item it = nxt;
+        if (w + (int)gridDim.x < L.n_items) nxt = L.items[w + gridDim.x];
         if (!__ldg(&S[it.slice].active) || __ldg(&G[it.slice].cluster)) continue;
         stage_struct(&s_g, G + it.slice);
         __syncthreads();
         const SliceGeom& g = s_g;
         account(P.acct, KF_CG_INIT, tile_px<T>(g, it) * 4 * (long long)sizeof(T));
+        // a^2 and the right-hand side are loaded together with the z tile
+        In x[TileVec<T>::R];
+        tile_vec_load<T>(g, it, load, x);
         load_tile<T, 1>(
             sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{z[d]}}; },
             [&](long long d) { return PVals<T, 1>{{ldv(z, d)}}; });
@@ -1345,14 +1379,8 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
         const T bt = T(__ldg(&S[it.slice].beta_t));
         double acc[3] = {0.0, 0.0, 0.0};
         T accT = T(0), acc_a2 = T(0), acc_b = T(0);
-        struct In {
-            Pack<T> a2, rz;
-        };
-        auto load = [&](long long d, int cnt) {
-            return In{ldv_n(P.f[RECON_F_A2], d, cnt), ldv_n(P.f[RECON_F_RHS_Z], d, cnt)};
-        };
-        for_tile_vectors2<T>(g, it, load, [&](long long d, int cnt, int ly, int lx0, const In& x) {
-            const Pack<T>&a2 = x.a2, &rz = x.rz;
+        tile_vec_use<T>(g, it, [&](long long d, int cnt, int ly, int lx0, const In& v) {
+            const Pack<T>&a2 = v.a2, &rz = v.rz;
             Pack<T> r;
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
@@ -1365,7 +1393,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
                 }
             }
             stv_n(P.f[RECON_F_CG_R], d, r, cnt);
-        });
+        }, x);
         acc[0] = (double)accT;
         acc[1] = (double)acc_a2;
         acc[2] = (double)acc_b;
