@@ -94,6 +94,15 @@ __device__ __forceinline__ T diff_of_products(T a, T b, T c, T d) {
 __device__ __forceinline__ float dscale(float sqrt_num, float a2, float b4) { return sqrt_num * rsqrtf(a2 + b4); }
 __device__ __forceinline__ double dscale(double sqrt_num, double a2, double b4) { return sqrt_num / sqrt(a2 + b4); }
 
+// 1 / (nx ny) in the kernel's precision.
+template <typename T>
+__device__ __forceinline__ T inv_n_of(const SliceGeom& g) {
+    if constexpr (sizeof(T) == 4)
+        return g.inv_n;
+    else
+        return 1.0 / ((double)g.nx * (double)g.ny);
+}
+
 template <typename T>
 __device__ __forceinline__ T thr_of(const SliceState& st);
 template <>
@@ -381,7 +390,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_thr_rhs(ItemList L, cons
         __syncthreads();
         const SliceConst& c = s_c;
         const T thr = thr_of<T>(s_st);
-        const T beta = T(s_st.beta), beta_t = T(s_st.beta_t);
+        const T beta = Sc<T>::beta(s_st), beta_t = Sc<T>::beta_t(s_st);
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         // image domain: uL, uH = mu_hat(E_L), mu_hat(E_H).  Sinogram domain
         // (domain 1): uL, uH = t_1, t_2 and G1, G2 = A^T A f1, A^T A f2
@@ -432,18 +441,20 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_thr_rhs(ItemList L, cons
                 const bool in = e < cnt;
                 const T div0 = div_of(0, ry, lx, in), div1 = div_of(1, ry, lx, in);
                 const T f1 = sm[0][ry][lx], f2 = sm[1][ry][lx], rho = sm[2][ry][lx], z = sm[3][ry][lx];
-                const T M1 = rho * (T(c.P1) * z + T(c.psi1));
-                const T M2 = rho * (T(c.P2) * z + T(c.psi2));
+                const T M1 = rho * (kc<T>(c, KC_P1) * z + kc<T>(c, KC_PSI1));
+                const T M2 = rho * (kc<T>(c, KC_P2) * z + kc<T>(c, KC_PSI2));
+                const T b00 = kc<T>(c, KC_B00), b01 = kc<T>(c, KC_B01), b10 = kc<T>(c, KC_B10),
+                        b11 = kc<T>(c, KC_B11), c12 = kc<T>(c, KC_C12);
                 if (!sino) {
-                    const T base1 = T(c.a00) * uL.v[e] + T(c.a01) * uH.v[e] + T(c.b00) * M1 + T(c.b01) * M2;
-                    const T base2 = T(c.a10) * uL.v[e] + T(c.a11) * uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2;
-                    o0.v[e] = base1 - T(c.c12) * f2 + beta * div0;
-                    o1.v[e] = (c.order ? base2 : base2 - T(c.c12) * f1) + beta * div1;
+                    const T base1 = kc<T>(c, KC_A00) * uL.v[e] + kc<T>(c, KC_A01) * uH.v[e] + b00 * M1 + b01 * M2;
+                    const T base2 = kc<T>(c, KC_A10) * uL.v[e] + kc<T>(c, KC_A11) * uH.v[e] + b10 * M1 + b11 * M2;
+                    o0.v[e] = base1 - c12 * f2 + beta * div0;
+                    o1.v[e] = (c.order ? base2 : base2 - c12 * f1) + beta * div1;
                 } else {
                     // t_k - cross A^T A f_o / gamma + sum_j b_kj (M_j - f_o b_oj) + beta div
-                    const T ag = T(c.fcross * c.inv_gamma), bc = T(c.c12 - c.fcross);
-                    o0.v[e] = uL.v[e] + T(c.b00) * M1 + T(c.b01) * M2 - ag * G2.v[e] - bc * f2 + beta * div0;
-                    o1.v[e] = uH.v[e] + T(c.b10) * M1 + T(c.b11) * M2 - ag * G1.v[e] - bc * f1 + beta * div1;
+                    const T ag = kc<T>(c, KC_SINO_AG), bc = kc<T>(c, KC_SINO_BC);
+                    o0.v[e] = uL.v[e] + b00 * M1 + b01 * M2 - ag * G2.v[e] - bc * f2 + beta * div0;
+                    o1.v[e] = uH.v[e] + b10 * M1 + b11 * M2 - ag * G1.v[e] - bc * f1 + beta * div1;
                 }
                 if (STATS && in) {
                     const double dL = sino ? 0.0 : c.a00 * (double)f1 + c.a10 * (double)f2 - (double)uL.v[e];
@@ -714,16 +725,16 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
                 (long long)nc * N * 4 * (long long)sizeof(T));
         cplx<T>* sp = P.s[J.spec[job]];
         const cplx<T>* tw = twpool + g.twy;
-        double cst, bet;
+        T cst, bet;
         switch (kind) {
-            case 0: cst = C[it.slice].c_f1; bet = __ldg(&st->beta); break;
-            case 1: cst = C[it.slice].c_f2; bet = __ldg(&st->beta); break;
-            case 2: cst = 1.0; bet = __ldg(&st->beta_t); break;
-            case 3: cst = __ldg(&st->abar2); bet = __ldg(&st->beta_t); break;
-            case 4: cst = C[it.slice].fa0 + C[it.slice].fcp0; bet = __ldg(&st->beta); break;
-            default: cst = C[it.slice].fa1 + C[it.slice].fcp1; bet = __ldg(&st->beta); break;
+            case 0: cst = kc<T>(C[it.slice], KC_CF1); bet = Sc<T>::beta(*st); break;
+            case 1: cst = kc<T>(C[it.slice], KC_CF2); bet = Sc<T>::beta(*st); break;
+            case 2: cst = T(1); bet = Sc<T>::beta_t(*st); break;
+            case 3: cst = Sc<T>::abar2(*st); bet = Sc<T>::beta_t(*st); break;
+            case 4: cst = kc<T>(C[it.slice], KC_SINO_D0); bet = Sc<T>::beta(*st); break;
+            default: cst = kc<T>(C[it.slice], KC_SINO_D1); bet = Sc<T>::beta(*st); break;
         }
-        const T inv_n = T(1.0 / ((double)g.nx * (double)g.ny));
+        const T inv_n = inv_n_of<T>(g);
         const T* symx = P.sym + g.symx;
         const T* symy = P.sym + g.symy;
         T accT = T(0);
@@ -733,10 +744,10 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
             cplx<T>* spc = sp + g.coff + col0;
             if (kind >= 3) {
                 RECON_P2_DISPATCH(N, cols_item_p2<T, NN, true>(spc, g.cpitch, nc, col0, g.nx, buf0, buf1, tw, symx,
-                                                               symy, T(cst), T(bet), inv_n, accT));
+                                                               symy, cst, bet, inv_n, accT));
             } else {
                 RECON_P2_DISPATCH(N, cols_item_p2<T, NN, false>(spc, g.cpitch, nc, col0, g.nx, buf0, buf1, tw, symx,
-                                                                symy, T(cst), T(bet), inv_n, accT));
+                                                                symy, cst, bet, inv_n, accT));
             }
         } else {
             {
@@ -773,7 +784,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
                 for (int q = threadIdx.x; q < nc * N; q += blockDim.x) {
                     const int cc = dN.div(q), ky = q - cc * N;
                     // |F dx|^2 + |F dy|^2 = 4 sin^2(pi kx / nx) + 4 sin^2(pi ky / ny)
-                    const T sc = inv_n / (T(cst) + T(bet) * (symx[col0 + cc] + symy[ky]));
+                    const T sc = inv_n / (cst + bet * (symx[col0 + cc] + symy[ky]));
                     cplx<T> v = buf[cc * ld + pad8(ky)];
                     if (kind >= 3) {
                         const int kx = col0 + cc;
@@ -794,12 +805,13 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_cols(ItemList L,
             __syncthreads();
         }
         if (kind >= 3) {
-            double acc[1] = {(double)accT};
-            block_sum<1>(acc, red);
+            const T part[1] = {accT};
+            double acc[1];
+            block_sum_t<T, 1>(part, acc, red);
             double tot[1];
             if (item_reduce<1>(L, item, it.slice, acc, tot, red)) {
                 SliceState& so = S[it.slice];
-                so.betacg = (so.cg_it == 0) ? 0.0 : tot[0] / so.ry;
+                set_betacg(so, (so.cg_it == 0) ? 0.0 : tot[0] / so.ry);
                 so.ry = tot[0];
             }
             __syncthreads();
@@ -996,9 +1008,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_fwd(ItemList
                                      P.f[RECON_F_A2] + d0,
                                      g.pitch,
                                      rows,
-                                     UPD ? T(__ldg(&sp->alpha)) : T(0),
-                                     T(sqrt(__ldg(&sp->abar2) + 4.0 * __ldg(&sp->beta_t))),
-                                     T(4.0 * __ldg(&sp->beta_t)),
+                                     UPD ? Sc<T>::alpha(*sp) : T(0),
+                                     Sc<T>::rnum(*sp),
+                                     Sc<T>::b4(*sp),
                                      acc};
         const cplx<T>* tw = twpool + g.twx;
         const cplx<T>* res;
@@ -1019,8 +1031,9 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_fwd(ItemList
         }
         rows_to_half_spectra(res, ld, N, g.nh, np, rows, P.s[0] + g.coff + (long long)r0 * g.cpitch, g.cpitch);
         if (UPD) {
-            double a[1] = {(double)acc};
-            block_sum<1>(a, red);
+            const T part[1] = {acc};
+            double a[1];
+            block_sum_t<T, 1>(part, a, red);
             double tot[1];
             if (item_reduce<1>(L, item, it.slice, a, tot, red)) {
                 SliceState& so = S[it.slice];
@@ -1185,22 +1198,23 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
         T* rx = reinterpret_cast<T*>(res);
         T* a2s = reinterpret_cast<T*>(res == buf ? buf2 : buf);   // a^2 of the interior rows
         const bool first = __ldg(&sp->cg_it) == 0;
-        const T bc = first ? T(0) : T(__ldg(&sp->betacg));
-        const T rnum = T(sqrt(__ldg(&sp->abar2) + 4.0 * __ldg(&sp->beta_t)));
-        const T b4 = T(4.0 * __ldg(&sp->beta_t));
-        const T bt = T(__ldg(&sp->beta_t));
+        const T bc = first ? T(0) : Sc<T>::betacg(*sp);
+        const T rnum = Sc<T>::rnum(*sp);
+        const T b4 = Sc<T>::b4(*sp);
+        const T bt = Sc<T>::beta_t(*sp);
         if constexpr (std::is_same<T, float>::value) {
             if (fast) {
                 T acc = T(0);
                 RECON_P2_DISPATCH(N, acc = pcg_inv_tail_p2<NN>(rx, a2s, ld, np, rows, r0, up, dn, g.off, g.pitch, a2,
                                                                pold, pnew, qo, first, bc, rnum, b4, bt));
-                double a[1] = {(double)acc};
-                block_sum<1>(a, red);
+                const T part[1] = {acc};
+                double a[1];
+                block_sum_t<T, 1>(part, a, red);
                 double tot[1];
                 if (item_reduce<1>(L, item, it.slice, a, tot, red)) {
                     SliceState& so = S[it.slice];
                     so.pq = tot[0];
-                    so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
+                    set_alpha(so, tot[0] > 0.0 ? so.ry / tot[0] : 0.0);
                 }
                 __syncthreads();
                 continue;
@@ -1255,13 +1269,14 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
             qo[d] = qq;
             acc = fma(c, qq, acc);
         }
-        double a[1] = {(double)acc};
-        block_sum<1>(a, red);
+        const T part[1] = {acc};
+        double a[1];
+        block_sum_t<T, 1>(part, a, red);
         double tot[1];
         if (item_reduce<1>(L, item, it.slice, a, tot, red)) {
             SliceState& so = S[it.slice];
             so.pq = tot[0];
-            so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
+            set_alpha(so, tot[0] > 0.0 ? so.ry / tot[0] : 0.0);
         }
         __syncthreads();
     }
@@ -1289,11 +1304,10 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
         const SliceGeom& g = s_g;
         const SliceConst& c = s_c;
         account(P.acct, KF_SYNTH, tile_px<T>(g, it) * 7 * (long long)sizeof(T));
-        double acc[2] = {0.0, 0.0};
         T acc0 = T(0), acc1 = T(0);
-        const T b00 = T(c.b00), b10 = T(c.b10), b01 = T(c.b01), b11 = T(c.b11);
-        const T rr_ = T(c.r), inv_crho = T(1.0 / c.c_rho), inv_aw = T(1.0 / c.a_w);
-        const T P1 = T(c.P1), P2 = T(c.P2), psi1 = T(c.psi1), psi2 = T(c.psi2);
+        const T b00 = kc<T>(c, KC_B00), b10 = kc<T>(c, KC_B10), b01 = kc<T>(c, KC_B01), b11 = kc<T>(c, KC_B11);
+        const T rr_ = kc<T>(c, KC_R), inv_crho = kc<T>(c, KC_INV_CRHO), inv_aw = kc<T>(c, KC_INV_AW);
+        const T P1 = kc<T>(c, KC_P1), P2 = kc<T>(c, KC_P2), psi1 = kc<T>(c, KC_PSI1), psi2 = kc<T>(c, KC_PSI2);
         for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
             const Pack<T> f1 = ldv_n(P.f[RECON_F_F1], d, cnt), f2 = ldv_n(P.f[RECON_F_F2], d, cnt);
             const Pack<T> dr = ldv_n(P.f[RECON_F_DIV_RHO], d, cnt), dz = ldv_n(P.f[RECON_F_DIV_Z], d, cnt);
@@ -1321,13 +1335,13 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
             stv_n(P.f[RECON_F_RHS_Z], d, orz, cnt);
         });
         if constexpr (REDUCE) {
-            acc[0] = (double)acc0;
-            acc[1] = (double)acc1;
-            block_sum<2>(acc, red);
+            const T part[2] = {acc0, acc1};
+            double acc[2];
+            block_sum_t<T, 2>(part, acc, red);
             double tot[2];
             if (item_reduce<2>(L, w, it.slice, acc, tot, red)) {
                 SliceState& so = S[it.slice];
-                so.abar2 = tot[0] / ((double)g.nx * (double)g.ny);
+                set_abar2(so, tot[0] / ((double)g.nx * (double)g.ny));
                 so.bb = tot[1];
             }
         }
@@ -1376,8 +1390,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
             sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{z[d]}}; },
             [&](long long d) { return PVals<T, 1>{{ldv(z, d)}}; });
         __syncthreads();
-        const T bt = T(__ldg(&S[it.slice].beta_t));
-        double acc[3] = {0.0, 0.0, 0.0};
+        const T bt = Sc<T>::beta_t(S[it.slice]);
         T accT = T(0), acc_a2 = T(0), acc_b = T(0);
         tile_vec_use<T>(g, it, [&](long long d, int cnt, int ly, int lx0, const In& v) {
             const Pack<T>&a2 = v.a2, &rz = v.rz;
@@ -1394,23 +1407,22 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
             }
             stv_n(P.f[RECON_F_CG_R], d, r, cnt);
         }, x);
-        acc[0] = (double)accT;
-        acc[1] = (double)acc_a2;
-        acc[2] = (double)acc_b;
-        block_sum<3>(acc, red);
+        const T part[3] = {accT, acc_a2, acc_b};
+        double acc[3];
+        block_sum_t<T, 3>(part, acc, red);
         double tot[3];
         if (item_reduce<3>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
             const double tol2 = C[it.slice].cg_tol * C[it.slice].cg_tol;
             // mean(a^2) sets the preconditioner's diagonal, ||rhs||^2 the
             // stopping test (of the a^2 and rhs this solve reads)
-            so.abar2 = tot[1] / ((double)g.nx * (double)g.ny);
+            set_abar2(so, tot[1] / ((double)g.nx * (double)g.ny));
             so.bb = tot[2];
             so.rr = tot[0];
             so.rr0 = tot[0];
             so.cg_it = 0;
             so.ry = 0.0;
-            so.betacg = 0.0;
+            set_betacg(so, 0.0);
             so.cg_done = (so.bb == 0.0 || !(tot[0] > tol2 * so.bb)) ? 1 : 0;
             if (!so.cg_done) atomicAdd(pending, 1);
         }
@@ -1429,8 +1441,8 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
 
 template <typename T>
 __device__ __forceinline__ void fcg_coeffs(const SliceConst& c, int k, T& al, T& cp) {
-    al = T((k ? c.fa1 : c.fa0) * c.inv_gamma);
-    cp = T(k ? c.fcp1 : c.fcp0);
+    al = kc<T>(c, k ? KC_SINO_AL1 : KC_SINO_AL0);
+    cp = kc<T>(c, k ? KC_SINO_CP1 : KC_SINO_CP0);
 }
 
 // r = rhs - (alpha/gamma A^T A x + c' x + beta L x); |rhs|^2, |r|^2; start of the solve
@@ -1457,8 +1469,8 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_init(ItemList L, const 
         __syncthreads();
         T al, cp;
         fcg_coeffs<T>(C[it.slice], k, al, cp);
-        const T bt = T(__ldg(&S[it.slice].beta));
-        double acc[2] = {0.0, 0.0};
+        const T bt = Sc<T>::beta(S[it.slice]);
+        T acc_b = T(0), acc_r = T(0);
         for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
             const Pack<T> gv = ldv_n(gx, d, cnt), b = ldv_n(rhs, d, cnt);
             Pack<T> r;
@@ -1467,13 +1479,15 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_init(ItemList L, const 
                 const T xc = sm[0][ly + 1][OFF + lx0 + e];
                 r.v[e] = b.v[e] - (al * gv.v[e] + cp * xc + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e));
                 if (e < cnt) {
-                    acc[0] += (double)b.v[e] * b.v[e];
-                    acc[1] += (double)r.v[e] * r.v[e];
+                    acc_b = fma(b.v[e], b.v[e], acc_b);
+                    acc_r = fma(r.v[e], r.v[e], acc_r);
                 }
             }
             stv_n(P.f[RECON_F_CG_R], d, r, cnt);
         });
-        block_sum<2>(acc, red);
+        const T part[2] = {acc_b, acc_r};
+        double acc[2];
+        block_sum_t<T, 2>(part, acc, red);
         double tot[2];
         if (item_reduce<2>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
@@ -1483,7 +1497,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_init(ItemList L, const 
             so.rr0 = tot[1];
             so.cg_it = 0;
             so.ry = 0.0;
-            so.betacg = 0.0;
+            set_betacg(so, 0.0);
             so.cg_done = (tot[0] == 0.0 || !(tot[1] > tol2 * tot[0])) ? 1 : 0;
             if (!so.cg_done) atomicAdd(pending, 1);
         }
@@ -1503,7 +1517,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_p(ItemList L, const Sli
         const SliceGeom g = G[it.slice];
         account(P.acct, KF_FCG, tile_px<T>(g, it) * 3 * (long long)sizeof(T));
         const bool first = __ldg(&sp->cg_it) == 0;
-        const T bc = first ? T(0) : T(__ldg(&sp->betacg));
+        const T bc = first ? T(0) : Sc<T>::betacg(*sp);
         for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
             const Pack<T> y = ldv_n(P.f[RECON_F_CG_Y], d, cnt);
             Pack<T> p = first ? y : ldv_n(P.f[RECON_F_CG_P0], d, cnt);
@@ -1539,7 +1553,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_q(ItemList L, const Sli
         __syncthreads();
         T al, cp;
         fcg_coeffs<T>(C[it.slice], k, al, cp);
-        const T bt = T(__ldg(&sp->beta));
+        const T bt = Sc<T>::beta(*sp);
         T accT = T(0);
         for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
             const Pack<T> ap = ldv_n(P.f[RECON_F_CG_P1], d, cnt);
@@ -1552,13 +1566,14 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_q(ItemList L, const Sli
             }
             stv_n(P.f[RECON_F_CG_Q], d, q, cnt);
         });
-        double acc[1] = {(double)accT};
-        block_sum<1>(acc, red);
+        const T part[1] = {accT};
+        double acc[1];
+        block_sum_t<T, 1>(part, acc, red);
         double tot[1];
         if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
             so.pq = tot[0];
-            so.alpha = tot[0] > 0.0 ? so.ry / tot[0] : 0.0;
+            set_alpha(so, tot[0] > 0.0 ? so.ry / tot[0] : 0.0);
         }
         __syncthreads();
     }
@@ -1577,7 +1592,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_update(ItemList L, cons
         if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
         const SliceGeom g = G[it.slice];
         account(P.acct, KF_FCG, tile_px<T>(g, it) * 6 * (long long)sizeof(T));
-        const T al = T(__ldg(&sp->alpha));
+        const T al = Sc<T>::alpha(*sp);
         T accT = T(0);
         for_tile_vectors<T>(g, it, [&](long long d, int cnt, int, int) {
             Pack<T> xv = ldv_n(x, d, cnt), r = ldv_n(P.f[RECON_F_CG_R], d, cnt);
@@ -1591,8 +1606,9 @@ __global__ void __launch_bounds__(kStencilThreads) k_fcg_update(ItemList L, cons
             stv_n(x, d, xv, cnt);
             stv_n(P.f[RECON_F_CG_R], d, r, cnt);
         });
-        double acc[1] = {(double)accT};
-        block_sum<1>(acc, red);
+        const T part[1] = {accT};
+        double acc[1];
+        block_sum_t<T, 1>(part, acc, red);
         double tot[1];
         if (item_reduce<1>(L, w, it.slice, acc, tot, red)) {
             SliceState& so = S[it.slice];
@@ -1622,10 +1638,7 @@ __global__ void k_next_beta(int n, const SliceConst* C, SliceState* S) {
     if (!st.active) return;
     const SliceConst& c = C[s];
     st.k += 1;
-    st.beta *= c.kappa;
-    st.beta_t = c.tau * st.beta;
-    st.thr_d = c.lambda / st.beta;
-    st.thr_f = (float)st.thr_d;
+    set_beta(st, st.beta * c.kappa, c);
     st.active = st.k < c.iters;
 }
 
@@ -1634,10 +1647,7 @@ __global__ void k_reset_state(int n, const SliceConst* C, SliceState* S) {
     if (s >= n) return;
     const SliceConst& c = C[s];
     SliceState st = {};
-    st.beta = c.beta0;
-    st.beta_t = c.tau * c.beta0;
-    st.thr_d = c.lambda / c.beta0;
-    st.thr_f = (float)st.thr_d;
+    set_beta(st, c.beta0, c);
     st.k = 0;
     st.active = c.iters > 0;
     st.cg_done = 1;
@@ -2207,6 +2217,7 @@ SliceConst slice_const(const recon_params& p, const Tables& t) {
     k.fcp1 = t.b[1][0] * t.b[1][0] + t.b[1][1] * t.b[1][1];
     k.fcross = t.a[0][0] * t.a[1][0] + t.a[0][1] * t.a[1][1];
     k.inv_gamma = 0.0;   // set once the geometry's gamma is known
+    finish_const(k);
     return k;
 }
 
@@ -2237,6 +2248,7 @@ int fft_item_slots(int nx, int ny, int budget) {
 
 void slice_items(Ctx& c, int s, std::vector<Item>& tiles, std::vector<Item>& rows, std::vector<Item>& cols) {
     SliceGeom& g = c.sg[s];
+    g.inv_n = (float)(1.0 / ((double)g.nx * (double)g.ny));
     const int budget = c.precision == 1 ? FftBudget<float>::E : FftBudget<double>::E;
     const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
     for (int ty = 0; ty < g.ny; ty += th)
@@ -2477,7 +2489,10 @@ int solver_setup_sino(Ctx& c) {
         set_error("domain 1: the projector misses the image (gamma = 0)");
         return RECON_EINVAL;
     }
-    for (int s = 0; s < c.n; ++s) c.hconst[s].inv_gamma = 1.0 / c.gamma;
+    for (int s = 0; s < c.n; ++s) {
+        c.hconst[s].inv_gamma = 1.0 / c.gamma;
+        finish_const(c.hconst[s]);
+    }
     RECON_CUDA(cudaMemcpy(c.d_const, c.hconst.data(), sizeof(SliceConst) * c.n, cudaMemcpyHostToDevice));
     c.domain = 1;
     return RECON_OK;
@@ -2671,10 +2686,7 @@ __global__ void k_reset_slots(const int* slots, int n, const SliceConst* C, Slic
     const int s = slots[i];
     const SliceConst& c = C[s];
     SliceState st = {};
-    st.beta = c.beta0;
-    st.beta_t = c.tau * c.beta0;
-    st.thr_d = c.lambda / c.beta0;
-    st.thr_f = (float)st.thr_d;
+    set_beta(st, c.beta0, c);
     st.active = c.iters > 0;
     st.cg_done = 1;
     S[s] = st;
