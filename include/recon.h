@@ -92,10 +92,27 @@ typedef struct recon_params {
     double cg_tol;                   /* relative residual of the Z^m PCG */
     double z_clip_max;               /* initial Z^m clipped to Z <= z_clip_max */
     double rho_air;                  /* initial Z^m set to water where rho_e < rho_air */
-    int32_t pcg_kernel;              /* 0: batched kernels; 1: cluster-resident Z^m solve where a slice fits */
+    int32_t pcg_kernel;              /* Z^m solve.  0: batched kernels, multigrid-preconditioned PCG on slices
+                                        whose sides halve down to a small grid (below), FFT-preconditioned
+                                        elsewhere; 1: as 0, and cluster-resident where a slice fits;
+                                        2: batched kernels, FFT-preconditioned PCG on every slice */
     int32_t domain;                  /* data terms of the arms: 0 on the image pair (Sec. II-B, as printed);
                                         1 on the sinograms through the projector (below) */
 } recon_params;
+
+/* Preconditioners of the Z^m PCG (Alg. 1, Z^m step: [diag(a^2) + beta~ L] z =
+ * rhs, L = dx'dx + dy'dy periodic).  Both stop at the relative residual
+ * cg_tol.  FFT: D^-1/2 (mean(a^2) + beta~ L)^-1 D^-1/2 with D = diag((a^2 +
+ * 4 beta~) / (mean(a^2) + 4 beta~)), applied by real FFTs.  Multigrid: one
+ * V(1,1)-cycle, a damped Jacobi step (weight 0.8) before and after the
+ * coarse correction, grids of half the sides (residual and a^2 restricted as
+ * 2x2 means, corrections prolonged piecewise constant, beta~/4 per level),
+ * an exact solve on the coarsest grid (its operator inverted once per Z^m
+ * solve).  A slice takes the multigrid cycle
+ * (pcg_kernel 0 or 1) when it has more than 4096 pixels and both sides stay
+ * even while it halves down to at most 4096 pixels and on to at most 64; the
+ * choice is per slice, so a slice gives the same result alone and in a
+ * batch. */
 
 /* domain = 1 (sinogram-domain data terms).  The paper fits the reconstructed
  * image pair; with sinograms s_L, s_H as data, the basis-fidelity terms of
@@ -294,7 +311,8 @@ int recon_model_tables(const recon_params* params, double* out);
 #define RECON_F_CG_P1 15
 #define RECON_F_CG_Q 16
 #define RECON_F_CG_Y 17
-#define RECON_F_COUNT 18
+#define RECON_F_CG_R2 18   /* second residual buffer of the multigrid PCG */
+#define RECON_F_COUNT 19
 
 /* Device pointer of field f of slice s (storage: float, or double when
  * precision = 0; row pitch in elements in *pitch). */
@@ -345,7 +363,7 @@ int recon_tuning(recon_ctx* ctx, int32_t* out2);
  * stream of the handle, ordered after earlier and before later work of the
  * handle's stream; the iteration that fills recon_stats, and iterations
  * while recon_profile is on, still run as separate launches.  Needs domain 0
- * and pcg_kernel 0 (RECON_EINVAL otherwise). */
+ * and pcg_kernel 0 or 2 (RECON_EINVAL otherwise). */
 int recon_set_graph(recon_ctx* ctx, int32_t on);
 
 /* Number of kernels this handle has launched since creation (counting
@@ -361,8 +379,11 @@ int64_t recon_kernel_launches(recon_ctx* ctx);
  * cluster-resident PCG (whole Z^m solve of a slice per thread-block
  * cluster), 10 the CG of the sinogram-domain f updates (its pointwise,
  * stencil and preconditioner column passes), 11 projector and backprojector
- * inside the solve (domain 1), 12 other. */
-#define RECON_KF_COUNT 13
+ * inside the solve (domain 1); the multigrid-preconditioned PCG: 12 update of
+ * z and r, convergence test and the first restriction, 13 fine-level
+ * correction and smoothing with r.y, 14 new search direction p, q = M p and
+ * p.q, 15 the coarse levels and the restriction of a^2; 16 other. */
+#define RECON_KF_COUNT 17
 
 /* Time the launches of the kernel families whose bit is set in mask with
  * CUDA events on the handle's stream (0 = off).  Algorithmic bytes and launch

@@ -26,7 +26,7 @@ bool seven_smooth(int n) {
 int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
-        (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 1) ||
+        (p.order != 0 && p.order != 1) || p.pcg_kernel < 0 || p.pcg_kernel > 2 ||
         (p.domain != 0 && p.domain != 1) || (p.domain == 1 && (p.precision != 1 || p.order != 0)) || !(p.e1_kev > 0) ||
         !(p.e2_kev > 0) || p.e1_kev == p.e2_kev) {
         set_error("invalid recon_params");
@@ -473,6 +473,7 @@ const char* recon_profile_name(int32_t f) {
     static const char* names[KF_COUNT] = {"thr_rhs",   "fft_rows_fwd", "fft_cols", "fft_rows_inv",
                                           "synth",     "pcg_start",    "pcg_fwd",  "pcg_cols",
                                           "pcg_inv",   "pcg_cluster",  "fcg",      "project",
+                                          "mg_fwd",    "mg_y",         "mg_pq",    "mg_levels",
                                           "other"};
     return (f >= 0 && f < KF_COUNT) ? names[f] : "?";
 }

@@ -36,6 +36,7 @@ struct SliceGeom {
     int rows_per_item, cols_per_item;
     int cluster;               // 1: the Z^m solve of this slice runs in the cluster kernel
     float inv_n;               // 1 / (nx ny) rounded to float (spectral scale of the FP32 transforms)
+    int lvl;                   // multigrid level of this grid (0: the slice's own grid)
 };
 
 // Model constants that the FP32 kernels read, by index: each is one FP64
@@ -221,6 +222,10 @@ enum KFam {
     KF_PCG_CLUSTER,
     KF_FCG,
     KF_PROJ,
+    KF_MG_FWD,      // multigrid PCG: update, convergence test, first restriction
+    KF_MG_Y,        // multigrid PCG: fine-level correction and smoothing, r.y
+    KF_MG_PQ,       // multigrid PCG: new direction p, q = M p, p.q
+    KF_MG_LEVELS,   // multigrid PCG: the coarse levels (and the a^2 restriction)
     KF_OTHER,
     KF_COUNT
 };

@@ -77,6 +77,17 @@ struct Ctx {
 
     DevItemList tiles, rows, cols;
     DevItemList tmp_tiles;       // per-slot operations of the serving engine
+    // multigrid preconditioner of the Z^m PCG (slices with mg_lb > 0)
+    std::vector<int> mg_lb;                   // per slice: tile levels below its own grid (0: FFT preconditioner)
+    int mg_max_lb = 0;
+    std::vector<std::vector<SliceGeom>> mg_sg;   // [l][s], l >= 1: grid of level l (nx = 0 where absent)
+    std::vector<SliceGeom*> d_mg_geom;        // [l]: device copies ([0] = d_geom)
+    SliceGeom* d_mg_block = nullptr;          // per slice: its block level (nx = 0: none)
+    std::vector<DevItemList> mg_tiles;        // [l], l < mg_max_lb: tiles of level l of the slices with mg_lb > l
+    void* mg_pool[3] = {};                    // residual f, a^2 and correction e of the levels >= 1
+    int mg_block_smem = 0, mg_inv_smem = 0;
+    void* mg_qinv = nullptr;                  // per slice: inverse of its coarsest operator (kMgCoarsePx^2)
+    DevItemList pcg_rows, pcg_cols;           // row and column items of the slices on the FFT preconditioner
     std::vector<SliceConst> hconst;
     // serving mode: every slot laid out at capacity; lists hold the active slots
     bool server_mode = false;

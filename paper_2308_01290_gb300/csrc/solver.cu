@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
+#include <memory>
 #include <vector>
 
 #include "ctx.h"
@@ -1431,6 +1432,593 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
 }
 
 // --------------------------------------------------------------------------
+// Multigrid preconditioner of the Z^m PCG
+// --------------------------------------------------------------------------
+// On slices whose sides halve down to a small grid, the PCG takes
+// y = B r with B one V(1,1)-cycle for M = diag(a^2) + beta~ L: a damped
+// Jacobi step (weight kMgOmega) before and after the coarse correction;
+// coarse grids of half the sides, the residual and a^2 restricted as 2x2
+// means, corrections prolonged piecewise constant, and beta~ / 4 per level
+// (the Laplacian on a grid of twice the spacing).  The restriction is 1/4 of
+// the transpose of the prolongation and both smoothing steps are the same
+// Jacobi step, so B is symmetric positive definite, as PCG needs.  Levels of
+// more than kMgBlockPx pixels run as tile kernels over all slices; the rest
+// of the cycle of a slice runs inside one thread block, with an exact solve
+// on the coarsest grid (at most kMgCoarsePx pixels) by the inverse of its
+// operator, formed once per Z^m solve.
+// The fine-level passes of one PCG step:
+//   k_mg_fwd   z += alpha p, r' = r - alpha q (into the other r buffer), r'.r'
+//              and the convergence test; pre-smoothing x1 = w r' / (a^2 + 4 beta~)
+//              and the restricted residual of level 1
+//   k_mg_down  the same restriction on each tile level below (no update)
+//   k_mg_block the levels of a slice that fit one block, and the coarsest solve
+//   k_mg_up    coarse correction and post-smoothing on each tile level
+//   k_mg_y     the same on the fine level: y = B r', r'.y -> beta_cg
+//   k_mg_pq    p = y + beta_cg p_old, q = M p, p.q -> alpha
+
+constexpr int kMgBlockPx = 4096;       // levels of at most this many pixels run inside one block
+constexpr int kMgCoarsePx = 64;        // the coarsest grid has at most this many pixels
+constexpr int kMgMaxBlockLevels = 8;
+constexpr int kMgBlockThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ T mg_omega() {
+    return T(0.8);
+}
+
+// beta~ / 4^lvl
+template <typename T>
+__device__ __forceinline__ T mg_bt(const SliceState& s, int lvl) {
+    T b = Sc<T>::beta_t(s);
+    for (int i = 0; i < lvl; ++i) b *= T(0.25);
+    return b;
+}
+
+// fn(row, col) for every element of a shared-memory tile and its halo
+template <typename T, typename F>
+__device__ __forceinline__ void for_halo_tile(F fn) {
+    constexpr int W = kTileW + 2, H = TileDim<T>::TH + 2, OFF = TileDim<T>::OFF;
+    for (int q = threadIdx.x; q < W * H; q += blockDim.x) {
+        const int ly = q / W, lx = q - ly * W;
+        fn(ly, OFF - 1 + lx);
+    }
+}
+
+// Restricted residual of the tile at (tx0, ty0) of level g: out at level g1 =
+// mean over each 2x2 block of f - (a^2 x + bt L x), with f, a^2, x on the tile
+// and its halo in shared memory.
+template <typename T>
+__device__ __forceinline__ void mg_restrict_residual(const T (*sf)[TileDim<T>::SW], const T (*sa)[TileDim<T>::SW],
+                                                     const T (*sx)[TileDim<T>::SW], const SliceGeom& g,
+                                                     const SliceGeom& g1, int tx0, int ty0, T bt, T* out) {
+    constexpr int OFF = TileDim<T>::OFF, CW = kTileW / 2, CH = TileDim<T>::TH / 2;
+    for (int q = threadIdx.x; q < CW * CH; q += blockDim.x) {
+        const int cy = q / CW, cx = q - cy * CW;
+        if (tx0 + 2 * cx >= g.nx || ty0 + 2 * cy >= g.ny) continue;
+        T s = T(0);
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+            for (int dx = 0; dx < 2; ++dx) {
+                const int ry = 1 + 2 * cy + dy, col = OFF + 2 * cx + dx;
+                s += sf[ry][col] - (sa[ry][col] * sx[ry][col] + bt * lap5<T>(sx, ry, col));
+            }
+        out[g1.off + (long long)(ty0 / 2 + cy) * g1.pitch + tx0 / 2 + cx] = T(0.25) * s;
+    }
+}
+
+// a^2 of level g1 = 2x2 means of level g (tiles of level g)
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads) k_mg_restrict(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                                 const SliceState* S, const T* a, T* a1,
+                                                                 unsigned long long* acct) {
+    constexpr int CW = kTileW / 2, CH = TileDim<T>::TH / 2;
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        if (!__ldg(&S[it.slice].active)) continue;
+        const SliceGeom g = G[it.slice], g1 = G1[it.slice];
+        account(acct, KF_MG_LEVELS, tile_px<T>(g, it) * 5 * (long long)sizeof(T) / 4);
+        for (int q = threadIdx.x; q < CW * CH; q += blockDim.x) {
+            const int cy = q / CW, cx = q - cy * CW;
+            const int x = it.a + 2 * cx, y = it.b + 2 * cy;
+            if (x >= g.nx || y >= g.ny) continue;
+            const long long d = g.off + (long long)y * g.pitch + x;
+            a1[g1.off + (long long)(y / 2) * g1.pitch + x / 2] =
+                T(0.25) * ((a[d] + a[d + 1]) + (a[d + g.pitch] + a[d + g.pitch + 1]));
+        }
+    }
+}
+
+// Fine level, start of a PCG step (UPD: after the update with alpha).  r is
+// read from rin and, updated, written to rout: other tiles read the old r on
+// their halo in the same launch.
+template <typename T, bool UPD>
+__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                             const SliceConst* C, SliceState* S, Ptrs<T> P, int par,
+                                                             const T* rin, T* rout, T* F1, int* pending) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW, TH = TileDim<T>::TH;
+    __shared__ __align__(16) T sm[3][TH + 2][SW];   // r, a^2, q (then x1)
+    __shared__ double red[32];
+    __shared__ SliceGeom s_g, s_g1;
+    T* z = P.f[RECON_F_Z];
+    const T* p = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
+    const T* q = P.f[RECON_F_CG_Q];
+    const T* a2 = P.f[RECON_F_A2];
+    struct In {
+        Pack<T> z, p;
+    };
+    auto load = [&](long long d, int cnt) { return In{ldv_n(z, d, cnt), ldv_n(p, d, cnt)}; };
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
+        stage_struct(&s_g1, G1 + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        // UPD: z, p, r, q, a^2 in, z, r out, level-1 residual out; else r, a^2 in
+        account(P.acct, KF_MG_FWD, tile_px<T>(g, it) * (UPD ? 29 : 9) * (long long)sizeof(T) / 4);
+        In v[TileVec<T>::R];
+        if (UPD) {
+            tile_vec_load<T>(g, it, load, v);
+            load_tile<T, 3>(
+                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 3>{{rin[d], a2[d], q[d]}}; },
+                [&](long long d) { return PVals<T, 3>{{ldv(rin, d), ldv(a2, d), ldv(q, d)}}; });
+        } else {
+            load_tile<T, 2>(
+                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{rin[d], a2[d]}}; },
+                [&](long long d) { return PVals<T, 2>{{ldv(rin, d), ldv(a2, d)}}; });
+        }
+        __syncthreads();
+        const T bt = Sc<T>::beta_t(*sp), b4 = Sc<T>::b4(*sp), om = mg_omega<T>();
+        T acc = T(0);
+        if (UPD) {
+            const T al = Sc<T>::alpha(*sp);
+            for_halo_tile<T>([&](int ly, int col) { sm[0][ly][col] = fma(-al, sm[2][ly][col], sm[0][ly][col]); });
+            __syncthreads();
+            tile_vec_use<T>(
+                g, it,
+                [&](long long d, int cnt, int ly, int lx0, const In& x) {
+                    Pack<T> zn, rn;
+#pragma unroll
+                    for (int e = 0; e < VN; ++e) {
+                        zn.v[e] = fma(al, x.p.v[e], x.z.v[e]);
+                        rn.v[e] = sm[0][ly + 1][OFF + lx0 + e];
+                        if (e < cnt) acc = fma(rn.v[e], rn.v[e], acc);
+                    }
+                    stv_n(z, d, zn, cnt);
+                    stv_n(rout, d, rn, cnt);
+                },
+                v);
+        }
+        // pre-smoothing from zero, on the tile and its halo (in place of q)
+        for_halo_tile<T>([&](int ly, int col) { sm[2][ly][col] = om * sm[0][ly][col] / (sm[1][ly][col] + b4); });
+        __syncthreads();
+        mg_restrict_residual<T>(sm[0], sm[1], sm[2], g, s_g1, it.a, it.b, bt, F1);
+        if (UPD) {
+            const T part[1] = {acc};
+            double a[1];
+            block_sum_t<T, 1>(part, a, red);
+            double tot[1];
+            if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
+                SliceState& so = S[it.slice];
+                const SliceConst& c = C[it.slice];
+                so.rr = tot[0];
+                so.cg_it += 1;
+                const bool conv = !(tot[0] > c.cg_tol * c.cg_tol * so.bb);
+                if (conv || so.cg_it >= c.cg_max) {
+                    so.cg_done = 1;
+                    atomicSub(pending, 1);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Tile level g (level >= 1): pre-smoothing from zero and the restricted
+// residual into level g1.
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_down(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                              const SliceState* S, const T* F, const T* A, T* F1,
+                                                              unsigned long long* acct) {
+    constexpr int SW = TileDim<T>::SW, TH = TileDim<T>::TH;
+    __shared__ __align__(16) T sm[3][TH + 2][SW];   // f, a^2, x1
+    __shared__ SliceGeom s_g, s_g1;
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
+        stage_struct(&s_g1, G1 + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        account(acct, KF_MG_LEVELS, tile_px<T>(g, it) * 9 * (long long)sizeof(T) / 4);
+        load_tile<T, 2>(
+            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{F[d], A[d]}}; },
+            [&](long long d) { return PVals<T, 2>{{ldv(F, d), ldv(A, d)}}; });
+        __syncthreads();
+        const T bt = mg_bt<T>(*sp, g.lvl), b4 = T(4) * bt, om = mg_omega<T>();
+        for_halo_tile<T>([&](int ly, int col) { sm[2][ly][col] = om * sm[0][ly][col] / (sm[1][ly][col] + b4); });
+        __syncthreads();
+        mg_restrict_residual<T>(sm[0], sm[1], sm[2], g, s_g1, it.a, it.b, bt, F1);
+        __syncthreads();
+    }
+}
+
+// Coarse correction and post-smoothing on the tile at (tx0, ty0) of level g:
+// x = w f / (a^2 + 4 bt) + e1 (the coarse correction of level g1, constant on
+// 2x2 blocks), then x + w (f - (a^2 x + bt L x)) / (a^2 + 4 bt) for each
+// pixel of the tile, passed to out(d, cnt, ly, lx0, value pack).  sm[0], sm[1]
+// hold f and a^2 on the tile and its halo; sm[2] receives x.
+template <typename T, typename FO>
+__device__ __forceinline__ void mg_correct_smooth(T (*sm)[TileDim<T>::TH + 2][TileDim<T>::SW],
+                                                  T (*ec)[kTileW / 2 + 2], const SliceGeom& g, const SliceGeom& g1,
+                                                  const Item& it, const T* E1, T bt, FO out) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, CH = TileDim<T>::TH / 2 + 2, CW = kTileW / 2 + 2;
+    // coarse cells under the tile and its halo (periodic)
+    const int X0 = it.a / 2 - 1, Y0 = it.b / 2 - 1;
+    for (int q = threadIdx.x; q < CH * CW; q += blockDim.x) {
+        const int cy = q / CW, cx = q - cy * CW;
+        ec[cy][cx] = E1[g1.off + (long long)wrap(Y0 + cy, g1.ny) * g1.pitch + wrap(X0 + cx, g1.nx)];
+    }
+    __syncthreads();
+    const T b4 = T(4) * bt, om = mg_omega<T>();
+    for_halo_tile<T>([&](int ly, int col) {
+        // row ly of the tile is pixel row it.b - 1 + ly: coarse row (ly + 1) >> 1 of ec
+        sm[2][ly][col] = om * sm[0][ly][col] / (sm[1][ly][col] + b4) + ec[(ly + 1) >> 1][(col - OFF + 2) >> 1];
+    });
+    __syncthreads();
+    for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
+        Pack<T> o;
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const int ry = ly + 1, col = OFF + lx0 + e;
+            const T x = sm[2][ry][col], a = sm[1][ry][col];
+            o.v[e] = x + om * (sm[0][ry][col] - (a * x + bt * lap5<T>(sm[2], ry, col))) / (a + b4);
+        }
+        out(d, cnt, ly, lx0, o);
+    });
+}
+
+// Tile level g (level >= 1): e = coarse correction and post-smoothing.
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                            const SliceState* S, const T* F, const T* A,
+                                                            const T* E1, T* E, unsigned long long* acct) {
+    constexpr int SW = TileDim<T>::SW, TH = TileDim<T>::TH;
+    __shared__ __align__(16) T sm[3][TH + 2][SW];   // f, a^2, x
+    __shared__ T ec[TH / 2 + 2][kTileW / 2 + 2];
+    __shared__ SliceGeom s_g, s_g1;
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
+        stage_struct(&s_g1, G1 + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        account(acct, KF_MG_LEVELS, tile_px<T>(g, it) * 13 * (long long)sizeof(T) / 4);
+        load_tile<T, 2>(
+            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{F[d], A[d]}}; },
+            [&](long long d) { return PVals<T, 2>{{ldv(F, d), ldv(A, d)}}; });
+        mg_correct_smooth<T>(sm, ec, g, s_g1, it, E1, mg_bt<T>(*sp, g.lvl),
+                             [&](long long d, int cnt, int, int, const Pack<T>& o) { stv_n(E, d, o, cnt); });
+        __syncthreads();
+    }
+}
+
+// Fine level: y = B r (correction from level 1 and post-smoothing), r.y ->
+// beta_cg.
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_y(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                           SliceState* S, Ptrs<T> P, const T* r, const T* E1) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW, TH = TileDim<T>::TH;
+    __shared__ __align__(16) T sm[3][TH + 2][SW];   // r, a^2, x
+    __shared__ T ec[TH / 2 + 2][kTileW / 2 + 2];
+    __shared__ double red[32];
+    __shared__ SliceGeom s_g, s_g1;
+    const T* a2 = P.f[RECON_F_A2];
+    T* y = P.f[RECON_F_CG_Y];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
+        stage_struct(&s_g1, G1 + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        account(P.acct, KF_MG_Y, tile_px<T>(g, it) * 13 * (long long)sizeof(T) / 4);
+        load_tile<T, 2>(
+            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{r[d], a2[d]}}; },
+            [&](long long d) { return PVals<T, 2>{{ldv(r, d), ldv(a2, d)}}; });
+        T acc = T(0);
+        mg_correct_smooth<T>(sm, ec, g, s_g1, it, E1, Sc<T>::beta_t(*sp),
+                             [&](long long d, int cnt, int ly, int lx0, const Pack<T>& o) {
+#pragma unroll
+                                 for (int e = 0; e < VN; ++e)
+                                     if (e < cnt) acc = fma(sm[0][ly + 1][OFF + lx0 + e], o.v[e], acc);
+                                 stv_n(y, d, o, cnt);
+                             });
+        const T part[1] = {acc};
+        double a[1];
+        block_sum_t<T, 1>(part, a, red);
+        double tot[1];
+        if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
+            SliceState& so = S[it.slice];
+            set_betacg(so, (so.cg_it == 0) ? 0.0 : tot[0] / so.ry);
+            so.ry = tot[0];
+        }
+        __syncthreads();
+    }
+}
+
+// Fine level: p = y + beta_cg p_old (p = y on the first step), q = M p, p.q
+// -> alpha.
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_pq(ItemList L, const SliceGeom* G, SliceState* S,
+                                                            Ptrs<T> P, int par) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW, TH = TileDim<T>::TH;
+    __shared__ __align__(16) T sm[2][TH + 2][SW];   // y (then p), p_old
+    __shared__ double red[32];
+    __shared__ SliceGeom s_g;
+    const T* y = P.f[RECON_F_CG_Y];
+    const T* pold = P.f[par ? RECON_F_CG_P1 : RECON_F_CG_P0];
+    T* pnew = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
+    const T* a2 = P.f[RECON_F_A2];
+    T* qo = P.f[RECON_F_CG_Q];
+    struct In {
+        Pack<T> a;
+    };
+    auto load = [&](long long d, int cnt) { return In{ldv_n(a2, d, cnt)}; };
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        stage_struct(&s_g, G + it.slice);
+        __syncthreads();
+        const SliceGeom& g = s_g;
+        const bool first = __ldg(&sp->cg_it) == 0;
+        account(P.acct, KF_MG_PQ, tile_px<T>(g, it) * (first ? 4 : 5) * (long long)sizeof(T));
+        In v[TileVec<T>::R];
+        tile_vec_load<T>(g, it, load, v);
+        if (first) {
+            load_tile<T, 1>(
+                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{y[d]}}; },
+                [&](long long d) { return PVals<T, 1>{{ldv(y, d)}}; });
+        } else {
+            load_tile<T, 2>(
+                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{y[d], pold[d]}}; },
+                [&](long long d) { return PVals<T, 2>{{ldv(y, d), ldv(pold, d)}}; });
+        }
+        __syncthreads();
+        if (!first) {
+            const T bc = Sc<T>::betacg(*sp);
+            for_halo_tile<T>([&](int ly, int col) { sm[0][ly][col] = fma(bc, sm[1][ly][col], sm[0][ly][col]); });
+            __syncthreads();
+        }
+        const T bt = Sc<T>::beta_t(*sp);
+        T acc = T(0);
+        tile_vec_use<T>(
+            g, it,
+            [&](long long d, int cnt, int ly, int lx0, const In& x) {
+                Pack<T> pv, qv;
+#pragma unroll
+                for (int e = 0; e < VN; ++e) {
+                    const int ry = ly + 1, col = OFF + lx0 + e;
+                    pv.v[e] = sm[0][ry][col];
+                    qv.v[e] = x.a.v[e] * pv.v[e] + bt * lap5<T>(sm[0], ry, col);
+                    if (e < cnt) acc = fma(pv.v[e], qv.v[e], acc);
+                }
+                stv_n(pnew, d, pv, cnt);
+                stv_n(qo, d, qv, cnt);
+            },
+            v);
+        const T part[1] = {acc};
+        double a[1];
+        block_sum_t<T, 1>(part, a, red);
+        double tot[1];
+        if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
+            SliceState& so = S[it.slice];
+            so.pq = tot[0];
+            set_alpha(so, tot[0] > 0.0 ? so.ry / tot[0] : 0.0);
+        }
+        __syncthreads();
+    }
+}
+
+// Sides of the in-block levels of a block level of bx x by pixels: halve while
+// both sides are even and the grid has more than kMgCoarsePx pixels.
+__host__ __device__ inline int mg_block_levels(int bx, int by, int* nx, int* ny) {
+    int j = 0;
+    nx[0] = bx;
+    ny[0] = by;
+    while (nx[j] * ny[j] > kMgCoarsePx && nx[j] % 2 == 0 && ny[j] % 2 == 0 && j + 1 < kMgMaxBlockLevels) {
+        nx[j + 1] = nx[j] / 2;
+        ny[j + 1] = ny[j] / 2;
+        ++j;
+    }
+    return j + 1;
+}
+
+// Inverse of the coarsest operator diag(a^2) + bt L of each multigrid slice
+// (once per Z^m solve; grid: one block per slice): a^2 restricted through
+// the slice's block levels as in k_mg_block, the dense n x n operator
+// (n <= kMgCoarsePx, periodic neighbours accumulate) inverted in FP64 by
+// Gauss-Jordan elimination without pivoting (the matrix is symmetric
+// positive definite), symmetrised, stored n x n in the kernel's precision.
+constexpr int kMgCoarseInvSmem =
+    (kMgCoarsePx * (kMgCoarsePx + 1) + kMgCoarsePx) * (int)sizeof(double);   // + the a^2 of the levels
+
+template <typename T>
+__global__ void __launch_bounds__(kMgBlockThreads) k_mg_coarse_inv(const SliceGeom* GB, const SliceState* S,
+                                                                   const T* A, T* Qinv) {
+    extern __shared__ __align__(16) unsigned char mgq_smem[];
+    double(*M)[kMgCoarsePx + 1] = reinterpret_cast<double(*)[kMgCoarsePx + 1]>(mgq_smem);
+    double* fac = reinterpret_cast<double*>(mgq_smem) + kMgCoarsePx * (kMgCoarsePx + 1);
+    T* a = reinterpret_cast<T*>(mgq_smem + kMgCoarseInvSmem);   // every level (sum of sizes)
+    const int s = blockIdx.x;
+    const SliceGeom g = GB[s];
+    if (g.nx == 0 || !__ldg(&S[s].active)) return;
+    int nx[kMgMaxBlockLevels], ny[kMgMaxBlockLevels], base[kMgMaxBlockLevels];
+    const int J = mg_block_levels(g.nx, g.ny, nx, ny);
+    int tot = 0;
+    for (int j = 0; j < J; ++j) {
+        base[j] = tot;
+        tot += nx[j] * ny[j];
+    }
+    for (int i = threadIdx.x; i < g.nx * g.ny; i += blockDim.x) {
+        const int yy = i / g.nx, xx = i - yy * g.nx;
+        a[i] = A[g.off + (long long)yy * g.pitch + xx];
+    }
+    __syncthreads();
+    for (int j = 1; j < J; ++j) {
+        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x) {
+            const int yy = i / nx[j], xx = i - yy * nx[j];
+            const T* u = a + base[j - 1];
+            const int w = nx[j - 1];
+            a[base[j] + i] = T(0.25) * ((u[2 * yy * w + 2 * xx] + u[2 * yy * w + 2 * xx + 1]) +
+                                        (u[(2 * yy + 1) * w + 2 * xx] + u[(2 * yy + 1) * w + 2 * xx + 1]));
+        }
+        __syncthreads();
+    }
+    const int j = J - 1, cx = nx[j], cy = ny[j], n = cx * cy;
+    double bt = S[s].beta_t;
+    for (int l = 0; l < g.lvl + j; ++l) bt *= 0.25;
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) M[q / n][q % n] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) {
+            const int yy = i / cx, xx = i - yy * cx;
+            M[i][i] += (double)a[base[j] + i] + 4.0 * bt;
+            const int nb[4] = {yy * cx + wrap(xx - 1, cx), yy * cx + wrap(xx + 1, cx), wrap(yy - 1, cy) * cx + xx,
+                               wrap(yy + 1, cy) * cx + xx};
+            for (int k = 0; k < 4; ++k) M[i][nb[k]] -= bt;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+        const double p = M[k][k];
+        __syncthreads();
+        for (int jj = threadIdx.x; jj < n; jj += blockDim.x) M[k][jj] = (jj == k ? 1.0 : M[k][jj]) / p;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = M[i][k];
+        __syncthreads();
+        for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+            const int i = q / n, jj = q - i * n;
+            if (i == k) continue;
+            M[i][jj] = (jj == k ? 0.0 : M[i][jj]) - fac[i] * M[k][jj];
+        }
+        __syncthreads();
+    }
+    T* Q = Qinv + (long long)s * kMgCoarsePx * kMgCoarsePx;
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
+        const int i = q / n, jj = q - i * n;
+        Q[q] = T(0.5 * (M[i][jj] + M[jj][i]));
+    }
+}
+
+// The levels of one slice that fit one block (grid: one block per slice):
+// f and a^2 of the slice's block level in, its correction e out.
+template <typename T>
+__global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* GB, const SliceState* S, const T* F,
+                                                              const T* A, T* E, const T* Qinv,
+                                                              unsigned long long* acct) {
+    extern __shared__ __align__(16) unsigned char mg_smem[];
+    T* sh = reinterpret_cast<T*>(mg_smem);
+    const int s = blockIdx.x;
+    const SliceGeom g = GB[s];
+    if (g.nx == 0 || !__ldg(&S[s].active) || __ldg(&S[s].cg_done)) return;
+    int nx[kMgMaxBlockLevels], ny[kMgMaxBlockLevels], base[kMgMaxBlockLevels];
+    const int J = mg_block_levels(g.nx, g.ny, nx, ny);
+    int tot = 0;
+    for (int j = 0; j < J; ++j) {
+        base[j] = tot;
+        tot += nx[j] * ny[j];
+    }
+    T* f = sh;             // f of every level
+    T* a = sh + tot;       // a^2
+    T* x = sh + 2 * tot;   // correction
+    if (threadIdx.x == 0) atomicAdd(acct + KF_MG_LEVELS, (unsigned long long)(g.nx * g.ny) * 3ull * sizeof(T));
+    const T om = mg_omega<T>();
+    T bt[kMgMaxBlockLevels];
+    bt[0] = mg_bt<T>(S[s], g.lvl);
+    for (int j = 1; j < J; ++j) bt[j] = bt[j - 1] * T(0.25);
+    for (int i = threadIdx.x; i < g.nx * g.ny; i += blockDim.x) {
+        const int yy = i / g.nx, xx = i - yy * g.nx;
+        const long long d = g.off + (long long)yy * g.pitch + xx;
+        f[i] = F[d];
+        a[i] = A[d];
+    }
+    __syncthreads();
+    auto at = [&](const T* v, int j, int yy, int xx) -> T {
+        return v[base[j] + wrap(yy, ny[j]) * nx[j] + wrap(xx, nx[j])];
+    };
+    auto mv = [&](const T* v, int j, int yy, int xx) -> T {   // (a^2 + bt L) v at a pixel of level j
+        const T c = at(v, j, yy, xx);
+        const T l = (T(4) * c - at(v, j, yy, xx - 1) - at(v, j, yy, xx + 1)) -
+                    (at(v, j, yy - 1, xx) + at(v, j, yy + 1, xx));
+        return at(a, j, yy, xx) * c + bt[j] * l;
+    };
+    for (int j = 1; j < J; ++j) {
+        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x) {
+            const int yy = i / nx[j], xx = i - yy * nx[j];
+            a[base[j] + i] = T(0.25) * ((at(a, j - 1, 2 * yy, 2 * xx) + at(a, j - 1, 2 * yy, 2 * xx + 1)) +
+                                        (at(a, j - 1, 2 * yy + 1, 2 * xx) + at(a, j - 1, 2 * yy + 1, 2 * xx + 1)));
+        }
+        __syncthreads();
+    }
+    // down: pre-smoothing from zero, restricted residual
+    for (int j = 0; j + 1 < J; ++j) {
+        const T b4 = T(4) * bt[j];
+        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x)
+            x[base[j] + i] = om * f[base[j] + i] / (a[base[j] + i] + b4);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nx[j + 1] * ny[j + 1]; i += blockDim.x) {
+            const int yy = i / nx[j + 1], xx = i - yy * nx[j + 1];
+            T sum = T(0);
+            for (int dy = 0; dy < 2; ++dy)
+                for (int dx = 0; dx < 2; ++dx)
+                    sum += at(f, j, 2 * yy + dy, 2 * xx + dx) - mv(x, j, 2 * yy + dy, 2 * xx + dx);
+            f[base[j + 1] + i] = T(0.25) * sum;
+        }
+        __syncthreads();
+    }
+    // coarsest: exact solve with the inverse of its operator (symmetric, so
+    // thread i reads column i, coalesced)
+    {
+        const int j = J - 1, n = nx[j] * ny[j];
+        const T* Q = Qinv + (long long)s * kMgCoarsePx * kMgCoarsePx;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            T acc = T(0);
+            for (int k = 0; k < n; ++k) acc = fma(Q[k * n + i], f[base[j] + k], acc);
+            x[base[j] + i] = acc;
+        }
+        __syncthreads();
+    }
+    // up: coarse correction, post-smoothing (the residual goes into f)
+    for (int j = J - 2; j >= 0; --j) {
+        const T b4 = T(4) * bt[j];
+        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x) {
+            const int yy = i / nx[j], xx = i - yy * nx[j];
+            x[base[j] + i] += x[base[j + 1] + (yy >> 1) * nx[j + 1] + (xx >> 1)];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x) {
+            const int yy = i / nx[j], xx = i - yy * nx[j];
+            f[base[j] + i] -= mv(x, j, yy, xx);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x)
+            x[base[j] + i] += om * f[base[j] + i] / (a[base[j] + i] + b4);
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < g.nx * g.ny; i += blockDim.x) {
+        const int yy = i / g.nx, xx = i - yy * g.nx;
+        E[g.off + (long long)yy * g.pitch + xx] = x[i];
+    }
+}
+
+// --------------------------------------------------------------------------
 // Sinogram-domain f updates (domain 1): conjugate gradients on
 //   [alpha_k A^T A / gamma + c'_k + beta L] f_k = rhs_k
 // preconditioned by (alpha_k + c'_k + beta K)^-1 applied by FFT (kinds 4, 5
@@ -1842,6 +2430,96 @@ int op_synth(Ctx& c) {
     return RECON_OK;
 }
 
+// Family timer that is skipped while a graph is captured.
+struct MaybeTimer {
+    std::unique_ptr<FamTimer> t;
+    MaybeTimer(Ctx& c, int fam, bool on) {
+        if (on) t.reset(new FamTimer(c, fam));
+    }
+};
+
+template <typename T>
+T* field_t(Ctx& c, int f) {
+    return static_cast<T*>(c.field[f]);
+}
+
+// Residual buffer k of the multigrid PCG (its steps alternate between two).
+template <typename T>
+T* mg_r(Ctx& c, int k) {
+    return field_t<T>(c, k ? RECON_F_CG_R2 : RECON_F_CG_R);
+}
+
+// a^2 of every multigrid level from the fine a^2 (once per Z^m solve).
+template <typename T>
+void mg_restrict_a2(Ctx& c, bool timed) {
+    MaybeTimer t(c, KF_MG_LEVELS, timed);
+    T* pa = static_cast<T*>(c.mg_pool[1]);
+    for (int l = 0; l < c.mg_max_lb; ++l) {
+        const DevItemList& L = c.mg_tiles[l];
+        const T* a = l == 0 ? field_t<T>(c, RECON_F_A2) : pa;
+        k_mg_restrict<T><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(L.view(), c.d_mg_geom[l],
+                                                                             c.d_mg_geom[l + 1], c.d_state, a, pa,
+                                                                             c.d_acct);
+        c.launches += 1;
+    }
+    k_mg_coarse_inv<T><<<c.n, kMgBlockThreads, c.mg_inv_smem, c.stream>>>(c.d_mg_block, c.d_state, pa,
+                                                                          static_cast<T*>(c.mg_qinv));
+    c.launches += 1;
+}
+
+// Fine-level start of a multigrid PCG step: UPD updates z and r (from
+// residual buffer rk into buffer rk ^ 1) and tests convergence.
+template <typename T, bool UPD>
+void mg_fwd(Ctx& c, int par, int rk, bool timed) {
+    MaybeTimer t(c, KF_MG_FWD, timed);
+    const DevItemList& L = c.mg_tiles[0];
+    k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(
+        L.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
+        mg_r<T>(c, rk ^ 1), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending);
+    c.launches += 1;
+}
+
+// Rest of a multigrid PCG step for residual buffer rk: the V-cycle below the
+// fine level, y and r.y, then p, q and p.q.
+template <typename T>
+void mg_tail(Ctx& c, int par, int rk, bool timed) {
+    T* pf = static_cast<T*>(c.mg_pool[0]);
+    T* pa = static_cast<T*>(c.mg_pool[1]);
+    T* pe = static_cast<T*>(c.mg_pool[2]);
+    {
+        MaybeTimer t(c, KF_MG_LEVELS, timed);
+        for (int l = 1; l < c.mg_max_lb; ++l) {
+            const DevItemList& L = c.mg_tiles[l];
+            k_mg_down<T><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(L.view(), c.d_mg_geom[l],
+                                                                             c.d_mg_geom[l + 1], c.d_state, pf, pa,
+                                                                             pf, c.d_acct);
+            c.launches += 1;
+        }
+        k_mg_block<T><<<c.n, kMgBlockThreads, c.mg_block_smem, c.stream>>>(
+            c.d_mg_block, c.d_state, pf, pa, pe, static_cast<const T*>(c.mg_qinv), c.d_acct);
+        c.launches += 1;
+        for (int l = c.mg_max_lb - 1; l >= 1; --l) {
+            const DevItemList& L = c.mg_tiles[l];
+            k_mg_up<T><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(L.view(), c.d_mg_geom[l],
+                                                                           c.d_mg_geom[l + 1], c.d_state, pf, pa, pe,
+                                                                           pe, c.d_acct);
+            c.launches += 1;
+        }
+    }
+    const DevItemList& L0 = c.mg_tiles[0];
+    {
+        MaybeTimer t(c, KF_MG_Y, timed);
+        k_mg_y<T><<<grid_for(c, L0.n), kStencilThreads, 0, c.stream>>>(L0.view(), c.d_geom, c.d_mg_geom[1], c.d_state,
+                                                                       ptrs<T>(c), mg_r<T>(c, rk), pe);
+    }
+    {
+        MaybeTimer t(c, KF_MG_PQ, timed);
+        k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 0, c.stream>>>(L0.view(), c.d_geom, c.d_state, ptrs<T>(c),
+                                                                        par);
+    }
+    c.launches += 2;
+}
+
 template <typename T>
 int op_solve_z(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
@@ -1857,45 +2535,64 @@ int op_solve_z(Ctx& c) {
                                                                               c.d_state, P, c.d_cg_pending);
     }
     c.launches += 1;
+    // slices on the FFT preconditioner (the row and column items of the PCG)
+    // and slices on the multigrid cycle run side by side, step by step
+    const bool mg = c.mg_max_lb > 0;
+    const DevItemList& prow = mg ? c.pcg_rows : c.rows;
+    const DevItemList& pcol = mg ? c.pcg_cols : c.cols;
+    const bool fft = prow.n > 0;
     const int smem = fft_smem_bytes<T>(c);
     const cplx<T>* tw = static_cast<const cplx<T>*>(c.d_tw);
     const int half = fft_half_slots<T>(c);
     const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 3);
     int par = c.cg_parity;
-    // Consecutive passes walk the items in opposite orders, so that each
+    int rk = 0;   // multigrid residual buffer (k_cg_init wrote CG_R)
+    // Consecutive FFT passes walk the items in opposite orders, so that each
     // pass starts on the slices the previous one touched last, which are
     // still in the L2 (the working set is many times the L2).  k_cg_init ran
     // forward, so the first PCG pass runs backward.
     int rev = 1;
-    {
+    if (fft) {
         FamTimer t(c, KF_PCG_FWD);
-        k_pcg_fwd<T, false><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, rev);
+        k_pcg_fwd<T, false><<<grid_for(c, prow.n), kFftThreads, smem, c.stream>>>(
+            prow.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, rev);
         rev ^= 1;
+        c.launches += 1;
     }
-    c.launches += 1;
+    if (mg) {
+        mg_restrict_a2<T>(c, true);
+        mg_fwd<T, false>(c, par, rk, true);
+    }
     int cap = 0;
     for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
     for (int it = 0; it < cap; ++it) {
-        {
-            FamTimer t(c, KF_COLS_PRE);
-            k_cols<T><<<grid_for(c, c.cols.n), kFftThreads, smem, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
-                                                                              c.d_state, P, pre, tw, half, rev);
-            rev ^= 1;
+        if (fft) {
+            {
+                FamTimer t(c, KF_COLS_PRE);
+                k_cols<T><<<grid_for(c, pcol.n), kFftThreads, smem, c.stream>>>(pcol.view(), c.d_geom, c.d_const,
+                                                                                c.d_state, P, pre, tw, half, rev);
+                rev ^= 1;
+            }
+            {
+                FamTimer t(c, KF_PCG_INV);
+                k_pcg_inv<T><<<grid_for(c, prow.n), kFftThreads, smem, c.stream>>>(prow.view(), c.d_geom, c.d_state,
+                                                                                  P, tw, half, par, rev);
+                rev ^= 1;
+            }
+            c.launches += 2;
         }
-        {
-            FamTimer t(c, KF_PCG_INV);
-            k_pcg_inv<T><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom, c.d_state,
-                                                                                P, tw, half, par, rev);
-            rev ^= 1;
-        }
-        {
+        if (mg) mg_tail<T>(c, par, rk, true);
+        if (fft) {
             FamTimer t(c, KF_PCG_FWD);
-            k_pcg_fwd<T, true><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-                c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, rev);
+            k_pcg_fwd<T, true><<<grid_for(c, prow.n), kFftThreads, smem, c.stream>>>(
+                prow.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, rev);
             rev ^= 1;
+            c.launches += 1;
         }
-        c.launches += 3;
+        if (mg) {
+            mg_fwd<T, true>(c, par, rk, true);
+            rk ^= 1;
+        }
         RECON_CUDA(cudaGetLastError());
         par ^= 1;
         if ((it & 3) == 3 || it == cap - 1) {
@@ -2019,11 +2716,11 @@ __global__ void k_pcg_loop_start(cudaGraphConditionalHandle h, const int* pendin
 // End of a body (two PCG steps): run another while a slice has not
 // converged and fewer than `cap` bodies have run (bounded loop).
 __global__ void k_pcg_loop_cond(cudaGraphConditionalHandle h, const int* pending, int* body, int cap,
-                                unsigned long long* launches) {
+                                unsigned long long* launches, int per_body) {
     const int b = *body + 1;
     *body = b;
     cudaGraphSetConditional(h, (*pending > 0 && b < cap) ? 1u : 0u);
-    atomicAdd(launches, 7ull);   // six PCG kernels and this one
+    atomicAdd(launches, (unsigned long long)per_body);   // the body's PCG kernels and this one
 }
 
 template <typename T>
@@ -2033,6 +2730,10 @@ int graph_build_t(Ctx& c) {
     const cplx<T>* tw = static_cast<const cplx<T>*>(c.d_tw);
     const int half = fft_half_slots<T>(c), half_c = half;
     const FftJobs pre = jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 3);
+    const bool mg = c.mg_max_lb > 0;
+    const DevItemList& prow = mg ? c.pcg_rows : c.rows;
+    const DevItemList& pcol = mg ? c.pcg_cols : c.cols;
+    const bool fft = prow.n > 0;
     int cap = 0;
     for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
     const int bodies = (cap + 1) / 2;
@@ -2063,10 +2764,18 @@ int graph_build_t(Ctx& c) {
         cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream);
         k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                               c.d_state, P, c.d_cg_pending);
-        k_pcg_fwd<T, false><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, 0, c.d_cg_pending, 1);
+        c.launches += 1;
+        if (fft) {
+            k_pcg_fwd<T, false><<<grid_for(c, prow.n), kFftThreads, smem, c.stream>>>(
+                prow.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, 0, c.d_cg_pending, 1);
+            c.launches += 1;
+        }
+        if (mg) {
+            mg_restrict_a2<T>(c, false);
+            mg_fwd<T, false>(c, 0, 0, false);
+        }
         k_pcg_loop_start<<<1, 1, 0, c.stream>>>(h, c.d_cg_pending, c.d_graph_body);
-        c.launches += 3;
+        c.launches += 1;
     }
     e = cudaStreamEndCapture(c.stream, &g);
     if (rc) {
@@ -2096,15 +2805,27 @@ int graph_build_t(Ctx& c) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     e = cudaStreamBeginCaptureToGraph(c.stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e != cudaSuccess) return fail(e, "capture (PCG body)");
-    for (int par = 0; par < 2; ++par) {   // six passes: directions alternate as in op_solve_z
-        k_cols<T><<<grid_for(c, c.cols.n), kFftThreads, smem_c, c.stream>>>(c.cols.view(), c.d_geom, c.d_const,
-                                                                            c.d_state, P, pre, tw, half_c, par);
-        k_pcg_inv<T><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(c.rows.view(), c.d_geom, c.d_state, P,
-                                                                            tw, half, par, par ^ 1);
-        k_pcg_fwd<T, true><<<grid_for(c, c.rows.n), kFftThreads, smem, c.stream>>>(
-            c.rows.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, par);
+    const long long lb0 = c.launches;
+    for (int par = 0; par < 2; ++par) {   // two PCG steps; FFT pass directions alternate as in op_solve_z
+        if (fft) {
+            k_cols<T><<<grid_for(c, pcol.n), kFftThreads, smem_c, c.stream>>>(pcol.view(), c.d_geom, c.d_const,
+                                                                              c.d_state, P, pre, tw, half_c, par);
+            k_pcg_inv<T><<<grid_for(c, prow.n), kFftThreads, smem, c.stream>>>(prow.view(), c.d_geom, c.d_state, P,
+                                                                              tw, half, par, par ^ 1);
+            c.launches += 2;
+        }
+        if (mg) mg_tail<T>(c, par, par, false);
+        if (fft) {
+            k_pcg_fwd<T, true><<<grid_for(c, prow.n), kFftThreads, smem, c.stream>>>(
+                prow.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, par, c.d_cg_pending, par);
+            c.launches += 1;
+        }
+        if (mg) mg_fwd<T, true>(c, par, par, false);   // residual buffers alternate with the steps
     }
-    k_pcg_loop_cond<<<1, 1, 0, c.stream>>>(h, c.d_cg_pending, c.d_graph_body, bodies, c.d_graph_launches);
+    const int per_body = (int)(c.launches - lb0) + 1;
+    c.launches = lb0;   // counted on the device as the bodies run
+    k_pcg_loop_cond<<<1, 1, 0, c.stream>>>(h, c.d_cg_pending, c.d_graph_body, bodies, c.d_graph_launches,
+                                           per_body);
     e = cudaStreamEndCapture(c.stream, &body);
     if (e != cudaSuccess) return fail(e, "capture end (PCG body)");
     // 3. beta schedule after the loop
@@ -2289,6 +3010,123 @@ int upload_list(Ctx& c, DevItemList& L) {
     return RECON_OK;
 }
 
+// Tile levels below the own grid of an nx x ny slice before its block level
+// (at most kMgBlockPx pixels); 0 when the slice takes the FFT preconditioner.
+// Each halving needs even sides, and the block level must halve on to at
+// most kMgCoarsePx pixels.
+int mg_tile_levels(int nx, int ny) {
+    int lb = 0;
+    while ((long long)nx * ny > kMgBlockPx) {
+        if (nx % 2 || ny % 2) return 0;
+        nx /= 2;
+        ny /= 2;
+        ++lb;
+    }
+    if (lb == 0) return 0;
+    int bx[kMgMaxBlockLevels], by[kMgMaxBlockLevels];
+    const int J = mg_block_levels(nx, ny, bx, by);
+    return bx[J - 1] * by[J - 1] <= kMgCoarsePx ? lb : 0;
+}
+
+// Levels, pools and item lists of the multigrid preconditioner, and the row
+// and column items of the slices that keep the FFT preconditioner.
+int mg_setup(Ctx& c) {
+    int rc;
+    c.mg_lb.assign(c.n, 0);
+    c.mg_max_lb = 0;
+    if (c.server_mode || c.prm[0].pcg_kernel == 2) return RECON_OK;
+    for (int s = 0; s < c.n; ++s) {
+        if (c.sg[s].cluster) continue;
+        c.mg_lb[s] = mg_tile_levels(c.sg[s].nx, c.sg[s].ny);
+        c.mg_max_lb = c.mg_lb[s] > c.mg_max_lb ? c.mg_lb[s] : c.mg_max_lb;
+    }
+    if (c.mg_max_lb == 0) return RECON_OK;
+    const int L = c.mg_max_lb;
+    // grids of levels 1 .. L (one pool per quantity, every level of every slice)
+    c.mg_sg.assign(L + 1, std::vector<SliceGeom>(c.n, SliceGeom{}));
+    long long off = 0;
+    for (int l = 1; l <= L; ++l)
+        for (int s = 0; s < c.n; ++s) {
+            if (c.mg_lb[s] < l) continue;
+            SliceGeom& g = c.mg_sg[l][s];
+            g.nx = c.sg[s].nx >> l;
+            g.ny = c.sg[s].ny >> l;
+            g.pitch = (g.nx + 31) / 32 * 32;
+            g.off = off;
+            g.lvl = l;
+            off += (long long)g.ny * g.pitch;
+        }
+    for (int k = 0; k < 3; ++k) {
+        if ((rc = alloc_dev(c, &c.mg_pool[k], c.elem * off))) return rc;
+        RECON_CUDA(cudaMemset(c.mg_pool[k], 0, c.elem * off));
+    }
+    c.d_mg_geom.assign(L + 1, nullptr);
+    c.d_mg_geom[0] = c.d_geom;
+    for (int l = 1; l <= L; ++l) {
+        if ((rc = alloc_dev(c, (void**)&c.d_mg_geom[l], sizeof(SliceGeom) * c.n))) return rc;
+        RECON_CUDA(cudaMemcpy(c.d_mg_geom[l], c.mg_sg[l].data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
+    }
+    std::vector<SliceGeom> blk(c.n, SliceGeom{});
+    int smem = 0;
+    for (int s = 0; s < c.n; ++s) {
+        if (!c.mg_lb[s]) continue;
+        blk[s] = c.mg_sg[c.mg_lb[s]][s];
+        int bx[kMgMaxBlockLevels], by[kMgMaxBlockLevels];
+        const int J = mg_block_levels(blk[s].nx, blk[s].ny, bx, by);
+        int tot = 0;
+        for (int j = 0; j < J; ++j) tot += bx[j] * by[j];
+        const int bytes = 3 * tot * (int)c.elem;
+        smem = bytes > smem ? bytes : smem;
+    }
+    if ((rc = alloc_dev(c, (void**)&c.d_mg_block, sizeof(SliceGeom) * c.n))) return rc;
+    RECON_CUDA(cudaMemcpy(c.d_mg_block, blk.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
+    c.mg_block_smem = smem;
+    // k_mg_coarse_inv: the dense operator and a^2 of every level (at most the f, a^2, x share of k_mg_block)
+    c.mg_inv_smem = kMgCoarseInvSmem + smem / 3 + (int)c.elem;
+    if (c.precision == 1) {
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_coarse_inv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        c.mg_inv_smem));
+    } else {
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_block<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_coarse_inv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        c.mg_inv_smem));
+    }
+    if ((rc = alloc_dev(c, &c.mg_qinv, c.elem * (size_t)kMgCoarsePx * kMgCoarsePx * c.n))) return rc;
+    // tiles of levels 0 .. L-1
+    const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
+    c.mg_tiles.assign(L, DevItemList{});
+    for (int l = 0; l < L; ++l) {
+        DevItemList& T = c.mg_tiles[l];
+        T.h_lo.assign(c.n, 0);
+        T.h_cnt.assign(c.n, 0);
+        for (int s = 0; s < c.n; ++s) {
+            T.h_lo[s] = (int)T.h_items.size();
+            if (c.mg_lb[s] <= l) continue;
+            const int nx = c.sg[s].nx >> l, ny = c.sg[s].ny >> l;
+            for (int ty = 0; ty < ny; ty += th)
+                for (int tx = 0; tx < nx; tx += kTileW) T.h_items.push_back(Item{s, tx, ty, 0});
+            T.h_cnt[s] = (int)T.h_items.size() - T.h_lo[s];
+        }
+        if ((rc = upload_list(c, T))) return rc;
+    }
+    // row and column items of the PCG on the slices that keep the FFT preconditioner
+    for (auto pr : {std::make_pair(&c.rows, &c.pcg_rows), std::make_pair(&c.cols, &c.pcg_cols)}) {
+        const DevItemList& A = *pr.first;
+        DevItemList& B = *pr.second;
+        B.h_lo.assign(c.n, 0);
+        B.h_cnt.assign(c.n, 0);
+        for (int s = 0; s < c.n; ++s) {
+            B.h_lo[s] = (int)B.h_items.size();
+            if (c.mg_lb[s]) continue;
+            for (int i = 0; i < A.h_cnt[s]; ++i) B.h_items.push_back(A.h_items[A.h_lo[s] + i]);
+            B.h_cnt[s] = A.h_cnt[s];
+        }
+        if ((rc = upload_list(c, B))) return rc;
+    }
+    return RECON_OK;
+}
+
 }  // namespace
 
 int solver_setup(Ctx& c) {
@@ -2454,6 +3292,7 @@ int solver_setup(Ctx& c) {
     RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, sizeof(int)));
     if (!c.server_mode && (rc = pcg_cluster_setup(c))) return rc;
     RECON_CUDA(cudaMemcpy(c.d_geom, c.sg.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
+    if ((rc = mg_setup(c))) return rc;
     if (c.precision == 1) return set_fft_smem<float>(c);
     return set_fft_smem<double>(c);
 }
@@ -2557,7 +3396,7 @@ void solver_free_graph(Ctx& c) {
 
 int solver_set_graph(Ctx& c, bool on) {
     if (on && (c.domain != 0 || c.use_cluster || c.server_mode)) {
-        set_error("graph capture needs domain 0, pcg_kernel 0 and a solve handle");
+        set_error("graph capture needs domain 0, pcg_kernel 0 or 2 and a solve handle");
         return RECON_EINVAL;
     }
     solver_free_graph(c);

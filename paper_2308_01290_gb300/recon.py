@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "librecon.so")
 
 RECON_MAX_FILTERS = 4
 FIELDS = dict(F1=0, F2=1, RHO=2, Z=3, MUL=4, MUH=5, RHS_F1=6, RHS_F2=7, DIV_RHO=8, DIV_Z=9, RHS_RHO=10, A2=11,
-              RHS_Z=12, CG_R=13, CG_P0=14, CG_P1=15, CG_Q=16, CG_Y=17)
+              RHS_Z=12, CG_R=13, CG_P0=14, CG_P1=15, CG_Q=16, CG_Y=17, CG_R2=18)
 OPS = dict(INIT=0, THRESH_RHS=1, SOLVE_F=2, SYNTH=3, SOLVE_RHO=4, SOLVE_Z=5, NEXT_BETA=6)
 
 
@@ -140,7 +140,7 @@ EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_
            "recon_set_autotune", "recon_tuning",
            "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name", "recon_server_create",
            "recon_submit", "recon_server_step", "recon_poll", "recon_server_stats", "recon_server_destroy")
-KF_COUNT = 13
+KF_COUNT = 17
 
 
 def _check(rc, what):

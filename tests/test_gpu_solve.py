@@ -249,6 +249,48 @@ def test_cluster_pcg_matches_batched_pcg(rc, shape):
     assert np.abs(out[0] - out[1]).max() <= 2e-3 * np.abs(out[1]).max()
 
 
+@pytest.mark.parametrize("shape,precision", [((128, 128), 1), ((256, 192), 1), ((320, 320), 1), ((128, 128), 0)])
+def test_multigrid_pcg_matches_fft_pcg(rc, shape, precision):
+    """The Z^m PCG with the multigrid V-cycle (pcg_kernel 0 on slices that
+    halve down to a small grid) and with the FFT preconditioner (pcg_kernel
+    2) on the same normal equations, built by the oracle from a noisy
+    phantom, with a step cap high enough for both: both reach the PCG
+    tolerance and the oracle's exact solution, and the multigrid cycle takes
+    fewer steps."""
+    nx, ny = shape
+    acq = ph.acquisition("small")
+    tab = model.Tables(acq.low, acq.high)
+    P = ph.small_phantom(31, n=max(nx, ny))
+    Z, rho = P["Z"][:ny, :nx], P["rhoe"][:ny, :nx]
+    L = (model.mu_mm(rho, Z, 60.0) + 4e-4 * ph.normal_field((ny, nx), 32)).astype(np.float32)
+    H = (model.mu_mm(rho, Z, 90.0) + 4e-4 * ph.normal_field((ny, nx), 33)).astype(np.float32)
+    st = alg1.init_state(L.astype(np.float64) / model.S_MM, H.astype(np.float64) / model.S_MM, tab)
+    bt = 0.3
+    hv = alg1.thresholds(st, 1e-2 / bt)
+    m1, m2 = alg1.synthesize(st["f1"], st["f2"], tab)
+    a2, rz = alg1.z_terms(m1, m2, hv["zt"], bt, tab)
+    a2, rz, z0 = [np.asarray(v, np.float32).astype(np.float64) for v in (a2, rz, st["zt"])]
+    zx = alg1.z_solve(a2, rz, bt)
+    steps = {}
+    for path in (2, 0):
+        p = rc.default_params(low=acq.low, high=acq.high, iters=50, pcg_kernel=path, beta0=bt, precision=precision,
+                              cg_max_iters=400)
+        s = rc.Solver(rc.geometry(nx, ny), p)
+        s.set_data(L, H)
+        s.write("A2", a2)
+        s.write("RHS_Z", rz)
+        s.write("Z", z0)
+        s.op("SOLVE_Z")
+        z = s.read("Z")
+        res = np.linalg.norm(a2 * z + bt * alg1.laplacian(z) - rz) / np.linalg.norm(rz)
+        steps[path] = s.scalars()["cg_iters"]
+        print(shape, precision, "pcg_kernel", path, "steps", steps[path], "relative residual", res)
+        assert res < (3e-5 if precision == 1 else 2e-6), (path, res)
+        assert np.abs(z - zx).max() <= 1e-3 * np.abs(zx).max(), path
+        s.close()
+    assert steps[0] < steps[2], steps
+
+
 def test_cluster_full_solve_matches_oracle(rc, small_case):
     """Whole 128^2 solve with the cluster-resident Z^m solve (the default run
     uses the batched kernels): within the final-map tolerance."""
