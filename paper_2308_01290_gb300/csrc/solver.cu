@@ -1461,6 +1461,16 @@ constexpr int kMgCoarsePx = 64;        // the coarsest grid has at most this man
 constexpr int kMgMaxBlockLevels = 8;
 constexpr int kMgBlockThreads = 256;
 
+// x / y for the Jacobi weights of the cycle: any fixed positive diagonal
+// keeps the cycle symmetric, so FP32 kernels use the fast reciprocal.
+__device__ __forceinline__ float mg_div(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double mg_div(double x, double y) { return x / y; }
+
+// i mod n for i in [-n, 2n)
+__device__ __forceinline__ int wrap_near(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// i mod n (non-negative) for any i: one compare and add in the common case
+__device__ __forceinline__ int wrap_any(int i, int n) { return (i >= -n && i < 2 * n) ? wrap_near(i, n) : wrap(i, n); }
+
 template <typename T>
 __device__ __forceinline__ T mg_omega() {
     return T(0.8);
@@ -1484,13 +1494,23 @@ __device__ __forceinline__ void for_halo_tile(F fn) {
     }
 }
 
+// Grid of one slice at one level, read once per item by every thread.
+struct TileGeo {
+    long long off;
+    int nx, ny, pitch, lvl;
+};
+__device__ __forceinline__ TileGeo tile_geo(const SliceGeom* G, int s) {
+    const SliceGeom* g = G + s;
+    return TileGeo{__ldg(&g->off), __ldg(&g->nx), __ldg(&g->ny), __ldg(&g->pitch), __ldg(&g->lvl)};
+}
+
 // Restricted residual of the tile at (tx0, ty0) of level g: out at level g1 =
 // mean over each 2x2 block of f - (a^2 x + bt L x), with f, a^2, x on the tile
 // and its halo in shared memory.
 template <typename T>
 __device__ __forceinline__ void mg_restrict_residual(const T (*sf)[TileDim<T>::SW], const T (*sa)[TileDim<T>::SW],
-                                                     const T (*sx)[TileDim<T>::SW], const SliceGeom& g,
-                                                     const SliceGeom& g1, int tx0, int ty0, T bt, T* out) {
+                                                     const T (*sx)[TileDim<T>::SW], const TileGeo& g,
+                                                     const TileGeo& g1, int tx0, int ty0, T bt, T* out) {
     constexpr int OFF = TileDim<T>::OFF, CW = kTileW / 2, CH = TileDim<T>::TH / 2;
     for (int q = threadIdx.x; q < CW * CH; q += blockDim.x) {
         const int cy = q / CW, cx = q - cy * CW;
@@ -1529,6 +1549,195 @@ __global__ void __launch_bounds__(kStencilThreads) k_mg_restrict(ItemList L, con
     }
 }
 
+// ---- asynchronous tile copies (cp.async: global -> shared, no registers) ----
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// 16 bytes; both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// one element of B = 4 or 8 bytes
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Start the copies of NM maps of the tile at (tx0, ty0) with its one-pixel
+// periodic halo into sm[m] (layout of load_tile).
+template <typename T, int NM>
+__device__ __forceinline__ void halo_async(T (*sm)[TileDim<T>::TH + 2][TileDim<T>::SW], const TileGeo& g, int tx0,
+                                           int ty0, const T* const (&src)[NM], int nm = NM) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
+    if (tx0 + kTileW <= g.nx) {
+        for (int q = threadIdx.x; q < (TH + 2) * VR; q += blockDim.x) {
+            const int ly = q / VR, lx = (q - ly * VR) * VN;
+            const long long d = g.off + (long long)wrap_any(ty0 - 1 + ly, g.ny) * g.pitch + tx0 + lx;
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                if (m < nm) cp_async16(&sm[m][ly][OFF + lx], src[m] + d);
+        }
+        for (int q = threadIdx.x; q < 2 * (TH + 2); q += blockDim.x) {
+            const int ly = q >> 1, side = q & 1;
+            const int gx = side ? wrap_any(tx0 + kTileW, g.nx) : wrap_any(tx0 - 1, g.nx);
+            const long long d = g.off + (long long)wrap_any(ty0 - 1 + ly, g.ny) * g.pitch + gx;
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                if (m < nm) cp_async_elem<sizeof(T)>(&sm[m][ly][side ? OFF + kTileW : OFF - 1], src[m] + d);
+        }
+    } else {
+        for (int q = threadIdx.x; q < (TH + 2) * (kTileW + 2); q += blockDim.x) {
+            const int ly = q / (kTileW + 2), lx = q - ly * (kTileW + 2);
+            const long long d =
+                g.off + (long long)wrap(ty0 - 1 + ly, g.ny) * g.pitch + wrap(tx0 - 1 + lx, g.nx);
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                if (m < nm) cp_async_elem<sizeof(T)>(&sm[m][ly][OFF - 1 + lx], src[m] + d);
+        }
+    }
+}
+
+// Start the copies of NM maps of the tile interior into si[m][ly][lx].
+template <typename T, int NM>
+__device__ __forceinline__ void inner_async(T (*si)[TileDim<T>::TH][kTileW], const TileGeo& g, int tx0, int ty0,
+                                            const T* const (&src)[NM]) {
+    constexpr int VN = TileDim<T>::VN, TH = TileDim<T>::TH, VR = kTileW / VN;
+    for (int q = threadIdx.x; q < TH * VR; q += blockDim.x) {
+        const int ly = q / VR, lx = (q - ly * VR) * VN;
+        const int y = ty0 + ly, x0 = tx0 + lx;
+        if (y >= g.ny || x0 >= g.nx) continue;
+        const long long d = g.off + (long long)y * g.pitch + x0;
+        if (x0 + VN <= g.nx) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) cp_async16(&si[m][ly][lx], src[m] + d);
+        } else {
+            for (int e = 0; e < g.nx - x0; ++e)
+#pragma unroll
+                for (int m = 0; m < NM; ++m) cp_async_elem<sizeof(T)>(&si[m][ly][lx + e], src[m] + d + e);
+        }
+    }
+}
+
+// Start the copies of the coarse cells under a tile of the finer level and
+// its halo (periodic on the coarse grid g1) into ec.
+template <typename T>
+__device__ __forceinline__ void coarse_async(T (*ec)[kTileW / 2 + 2], const TileGeo& g1, int tx0, int ty0,
+                                             const T* E1) {
+    constexpr int CH = TileDim<T>::TH / 2 + 2, CW = kTileW / 2 + 2;
+    const int X0 = tx0 / 2 - 1, Y0 = ty0 / 2 - 1;
+    for (int q = threadIdx.x; q < CH * CW; q += blockDim.x) {
+        const int cy = q / CW, cx = q - cy * CW;
+        cp_async_elem<sizeof(T)>(
+            &ec[cy][cx], E1 + g1.off + (long long)wrap_any(Y0 + cy, g1.ny) * g1.pitch + wrap_any(X0 + cx, g1.nx));
+    }
+}
+
+// An item of a pipelined stencil kernel: the tile, its slice's grid(s) and
+// whether it runs (slice active, PCG not converged).
+struct PipeItem {
+    Item it;
+    TileGeo g, g1;
+    int first;   // PCG step count is 0
+    bool ok;
+};
+
+// Persistent loop over the items of L in which the copies of the next item
+// run while the current one is computed (two buffers).  make(item) fills a
+// PipeItem, issue(p, buf) starts the copies of p, compute(p, buf, index)
+// runs with the copies of p complete.  Item descriptors are read two items
+// ahead.  Every thread of the block takes the same path.
+template <typename Buf, typename FM, typename FI, typename FC>
+__device__ __forceinline__ void pipeline_items(const ItemList& L, Buf* buf, FM make, FI issue, FC compute) {
+    const int step = gridDim.x, n = L.n_items;
+    int w = blockIdx.x;
+    if (w >= n) return;
+    PipeItem cur = make(L.items[w]);
+    Item i1 = w + step < n ? L.items[w + step] : Item{};
+    if (cur.ok) issue(cur, buf[0]);
+    cp_async_commit();
+    for (int k = 0; w < n; w += step, k ^= 1) {
+        PipeItem nxt;
+        nxt.ok = false;
+        if (w + step < n) {
+            nxt = make(i1);
+            if (w + 2 * step < n) i1 = L.items[w + 2 * step];
+            if (nxt.ok) issue(nxt, buf[k ^ 1]);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        if (cur.ok) compute(cur, buf[k], w);
+        __syncthreads();
+        cur = nxt;
+    }
+    cp_async_wait<0>();
+}
+
+// x on the tile and its halo (sx) = w f / (a^2 + 4 bt) + e1 (the coarse
+// correction of level g1, constant on 2x2 blocks, from ec); then for each
+// pixel of the tile x + w (f - (a^2 x + bt L x)) / (a^2 + 4 bt), passed to
+// out(d, cnt, ly, lx0, value pack).  sf, sa: f and a^2 on the tile and halo.
+template <typename T, typename FO>
+__device__ __forceinline__ void mg_correct_smooth(const T (*sf)[TileDim<T>::SW], const T (*sa)[TileDim<T>::SW],
+                                                  T (*sx)[TileDim<T>::SW], const T (*ec)[kTileW / 2 + 2],
+                                                  const TileGeo& g, const Item& it, T bt, FO out) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
+    const T b4 = T(4) * bt, om = mg_omega<T>();
+    for_halo_tile<T>([&](int ly, int col) {
+        // tile row ly is pixel row it.b - 1 + ly: coarse row (ly + 1) >> 1 of ec
+        sx[ly][col] = mg_div(om * sf[ly][col], sa[ly][col] + b4) + ec[(ly + 1) >> 1][(col - OFF + 2) >> 1];
+    });
+    __syncthreads();
+    for (int q = threadIdx.x; q < TH * VR; q += blockDim.x) {
+        const int ly = q / VR, lx0 = (q - ly * VR) * VN;
+        const int y = it.b + ly, x0 = it.a + lx0;
+        if (y >= g.ny || x0 >= g.nx) continue;
+        const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
+        Pack<T> o;
+#pragma unroll
+        for (int e = 0; e < VN; ++e) {
+            const int ry = ly + 1, col = OFF + lx0 + e;
+            const T x = sx[ry][col], a = sa[ry][col];
+            o.v[e] = x + mg_div(om * (sf[ry][col] - (a * x + bt * lap5<T>(sx, ry, col))), a + b4);
+        }
+        out(g.off + (long long)y * g.pitch + x0, cnt, ly, lx0, o);
+    }
+}
+
+template <typename T>
+struct MgBufFwd {   // r, a^2, q with halo
+    T h[3][TileDim<T>::TH + 2][TileDim<T>::SW];
+};
+template <typename T>
+struct MgBufHalo2 {   // f (or r), a^2 with halo; the coarse correction under the tile
+    T h[2][TileDim<T>::TH + 2][TileDim<T>::SW];
+    T ec[TileDim<T>::TH / 2 + 2][kTileW / 2 + 2];
+};
+template <typename T>
+struct MgBufPq {   // y, p_old with halo; a^2 interior
+    T h[2][TileDim<T>::TH + 2][TileDim<T>::SW];
+    T in[1][TileDim<T>::TH][kTileW];
+};
+
+// PipeItem of a multigrid kernel: slice active and its PCG not converged.
+__device__ __forceinline__ PipeItem mg_item(const Item& it, const SliceGeom* G, const SliceGeom* G1,
+                                            const SliceState* S) {
+    PipeItem p;
+    p.it = it;
+    const SliceState* sp = S + it.slice;
+    p.ok = __ldg(&sp->active) && !__ldg(&sp->cg_done);
+    p.first = __ldg(&sp->cg_it) == 0;
+    if (p.ok) {
+        p.g = tile_geo(G, it.slice);
+        if (G1) p.g1 = tile_geo(G1, it.slice);
+    }
+    return p;
+}
+
 // Fine level, start of a PCG step (UPD: after the update with alpha).  r is
 // read from rin and, updated, written to rout: other tiles read the old r on
 // their halo in the same launch.
@@ -1536,54 +1745,47 @@ template <typename T, bool UPD>
 __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                              const SliceConst* C, SliceState* S, Ptrs<T> P, int par,
                                                              const T* rin, T* rout, T* F1, int* pending) {
-    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW, TH = TileDim<T>::TH;
-    __shared__ __align__(16) T sm[3][TH + 2][SW];   // r, a^2, q (then x1)
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
+    extern __shared__ __align__(16) unsigned char mg_dsm[];
+    MgBufFwd<T>* buf = reinterpret_cast<MgBufFwd<T>*>(mg_dsm);
     __shared__ double red[32];
-    __shared__ SliceGeom s_g, s_g1;
     T* z = P.f[RECON_F_Z];
     const T* p = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
     const T* q = P.f[RECON_F_CG_Q];
     const T* a2 = P.f[RECON_F_A2];
+    auto make = [&](const Item& it) { return mg_item(it, G, G1, S); };
+    auto issue = [&](const PipeItem& c, MgBufFwd<T>& b) {
+        const T* hs[3] = {rin, a2, q};
+        halo_async<T, 3>(b.h, c.g, c.it.a, c.it.b, hs, UPD ? 3 : 2);
+    };
     struct In {
         Pack<T> z, p;
     };
     auto load = [&](long long d, int cnt) { return In{ldv_n(z, d, cnt), ldv_n(p, d, cnt)}; };
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
-        const SliceState* sp = S + it.slice;
-        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
-        stage_struct(&s_g, G + it.slice);
-        stage_struct(&s_g1, G1 + it.slice);
-        __syncthreads();
-        const SliceGeom& g = s_g;
-        // UPD: z, p, r, q, a^2 in, z, r out, level-1 residual out; else r, a^2 in
-        account(P.acct, KF_MG_FWD, tile_px<T>(g, it) * (UPD ? 29 : 9) * (long long)sizeof(T) / 4);
-        In v[TileVec<T>::R];
-        if (UPD) {
-            tile_vec_load<T>(g, it, load, v);
-            load_tile<T, 3>(
-                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 3>{{rin[d], a2[d], q[d]}}; },
-                [&](long long d) { return PVals<T, 3>{{ldv(rin, d), ldv(a2, d), ldv(q, d)}}; });
-        } else {
-            load_tile<T, 2>(
-                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{rin[d], a2[d]}}; },
-                [&](long long d) { return PVals<T, 2>{{ldv(rin, d), ldv(a2, d)}}; });
-        }
-        __syncthreads();
+    auto compute = [&](const PipeItem& c, MgBufFwd<T>& b, int w) {
+        const TileGeo& g = c.g;
+        const SliceState* sp = S + c.it.slice;
+        account(P.acct, KF_MG_FWD,
+                (long long)min(TH, g.ny - c.it.b) * min(kTileW, g.nx - c.it.a) * (UPD ? 29 : 9) * (long long)sizeof(T) /
+                    4);
         const T bt = Sc<T>::beta_t(*sp), b4 = Sc<T>::b4(*sp), om = mg_omega<T>();
         T acc = T(0);
         if (UPD) {
+            // z and p are pointwise: loaded into registers, in flight during the r update
+            const SliceGeom gs{g.nx, g.ny, g.pitch, 0, 0, g.off};
+            In v[TileVec<T>::R];
+            tile_vec_load<T>(gs, c.it, load, v);
             const T al = Sc<T>::alpha(*sp);
-            for_halo_tile<T>([&](int ly, int col) { sm[0][ly][col] = fma(-al, sm[2][ly][col], sm[0][ly][col]); });
+            for_halo_tile<T>([&](int ly, int col) { b.h[0][ly][col] = fma(-al, b.h[2][ly][col], b.h[0][ly][col]); });
             __syncthreads();
             tile_vec_use<T>(
-                g, it,
+                gs, c.it,
                 [&](long long d, int cnt, int ly, int lx0, const In& x) {
                     Pack<T> zn, rn;
 #pragma unroll
                     for (int e = 0; e < VN; ++e) {
                         zn.v[e] = fma(al, x.p.v[e], x.z.v[e]);
-                        rn.v[e] = sm[0][ly + 1][OFF + lx0 + e];
+                        rn.v[e] = b.h[0][ly + 1][OFF + lx0 + e];
                         if (e < cnt) acc = fma(rn.v[e], rn.v[e], acc);
                     }
                     stv_n(z, d, zn, cnt);
@@ -1592,28 +1794,28 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const
                 v);
         }
         // pre-smoothing from zero, on the tile and its halo (in place of q)
-        for_halo_tile<T>([&](int ly, int col) { sm[2][ly][col] = om * sm[0][ly][col] / (sm[1][ly][col] + b4); });
+        for_halo_tile<T>([&](int ly, int col) { b.h[2][ly][col] = mg_div(om * b.h[0][ly][col], b.h[1][ly][col] + b4); });
         __syncthreads();
-        mg_restrict_residual<T>(sm[0], sm[1], sm[2], g, s_g1, it.a, it.b, bt, F1);
+        mg_restrict_residual<T>(b.h[0], b.h[1], b.h[2], g, c.g1, c.it.a, c.it.b, bt, F1);
         if (UPD) {
             const T part[1] = {acc};
             double a[1];
             block_sum_t<T, 1>(part, a, red);
             double tot[1];
-            if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
-                SliceState& so = S[it.slice];
-                const SliceConst& c = C[it.slice];
+            if (item_reduce<1>(L, w, c.it.slice, a, tot, red)) {
+                SliceState& so = S[c.it.slice];
+                const SliceConst& cs = C[c.it.slice];
                 so.rr = tot[0];
                 so.cg_it += 1;
-                const bool conv = !(tot[0] > c.cg_tol * c.cg_tol * so.bb);
-                if (conv || so.cg_it >= c.cg_max) {
+                const bool conv = !(tot[0] > cs.cg_tol * cs.cg_tol * so.bb);
+                if (conv || so.cg_it >= cs.cg_max) {
                     so.cg_done = 1;
                     atomicSub(pending, 1);
                 }
             }
         }
-        __syncthreads();
-    }
+    };
+    pipeline_items(L, buf, make, issue, compute);
 }
 
 // Tile level g (level >= 1): pre-smoothing from zero and the restricted
@@ -1622,63 +1824,25 @@ template <typename T>
 __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_down(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                               const SliceState* S, const T* F, const T* A, T* F1,
                                                               unsigned long long* acct) {
-    constexpr int SW = TileDim<T>::SW, TH = TileDim<T>::TH;
-    __shared__ __align__(16) T sm[3][TH + 2][SW];   // f, a^2, x1
-    __shared__ SliceGeom s_g, s_g1;
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
-        const SliceState* sp = S + it.slice;
-        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
-        stage_struct(&s_g, G + it.slice);
-        stage_struct(&s_g1, G1 + it.slice);
+    constexpr int TH = TileDim<T>::TH;
+    extern __shared__ __align__(16) unsigned char mg_dsm[];
+    MgBufHalo2<T>* buf = reinterpret_cast<MgBufHalo2<T>*>(mg_dsm);
+    __shared__ __align__(16) T sx[TH + 2][TileDim<T>::SW];
+    auto make = [&](const Item& it) { return mg_item(it, G, G1, S); };
+    auto issue = [&](const PipeItem& c, MgBufHalo2<T>& b) {
+        const T* hs[2] = {F, A};
+        halo_async<T, 2>(b.h, c.g, c.it.a, c.it.b, hs);
+    };
+    auto compute = [&](const PipeItem& c, MgBufHalo2<T>& b, int) {
+        const TileGeo& g = c.g;
+        account(acct, KF_MG_LEVELS,
+                (long long)min(TH, g.ny - c.it.b) * min(kTileW, g.nx - c.it.a) * 9 * (long long)sizeof(T) / 4);
+        const T bt = mg_bt<T>(S[c.it.slice], g.lvl), b4 = T(4) * bt, om = mg_omega<T>();
+        for_halo_tile<T>([&](int ly, int col) { sx[ly][col] = mg_div(om * b.h[0][ly][col], b.h[1][ly][col] + b4); });
         __syncthreads();
-        const SliceGeom& g = s_g;
-        account(acct, KF_MG_LEVELS, tile_px<T>(g, it) * 9 * (long long)sizeof(T) / 4);
-        load_tile<T, 2>(
-            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{F[d], A[d]}}; },
-            [&](long long d) { return PVals<T, 2>{{ldv(F, d), ldv(A, d)}}; });
-        __syncthreads();
-        const T bt = mg_bt<T>(*sp, g.lvl), b4 = T(4) * bt, om = mg_omega<T>();
-        for_halo_tile<T>([&](int ly, int col) { sm[2][ly][col] = om * sm[0][ly][col] / (sm[1][ly][col] + b4); });
-        __syncthreads();
-        mg_restrict_residual<T>(sm[0], sm[1], sm[2], g, s_g1, it.a, it.b, bt, F1);
-        __syncthreads();
-    }
-}
-
-// Coarse correction and post-smoothing on the tile at (tx0, ty0) of level g:
-// x = w f / (a^2 + 4 bt) + e1 (the coarse correction of level g1, constant on
-// 2x2 blocks), then x + w (f - (a^2 x + bt L x)) / (a^2 + 4 bt) for each
-// pixel of the tile, passed to out(d, cnt, ly, lx0, value pack).  sm[0], sm[1]
-// hold f and a^2 on the tile and its halo; sm[2] receives x.
-template <typename T, typename FO>
-__device__ __forceinline__ void mg_correct_smooth(T (*sm)[TileDim<T>::TH + 2][TileDim<T>::SW],
-                                                  T (*ec)[kTileW / 2 + 2], const SliceGeom& g, const SliceGeom& g1,
-                                                  const Item& it, const T* E1, T bt, FO out) {
-    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, CH = TileDim<T>::TH / 2 + 2, CW = kTileW / 2 + 2;
-    // coarse cells under the tile and its halo (periodic)
-    const int X0 = it.a / 2 - 1, Y0 = it.b / 2 - 1;
-    for (int q = threadIdx.x; q < CH * CW; q += blockDim.x) {
-        const int cy = q / CW, cx = q - cy * CW;
-        ec[cy][cx] = E1[g1.off + (long long)wrap(Y0 + cy, g1.ny) * g1.pitch + wrap(X0 + cx, g1.nx)];
-    }
-    __syncthreads();
-    const T b4 = T(4) * bt, om = mg_omega<T>();
-    for_halo_tile<T>([&](int ly, int col) {
-        // row ly of the tile is pixel row it.b - 1 + ly: coarse row (ly + 1) >> 1 of ec
-        sm[2][ly][col] = om * sm[0][ly][col] / (sm[1][ly][col] + b4) + ec[(ly + 1) >> 1][(col - OFF + 2) >> 1];
-    });
-    __syncthreads();
-    for_tile_vectors<T>(g, it, [&](long long d, int cnt, int ly, int lx0) {
-        Pack<T> o;
-#pragma unroll
-        for (int e = 0; e < VN; ++e) {
-            const int ry = ly + 1, col = OFF + lx0 + e;
-            const T x = sm[2][ry][col], a = sm[1][ry][col];
-            o.v[e] = x + om * (sm[0][ry][col] - (a * x + bt * lap5<T>(sm[2], ry, col))) / (a + b4);
-        }
-        out(d, cnt, ly, lx0, o);
-    });
+        mg_restrict_residual<T>(b.h[0], b.h[1], sx, g, c.g1, c.it.a, c.it.b, bt, F1);
+    };
+    pipeline_items(L, buf, make, issue, compute);
 }
 
 // Tile level g (level >= 1): e = coarse correction and post-smoothing.
@@ -1686,26 +1850,24 @@ template <typename T>
 __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                             const SliceState* S, const T* F, const T* A,
                                                             const T* E1, T* E, unsigned long long* acct) {
-    constexpr int SW = TileDim<T>::SW, TH = TileDim<T>::TH;
-    __shared__ __align__(16) T sm[3][TH + 2][SW];   // f, a^2, x
-    __shared__ T ec[TH / 2 + 2][kTileW / 2 + 2];
-    __shared__ SliceGeom s_g, s_g1;
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
-        const SliceState* sp = S + it.slice;
-        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
-        stage_struct(&s_g, G + it.slice);
-        stage_struct(&s_g1, G1 + it.slice);
-        __syncthreads();
-        const SliceGeom& g = s_g;
-        account(acct, KF_MG_LEVELS, tile_px<T>(g, it) * 13 * (long long)sizeof(T) / 4);
-        load_tile<T, 2>(
-            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{F[d], A[d]}}; },
-            [&](long long d) { return PVals<T, 2>{{ldv(F, d), ldv(A, d)}}; });
-        mg_correct_smooth<T>(sm, ec, g, s_g1, it, E1, mg_bt<T>(*sp, g.lvl),
+    constexpr int TH = TileDim<T>::TH;
+    extern __shared__ __align__(16) unsigned char mg_dsm[];
+    MgBufHalo2<T>* buf = reinterpret_cast<MgBufHalo2<T>*>(mg_dsm);
+    __shared__ __align__(16) T sx[TH + 2][TileDim<T>::SW];
+    auto make = [&](const Item& it) { return mg_item(it, G, G1, S); };
+    auto issue = [&](const PipeItem& c, MgBufHalo2<T>& b) {
+        const T* hs[2] = {F, A};
+        halo_async<T, 2>(b.h, c.g, c.it.a, c.it.b, hs);
+        coarse_async<T>(b.ec, c.g1, c.it.a, c.it.b, E1);
+    };
+    auto compute = [&](const PipeItem& c, MgBufHalo2<T>& b, int) {
+        const TileGeo& g = c.g;
+        account(acct, KF_MG_LEVELS,
+                (long long)min(TH, g.ny - c.it.b) * min(kTileW, g.nx - c.it.a) * 13 * (long long)sizeof(T) / 4);
+        mg_correct_smooth<T>(b.h[0], b.h[1], sx, b.ec, g, c.it, mg_bt<T>(S[c.it.slice], g.lvl),
                              [&](long long d, int cnt, int, int, const Pack<T>& o) { stv_n(E, d, o, cnt); });
-        __syncthreads();
-    }
+    };
+    pipeline_items(L, buf, make, issue, compute);
 }
 
 // Fine level: y = B r (correction from level 1 and post-smoothing), r.y ->
@@ -1713,44 +1875,42 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_up(ItemList L, const 
 template <typename T>
 __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_y(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                            SliceState* S, Ptrs<T> P, const T* r, const T* E1) {
-    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW, TH = TileDim<T>::TH;
-    __shared__ __align__(16) T sm[3][TH + 2][SW];   // r, a^2, x
-    __shared__ T ec[TH / 2 + 2][kTileW / 2 + 2];
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH;
+    extern __shared__ __align__(16) unsigned char mg_dsm[];
+    MgBufHalo2<T>* buf = reinterpret_cast<MgBufHalo2<T>*>(mg_dsm);
+    __shared__ __align__(16) T sx[TH + 2][TileDim<T>::SW];
     __shared__ double red[32];
-    __shared__ SliceGeom s_g, s_g1;
     const T* a2 = P.f[RECON_F_A2];
     T* y = P.f[RECON_F_CG_Y];
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
-        const SliceState* sp = S + it.slice;
-        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
-        stage_struct(&s_g, G + it.slice);
-        stage_struct(&s_g1, G1 + it.slice);
-        __syncthreads();
-        const SliceGeom& g = s_g;
-        account(P.acct, KF_MG_Y, tile_px<T>(g, it) * 13 * (long long)sizeof(T) / 4);
-        load_tile<T, 2>(
-            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{r[d], a2[d]}}; },
-            [&](long long d) { return PVals<T, 2>{{ldv(r, d), ldv(a2, d)}}; });
+    auto make = [&](const Item& it) { return mg_item(it, G, G1, S); };
+    auto issue = [&](const PipeItem& c, MgBufHalo2<T>& b) {
+        const T* hs[2] = {r, a2};
+        halo_async<T, 2>(b.h, c.g, c.it.a, c.it.b, hs);
+        coarse_async<T>(b.ec, c.g1, c.it.a, c.it.b, E1);
+    };
+    auto compute = [&](const PipeItem& c, MgBufHalo2<T>& b, int w) {
+        const TileGeo& g = c.g;
+        account(P.acct, KF_MG_Y,
+                (long long)min(TH, g.ny - c.it.b) * min(kTileW, g.nx - c.it.a) * 13 * (long long)sizeof(T) / 4);
         T acc = T(0);
-        mg_correct_smooth<T>(sm, ec, g, s_g1, it, E1, Sc<T>::beta_t(*sp),
+        mg_correct_smooth<T>(b.h[0], b.h[1], sx, b.ec, g, c.it, Sc<T>::beta_t(S[c.it.slice]),
                              [&](long long d, int cnt, int ly, int lx0, const Pack<T>& o) {
 #pragma unroll
                                  for (int e = 0; e < VN; ++e)
-                                     if (e < cnt) acc = fma(sm[0][ly + 1][OFF + lx0 + e], o.v[e], acc);
+                                     if (e < cnt) acc = fma(b.h[0][ly + 1][OFF + lx0 + e], o.v[e], acc);
                                  stv_n(y, d, o, cnt);
                              });
         const T part[1] = {acc};
         double a[1];
         block_sum_t<T, 1>(part, a, red);
         double tot[1];
-        if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
-            SliceState& so = S[it.slice];
+        if (item_reduce<1>(L, w, c.it.slice, a, tot, red)) {
+            SliceState& so = S[c.it.slice];
             set_betacg(so, (so.cg_it == 0) ? 0.0 : tot[0] / so.ry);
             so.ry = tot[0];
         }
-        __syncthreads();
-    }
+    };
+    pipeline_items(L, buf, make, issue, compute);
 }
 
 // Fine level: p = y + beta_cg p_old (p = y on the first step), q = M p, p.q
@@ -1758,73 +1918,63 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_y(ItemList L, const S
 template <typename T>
 __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_pq(ItemList L, const SliceGeom* G, SliceState* S,
                                                             Ptrs<T> P, int par) {
-    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW, TH = TileDim<T>::TH;
-    __shared__ __align__(16) T sm[2][TH + 2][SW];   // y (then p), p_old
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
+    extern __shared__ __align__(16) unsigned char mg_dsm[];
+    MgBufPq<T>* buf = reinterpret_cast<MgBufPq<T>*>(mg_dsm);
     __shared__ double red[32];
-    __shared__ SliceGeom s_g;
     const T* y = P.f[RECON_F_CG_Y];
     const T* pold = P.f[par ? RECON_F_CG_P1 : RECON_F_CG_P0];
     T* pnew = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
     const T* a2 = P.f[RECON_F_A2];
     T* qo = P.f[RECON_F_CG_Q];
-    struct In {
-        Pack<T> a;
+    auto make = [&](const Item& it) { return mg_item(it, G, nullptr, S); };
+    auto issue = [&](const PipeItem& c, MgBufPq<T>& b) {
+        const T* hs[2] = {y, pold};
+        halo_async<T, 2>(b.h, c.g, c.it.a, c.it.b, hs, c.first ? 1 : 2);   // no p_old on the first step
+        const T* is[1] = {a2};
+        inner_async<T, 1>(b.in, c.g, c.it.a, c.it.b, is);
     };
-    auto load = [&](long long d, int cnt) { return In{ldv_n(a2, d, cnt)}; };
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = L.items[w];
-        const SliceState* sp = S + it.slice;
-        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
-        stage_struct(&s_g, G + it.slice);
-        __syncthreads();
-        const SliceGeom& g = s_g;
-        const bool first = __ldg(&sp->cg_it) == 0;
-        account(P.acct, KF_MG_PQ, tile_px<T>(g, it) * (first ? 4 : 5) * (long long)sizeof(T));
-        In v[TileVec<T>::R];
-        tile_vec_load<T>(g, it, load, v);
-        if (first) {
-            load_tile<T, 1>(
-                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{y[d]}}; },
-                [&](long long d) { return PVals<T, 1>{{ldv(y, d)}}; });
-        } else {
-            load_tile<T, 2>(
-                sm, g, it.a, it.b, [&](long long d) { return Vals<T, 2>{{y[d], pold[d]}}; },
-                [&](long long d) { return PVals<T, 2>{{ldv(y, d), ldv(pold, d)}}; });
-        }
-        __syncthreads();
-        if (!first) {
+    auto compute = [&](const PipeItem& c, MgBufPq<T>& b, int w) {
+        const TileGeo& g = c.g;
+        const SliceState* sp = S + c.it.slice;
+        account(P.acct, KF_MG_PQ,
+                (long long)min(TH, g.ny - c.it.b) * min(kTileW, g.nx - c.it.a) * (c.first ? 4 : 5) *
+                    (long long)sizeof(T));
+        if (!c.first) {
             const T bc = Sc<T>::betacg(*sp);
-            for_halo_tile<T>([&](int ly, int col) { sm[0][ly][col] = fma(bc, sm[1][ly][col], sm[0][ly][col]); });
+            for_halo_tile<T>([&](int ly, int col) { b.h[0][ly][col] = fma(bc, b.h[1][ly][col], b.h[0][ly][col]); });
             __syncthreads();
         }
         const T bt = Sc<T>::beta_t(*sp);
         T acc = T(0);
-        tile_vec_use<T>(
-            g, it,
-            [&](long long d, int cnt, int ly, int lx0, const In& x) {
-                Pack<T> pv, qv;
+        for (int qq = threadIdx.x; qq < TH * VR; qq += blockDim.x) {
+            const int ly = qq / VR, lx0 = (qq - ly * VR) * VN;
+            const int yy = c.it.b + ly, x0 = c.it.a + lx0;
+            if (yy >= g.ny || x0 >= g.nx) continue;
+            const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
+            Pack<T> pv, qv;
 #pragma unroll
-                for (int e = 0; e < VN; ++e) {
-                    const int ry = ly + 1, col = OFF + lx0 + e;
-                    pv.v[e] = sm[0][ry][col];
-                    qv.v[e] = x.a.v[e] * pv.v[e] + bt * lap5<T>(sm[0], ry, col);
-                    if (e < cnt) acc = fma(pv.v[e], qv.v[e], acc);
-                }
-                stv_n(pnew, d, pv, cnt);
-                stv_n(qo, d, qv, cnt);
-            },
-            v);
+            for (int e = 0; e < VN; ++e) {
+                const int ry = ly + 1, col = OFF + lx0 + e;
+                pv.v[e] = b.h[0][ry][col];
+                qv.v[e] = b.in[0][ly][lx0 + e] * pv.v[e] + bt * lap5<T>(b.h[0], ry, col);
+                if (e < cnt) acc = fma(pv.v[e], qv.v[e], acc);
+            }
+            const long long d = g.off + (long long)yy * g.pitch + x0;
+            stv_n(pnew, d, pv, cnt);
+            stv_n(qo, d, qv, cnt);
+        }
         const T part[1] = {acc};
         double a[1];
         block_sum_t<T, 1>(part, a, red);
         double tot[1];
-        if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
-            SliceState& so = S[it.slice];
+        if (item_reduce<1>(L, w, c.it.slice, a, tot, red)) {
+            SliceState& so = S[c.it.slice];
             so.pq = tot[0];
             set_alpha(so, tot[0] > 0.0 ? so.ry / tot[0] : 0.0);
         }
-        __syncthreads();
-    }
+    };
+    pipeline_items(L, buf, make, issue, compute);
 }
 
 // Sides of the in-block levels of a block level of bx x by pixels: halve while
@@ -1951,7 +2101,7 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* G
     }
     __syncthreads();
     auto at = [&](const T* v, int j, int yy, int xx) -> T {
-        return v[base[j] + wrap(yy, ny[j]) * nx[j] + wrap(xx, nx[j])];
+        return v[base[j] + wrap_near(yy, ny[j]) * nx[j] + wrap_near(xx, nx[j])];
     };
     auto mv = [&](const T* v, int j, int yy, int xx) -> T {   // (a^2 + bt L) v at a pixel of level j
         const T c = at(v, j, yy, xx);
@@ -1971,7 +2121,7 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* G
     for (int j = 0; j + 1 < J; ++j) {
         const T b4 = T(4) * bt[j];
         for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x)
-            x[base[j] + i] = om * f[base[j] + i] / (a[base[j] + i] + b4);
+            x[base[j] + i] = mg_div(om * f[base[j] + i], a[base[j] + i] + b4);
         __syncthreads();
         for (int i = threadIdx.x; i < nx[j + 1] * ny[j + 1]; i += blockDim.x) {
             const int yy = i / nx[j + 1], xx = i - yy * nx[j + 1];
@@ -2009,7 +2159,7 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* G
         }
         __syncthreads();
         for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x)
-            x[base[j] + i] += om * f[base[j] + i] / (a[base[j] + i] + b4);
+            x[base[j] + i] += mg_div(om * f[base[j] + i], a[base[j] + i] + b4);
         __syncthreads();
     }
     for (int i = threadIdx.x; i < g.nx * g.ny; i += blockDim.x) {
@@ -2473,7 +2623,7 @@ template <typename T, bool UPD>
 void mg_fwd(Ctx& c, int par, int rk, bool timed) {
     MaybeTimer t(c, KF_MG_FWD, timed);
     const DevItemList& L = c.mg_tiles[0];
-    k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(
+    k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufFwd<T>), c.stream>>>(
         L.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
         mg_r<T>(c, rk ^ 1), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending);
     c.launches += 1;
@@ -2490,7 +2640,8 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
         MaybeTimer t(c, KF_MG_LEVELS, timed);
         for (int l = 1; l < c.mg_max_lb; ++l) {
             const DevItemList& L = c.mg_tiles[l];
-            k_mg_down<T><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(L.view(), c.d_mg_geom[l],
+            k_mg_down<T><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
+                L.view(), c.d_mg_geom[l],
                                                                              c.d_mg_geom[l + 1], c.d_state, pf, pa,
                                                                              pf, c.d_acct);
             c.launches += 1;
@@ -2500,7 +2651,8 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
         c.launches += 1;
         for (int l = c.mg_max_lb - 1; l >= 1; --l) {
             const DevItemList& L = c.mg_tiles[l];
-            k_mg_up<T><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(L.view(), c.d_mg_geom[l],
+            k_mg_up<T><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
+                L.view(), c.d_mg_geom[l],
                                                                            c.d_mg_geom[l + 1], c.d_state, pf, pa, pe,
                                                                            pe, c.d_acct);
             c.launches += 1;
@@ -2509,13 +2661,13 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
     const DevItemList& L0 = c.mg_tiles[0];
     {
         MaybeTimer t(c, KF_MG_Y, timed);
-        k_mg_y<T><<<grid_for(c, L0.n), kStencilThreads, 0, c.stream>>>(L0.view(), c.d_geom, c.d_mg_geom[1], c.d_state,
-                                                                       ptrs<T>(c), mg_r<T>(c, rk), pe);
+        k_mg_y<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
+            L0.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk), pe);
     }
     {
         MaybeTimer t(c, KF_MG_PQ, timed);
-        k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 0, c.stream>>>(L0.view(), c.d_geom, c.d_state, ptrs<T>(c),
-                                                                        par);
+        k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(
+            L0.view(), c.d_geom, c.d_state, ptrs<T>(c), par);
     }
     c.launches += 2;
 }
@@ -3028,6 +3180,19 @@ int mg_tile_levels(int nx, int ny) {
     return bx[J - 1] * by[J - 1] <= kMgCoarsePx ? lb : 0;
 }
 
+// Shared-memory limits of the pipelined multigrid kernels (two buffers each).
+template <typename T>
+int mg_set_smem() {
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    RECON_CUDA(cudaFuncSetAttribute(k_mg_fwd<T, false>, A, (int)(2 * sizeof(MgBufFwd<T>))));
+    RECON_CUDA(cudaFuncSetAttribute(k_mg_fwd<T, true>, A, (int)(2 * sizeof(MgBufFwd<T>))));
+    RECON_CUDA(cudaFuncSetAttribute(k_mg_down<T>, A, (int)(2 * sizeof(MgBufHalo2<T>))));
+    RECON_CUDA(cudaFuncSetAttribute(k_mg_up<T>, A, (int)(2 * sizeof(MgBufHalo2<T>))));
+    RECON_CUDA(cudaFuncSetAttribute(k_mg_y<T>, A, (int)(2 * sizeof(MgBufHalo2<T>))));
+    RECON_CUDA(cudaFuncSetAttribute(k_mg_pq<T>, A, (int)(2 * sizeof(MgBufPq<T>))));
+    return RECON_OK;
+}
+
 // Levels, pools and item lists of the multigrid preconditioner, and the row
 // and column items of the slices that keep the FFT preconditioner.
 int mg_setup(Ctx& c) {
@@ -3093,6 +3258,7 @@ int mg_setup(Ctx& c) {
                                         c.mg_inv_smem));
     }
     if ((rc = alloc_dev(c, &c.mg_qinv, c.elem * (size_t)kMgCoarsePx * kMgCoarsePx * c.n))) return rc;
+    if ((rc = c.precision == 1 ? mg_set_smem<float>() : mg_set_smem<double>())) return rc;
     // tiles of levels 0 .. L-1
     const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
     c.mg_tiles.assign(L, DevItemList{});
