@@ -465,9 +465,9 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     l0 = solver.launches()
-    # device working set: 18 maps and 3 half spectra per slice, plus the sinograms
+    # device working set: 19 maps and 3 half spectra per slice, plus the sinograms
     elem = 4 if args.precision == 1 else 8
-    work_bytes = sum(elem * g.ny * (-(-g.nx // 32) * 32) * 18 + 2 * elem * g.ny * (-(-(g.nx // 2 + 1) // 16) * 16) * 3
+    work_bytes = sum(elem * g.ny * (-(-g.nx // 32) * 32) * 19 + 2 * elem * g.ny * (-(-(g.nx // 2 + 1) // 16) * 16) * 3
                      for g in geoms) + 4 * (sino_lo.numel() + sino_hi.numel())
     flush = work_bytes < 2 * L2_BYTES
     flush_buf = torch.empty(4 * L2_BYTES // 4, dtype=torch.float32, device="cuda") if flush else None

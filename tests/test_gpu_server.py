@@ -71,7 +71,7 @@ def test_mixed_arrivals_equal_alone(rc):
 
 def test_budget_serialises_admission(rc):
     reqs = [request(rc, 10 + k, 64, 6, 1e-2) for k in range(3)]
-    one = 18 * 64 * 64 * 4 + 6 * 64 * 48 * 4   # one 64^2 solve (fields + spectra)
+    one = 19 * 64 * 64 * 4 + 6 * 64 * 48 * 4   # one 64^2 solve (fields + spectra)
     srv = rc.Server(max_slots=3, max_nx=64, max_ny=64, hbm_budget_bytes=1.5 * one)
     ts = [srv.submit(*r) for r in reqs]
     srv.step(0)
