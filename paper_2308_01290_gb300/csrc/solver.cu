@@ -3162,6 +3162,24 @@ int upload_list(Ctx& c, DevItemList& L) {
     return RECON_OK;
 }
 
+// Row and column items of the FFT-preconditioned PCG: those of c.rows and
+// c.cols on the slices without multigrid levels (host vectors).
+void pcg_split_host(Ctx& c) {
+    for (auto pr : {std::make_pair(&c.rows, &c.pcg_rows), std::make_pair(&c.cols, &c.pcg_cols)}) {
+        const DevItemList& A = *pr.first;
+        DevItemList& B = *pr.second;
+        B.h_items.clear();
+        B.h_lo.assign(c.n, 0);
+        B.h_cnt.assign(c.n, 0);
+        for (int s = 0; s < c.n; ++s) {
+            B.h_lo[s] = (int)B.h_items.size();
+            if (c.mg_lb[s]) continue;
+            for (int i = 0; i < A.h_cnt[s]; ++i) B.h_items.push_back(A.h_items[A.h_lo[s] + i]);
+            B.h_cnt[s] = A.h_cnt[s];
+        }
+    }
+}
+
 // Tile levels below the own grid of an nx x ny slice before its block level
 // (at most kMgBlockPx pixels); 0 when the slice takes the FFT preconditioner.
 // Each halving needs even sides, and the block level must halve on to at
@@ -3277,19 +3295,8 @@ int mg_setup(Ctx& c) {
         if ((rc = upload_list(c, T))) return rc;
     }
     // row and column items of the PCG on the slices that keep the FFT preconditioner
-    for (auto pr : {std::make_pair(&c.rows, &c.pcg_rows), std::make_pair(&c.cols, &c.pcg_cols)}) {
-        const DevItemList& A = *pr.first;
-        DevItemList& B = *pr.second;
-        B.h_lo.assign(c.n, 0);
-        B.h_cnt.assign(c.n, 0);
-        for (int s = 0; s < c.n; ++s) {
-            B.h_lo[s] = (int)B.h_items.size();
-            if (c.mg_lb[s]) continue;
-            for (int i = 0; i < A.h_cnt[s]; ++i) B.h_items.push_back(A.h_items[A.h_lo[s] + i]);
-            B.h_cnt[s] = A.h_cnt[s];
-        }
-        if ((rc = upload_list(c, B))) return rc;
-    }
+    pcg_split_host(c);
+    if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols))) return rc;
     return RECON_OK;
 }
 
@@ -3607,6 +3614,17 @@ int fill_list(Ctx& c, DevItemList& L) {
     return RECON_OK;
 }
 
+// The FFT-preconditioned PCG's row and column lists after c.rows and c.cols
+// were rebuilt (no-op without multigrid slices: the PCG then uses c.rows and
+// c.cols themselves).
+int pcg_split_lists(Ctx& c) {
+    if (c.mg_max_lb == 0) return RECON_OK;
+    pcg_split_host(c);
+    int rc;
+    if ((rc = fill_list(c, c.pcg_rows)) || (rc = fill_list(c, c.pcg_cols))) return rc;
+    return RECON_OK;
+}
+
 void lists_for(Ctx& c, const std::vector<int>& slots, DevItemList* tiles, DevItemList* rows, DevItemList* cols) {
     std::vector<Item> dr, dc;
     for (DevItemList* L : {tiles, rows, cols}) {
@@ -3651,6 +3669,7 @@ int solver_autotune(Ctx& c) {
         c.row_budget = b;
         lists_for(c, all, &c.tiles, &c.rows, &c.cols);
         if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+        if ((rc = pcg_split_lists(c))) return rc;
         if ((rc = c.precision == 1 ? set_fft_smem<float>(c) : set_fft_smem<double>(c))) return rc;
         for (int m : {4, 8, 16}) {
             c.grid_mult = m;
@@ -3667,6 +3686,7 @@ int solver_autotune(Ctx& c) {
     c.row_budget = best_b;
     lists_for(c, all, &c.tiles, &c.rows, &c.cols);
     if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+    if ((rc = pcg_split_lists(c))) return rc;
     if ((rc = c.precision == 1 ? set_fft_smem<float>(c) : set_fft_smem<double>(c))) return rc;
     c.tuned = true;
     solver_free_graph(c);   // a captured graph holds the old launch shapes

@@ -330,6 +330,32 @@ def test_graph_iterations_equal_separate_launches(rc, small_case):
         assert np.array_equal(a, b)
 
 
+def test_autotune_mixed_preconditioners(rc, small_case):
+    """A batch with a multigrid slice (128^2) and an FFT-preconditioned one
+    (100 x 70, whose sides do not halve down): autotune mode 2 regroups the
+    row items of both the f solves and the FFT-preconditioned PCG, and both
+    slices stay within the final-map tolerance of the untuned solve."""
+    c = small_case
+    acq = c["acq"]
+    g0, g1 = rc.geometry(acq.nx, acq.ny), rc.geometry(100, 70)
+    p = rc.default_params(low=acq.low, high=acq.high, iters=8)
+    lo = np.concatenate([c["muL"].ravel(), c["muL"][:70, :100].ravel()]).astype(np.float32)
+    hi = np.concatenate([c["muH"].ravel(), c["muH"][:70, :100].ravel()]).astype(np.float32)
+    out = []
+    for mode in (0, 2):
+        s = rc.Solver([g0, g1], [p, p])
+        s.set_autotune(mode)
+        s.set_data(lo, hi)
+        s.step(8)
+        out.append(s.get_host())
+        s.close()
+    body = c["P"]["rhoe"] >= 0.1
+    for k, b in enumerate((body, body[:70, :100])):
+        assert np.isfinite(out[1][0][k]).all()
+        assert np.abs(out[1][0][k] - out[0][0][k])[b].mean() <= 0.01, k
+        assert np.abs(out[1][1][k] - out[0][1][k])[b].mean() <= 1e-3, k
+
+
 def test_autotune_keeps_results(rc, small_case):
     """Autotune mode 1 picks a grid of {4, 8, 16} x SMs and leaves every
     result bitwise as it was; mode 2 also picks a row-item size and stays
