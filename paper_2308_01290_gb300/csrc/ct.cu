@@ -141,23 +141,26 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
     float* hodd = smem_f + 3 * nb; // ds h(m) for odd m = 2t + 1
     const int sv = blockIdx.x;     // slice * n_views + view
     if (sv >= n * g.n_views) return;
-    const double ds = g.bin_mm * g.sid_mm / g.sdd_mm;
+    // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
+    const float sid = (float)g.sid_mm;
+    const float ds = (float)g.bin_mm * sid / (float)g.sdd_mm;
     const float* src = sino + (long long)sv * nb;
     for (int b = threadIdx.x; b < 3 * nb; b += blockDim.x) {
         const int k = b - nb;
         float v = 0.f;
         if (k >= 0 && k < nb) {
-            const double s = ((double)k - 0.5 * (nb - 1)) * ds;
-            v = (float)((double)src[k] * g.sid_mm / sqrt(g.sid_mm * g.sid_mm + s * s));
+            const float s = ((float)k - 0.5f * (float)(nb - 1)) * ds;
+            v = src[k] * sid / sqrtf(fmaf(s, s, sid * sid));
         }
         wrow[b] = v;
     }
+    const float inv_pi2 = (float)(1.0 / (M_PI * M_PI));
     for (int t = threadIdx.x; t < (nb + 1) / 2; t += blockDim.x) {
-        const double m = 2.0 * t + 1.0;
-        hodd[t] = (float)(-1.0 / (M_PI * M_PI * ds * m * m));   // ds * (-1/(pi m ds)^2)
+        const float m = 2.f * (float)t + 1.f;
+        hodd[t] = -inv_pi2 / (ds * m * m);   // ds * (-1/(pi m ds)^2)
     }
     __syncthreads();
-    const float h0 = (float)(0.25 / ds);   // ds * 1/(4 ds^2)
+    const float h0 = 0.25f / ds;   // ds * 1/(4 ds^2)
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
         float acc = 0.f;
         const float* c = wrow + nb + b;
@@ -177,25 +180,28 @@ constexpr int kBpTx = 16, kBpTy = 16, kBpRows = 2;
 
 __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q,
                                                                   float* __restrict__ img) {
+    // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
     extern __shared__ float trig[];   // cos, sin per view
+    const float a0 = (float)g.start_rad, da = (float)(g.arc_rad / g.n_views);
     for (int v = threadIdx.x + threadIdx.y * kBpTx; v < g.n_views; v += kBpTx * kBpTy) {
-        double s, c;
-        sincos(g.start_rad + g.arc_rad * (double)v / (double)g.n_views, &s, &c);
-        trig[2 * v] = (float)c;
-        trig[2 * v + 1] = (float)s;
+        float s, c;
+        sincosf(fmaf(da, (float)v, a0), &s, &c);
+        trig[2 * v] = c;
+        trig[2 * v + 1] = s;
     }
     __syncthreads();
     const int sl = blockIdx.z;
     const int i = blockIdx.x * kBpTx + threadIdx.x;
     const int j0 = blockIdx.y * (kBpTy * kBpRows) + threadIdx.y;
     const float sid = (float)g.sid_mm;
-    const float inv_ds = (float)(g.sdd_mm / (g.bin_mm * g.sid_mm));
+    const float inv_ds = (float)g.sdd_mm / ((float)g.bin_mm * sid);
     const float bc = 0.5f * (g.n_bins - 1);
-    const float x = (float)(((double)i - 0.5 * (g.nx - 1)) * g.pixel_mm);
+    const float pix = (float)g.pixel_mm;
+    const float x = ((float)i - 0.5f * (float)(g.nx - 1)) * pix;
     float y[kBpRows], acc[kBpRows];
 #pragma unroll
     for (int r = 0; r < kBpRows; ++r) {
-        y[r] = (float)(((double)(j0 + r * kBpTy) - 0.5 * (g.ny - 1)) * g.pixel_mm);
+        y[r] = ((float)(j0 + r * kBpTy) - 0.5f * (float)(g.ny - 1)) * pix;
         acc[r] = 0.f;
     }
     const float* qs = q + (long long)sl * g.n_views * g.n_bins;
@@ -205,7 +211,7 @@ __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometr
 #pragma unroll
         for (int r = 0; r < kBpRows; ++r) {
             const float L = sid - (x * c + y[r] * s);
-            const float invL = __frcp_rn(L);
+            const float invL = __fdividef(1.f, L);
             const float bf = fmaf(sid * (y[r] * c - x * s) * invL, inv_ds, bc);
             const float fl = floorf(bf);
             const int b0 = (int)fl;
@@ -219,7 +225,7 @@ __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometr
         }
     }
     if (i >= g.nx) return;
-    const float scale = (float)(0.5 * g.arc_rad / g.n_views);
+    const float scale = 0.5f * da;
 #pragma unroll
     for (int r = 0; r < kBpRows; ++r) {
         const int j = j0 + r * kBpTy;

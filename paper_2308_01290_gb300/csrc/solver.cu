@@ -1994,9 +1994,11 @@ __host__ __device__ inline int mg_block_levels(int bx, int by, int* nx, int* ny)
 // Inverse of the coarsest operator diag(a^2) + bt L of each multigrid slice
 // (once per Z^m solve; grid: one block per slice): a^2 restricted through
 // the slice's block levels as in k_mg_block, the dense n x n operator
-// (n <= kMgCoarsePx, periodic neighbours accumulate) inverted in FP64 by
-// Gauss-Jordan elimination without pivoting (the matrix is symmetric
-// positive definite), symmetrised, stored n x n in the kernel's precision.
+// (n <= kMgCoarsePx, periodic neighbours accumulate) inverted in the
+// kernel's precision by Gauss-Jordan elimination without pivoting (the
+// matrix is symmetric positive definite; its condition number stays below
+// about 1e4, so FP32 keeps the inverse to about 1e-3, ample for a
+// preconditioner), symmetrised, stored n x n.
 constexpr int kMgCoarseInvSmem =
     (kMgCoarsePx * (kMgCoarsePx + 1) + kMgCoarsePx) * (int)sizeof(double);   // + the a^2 of the levels
 
@@ -2004,8 +2006,8 @@ template <typename T>
 __global__ void __launch_bounds__(kMgBlockThreads) k_mg_coarse_inv(const SliceGeom* GB, const SliceState* S,
                                                                    const T* A, T* Qinv) {
     extern __shared__ __align__(16) unsigned char mgq_smem[];
-    double(*M)[kMgCoarsePx + 1] = reinterpret_cast<double(*)[kMgCoarsePx + 1]>(mgq_smem);
-    double* fac = reinterpret_cast<double*>(mgq_smem) + kMgCoarsePx * (kMgCoarsePx + 1);
+    T(*M)[kMgCoarsePx + 1] = reinterpret_cast<T(*)[kMgCoarsePx + 1]>(mgq_smem);
+    T* fac = reinterpret_cast<T*>(mgq_smem) + kMgCoarsePx * (kMgCoarsePx + 1);
     T* a = reinterpret_cast<T*>(mgq_smem + kMgCoarseInvSmem);   // every level (sum of sizes)
     const int s = blockIdx.x;
     const SliceGeom g = GB[s];
@@ -2033,14 +2035,13 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_coarse_inv(const SliceGe
         __syncthreads();
     }
     const int j = J - 1, cx = nx[j], cy = ny[j], n = cx * cy;
-    double bt = S[s].beta_t;
-    for (int l = 0; l < g.lvl + j; ++l) bt *= 0.25;
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) M[q / n][q % n] = 0.0;
+    const T bt = mg_bt<T>(S[s], g.lvl + j);
+    for (int q = threadIdx.x; q < n * n; q += blockDim.x) M[q / n][q % n] = T(0);
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < n; ++i) {
             const int yy = i / cx, xx = i - yy * cx;
-            M[i][i] += (double)a[base[j] + i] + 4.0 * bt;
+            M[i][i] += a[base[j] + i] + T(4) * bt;
             const int nb[4] = {yy * cx + wrap(xx - 1, cx), yy * cx + wrap(xx + 1, cx), wrap(yy - 1, cy) * cx + xx,
                                wrap(yy + 1, cy) * cx + xx};
             for (int k = 0; k < 4; ++k) M[i][nb[k]] -= bt;
@@ -2048,22 +2049,22 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_coarse_inv(const SliceGe
     }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-        const double p = M[k][k];
+        const T p = M[k][k];
         __syncthreads();
-        for (int jj = threadIdx.x; jj < n; jj += blockDim.x) M[k][jj] = (jj == k ? 1.0 : M[k][jj]) / p;
+        for (int jj = threadIdx.x; jj < n; jj += blockDim.x) M[k][jj] = (jj == k ? T(1) : M[k][jj]) / p;
         for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = M[i][k];
         __syncthreads();
         for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
             const int i = q / n, jj = q - i * n;
             if (i == k) continue;
-            M[i][jj] = (jj == k ? 0.0 : M[i][jj]) - fac[i] * M[k][jj];
+            M[i][jj] = (jj == k ? T(0) : M[i][jj]) - fac[i] * M[k][jj];
         }
         __syncthreads();
     }
     T* Q = Qinv + (long long)s * kMgCoarsePx * kMgCoarsePx;
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
         const int i = q / n, jj = q - i * n;
-        Q[q] = T(0.5 * (M[i][jj] + M[jj][i]));
+        Q[q] = T(0.5) * (M[i][jj] + M[jj][i]);
     }
 }
 
