@@ -295,10 +295,10 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float h2, float l2) {
 }
 
 // Block-wide sum of the NV per-thread partials x of a kernel computing in
-// T; result in thread 0.  FP32 kernels sum across each warp in compensated
-// float-float arithmetic, which runs on the FP32 pipes (GB300 issues FP64 at
-// a small fraction of the FP32 rate), and add the per-warp sums in FP64;
-// FP64 kernels sum in FP64.
+// T; result in thread 0.  FP32 kernels sum in compensated float-float
+// arithmetic (across each warp, then across the warps), which runs on the
+// FP32 pipes (GB300 issues FP64 at a small fraction of the FP32 rate), and
+// convert once to FP64; FP64 kernels sum in FP64.
 template <typename T, int NV>
 __device__ __forceinline__ void block_sum_t(const T (&x)[NV], double (&v)[NV], double* sh /* NV * 32 */) {
     if constexpr (sizeof(T) == 8) {
@@ -307,6 +307,7 @@ __device__ __forceinline__ void block_sum_t(const T (&x)[NV], double (&v)[NV], d
         block_sum<NV>(v, sh);
     } else {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+        float* shf = reinterpret_cast<float*>(sh);   // (h, l) per warp: NV * 64 floats
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             float h = (float)x[q], l = 0.f;
@@ -316,15 +317,19 @@ __device__ __forceinline__ void block_sum_t(const T (&x)[NV], double (&v)[NV], d
                 const float l2 = __shfl_down_sync(0xffffffffu, l, o);
                 ff_add(h, l, h2, l2);
             }
-            if (lane == 0) sh[q * 32 + warp] = (double)h + (double)l;
+            if (lane == 0) {
+                shf[q * 64 + 2 * warp] = h;
+                shf[q * 64 + 2 * warp + 1] = l;
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0) {
+            // the warp sums in float-float too; one conversion to FP64 per value
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
-                double t = 0.0;
-                for (int w = 0; w < nw; ++w) t += sh[q * 32 + w];
-                v[q] = t;
+                float h = 0.f, l = 0.f;
+                for (int w = 0; w < nw; ++w) ff_add(h, l, shf[q * 64 + 2 * w], shf[q * 64 + 2 * w + 1]);
+                v[q] = (double)h + (double)l;
             }
         }
         __syncthreads();

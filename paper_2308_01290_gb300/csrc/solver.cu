@@ -1504,6 +1504,65 @@ __device__ __forceinline__ TileGeo tile_geo(const SliceGeom* G, int s) {
     return TileGeo{__ldg(&g->off), __ldg(&g->nx), __ldg(&g->ny), __ldg(&g->pitch), __ldg(&g->lvl)};
 }
 
+// A VN-vector of shared memory at a 16-byte aligned address.
+template <typename T>
+__device__ __forceinline__ Pack<T> lds_pack(const T* p) {
+    return *reinterpret_cast<const Pack<T>*>(p);
+}
+template <typename T>
+__device__ __forceinline__ void sts_pack(T* p, const Pack<T>& v) {
+    *reinterpret_cast<Pack<T>*>(p) = v;
+}
+
+// Over a tile and its halo in shared memory: fv(row, c0) for the interior
+// columns as VN-vectors (c0 = OFF + k VN), fs(row, col) for the two halo
+// columns.
+template <typename T, typename FV, typename FS>
+__device__ __forceinline__ void for_halo_vec(FV fv, FS fs) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, H = TileDim<T>::TH + 2, VR = kTileW / VN;
+    for (int q = threadIdx.x; q < H * VR; q += blockDim.x) {
+        const int ry = q / VR;
+        fv(ry, OFF + (q - ry * VR) * VN);
+    }
+    for (int q = threadIdx.x; q < 2 * H; q += blockDim.x) fs(q >> 1, (q & 1) ? OFF + kTileW : OFF - 1);
+}
+
+// (a^2 x + bt L x) for the VN pixels of row ry from column c0 (x in sx with
+// its halo), given a^2 there.
+template <typename T>
+__device__ __forceinline__ Pack<T> mx_pack(const T (*sx)[TileDim<T>::SW], int ry, int c0, const Pack<T>& a, T bt,
+                                           Pack<T>& xc) {
+    constexpr int VN = TileDim<T>::VN;
+    xc = lds_pack<T>(&sx[ry][c0]);
+    const Pack<T> xu = lds_pack<T>(&sx[ry - 1][c0]), xd = lds_pack<T>(&sx[ry + 1][c0]);
+    const T xl = sx[ry][c0 - 1], xr = sx[ry][c0 + VN];
+    Pack<T> o;
+#pragma unroll
+    for (int e = 0; e < VN; ++e) {
+        const T l = e == 0 ? xl : xc.v[e - 1];
+        const T r = e == VN - 1 ? xr : xc.v[e + 1];
+        const T lap = (T(4) * xc.v[e] - l - r) - (xu.v[e] + xd.v[e]);
+        o.v[e] = a.v[e] * xc.v[e] + bt * lap;
+    }
+    return o;
+}
+
+// Pre-smoothing from zero on the tile and its halo: x = w f / (a^2 + 4 bt).
+template <typename T>
+__device__ __forceinline__ void mg_presmooth(const T (*sf)[TileDim<T>::SW], const T (*sa)[TileDim<T>::SW],
+                                             T (*sx)[TileDim<T>::SW], T om, T b4) {
+    constexpr int VN = TileDim<T>::VN;
+    for_halo_vec<T>(
+        [&](int ry, int c0) {
+            const Pack<T> f = lds_pack<T>(&sf[ry][c0]), a = lds_pack<T>(&sa[ry][c0]);
+            Pack<T> x;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) x.v[e] = mg_div(om * f.v[e], a.v[e] + b4);
+            sts_pack<T>(&sx[ry][c0], x);
+        },
+        [&](int ry, int c) { sx[ry][c] = mg_div(om * sf[ry][c], sa[ry][c] + b4); });
+}
+
 // Restricted residual of the tile at (tx0, ty0) of level g: out at level g1 =
 // mean over each 2x2 block of f - (a^2 x + bt L x), with f, a^2, x on the tile
 // and its halo in shared memory.
@@ -1511,19 +1570,29 @@ template <typename T>
 __device__ __forceinline__ void mg_restrict_residual(const T (*sf)[TileDim<T>::SW], const T (*sa)[TileDim<T>::SW],
                                                      const T (*sx)[TileDim<T>::SW], const TileGeo& g,
                                                      const TileGeo& g1, int tx0, int ty0, T bt, T* out) {
-    constexpr int OFF = TileDim<T>::OFF, CW = kTileW / 2, CH = TileDim<T>::TH / 2;
-    for (int q = threadIdx.x; q < CW * CH; q += blockDim.x) {
-        const int cy = q / CW, cx = q - cy * CW;
-        if (tx0 + 2 * cx >= g.nx || ty0 + 2 * cy >= g.ny) continue;
-        T s = T(0);
+    // one task: two fine rows x VN fine columns = VN / 2 coarse cells
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, CH = TileDim<T>::TH / 2, VR = kTileW / VN;
+    for (int q = threadIdx.x; q < CH * VR; q += blockDim.x) {
+        const int cy = q / VR, k = q - cy * VR;
+        const int x0 = tx0 + k * VN;
+        if (x0 >= g.nx || ty0 + 2 * cy >= g.ny) continue;
+        const int c0 = OFF + k * VN;
+        T sum[VN / 2];
 #pragma unroll
-        for (int dy = 0; dy < 2; ++dy)
+        for (int i = 0; i < VN / 2; ++i) sum[i] = T(0);
 #pragma unroll
-            for (int dx = 0; dx < 2; ++dx) {
-                const int ry = 1 + 2 * cy + dy, col = OFF + 2 * cx + dx;
-                s += sf[ry][col] - (sa[ry][col] * sx[ry][col] + bt * lap5<T>(sx, ry, col));
-            }
-        out[g1.off + (long long)(ty0 / 2 + cy) * g1.pitch + tx0 / 2 + cx] = T(0.25) * s;
+        for (int dy = 0; dy < 2; ++dy) {
+            const int ry = 1 + 2 * cy + dy;
+            const Pack<T> a = lds_pack<T>(&sa[ry][c0]), f = lds_pack<T>(&sf[ry][c0]);
+            Pack<T> xc;
+            const Pack<T> m = mx_pack<T>(sx, ry, c0, a, bt, xc);
+#pragma unroll
+            for (int e = 0; e < VN; ++e) sum[e >> 1] += f.v[e] - m.v[e];
+        }
+        T* o = out + g1.off + (long long)(ty0 / 2 + cy) * g1.pitch + x0 / 2;
+#pragma unroll
+        for (int i = 0; i < VN / 2; ++i)
+            if (x0 + 2 * i < g.nx) o[i] = T(0.25) * sum[i];
     }
 }
 
@@ -1687,23 +1756,33 @@ __device__ __forceinline__ void mg_correct_smooth(const T (*sf)[TileDim<T>::SW],
                                                   const TileGeo& g, const Item& it, T bt, FO out) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
     const T b4 = T(4) * bt, om = mg_omega<T>();
-    for_halo_tile<T>([&](int ly, int col) {
-        // tile row ly is pixel row it.b - 1 + ly: coarse row (ly + 1) >> 1 of ec
-        sx[ly][col] = mg_div(om * sf[ly][col], sa[ly][col] + b4) + ec[(ly + 1) >> 1][(col - OFF + 2) >> 1];
-    });
+    // tile row ry is pixel row it.b - 1 + ry: coarse row (ry + 1) >> 1 of ec;
+    // column c is coarse column (c - OFF + 2) >> 1
+    for_halo_vec<T>(
+        [&](int ry, int c0) {
+            const Pack<T> f = lds_pack<T>(&sf[ry][c0]), a = lds_pack<T>(&sa[ry][c0]);
+            const T* e = ec[(ry + 1) >> 1];
+            Pack<T> x;
+#pragma unroll
+            for (int i = 0; i < VN; ++i) x.v[i] = mg_div(om * f.v[i], a.v[i] + b4) + e[(c0 + i - OFF + 2) >> 1];
+            sts_pack<T>(&sx[ry][c0], x);
+        },
+        [&](int ry, int c) {
+            sx[ry][c] = mg_div(om * sf[ry][c], sa[ry][c] + b4) + ec[(ry + 1) >> 1][(c - OFF + 2) >> 1];
+        });
     __syncthreads();
     for (int q = threadIdx.x; q < TH * VR; q += blockDim.x) {
         const int ly = q / VR, lx0 = (q - ly * VR) * VN;
         const int y = it.b + ly, x0 = it.a + lx0;
         if (y >= g.ny || x0 >= g.nx) continue;
         const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
+        const int ry = ly + 1, c0 = OFF + lx0;
+        const Pack<T> a = lds_pack<T>(&sa[ry][c0]), f = lds_pack<T>(&sf[ry][c0]);
+        Pack<T> xc;
+        const Pack<T> m = mx_pack<T>(sx, ry, c0, a, bt, xc);
         Pack<T> o;
 #pragma unroll
-        for (int e = 0; e < VN; ++e) {
-            const int ry = ly + 1, col = OFF + lx0 + e;
-            const T x = sx[ry][col], a = sa[ry][col];
-            o.v[e] = x + mg_div(om * (sf[ry][col] - (a * x + bt * lap5<T>(sx, ry, col))), a + b4);
-        }
+        for (int e = 0; e < VN; ++e) o.v[e] = xc.v[e] + mg_div(om * (f.v[e] - m.v[e]), a.v[e] + b4);
         out(g.off + (long long)y * g.pitch + x0, cnt, ly, lx0, o);
     }
 }
@@ -1776,7 +1855,15 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const
             In v[TileVec<T>::R];
             tile_vec_load<T>(gs, c.it, load, v);
             const T al = Sc<T>::alpha(*sp);
-            for_halo_tile<T>([&](int ly, int col) { b.h[0][ly][col] = fma(-al, b.h[2][ly][col], b.h[0][ly][col]); });
+            for_halo_vec<T>(
+                [&](int ry, int c0) {
+                    Pack<T> r = lds_pack<T>(&b.h[0][ry][c0]);
+                    const Pack<T> qv = lds_pack<T>(&b.h[2][ry][c0]);
+#pragma unroll
+                    for (int e = 0; e < VN; ++e) r.v[e] = fma(-al, qv.v[e], r.v[e]);
+                    sts_pack<T>(&b.h[0][ry][c0], r);
+                },
+                [&](int ry, int col) { b.h[0][ry][col] = fma(-al, b.h[2][ry][col], b.h[0][ry][col]); });
             __syncthreads();
             tile_vec_use<T>(
                 gs, c.it,
@@ -1794,7 +1881,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const
                 v);
         }
         // pre-smoothing from zero, on the tile and its halo (in place of q)
-        for_halo_tile<T>([&](int ly, int col) { b.h[2][ly][col] = mg_div(om * b.h[0][ly][col], b.h[1][ly][col] + b4); });
+        mg_presmooth<T>(b.h[0], b.h[1], b.h[2], om, b4);
         __syncthreads();
         mg_restrict_residual<T>(b.h[0], b.h[1], b.h[2], g, c.g1, c.it.a, c.it.b, bt, F1);
         if (UPD) {
@@ -1838,7 +1925,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_down(ItemList L, cons
         account(acct, KF_MG_LEVELS,
                 (long long)min(TH, g.ny - c.it.b) * min(kTileW, g.nx - c.it.a) * 9 * (long long)sizeof(T) / 4);
         const T bt = mg_bt<T>(S[c.it.slice], g.lvl), b4 = T(4) * bt, om = mg_omega<T>();
-        for_halo_tile<T>([&](int ly, int col) { sx[ly][col] = mg_div(om * b.h[0][ly][col], b.h[1][ly][col] + b4); });
+        mg_presmooth<T>(b.h[0], b.h[1], sx, om, b4);
         __syncthreads();
         mg_restrict_residual<T>(b.h[0], b.h[1], sx, g, c.g1, c.it.a, c.it.b, bt, F1);
     };
@@ -1942,7 +2029,15 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_pq(ItemList L, const 
                     (long long)sizeof(T));
         if (!c.first) {
             const T bc = Sc<T>::betacg(*sp);
-            for_halo_tile<T>([&](int ly, int col) { b.h[0][ly][col] = fma(bc, b.h[1][ly][col], b.h[0][ly][col]); });
+            for_halo_vec<T>(
+                [&](int ry, int c0) {
+                    Pack<T> pv = lds_pack<T>(&b.h[0][ry][c0]);
+                    const Pack<T> po = lds_pack<T>(&b.h[1][ry][c0]);
+#pragma unroll
+                    for (int e = 0; e < VN; ++e) pv.v[e] = fma(bc, po.v[e], pv.v[e]);
+                    sts_pack<T>(&b.h[0][ry][c0], pv);
+                },
+                [&](int ry, int col) { b.h[0][ry][col] = fma(bc, b.h[1][ry][col], b.h[0][ry][col]); });
             __syncthreads();
         }
         const T bt = Sc<T>::beta_t(*sp);
@@ -1952,14 +2047,11 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_pq(ItemList L, const 
             const int yy = c.it.b + ly, x0 = c.it.a + lx0;
             if (yy >= g.ny || x0 >= g.nx) continue;
             const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
-            Pack<T> pv, qv;
+            Pack<T> pv;
+            const Pack<T> qv = mx_pack<T>(b.h[0], ly + 1, OFF + lx0, lds_pack<T>(&b.in[0][ly][lx0]), bt, pv);
 #pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                const int ry = ly + 1, col = OFF + lx0 + e;
-                pv.v[e] = b.h[0][ry][col];
-                qv.v[e] = b.in[0][ly][lx0 + e] * pv.v[e] + bt * lap5<T>(b.h[0], ry, col);
+            for (int e = 0; e < VN; ++e)
                 if (e < cnt) acc = fma(pv.v[e], qv.v[e], acc);
-            }
             const long long d = g.off + (long long)yy * g.pitch + x0;
             stv_n(pnew, d, pv, cnt);
             stv_n(qo, d, qv, cnt);
