@@ -1443,7 +1443,8 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
 // the transpose of the prolongation and both smoothing steps are the same
 // Jacobi step, so B is symmetric positive definite, as PCG needs.  Levels of
 // more than kMgBlockPx pixels run as tile kernels over all slices; the rest
-// of the cycle of a slice runs inside one thread block, with an exact solve
+// of the cycle of a slice runs inside one thread block (kMgBlockSweeps Jacobi
+// steps before and after the correction there), with an exact solve
 // on the coarsest grid (at most kMgCoarsePx pixels) by the inverse of its
 // operator, formed once per Z^m solve.
 // The fine-level passes of one PCG step:
@@ -1459,6 +1460,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, cons
 constexpr int kMgBlockPx = 4096;       // levels of at most this many pixels run inside one block
 constexpr int kMgCoarsePx = 64;        // the coarsest grid has at most this many pixels
 constexpr int kMgMaxBlockLevels = 8;
+constexpr int kMgBlockSweeps = 2;      // Jacobi sweeps before and after the correction on the block's levels
 constexpr int kMgBlockThreads = 256;
 
 // x / y for the Jacobi weights of the cycle: any fixed positive diagonal
@@ -2181,6 +2183,7 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* G
     T* f = sh;             // f of every level
     T* a = sh + tot;       // a^2
     T* x = sh + 2 * tot;   // correction
+    T* r = sh + 3 * tot;   // residual of a smoothing sweep (size of the first level)
     if (threadIdx.x == 0) atomicAdd(acct + KF_MG_LEVELS, (unsigned long long)(g.nx * g.ny) * 3ull * sizeof(T));
     const T om = mg_omega<T>();
     T bt[kMgMaxBlockLevels];
@@ -2210,12 +2213,27 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* G
         }
         __syncthreads();
     }
+    // kMgBlockSweeps damped Jacobi sweeps of level j from the current x
+    auto sweeps = [&](int j, int n_sweeps) {
+        const T b4 = T(4) * bt[j];
+        for (int sw = 0; sw < n_sweeps; ++sw) {
+            for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x) {
+                const int yy = i / nx[j], xx = i - yy * nx[j];
+                r[i] = f[base[j] + i] - mv(x, j, yy, xx);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x)
+                x[base[j] + i] += mg_div(om * r[i], a[base[j] + i] + b4);
+            __syncthreads();
+        }
+    };
     // down: pre-smoothing from zero, restricted residual
     for (int j = 0; j + 1 < J; ++j) {
         const T b4 = T(4) * bt[j];
         for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x)
             x[base[j] + i] = mg_div(om * f[base[j] + i], a[base[j] + i] + b4);
         __syncthreads();
+        sweeps(j, kMgBlockSweeps - 1);
         for (int i = threadIdx.x; i < nx[j + 1] * ny[j + 1]; i += blockDim.x) {
             const int yy = i / nx[j + 1], xx = i - yy * nx[j + 1];
             T sum = T(0);
@@ -2238,22 +2256,14 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* G
         }
         __syncthreads();
     }
-    // up: coarse correction, post-smoothing (the residual goes into f)
+    // up: coarse correction, post-smoothing
     for (int j = J - 2; j >= 0; --j) {
-        const T b4 = T(4) * bt[j];
         for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x) {
             const int yy = i / nx[j], xx = i - yy * nx[j];
             x[base[j] + i] += x[base[j + 1] + (yy >> 1) * nx[j + 1] + (xx >> 1)];
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x) {
-            const int yy = i / nx[j], xx = i - yy * nx[j];
-            f[base[j] + i] -= mv(x, j, yy, xx);
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < nx[j] * ny[j]; i += blockDim.x)
-            x[base[j] + i] += mg_div(om * f[base[j] + i], a[base[j] + i] + b4);
-        __syncthreads();
+        sweeps(j, kMgBlockSweeps);
     }
     for (int i = threadIdx.x; i < g.nx * g.ny; i += blockDim.x) {
         const int yy = i / g.nx, xx = i - yy * g.nx;
@@ -3351,13 +3361,13 @@ int mg_setup(Ctx& c) {
         const int J = mg_block_levels(blk[s].nx, blk[s].ny, bx, by);
         int tot = 0;
         for (int j = 0; j < J; ++j) tot += bx[j] * by[j];
-        const int bytes = 3 * tot * (int)c.elem;
+        const int bytes = (3 * tot + bx[0] * by[0]) * (int)c.elem;
         smem = bytes > smem ? bytes : smem;
     }
     if ((rc = alloc_dev(c, (void**)&c.d_mg_block, sizeof(SliceGeom) * c.n))) return rc;
     RECON_CUDA(cudaMemcpy(c.d_mg_block, blk.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
     c.mg_block_smem = smem;
-    // k_mg_coarse_inv: the dense operator and a^2 of every level (at most the f, a^2, x share of k_mg_block)
+    // k_mg_coarse_inv: the dense operator and a^2 of every level (within a third of k_mg_block's share)
     c.mg_inv_smem = kMgCoarseInvSmem + smem / 3 + (int)c.elem;
     if (c.precision == 1) {
         RECON_CUDA(cudaFuncSetAttribute(k_mg_block<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
