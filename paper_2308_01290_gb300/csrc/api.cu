@@ -23,6 +23,14 @@ bool seven_smooth(int n) {
     return n == 1;
 }
 
+constexpr int kFbpGroup = 8;   // slices per FBP launch pair in recon_set_data
+
+bool same_geometry(const recon_geometry& a, const recon_geometry& b) {
+    return a.nx == b.nx && a.ny == b.ny && a.pixel_mm == b.pixel_mm && a.n_views == b.n_views &&
+           a.n_bins == b.n_bins && a.sid_mm == b.sid_mm && a.sdd_mm == b.sdd_mm && a.bin_mm == b.bin_mm &&
+           a.start_rad == b.start_rad && a.arc_rad == b.arc_rad;
+}
+
 int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
@@ -174,7 +182,8 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
             else c.allocations.push_back(c.d_sino[i]);
         }
         if (!rc) {
-            cudaError_t e = cudaMalloc((void**)&c.d_filt, sizeof(float) * max_one);
+            // filtered sinograms of up to kFbpGroup slices (one FBP launch pair per group)
+            cudaError_t e = cudaMalloc((void**)&c.d_filt, sizeof(float) * max_one * kFbpGroup);
             if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc filter scratch");
             else c.allocations.push_back(c.d_filt);
         }
@@ -206,12 +215,17 @@ int recon_set_data(recon_ctx* h, const float* low, const float* high, int on_dev
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         RECON_CUDA(cudaMemcpyAsync(c.d_sino[0], low, sizeof(float) * c.sino_elems, kind, c.stream));
         RECON_CUDA(cudaMemcpyAsync(c.d_sino[1], high, sizeof(float) * c.sino_elems, kind, c.stream));
-        for (int s = 0; s < c.n; ++s) {
+        // consecutive slices of one geometry go through the FBP together, up to
+        // kFbpGroup at a time (their sinograms and images are contiguous)
+        for (int s = 0; s < c.n;) {
+            int k = 1;
+            while (k < kFbpGroup && s + k < c.n && same_geometry(c.geo[s + k], c.geo[s])) ++k;
             for (int a = 0; a < 2; ++a) {
-                rc = ct_fbp(c.geo[s], 1, c.d_sino[a] + c.sino_off[s], c.d_stage[a] + c.sg[s].ext_off, c.d_filt,
+                rc = ct_fbp(c.geo[s], k, c.d_sino[a] + c.sino_off[s], c.d_stage[a] + c.sg[s].ext_off, c.d_filt,
                             c.stream, &c.launches);
                 if (rc) return rc;
             }
+            s += k;
         }
         lo = c.d_stage[0];
         hi = c.d_stage[1];

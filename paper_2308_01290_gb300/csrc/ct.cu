@@ -205,27 +205,29 @@ __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometr
         acc[r] = 0.f;
     }
     const float* qs = q + (long long)sl * g.n_views * g.n_bins;
+    const float kb = sid * inv_ds;
+    const unsigned nb = (unsigned)g.n_bins;
     for (int v = 0; v < g.n_views; ++v) {
         const float c = trig[2 * v], s = trig[2 * v + 1];
+        const float xc = x * c, xs = x * s;
         const float* row = qs + (long long)v * g.n_bins;
 #pragma unroll
         for (int r = 0; r < kBpRows; ++r) {
-            const float L = sid - (x * c + y[r] * s);
+            const float L = sid - fmaf(y[r], s, xc);
             const float invL = __fdividef(1.f, L);
-            const float bf = fmaf(sid * (y[r] * c - x * s) * invL, inv_ds, bc);
+            const float bf = fmaf(fmaf(y[r], c, -xs) * kb, invL, bc);
             const float fl = floorf(bf);
             const int b0 = (int)fl;
             const float w1 = bf - fl;
             float val = 0.f;
-            if (b0 >= 0 && b0 < g.n_bins) val += (1.f - w1) * __ldg(row + b0);
-            if (b0 + 1 >= 0 && b0 + 1 < g.n_bins) val += w1 * __ldg(row + b0 + 1);
-            // 1/U^2 = (sid / L)^2
-            const float su = sid * invL;
-            acc[r] = fmaf(val, su * su, acc[r]);
+            if ((unsigned)b0 < nb) val += (1.f - w1) * __ldg(row + b0);
+            if ((unsigned)(b0 + 1) < nb) val += w1 * __ldg(row + b0 + 1);
+            // 1/U^2 = (sid / L)^2: sid^2 applied after the sum
+            acc[r] = fmaf(val * invL, invL, acc[r]);
         }
     }
     if (i >= g.nx) return;
-    const float scale = 0.5f * da;
+    const float scale = 0.5f * da * sid * sid;
 #pragma unroll
     for (int r = 0; r < kBpRows; ++r) {
         const int j = j0 + r * kBpTy;

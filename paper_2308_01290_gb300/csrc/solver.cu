@@ -1360,77 +1360,6 @@ __device__ __forceinline__ T lap5(const T (*sm)[TileDim<T>::SW], int ry, int cx)
     return (T(4) * c - sm[ry][cx - 1] - sm[ry][cx + 1]) - (sm[ry - 1][cx] + sm[ry + 1][cx]);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
-                                                             SliceState* S, Ptrs<T> P, int* pending) {
-    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
-    __shared__ __align__(16) T sm[1][TileDim<T>::TH + 2][SW];
-    __shared__ double red[3 * 32];
-    __shared__ SliceGeom s_g;
-    const T* z = P.f[RECON_F_Z];
-    struct In {
-        Pack<T> a2, rz;
-    };
-    auto load = [&](long long d, int cnt) {
-        return In{ldv_n(P.f[RECON_F_A2], d, cnt), ldv_n(P.f[RECON_F_RHS_Z], d, cnt)};
-    };
-    // the next item's descriptor is fetched while this one is processed
-    Item nxt = blockIdx.x < (unsigned)L.n_items ? L.items[blockIdx.x] : Item{};
-    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
-        const Item it = nxt;
-        if (w + (int)gridDim.x < L.n_items) nxt = L.items[w + gridDim.x];
-        if (!__ldg(&S[it.slice].active) || __ldg(&G[it.slice].cluster)) continue;
-        stage_struct(&s_g, G + it.slice);
-        __syncthreads();
-        const SliceGeom& g = s_g;
-        account(P.acct, KF_CG_INIT, tile_px<T>(g, it) * 4 * (long long)sizeof(T));
-        // a^2 and the right-hand side are loaded together with the z tile
-        In x[TileVec<T>::R];
-        tile_vec_load<T>(g, it, load, x);
-        load_tile<T, 1>(
-            sm, g, it.a, it.b, [&](long long d) { return Vals<T, 1>{{z[d]}}; },
-            [&](long long d) { return PVals<T, 1>{{ldv(z, d)}}; });
-        __syncthreads();
-        const T bt = Sc<T>::beta_t(S[it.slice]);
-        T accT = T(0), acc_a2 = T(0), acc_b = T(0);
-        tile_vec_use<T>(g, it, [&](long long d, int cnt, int ly, int lx0, const In& v) {
-            const Pack<T>&a2 = v.a2, &rz = v.rz;
-            Pack<T> r;
-#pragma unroll
-            for (int e = 0; e < VN; ++e) {
-                const T Mz = a2.v[e] * sm[0][ly + 1][OFF + lx0 + e] + bt * lap5<T>(sm[0], ly + 1, OFF + lx0 + e);
-                r.v[e] = rz.v[e] - Mz;
-                if (e < cnt) {
-                    accT = fma(r.v[e], r.v[e], accT);
-                    acc_a2 += a2.v[e];
-                    acc_b = fma(rz.v[e], rz.v[e], acc_b);
-                }
-            }
-            stv_n(P.f[RECON_F_CG_R], d, r, cnt);
-        }, x);
-        const T part[3] = {accT, acc_a2, acc_b};
-        double acc[3];
-        block_sum_t<T, 3>(part, acc, red);
-        double tot[3];
-        if (item_reduce<3>(L, w, it.slice, acc, tot, red)) {
-            SliceState& so = S[it.slice];
-            const double tol2 = C[it.slice].cg_tol * C[it.slice].cg_tol;
-            // mean(a^2) sets the preconditioner's diagonal, ||rhs||^2 the
-            // stopping test (of the a^2 and rhs this solve reads)
-            set_abar2(so, tot[1] / ((double)g.nx * (double)g.ny));
-            so.bb = tot[2];
-            so.rr = tot[0];
-            so.rr0 = tot[0];
-            so.cg_it = 0;
-            so.ry = 0.0;
-            set_betacg(so, 0.0);
-            so.cg_done = (so.bb == 0.0 || !(tot[0] > tol2 * so.bb)) ? 1 : 0;
-            if (!so.cg_done) atomicAdd(pending, 1);
-        }
-        __syncthreads();
-    }
-}
-
 // --------------------------------------------------------------------------
 // Multigrid preconditioner of the Z^m PCG
 // --------------------------------------------------------------------------
@@ -1746,6 +1675,88 @@ __device__ __forceinline__ void pipeline_items(const ItemList& L, Buf* buf, FM m
         cur = nxt;
     }
     cp_async_wait<0>();
+}
+
+// ---- start of the Z^m PCG: r = rhs - M z, with mean(a^2), ||rhs||^2, r.r ----
+
+template <typename T>
+struct CgInitBuf {
+    T h[1][TileDim<T>::TH + 2][TileDim<T>::SW];   // z with halo
+    T in[2][TileDim<T>::TH][kTileW];              // a^2, rhs
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
+                                                             SliceState* S, Ptrs<T> P, int* pending) {
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
+    extern __shared__ __align__(16) unsigned char cg_dsm[];
+    CgInitBuf<T>* buf = reinterpret_cast<CgInitBuf<T>*>(cg_dsm);
+    __shared__ double red[3 * 32];
+    const T* z = P.f[RECON_F_Z];
+    const T* a2 = P.f[RECON_F_A2];
+    const T* rz = P.f[RECON_F_RHS_Z];
+    T* r = P.f[RECON_F_CG_R];
+    auto make = [&](const Item& it) {
+        PipeItem p;
+        p.it = it;
+        p.first = 0;
+        p.ok = __ldg(&S[it.slice].active) && !__ldg(&G[it.slice].cluster);
+        if (p.ok) p.g = tile_geo(G, it.slice);
+        return p;
+    };
+    auto issue = [&](const PipeItem& c, CgInitBuf<T>& b) {
+        const T* hs[1] = {z};
+        halo_async<T, 1>(b.h, c.g, c.it.a, c.it.b, hs);
+        const T* is[2] = {a2, rz};
+        inner_async<T, 2>(b.in, c.g, c.it.a, c.it.b, is);
+    };
+    auto compute = [&](const PipeItem& c, CgInitBuf<T>& b, int w) {
+        const TileGeo& g = c.g;
+        account(P.acct, KF_CG_INIT,
+                (long long)min(TH, g.ny - c.it.b) * min(kTileW, g.nx - c.it.a) * 4 * (long long)sizeof(T));
+        const T bt = Sc<T>::beta_t(S[c.it.slice]);
+        T accT = T(0), acc_a2 = T(0), acc_b = T(0);
+        for (int q = threadIdx.x; q < TH * VR; q += blockDim.x) {
+            const int ly = q / VR, lx0 = (q - ly * VR) * VN;
+            const int y = c.it.b + ly, x0 = c.it.a + lx0;
+            if (y >= g.ny || x0 >= g.nx) continue;
+            const int cnt = g.nx - x0 < VN ? g.nx - x0 : VN;
+            const Pack<T> av = lds_pack<T>(&b.in[0][ly][lx0]), bv = lds_pack<T>(&b.in[1][ly][lx0]);
+            Pack<T> zc;
+            const Pack<T> m = mx_pack<T>(b.h[0], ly + 1, OFF + lx0, av, bt, zc);
+            Pack<T> rv;
+#pragma unroll
+            for (int e = 0; e < VN; ++e) {
+                rv.v[e] = bv.v[e] - m.v[e];
+                if (e < cnt) {
+                    accT = fma(rv.v[e], rv.v[e], accT);
+                    acc_a2 += av.v[e];
+                    acc_b = fma(bv.v[e], bv.v[e], acc_b);
+                }
+            }
+            stv_n(r, g.off + (long long)y * g.pitch + x0, rv, cnt);
+        }
+        const T part[3] = {accT, acc_a2, acc_b};
+        double acc[3];
+        block_sum_t<T, 3>(part, acc, red);
+        double tot[3];
+        if (item_reduce<3>(L, w, c.it.slice, acc, tot, red)) {
+            SliceState& so = S[c.it.slice];
+            const double tol2 = C[c.it.slice].cg_tol * C[c.it.slice].cg_tol;
+            // mean(a^2) sets the preconditioner's diagonal, ||rhs||^2 the
+            // stopping test (of the a^2 and rhs this solve reads)
+            set_abar2(so, tot[1] / ((double)g.nx * (double)g.ny));
+            so.bb = tot[2];
+            so.rr = tot[0];
+            so.rr0 = tot[0];
+            so.cg_it = 0;
+            so.ry = 0.0;
+            set_betacg(so, 0.0);
+            so.cg_done = (so.bb == 0.0 || !(tot[0] > tol2 * so.bb)) ? 1 : 0;
+            if (!so.cg_done) atomicAdd(pending, 1);
+        }
+    };
+    pipeline_items(L, buf, make, issue, compute);
 }
 
 // x on the tile and its halo (sx) = w f / (a^2 + 4 bt) + e1 (the coarse
@@ -2786,7 +2797,7 @@ int op_solve_z(Ctx& c) {
     RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream));
     {
         FamTimer t0(c, KF_CG_INIT);
-        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 2 * sizeof(CgInitBuf<T>), c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                               c.d_state, P, c.d_cg_pending);
     }
     c.launches += 1;
@@ -3017,7 +3028,7 @@ int graph_build_t(Ctx& c) {
     if (!rc) rc = fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2));
     if (!rc) {
         cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream);
-        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 2 * sizeof(CgInitBuf<T>), c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                               c.d_state, P, c.d_cg_pending);
         c.launches += 1;
         if (fft) {
@@ -3569,6 +3580,12 @@ int solver_setup(Ctx& c) {
     if (!c.server_mode && (rc = pcg_cluster_setup(c))) return rc;
     RECON_CUDA(cudaMemcpy(c.d_geom, c.sg.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
     if ((rc = mg_setup(c))) return rc;
+    if (c.precision == 1)
+        RECON_CUDA(cudaFuncSetAttribute(k_cg_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(2 * sizeof(CgInitBuf<float>))));
+    else
+        RECON_CUDA(cudaFuncSetAttribute(k_cg_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(2 * sizeof(CgInitBuf<double>))));
     if (c.precision == 1) return set_fft_smem<float>(c);
     return set_fft_smem<double>(c);
 }
@@ -3649,7 +3666,7 @@ int tune_time(Ctx& c, int reps, float* ms) {
     int rc = RECON_OK;
     for (int r = -1; r < reps && !rc; ++r) {   // r = -1: warm-up
         if (r == 0) cudaEventRecord(a, c.stream);
-        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 2 * sizeof(CgInitBuf<T>), c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
                                                                               c.d_state, P, c.d_cg_pending);
         c.launches += 1;
         rc = fft_solve<T>(c, jobs1(RECON_F_CG_R, 0, RECON_F_CG_Y, 2));
