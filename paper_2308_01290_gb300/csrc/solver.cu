@@ -3327,11 +3327,96 @@ int mg_set_smem() {
 
 // Levels, pools and item lists of the multigrid preconditioner, and the row
 // and column items of the slices that keep the FFT preconditioner.
+int fill_list(Ctx& c, DevItemList& L);
+int pcg_split_lists(Ctx& c);
+
+// Tiles of the multigrid levels 0 .. mg_max_lb - 1 of the given slots (a
+// slot's level l has tiles while mg_lb > l), uploaded.
+int mg_lists_for(Ctx& c, const std::vector<int>& slots) {
+    const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
+    int rc;
+    for (int l = 0; l < c.mg_max_lb; ++l) {
+        DevItemList& T = c.mg_tiles[l];
+        T.h_items.clear();
+        T.h_lo.assign(c.n, 0);
+        T.h_cnt.assign(c.n, 0);
+        for (int s : slots) {
+            T.h_lo[s] = (int)T.h_items.size();
+            if (c.mg_lb[s] <= l) continue;
+            const int nx = c.sg[s].nx >> l, ny = c.sg[s].ny >> l;
+            for (int ty = 0; ty < ny; ty += th)
+                for (int tx = 0; tx < nx; tx += kTileW) T.h_items.push_back(Item{s, tx, ty, 0});
+            T.h_cnt[s] = (int)T.h_items.size() - T.h_lo[s];
+        }
+        if ((rc = fill_list(c, T))) return rc;
+    }
+    return pcg_split_lists(c);
+}
+
+// Serving engine: every slot gets the multigrid levels of the capacity at
+// fixed offsets (like its fields); a slot's levels are sized when a request
+// is configured into it (mg_configure_slot).
+int mg_setup_server(Ctx& c) {
+    int rc;
+    int L = 0;
+    for (int nx = c.cap_nx, ny = c.cap_ny; (long long)nx * ny > kMgBlockPx && nx > 1 && ny > 1; nx /= 2, ny /= 2) ++L;
+    if (L == 0) return RECON_OK;
+    c.mg_max_lb = L;
+    c.mg_sg.assign(L + 1, std::vector<SliceGeom>(c.n, SliceGeom{}));
+    long long off = 0;
+    for (int l = 1; l <= L; ++l)
+        for (int s = 0; s < c.n; ++s) {
+            SliceGeom& g = c.mg_sg[l][s];
+            g.pitch = ((c.cap_nx >> l) + 31) / 32 * 32;
+            g.off = off;
+            g.lvl = l;
+            off += (long long)(c.cap_ny >> l) * g.pitch;
+        }
+    for (int k = 0; k < 3; ++k) {
+        if ((rc = alloc_dev(c, &c.mg_pool[k], c.elem * off))) return rc;
+        RECON_CUDA(cudaMemset(c.mg_pool[k], 0, c.elem * off));
+    }
+    c.d_mg_geom.assign(L + 1, nullptr);
+    c.d_mg_geom[0] = c.d_geom;
+    for (int l = 1; l <= L; ++l) {
+        if ((rc = alloc_dev(c, (void**)&c.d_mg_geom[l], sizeof(SliceGeom) * c.n))) return rc;
+        RECON_CUDA(cudaMemcpy(c.d_mg_geom[l], c.mg_sg[l].data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
+    }
+    const std::vector<SliceGeom> blk(c.n, SliceGeom{});
+    if ((rc = alloc_dev(c, (void**)&c.d_mg_block, sizeof(SliceGeom) * c.n))) return rc;
+    RECON_CUDA(cudaMemcpy(c.d_mg_block, blk.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
+    // the largest block level any slot can have: at most kMgBlockPx pixels and its coarser grids
+    int tot = 0;
+    for (int px = kMgBlockPx; px >= 1; px /= 4) tot += px;
+    c.mg_block_smem = (3 * tot + kMgBlockPx) * (int)c.elem;
+    c.mg_inv_smem = kMgCoarseInvSmem + tot * (int)c.elem + (int)c.elem;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (c.precision == 1) {
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_block<float>, A, c.mg_block_smem));
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_coarse_inv<float>, A, c.mg_inv_smem));
+    } else {
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_block<double>, A, c.mg_block_smem));
+        RECON_CUDA(cudaFuncSetAttribute(k_mg_coarse_inv<double>, A, c.mg_inv_smem));
+    }
+    if ((rc = alloc_dev(c, &c.mg_qinv, c.elem * (size_t)kMgCoarsePx * kMgCoarsePx * c.n))) return rc;
+    if ((rc = c.precision == 1 ? mg_set_smem<float>() : mg_set_smem<double>())) return rc;
+    c.mg_tiles.assign(L, DevItemList{});
+    for (int l = 0; l < L; ++l) {
+        c.mg_tiles[l].h_lo.assign(c.n, 0);
+        c.mg_tiles[l].h_cnt.assign(c.n, 0);
+        if ((rc = upload_list(c, c.mg_tiles[l]))) return rc;
+    }
+    pcg_split_host(c);
+    if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols))) return rc;
+    return RECON_OK;
+}
+
 int mg_setup(Ctx& c) {
     int rc;
     c.mg_lb.assign(c.n, 0);
     c.mg_max_lb = 0;
-    if (c.server_mode || c.prm[0].pcg_kernel == 2) return RECON_OK;
+    if (c.server_mode) return mg_setup_server(c);
+    if (c.prm[0].pcg_kernel == 2) return RECON_OK;
     for (int s = 0; s < c.n; ++s) {
         if (c.sg[s].cluster) continue;
         c.mg_lb[s] = mg_tile_levels(c.sg[s].nx, c.sg[s].ny);
@@ -3867,6 +3952,19 @@ int solver_configure_slot(Ctx& c, int s, const recon_geometry& geo, const recon_
     slice_items(c, s, a, b, d);   // sets rows_per_item / cols_per_item
     c.tab[s] = make_tables(p);
     c.hconst[s] = slice_const(p, c.tab[s]);
+    if (c.mg_max_lb > 0) {
+        // the request's multigrid levels inside the slot's capacity regions
+        const int lb = p.pcg_kernel == 2 ? 0 : mg_tile_levels(geo.nx, geo.ny);
+        c.mg_lb[s] = lb;
+        for (int l = 1; l <= c.mg_max_lb; ++l) {
+            SliceGeom& gl = c.mg_sg[l][s];
+            gl.nx = l <= lb ? geo.nx >> l : 0;
+            gl.ny = l <= lb ? geo.ny >> l : 0;
+            RECON_CUDA(cudaMemcpyAsync(c.d_mg_geom[l] + s, &gl, sizeof(SliceGeom), cudaMemcpyHostToDevice, c.stream));
+        }
+        const SliceGeom blk = lb ? c.mg_sg[lb][s] : SliceGeom{};
+        RECON_CUDA(cudaMemcpyAsync(c.d_mg_block + s, &blk, sizeof(SliceGeom), cudaMemcpyHostToDevice, c.stream));
+    }
     RECON_CUDA(cudaMemcpyAsync(c.d_geom + s, &c.sg[s], sizeof(SliceGeom), cudaMemcpyHostToDevice, c.stream));
     RECON_CUDA(cudaMemcpyAsync(c.d_const + s, &c.hconst[s], sizeof(SliceConst), cudaMemcpyHostToDevice, c.stream));
     RECON_CUDA(cudaStreamSynchronize(c.stream));
@@ -3877,6 +3975,7 @@ int solver_rebuild_lists(Ctx& c, const std::vector<int>& active) {
     lists_for(c, active, &c.tiles, &c.rows, &c.cols);
     int rc;
     if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+    if (c.mg_max_lb > 0 && (rc = mg_lists_for(c, active))) return rc;
     return RECON_OK;
 }
 

@@ -28,9 +28,6 @@ def request(rc, k, n, iters, lam):
 
 
 def alone(rc, g, p, L, H):
-    # the serving engine runs the FFT-preconditioned PCG on every slot
-    p = type(p).from_buffer_copy(p)
-    p.pcg_kernel = 2
     s = rc.Solver(g, p)
     s.set_data(L, H)
     s.step(p.iters)
