@@ -1921,7 +1921,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const
 // Tile level g (level >= 1): pre-smoothing from zero and the restricted
 // residual into level g1.
 template <typename T>
-__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_down(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+__global__ void __launch_bounds__(kStencilThreads, 4) k_mg_down(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                               const SliceState* S, const T* F, const T* A, T* F1,
                                                               unsigned long long* acct) {
     constexpr int TH = TileDim<T>::TH;
@@ -1947,7 +1947,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_down(ItemList L, cons
 
 // Tile level g (level >= 1): e = coarse correction and post-smoothing.
 template <typename T>
-__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+__global__ void __launch_bounds__(kStencilThreads, 4) k_mg_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                             const SliceState* S, const T* F, const T* A,
                                                             const T* E1, T* E, unsigned long long* acct) {
     constexpr int TH = TileDim<T>::TH;
@@ -1973,7 +1973,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_up(ItemList L, const 
 // Fine level: y = B r (correction from level 1 and post-smoothing), r.y ->
 // beta_cg.
 template <typename T>
-__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_y(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+__global__ void __launch_bounds__(kStencilThreads, 4) k_mg_y(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                            SliceState* S, Ptrs<T> P, const T* r, const T* E1) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH;
     extern __shared__ __align__(16) unsigned char mg_dsm[];
@@ -2016,7 +2016,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_y(ItemList L, const S
 // Fine level: p = y + beta_cg p_old (p = y on the first step), q = M p, p.q
 // -> alpha.
 template <typename T>
-__global__ void __launch_bounds__(kStencilThreads, 3) k_mg_pq(ItemList L, const SliceGeom* G, SliceState* S,
+__global__ void __launch_bounds__(kStencilThreads, 4) k_mg_pq(ItemList L, const SliceGeom* G, SliceState* S,
                                                             Ptrs<T> P, int par) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
     extern __shared__ __align__(16) unsigned char mg_dsm[];

@@ -385,6 +385,29 @@ def test_autotune_mixed_preconditioners(rc, small_case):
         assert np.abs(out[1][1][k] - out[0][1][k])[b].mean() <= 1e-3, k
 
 
+def test_graph_mixed_preconditioners_equal_separate_launches(rc, small_case):
+    """Graph mode with a multigrid slice and an FFT-preconditioned one in the
+    same batch: bitwise the maps of separate launches."""
+    c = small_case
+    acq = c["acq"]
+    g0, g1 = rc.geometry(acq.nx, acq.ny), rc.geometry(100, 70)
+    p = rc.default_params(low=acq.low, high=acq.high, iters=6)
+    lo = np.concatenate([c["muL"].ravel(), c["muL"][:70, :100].ravel()]).astype(np.float32)
+    hi = np.concatenate([c["muH"].ravel(), c["muH"][:70, :100].ravel()]).astype(np.float32)
+    out = []
+    for graph in (False, True):
+        s = rc.Solver([g0, g1], [p, p])
+        if graph:
+            s.set_graph(True)
+        s.set_data(lo, hi)
+        s.step(6)
+        out.append(s.get_host())
+        s.close()
+    for a, b in zip(out[0], out[1]):
+        for k in range(2):
+            assert np.array_equal(a[k], b[k]), k
+
+
 def test_autotune_keeps_results(rc, small_case):
     """Autotune mode 1 picks a grid of {4, 8, 16} x SMs and leaves every
     result bitwise as it was; mode 2 also picks a row-item size and stays
