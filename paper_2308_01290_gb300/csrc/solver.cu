@@ -363,7 +363,7 @@ __device__ __forceinline__ void stv_n(T* p, long long d, const Pack<T>& v, int c
 // --------------------------------------------------------------------------
 
 template <typename T, bool STATS>
-__global__ void __launch_bounds__(kStencilThreads, 3) k_thr_rhs(ItemList L, const SliceGeom* G, const SliceConst* C,
+__global__ void __launch_bounds__(kStencilThreads, 4) k_thr_rhs(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                              SliceState* S, Ptrs<T> P) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, SW = TileDim<T>::SW;
     __shared__ __align__(16) T sm[4][TileDim<T>::TH + 2][SW];
@@ -1686,7 +1686,7 @@ struct CgInitBuf {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kStencilThreads, 3) k_cg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
+__global__ void __launch_bounds__(kStencilThreads, 4) k_cg_init(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                              SliceState* S, Ptrs<T> P, int* pending) {
     constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
     extern __shared__ __align__(16) unsigned char cg_dsm[];
