@@ -338,10 +338,10 @@ int recon_debug_op(recon_ctx* ctx, int32_t op);
  * steps of the last solve, [5] final relative residual. */
 int recon_debug_scalars(recon_ctx* ctx, int32_t slice, double* out);
 
-/* Autotuner of the launch shapes.  mode 0: off (default; grid 8 x SMs and
+/* Autotuner of the launch shapes.  mode 0: off (default; grid 32 x SMs and
  * the built-in item sizes).  1: the next recon_set_data also times one
  * stencil kernel and one FFT solve on scratch fields with grids of
- * {4, 8, 16} x SMs and keeps the fastest; the arithmetic, and so every
+ * {16, 32, 64} x SMs and keeps the fastest; the arithmetic, and so every
  * result, is unchanged.  2: as 1, and row items of {2048, 3072, 4096}
  * complex slots (FP32), which regroups the per-item partial sums of the
  * PCG reductions and so changes results in the last bits.  The choice holds

@@ -110,7 +110,7 @@ struct Ctx {
     unsigned long long* d_graph_launches = nullptr;   // kernels run inside the loops
     long long graph_static_launches = 0;
     // launch shape and row-item size (autotuned on request, recon_set_autotune)
-    int grid_mult = 8;           // grid = grid_mult x SMs (grid-stride over items)
+    int grid_mult = 32;          // grid = grid_mult x SMs (grid-stride over items)
     int row_budget = 0;          // complex slots of a row item; 0: the FFT budget
     int autotune = 0;            // 0 off, 1 grid, 2 grid and row-item size
     bool tuned = false;

@@ -3856,7 +3856,7 @@ void lists_for(Ctx& c, const std::vector<int>& slots, DevItemList* tiles, DevIte
 }
 }  // namespace
 
-// Candidates: grid = {4, 8, 16} x SMs (the arithmetic is the same for all;
+// Candidates: grid = {16, 32, 64} x SMs (the arithmetic is the same for all;
 // items and their partial sums do not change), and with autotune = 2 (FP32)
 // row items of {2048, 3072, 4096} complex slots, which regroups the per-item
 // partial sums of the PCG reductions (last-bit differences).  Best of three
@@ -3876,7 +3876,7 @@ int solver_autotune(Ctx& c) {
         if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
         if ((rc = pcg_split_lists(c))) return rc;
         if ((rc = c.precision == 1 ? set_fft_smem<float>(c) : set_fft_smem<double>(c))) return rc;
-        for (int m : {4, 8, 16}) {
+        for (int m : {16, 32, 64}) {
             c.grid_mult = m;
             float ms = 0.f;
             if ((rc = c.precision == 1 ? tune_time<float>(c, 3, &ms) : tune_time<double>(c, 3, &ms))) return rc;

@@ -409,7 +409,7 @@ def test_graph_mixed_preconditioners_equal_separate_launches(rc, small_case):
 
 
 def test_autotune_keeps_results(rc, small_case):
-    """Autotune mode 1 picks a grid of {4, 8, 16} x SMs and leaves every
+    """Autotune mode 1 picks a grid of {16, 32, 64} x SMs and leaves every
     result bitwise as it was; mode 2 also picks a row-item size and stays
     within the final-map tolerance of the untuned solve."""
     c = small_case
@@ -427,9 +427,9 @@ def test_autotune_keeps_results(rc, small_case):
         out.append(s.get_host())
         tunes.append(s.tuning())
         s.close()
-    assert tunes[0] == (8, 0)
-    assert tunes[1][0] in (4, 8, 16) and tunes[1][1] == 0
-    assert tunes[2][0] in (4, 8, 16) and tunes[2][1] in (2048, 3072, 4096)
+    assert tunes[0] == (32, 0)
+    assert tunes[1][0] in (16, 32, 64) and tunes[1][1] == 0
+    assert tunes[2][0] in (16, 32, 64) and tunes[2][1] in (2048, 3072, 4096)
     for a, b in zip(out[0], out[1]):
         assert np.array_equal(a, b)
     body = c["P"]["rhoe"] >= 0.1
