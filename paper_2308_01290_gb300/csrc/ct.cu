@@ -173,10 +173,12 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
 // FBP step 2: pixel-driven backprojection of the filtered rows with weight
 // 1/U^2, U = (sid - x cos t - y sin t) / sid, detector coordinate at the
 // isocentre s' = sid (-x sin t + y cos t) / (U sid), linear interpolation,
-// times (arc / n_views) / 2 for a full scan.  A block covers a 16 x 32 pixel
-// tile (each thread two pixels 16 rows apart) so that, for one view, the
-// tile's samples fall in a narrow range of bins.
-constexpr int kBpTx = 16, kBpTy = 16, kBpRows = 2;
+// times (arc / n_views) / 2 for a full scan.  A block covers a 16 x 16 pixel
+// tile of up to kBpSlices slices (blockIdx.z: the group of slices); each
+// thread takes one pixel of every slice of its group, so the bin, the
+// interpolation weights and 1/U^2 of a (pixel, view) pair are formed once
+// for all of them.
+constexpr int kBpTx = 16, kBpTy = 16, kBpSlices = 8;
 
 __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q,
                                                                   float* __restrict__ img) {
@@ -190,49 +192,50 @@ __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometr
         trig[2 * v + 1] = s;
     }
     __syncthreads();
-    const int sl = blockIdx.z;
+    const int s0 = blockIdx.z * kBpSlices;
+    const int ns = n - s0 < kBpSlices ? n - s0 : kBpSlices;
     const int i = blockIdx.x * kBpTx + threadIdx.x;
-    const int j0 = blockIdx.y * (kBpTy * kBpRows) + threadIdx.y;
+    const int j = blockIdx.y * kBpTy + threadIdx.y;
     const float sid = (float)g.sid_mm;
     const float inv_ds = (float)g.sdd_mm / ((float)g.bin_mm * sid);
     const float bc = 0.5f * (g.n_bins - 1);
     const float pix = (float)g.pixel_mm;
     const float x = ((float)i - 0.5f * (float)(g.nx - 1)) * pix;
-    float y[kBpRows], acc[kBpRows];
-#pragma unroll
-    for (int r = 0; r < kBpRows; ++r) {
-        y[r] = ((float)(j0 + r * kBpTy) - 0.5f * (float)(g.ny - 1)) * pix;
-        acc[r] = 0.f;
-    }
-    const float* qs = q + (long long)sl * g.n_views * g.n_bins;
+    const float y = ((float)j - 0.5f * (float)(g.ny - 1)) * pix;
+    const long long sstride = (long long)g.n_views * g.n_bins;
+    const float* qs = q + s0 * sstride;
     const float kb = sid * inv_ds;
     const unsigned nb = (unsigned)g.n_bins;
+    float acc[kBpSlices];
+#pragma unroll
+    for (int k = 0; k < kBpSlices; ++k) acc[k] = 0.f;
     for (int v = 0; v < g.n_views; ++v) {
         const float c = trig[2 * v], s = trig[2 * v + 1];
-        const float xc = x * c, xs = x * s;
+        const float L = sid - fmaf(y, s, x * c);
+        const float invL = __fdividef(1.f, L);
+        const float bf = fmaf(fmaf(y, c, -(x * s)) * kb, invL, bc);
+        const float fl = floorf(bf);
+        const int b0 = (int)fl;
+        const float w1 = bf - fl;
+        // 1/U^2 = (sid / L)^2, sid^2 applied after the sum; bins off the
+        // detector take weight 0 (and read bin 0)
+        const float u2 = invL * invL;
+        const bool in0 = (unsigned)b0 < nb, in1 = (unsigned)(b0 + 1) < nb;
+        const float e0 = in0 ? (1.f - w1) * u2 : 0.f, e1 = in1 ? w1 * u2 : 0.f;
+        const int o0 = in0 ? b0 : 0, o1 = in1 ? b0 + 1 : 0;
         const float* row = qs + (long long)v * g.n_bins;
 #pragma unroll
-        for (int r = 0; r < kBpRows; ++r) {
-            const float L = sid - fmaf(y[r], s, xc);
-            const float invL = __fdividef(1.f, L);
-            const float bf = fmaf(fmaf(y[r], c, -xs) * kb, invL, bc);
-            const float fl = floorf(bf);
-            const int b0 = (int)fl;
-            const float w1 = bf - fl;
-            float val = 0.f;
-            if ((unsigned)b0 < nb) val += (1.f - w1) * __ldg(row + b0);
-            if ((unsigned)(b0 + 1) < nb) val += w1 * __ldg(row + b0 + 1);
-            // 1/U^2 = (sid / L)^2: sid^2 applied after the sum
-            acc[r] = fmaf(val * invL, invL, acc[r]);
-        }
+        for (int k = 0; k < kBpSlices; ++k)
+            if (k < ns) {
+                const float* rk = row + k * sstride;
+                acc[k] = fmaf(e0, __ldg(rk + o0), fmaf(e1, __ldg(rk + o1), acc[k]));
+            }
     }
-    if (i >= g.nx) return;
+    if (i >= g.nx || j >= g.ny) return;
     const float scale = 0.5f * da * sid * sid;
 #pragma unroll
-    for (int r = 0; r < kBpRows; ++r) {
-        const int j = j0 + r * kBpTy;
-        if (j < g.ny) img[(long long)sl * g.nx * g.ny + (long long)j * g.nx + i] = acc[r] * scale;
-    }
+    for (int k = 0; k < kBpSlices; ++k)
+        if (k < ns) img[(long long)(s0 + k) * g.nx * g.ny + (long long)j * g.nx + i] = acc[k] * scale;
 }
 
 // rho_e z with z = (Z / Z_w)^m (the photoelectric line-integral map)
@@ -323,7 +326,7 @@ int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float*
     }
     k_fbp_filter<<<n * g.n_views, 256, (3 * g.n_bins + (g.n_bins + 1) / 2) * sizeof(float), st>>>(g, n, sino,
                                                                                                    scratch);
-    const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy * kBpRows - 1) / (kBpTy * kBpRows), n);
+    const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy - 1) / kBpTy, (n + kBpSlices - 1) / kBpSlices);
     k_fbp_backproject<<<grid, dim3(kBpTx, kBpTy), 2 * g.n_views * sizeof(float), st>>>(g, n, scratch, img);
     if (launches) *launches += 2;
     RECON_CUDA(cudaGetLastError());

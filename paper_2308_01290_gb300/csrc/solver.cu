@@ -1837,7 +1837,7 @@ template <typename T, bool UPD>
 __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                              const SliceConst* C, SliceState* S, Ptrs<T> P, int par,
                                                              const T* rin, T* rout, T* F1, int* pending) {
-    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH, VR = kTileW / VN;
+    constexpr int VN = TileDim<T>::VN, OFF = TileDim<T>::OFF, TH = TileDim<T>::TH;
     extern __shared__ __align__(16) unsigned char mg_dsm[];
     MgBufFwd<T>* buf = reinterpret_cast<MgBufFwd<T>*>(mg_dsm);
     __shared__ double red[32];
@@ -2103,9 +2103,14 @@ __host__ __device__ inline int mg_block_levels(int bx, int by, int* nx, int* ny)
 // kernel's precision by Gauss-Jordan elimination without pivoting (the
 // matrix is symmetric positive definite; its condition number stays below
 // about 1e4, so FP32 keeps the inverse to about 1e-3, ample for a
-// preconditioner), symmetrised, stored n x n.
+// preconditioner), symmetrised, stored n x n.  Thread t keeps row t / 4 of
+// the matrix (padded to kMgCoarsePx with identity rows), columns
+// kMgInvCols (t % 4) onward, in registers; a pivot step publishes column k
+// and the scaled pivot row through shared memory (two barriers a step).
+constexpr int kMgInvCols = kMgCoarsePx / 4;
+static_assert(kMgBlockThreads == 4 * kMgCoarsePx, "one row of the coarsest operator per four threads");
 constexpr int kMgCoarseInvSmem =
-    (kMgCoarsePx * (kMgCoarsePx + 1) + kMgCoarsePx) * (int)sizeof(double);   // + the a^2 of the levels
+    (kMgCoarsePx * (kMgCoarsePx + 1) + 2 * kMgCoarsePx) * (int)sizeof(double);   // + the a^2 of the levels
 
 template <typename T>
 __global__ void __launch_bounds__(kMgBlockThreads) k_mg_coarse_inv(const SliceGeom* GB, const SliceState* S,
@@ -2141,31 +2146,61 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_coarse_inv(const SliceGe
     }
     const int j = J - 1, cx = nx[j], cy = ny[j], n = cx * cy;
     const T bt = mg_bt<T>(S[s], g.lvl + j);
-    for (int q = threadIdx.x; q < n * n; q += blockDim.x) M[q / n][q % n] = T(0);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < n; ++i) {
-            const int yy = i / cx, xx = i - yy * cx;
-            M[i][i] += a[base[j] + i] + T(4) * bt;
-            const int nb[4] = {yy * cx + wrap(xx - 1, cx), yy * cx + wrap(xx + 1, cx), wrap(yy - 1, cy) * cx + xx,
-                               wrap(yy + 1, cy) * cx + xx};
-            for (int k = 0; k < 4; ++k) M[i][nb[k]] -= bt;
+    T* rowk = fac + kMgCoarsePx;
+    const int row = threadIdx.x >> 2, c0 = (threadIdx.x & 3) * kMgInvCols;
+    T m[kMgInvCols];
+    {
+        // row `row` of the operator: a^2 + 4 beta~ on the diagonal, -beta~ per
+        // periodic neighbour (coinciding neighbours accumulate)
+        int nb[4] = {-1, -1, -1, -1};
+        T dg = T(0);
+        if (row < n) {
+            const int yy = row / cx, xx = row - yy * cx;
+            dg = a[base[j] + row] + T(4) * bt;
+            nb[0] = yy * cx + wrap(xx - 1, cx);
+            nb[1] = yy * cx + wrap(xx + 1, cx);
+            nb[2] = wrap(yy - 1, cy) * cx + xx;
+            nb[3] = wrap(yy + 1, cy) * cx + xx;
+        }
+#pragma unroll
+        for (int t = 0; t < kMgInvCols; ++t) {
+            const int jj = c0 + t;
+            T v = T(0);
+            if (row < n) {
+                if (jj == row) v += dg;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (nb[k] == jj) v -= bt;
+            } else if (jj == row) {
+                v = T(1);
+            }
+            m[t] = v;
         }
     }
-    __syncthreads();
     for (int k = 0; k < n; ++k) {
-        const T p = M[k][k];
+        // column k (M[row][k] for every row; M[k][k] is the pivot)
+#pragma unroll
+        for (int t = 0; t < kMgInvCols; ++t)
+            if (c0 + t == k) fac[row] = m[t];
         __syncthreads();
-        for (int jj = threadIdx.x; jj < n; jj += blockDim.x) M[k][jj] = (jj == k ? T(1) : M[k][jj]) / p;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = M[i][k];
-        __syncthreads();
-        for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
-            const int i = q / n, jj = q - i * n;
-            if (i == k) continue;
-            M[i][jj] = (jj == k ? T(0) : M[i][jj]) - fac[i] * M[k][jj];
+        const T f = fac[row];
+        if (row == k) {
+            const T inv = T(1) / fac[k];
+#pragma unroll
+            for (int t = 0; t < kMgInvCols; ++t) {
+                m[t] = (c0 + t == k ? T(1) : m[t]) * inv;
+                rowk[c0 + t] = m[t];
+            }
         }
         __syncthreads();
+        if (row != k) {
+#pragma unroll
+            for (int t = 0; t < kMgInvCols; ++t) m[t] = fma(-f, rowk[c0 + t], c0 + t == k ? T(0) : m[t]);
+        }
     }
+#pragma unroll
+    for (int t = 0; t < kMgInvCols; ++t) M[row][c0 + t] = m[t];
+    __syncthreads();
     T* Q = Qinv + (long long)s * kMgCoarsePx * kMgCoarsePx;
     for (int q = threadIdx.x; q < n * n; q += blockDim.x) {
         const int i = q / n, jj = q - i * n;
@@ -2507,22 +2542,13 @@ __global__ void k_reset_state(int n, const SliceConst* C, SliceState* S) {
 }
 
 // --------------------------------------------------------------------------
-// Z = Z_w (Z^m / Z_w^m)^(1/m) by FP64 Newton on y^m = z (Sec. II-D: Z is the
-// m-th root of Z^m); Z = 1 where z <= 0.
+// Z = Z_w (Z^m / Z_w^m)^(1/m) in FP64 (Sec. II-D: Z is the m-th root of
+// Z^m); Z = 1 where z <= 0.
 // --------------------------------------------------------------------------
-
-__device__ __forceinline__ double mth_root_newton(double z, double m) {
-    double y = (double)powf((float)z, (float)(1.0 / m));  // FP32 start
-    for (int i = 0; i < 3; ++i) {
-        const double ym = pow(y, m);
-        y = y - (ym - z) / (m * ym / y);
-    }
-    return y;
-}
 
 template <typename T>
 __global__ void k_extract(ItemList L, const SliceGeom* G, Ptrs<T> P, float* Z, float* rhoe, float* f1, float* f2,
-                          double zw, double m) {
+                          double zw, double inv_m) {
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
         const SliceGeom g = G[it.slice];
@@ -2533,7 +2559,7 @@ __global__ void k_extract(ItemList L, const SliceGeom* G, Ptrs<T> P, float* Z, f
             const long long e = g.ext_off + (long long)y * g.nx + x;
             if (Z) {
                 const double z = P.f[RECON_F_Z][d];
-                Z[e] = z > 0.0 ? (float)(zw * mth_root_newton(z, m)) : 1.0f;
+                Z[e] = z > 0.0 ? (float)(zw * pow(z, inv_m)) : 1.0f;
             }
             if (rhoe) rhoe[e] = (float)P.f[RECON_F_RHO][d];
             if (f1) f1[e] = (float)P.f[RECON_F_F1][d];
@@ -3163,7 +3189,7 @@ int load_t(Ctx& c, const float* lo, const float* hi) {
 template <typename T>
 int extract_t(Ctx& c, float* Z, float* rhoe, float* f1, float* f2) {
     k_extract<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, ptrs<T>(c), Z,
-                                                                           rhoe, f1, f2, water_z(), z_exponent());
+                                                                           rhoe, f1, f2, water_z(), 1.0 / z_exponent());
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
@@ -4017,10 +4043,10 @@ int solver_extract_slots(Ctx& c, const std::vector<int>& slots, float* Z, float*
     const int grid = grid_for(c, L.n_items);
     if (c.precision == 1)
         k_extract<float><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, ptrs<float>(c), Z, rhoe, nullptr,
-                                                                 nullptr, water_z(), z_exponent());
+                                                                 nullptr, water_z(), 1.0 / z_exponent());
     else
         k_extract<double><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, ptrs<double>(c), Z, rhoe, nullptr,
-                                                                  nullptr, water_z(), z_exponent());
+                                                                  nullptr, water_z(), 1.0 / z_exponent());
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
