@@ -133,20 +133,28 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
 
 // FBP step 1: cosine weight sid / sqrt(sid^2 + s^2) (s at the isocentre
 // plane) and Ram-Lak ramp h(0) = 1/(4 ds^2), h(odd m) = -1/(pi m ds)^2,
-// q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view).
+// q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view); a thread forms
+// kFiltOut consecutive outputs, sliding their windows of left and right taps
+// by two bins per odd offset (each output's sum in the order of a plain
+// loop over the offsets).
+constexpr int kFiltOut = 4;
+constexpr int kFiltPad = 8;   // zeros beyond the two nb-wide pads: the windows' last loads
+
+__host__ __device__ inline int fbp_filter_smem_floats(int nb) { return 3 * nb + kFiltPad + (nb + 1) / 2; }
+
 __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ sino, float* __restrict__ q) {
     extern __shared__ float smem_f[];
     const int nb = g.n_bins;
-    float* wrow = smem_f;          // weighted row, zero-padded by nb on both sides
-    float* hodd = smem_f + 3 * nb; // ds h(m) for odd m = 2t + 1
-    const int sv = blockIdx.x;     // slice * n_views + view
+    float* wrow = smem_f;                       // weighted row at nb + 2, zero-padded
+    float* hodd = smem_f + 3 * nb + kFiltPad;   // ds h(m) for odd m = 2t + 1
+    const int sv = blockIdx.x;                  // slice * n_views + view
     if (sv >= n * g.n_views) return;
     // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
     const float sid = (float)g.sid_mm;
     const float ds = (float)g.bin_mm * sid / (float)g.sdd_mm;
     const float* src = sino + (long long)sv * nb;
-    for (int b = threadIdx.x; b < 3 * nb; b += blockDim.x) {
-        const int k = b - nb;
+    for (int b = threadIdx.x; b < 3 * nb + kFiltPad; b += blockDim.x) {
+        const int k = b - (nb + 2);
         float v = 0.f;
         if (k >= 0 && k < nb) {
             const float s = ((float)k - 0.5f * (float)(nb - 1)) * ds;
@@ -161,12 +169,33 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
     }
     __syncthreads();
     const float h0 = 0.25f / ds;   // ds * 1/(4 ds^2)
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        float acc = 0.f;
-        const float* c = wrow + nb + b;
-        // odd offsets m = 2t + 1 on both sides (zero padding outside the row)
-        for (int t = 0; 2 * t + 1 < nb; ++t) acc = fmaf(hodd[t], c[-(2 * t + 1)] + c[2 * t + 1], acc);
-        q[(long long)sv * nb + b] = fmaf(h0, c[0], acc);
+    for (int b0 = threadIdx.x * kFiltOut; b0 < nb; b0 += blockDim.x * kFiltOut) {
+        const float* c = wrow + nb + 2 + b0;
+        // lf[j] = c[j - m], rt[j] = c[j + m] for the offset m = 2t + 1
+        float lf[kFiltOut], rt[kFiltOut], acc[kFiltOut];
+#pragma unroll
+        for (int j = 0; j < kFiltOut; ++j) {
+            lf[j] = c[j - 1];
+            rt[j] = c[j + 1];
+            acc[j] = 0.f;
+        }
+        for (int t = 0; 2 * t + 1 < nb; ++t) {
+            const float h = hodd[t];
+#pragma unroll
+            for (int j = 0; j < kFiltOut; ++j) acc[j] = fmaf(h, lf[j] + rt[j], acc[j]);
+            const int m = 2 * t + 1;
+#pragma unroll
+            for (int j = kFiltOut - 1; j >= 2; --j) lf[j] = lf[j - 2];
+            lf[1] = c[-m - 1];
+            lf[0] = c[-m - 2];
+#pragma unroll
+            for (int j = 0; j + 2 < kFiltOut; ++j) rt[j] = rt[j + 2];
+            rt[kFiltOut - 2] = c[kFiltOut - 2 + m + 2];
+            rt[kFiltOut - 1] = c[kFiltOut - 1 + m + 2];
+        }
+#pragma unroll
+        for (int j = 0; j < kFiltOut; ++j)
+            if (b0 + j < nb) q[(long long)sv * nb + b0 + j] = fmaf(h0, c[j], acc[j]);
     }
 }
 
@@ -319,13 +348,12 @@ int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float*
            long long* launches) {
     int rc = check_geom(g);
     if (rc) return rc;
-    if (g.n_views * 2 * sizeof(float) > 48 * 1024 || (3.5 * g.n_bins + 1) * sizeof(float) > 48 * 1024 ||
-        n > 65535) {
+    if (g.n_views * 2 * sizeof(float) > 48 * 1024 ||
+        (size_t)fbp_filter_smem_floats(g.n_bins) * sizeof(float) > 48 * 1024 || n > 65535 * kBpSlices) {
         set_error("too many views or bins");
         return RECON_EINVAL;
     }
-    k_fbp_filter<<<n * g.n_views, 256, (3 * g.n_bins + (g.n_bins + 1) / 2) * sizeof(float), st>>>(g, n, sino,
-                                                                                                   scratch);
+    k_fbp_filter<<<n * g.n_views, 256, fbp_filter_smem_floats(g.n_bins) * sizeof(float), st>>>(g, n, sino, scratch);
     const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy - 1) / kBpTy, (n + kBpSlices - 1) / kBpSlices);
     k_fbp_backproject<<<grid, dim3(kBpTx, kBpTy), 2 * g.n_views * sizeof(float), st>>>(g, n, scratch, img);
     if (launches) *launches += 2;
