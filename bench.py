@@ -147,13 +147,22 @@ def read_traffic(kernel, alg_bytes_per_launch):
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2308_01290_gb300", "csrc")
-    h = hashlib.sha256()
-    for name in sorted(os.listdir(src)):
-        with open(os.path.join(src, name), "rb") as f:
-            h.update(f.read())
     e = d.get(kernel)
-    if not e or e.get("source_sha256") != h.hexdigest():
+    if not e:
+        return None
+    # the sources of the kernel's translation unit (and the build flags), in
+    # the record's order; without a list, every file of csrc
+    src = os.path.join(ROOT, "paper_2308_01290_gb300", "csrc")
+    files = [os.path.join(ROOT, f) for f in e.get("sources", [])] or \
+        [os.path.join(src, name) for name in sorted(os.listdir(src))]
+    h = hashlib.sha256()
+    try:
+        for name in files:
+            with open(name, "rb") as f:
+                h.update(f.read())
+    except OSError:
+        return None
+    if e.get("source_sha256") != h.hexdigest():
         return None
     # the capture's traffic scaled to this launch's algorithmic size
     return e["dram_bytes_per_launch"] * alg_bytes_per_launch / e["algorithmic_bytes_per_launch"]

@@ -133,28 +133,20 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
 
 // FBP step 1: cosine weight sid / sqrt(sid^2 + s^2) (s at the isocentre
 // plane) and Ram-Lak ramp h(0) = 1/(4 ds^2), h(odd m) = -1/(pi m ds)^2,
-// q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view); a thread forms
-// kFiltOut consecutive outputs, sliding their windows of left and right taps
-// by two bins per odd offset (each output's sum in the order of a plain
-// loop over the offsets).
-constexpr int kFiltOut = 4;
-constexpr int kFiltPad = 8;   // zeros beyond the two nb-wide pads: the windows' last loads
-
-__host__ __device__ inline int fbp_filter_smem_floats(int nb) { return 3 * nb + kFiltPad + (nb + 1) / 2; }
-
+// q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view).
 __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ sino, float* __restrict__ q) {
     extern __shared__ float smem_f[];
     const int nb = g.n_bins;
-    float* wrow = smem_f;                       // weighted row at nb + 2, zero-padded
-    float* hodd = smem_f + 3 * nb + kFiltPad;   // ds h(m) for odd m = 2t + 1
-    const int sv = blockIdx.x;                  // slice * n_views + view
+    float* wrow = smem_f;          // weighted row, zero-padded by nb on both sides
+    float* hodd = smem_f + 3 * nb; // ds h(m) for odd m = 2t + 1
+    const int sv = blockIdx.x;     // slice * n_views + view
     if (sv >= n * g.n_views) return;
     // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
     const float sid = (float)g.sid_mm;
     const float ds = (float)g.bin_mm * sid / (float)g.sdd_mm;
     const float* src = sino + (long long)sv * nb;
-    for (int b = threadIdx.x; b < 3 * nb + kFiltPad; b += blockDim.x) {
-        const int k = b - (nb + 2);
+    for (int b = threadIdx.x; b < 3 * nb; b += blockDim.x) {
+        const int k = b - nb;
         float v = 0.f;
         if (k >= 0 && k < nb) {
             const float s = ((float)k - 0.5f * (float)(nb - 1)) * ds;
@@ -169,46 +161,29 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
     }
     __syncthreads();
     const float h0 = 0.25f / ds;   // ds * 1/(4 ds^2)
-    for (int b0 = threadIdx.x * kFiltOut; b0 < nb; b0 += blockDim.x * kFiltOut) {
-        const float* c = wrow + nb + 2 + b0;
-        // lf[j] = c[j - m], rt[j] = c[j + m] for the offset m = 2t + 1
-        float lf[kFiltOut], rt[kFiltOut], acc[kFiltOut];
-#pragma unroll
-        for (int j = 0; j < kFiltOut; ++j) {
-            lf[j] = c[j - 1];
-            rt[j] = c[j + 1];
-            acc[j] = 0.f;
-        }
-        for (int t = 0; 2 * t + 1 < nb; ++t) {
-            const float h = hodd[t];
-#pragma unroll
-            for (int j = 0; j < kFiltOut; ++j) acc[j] = fmaf(h, lf[j] + rt[j], acc[j]);
-            const int m = 2 * t + 1;
-#pragma unroll
-            for (int j = kFiltOut - 1; j >= 2; --j) lf[j] = lf[j - 2];
-            lf[1] = c[-m - 1];
-            lf[0] = c[-m - 2];
-#pragma unroll
-            for (int j = 0; j + 2 < kFiltOut; ++j) rt[j] = rt[j + 2];
-            rt[kFiltOut - 2] = c[kFiltOut - 2 + m + 2];
-            rt[kFiltOut - 1] = c[kFiltOut - 1 + m + 2];
-        }
-#pragma unroll
-        for (int j = 0; j < kFiltOut; ++j)
-            if (b0 + j < nb) q[(long long)sv * nb + b0 + j] = fmaf(h0, c[j], acc[j]);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        float acc = 0.f;
+        const float* c = wrow + nb + b;
+        // odd offsets m = 2t + 1 on both sides (zero padding outside the row)
+        for (int t = 0; 2 * t + 1 < nb; ++t) acc = fmaf(hodd[t], c[-(2 * t + 1)] + c[2 * t + 1], acc);
+        q[(long long)sv * nb + b] = fmaf(h0, c[0], acc);
     }
 }
 
 // FBP step 2: pixel-driven backprojection of the filtered rows with weight
 // 1/U^2, U = (sid - x cos t - y sin t) / sid, detector coordinate at the
 // isocentre s' = sid (-x sin t + y cos t) / (U sid), linear interpolation,
-// times (arc / n_views) / 2 for a full scan.  A block covers a 16 x 16 pixel
-// tile of up to kBpSlices slices (blockIdx.z: the group of slices); each
-// thread takes one pixel of every slice of its group, so the bin, the
-// interpolation weights and 1/U^2 of a (pixel, view) pair are formed once
-// for all of them.
-constexpr int kBpTx = 16, kBpTy = 16, kBpSlices = 8;
+// times (arc / n_views) / 2 for a full scan.  A block covers a 16 x (16 R)
+// pixel tile of up to S slices (blockIdx.z: the group of slices); each thread
+// takes R pixels (16 rows apart) of every slice of its group, so the bin,
+// the interpolation weights and 1/U^2 of a (pixel, view) pair are formed
+// once for all S slices.  Groups of several slices of one geometry run with
+// S = 8, R = 1; single slices with S = 1, R = 2.  Every product that could
+// be contracted is written as an explicit FMA or kept apart, so a pixel's
+// value is the same in both forms, bit for bit.
+constexpr int kBpTx = 16, kBpTy = 16, kBpGroup = 8;
 
+template <int S, int R>
 __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q,
                                                                   float* __restrict__ img) {
     // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
@@ -221,50 +196,64 @@ __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometr
         trig[2 * v + 1] = s;
     }
     __syncthreads();
-    const int s0 = blockIdx.z * kBpSlices;
-    const int ns = n - s0 < kBpSlices ? n - s0 : kBpSlices;
+    const int s0 = blockIdx.z * S;
+    const int ns = n - s0 < S ? n - s0 : S;
     const int i = blockIdx.x * kBpTx + threadIdx.x;
-    const int j = blockIdx.y * kBpTy + threadIdx.y;
+    const int j0 = blockIdx.y * (kBpTy * R) + threadIdx.y;
     const float sid = (float)g.sid_mm;
     const float inv_ds = (float)g.sdd_mm / ((float)g.bin_mm * sid);
     const float bc = 0.5f * (g.n_bins - 1);
     const float pix = (float)g.pixel_mm;
-    const float x = ((float)i - 0.5f * (float)(g.nx - 1)) * pix;
-    const float y = ((float)j - 0.5f * (float)(g.ny - 1)) * pix;
+    const float x = fmaf(-0.5f, (float)(g.nx - 1), (float)i) * pix;
+    float y[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) y[r] = fmaf(-0.5f, (float)(g.ny - 1), (float)(j0 + r * kBpTy)) * pix;
     const long long sstride = (long long)g.n_views * g.n_bins;
     const float* qs = q + s0 * sstride;
     const float kb = sid * inv_ds;
     const unsigned nb = (unsigned)g.n_bins;
-    float acc[kBpSlices];
+    float acc[R][S];
 #pragma unroll
-    for (int k = 0; k < kBpSlices; ++k) acc[k] = 0.f;
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < S; ++k) acc[r][k] = 0.f;
     for (int v = 0; v < g.n_views; ++v) {
         const float c = trig[2 * v], s = trig[2 * v + 1];
-        const float L = sid - fmaf(y, s, x * c);
-        const float invL = __fdividef(1.f, L);
-        const float bf = fmaf(fmaf(y, c, -(x * s)) * kb, invL, bc);
-        const float fl = floorf(bf);
-        const int b0 = (int)fl;
-        const float w1 = bf - fl;
-        // 1/U^2 = (sid / L)^2, sid^2 applied after the sum; bins off the
-        // detector take weight 0 (and read bin 0)
-        const float u2 = invL * invL;
-        const bool in0 = (unsigned)b0 < nb, in1 = (unsigned)(b0 + 1) < nb;
-        const float e0 = in0 ? (1.f - w1) * u2 : 0.f, e1 = in1 ? w1 * u2 : 0.f;
-        const int o0 = in0 ? b0 : 0, o1 = in1 ? b0 + 1 : 0;
+        const float xc = x * c, xs = x * s;
         const float* row = qs + (long long)v * g.n_bins;
 #pragma unroll
-        for (int k = 0; k < kBpSlices; ++k)
-            if (k < ns) {
-                const float* rk = row + k * sstride;
-                acc[k] = fmaf(e0, __ldg(rk + o0), fmaf(e1, __ldg(rk + o1), acc[k]));
-            }
+        for (int r = 0; r < R; ++r) {
+            const float L = sid - fmaf(y[r], s, xc);
+            const float invL = __fdividef(1.f, L);
+            const float bf = fmaf(fmaf(y[r], c, -xs) * kb, invL, bc);
+            const float fl = floorf(bf);
+            const int b0 = (int)fl;
+            const float w1 = bf - fl;
+            // 1/U^2 = (sid / L)^2, sid^2 applied after the sum; bins off the
+            // detector take weight 0 (and read bin 0)
+            const float u2 = invL * invL;
+            const float w0 = 1.f - w1;
+            const bool in0 = (unsigned)b0 < nb, in1 = (unsigned)(b0 + 1) < nb;
+            const float e0 = in0 ? w0 * u2 : 0.f, e1 = in1 ? w1 * u2 : 0.f;
+            const int o0 = in0 ? b0 : 0, o1 = in1 ? b0 + 1 : 0;
+#pragma unroll
+            for (int k = 0; k < S; ++k)
+                if (k < ns) {
+                    const float* rk = row + k * sstride;
+                    acc[r][k] = fmaf(e0, __ldg(rk + o0), fmaf(e1, __ldg(rk + o1), acc[r][k]));
+                }
+        }
     }
-    if (i >= g.nx || j >= g.ny) return;
+    if (i >= g.nx) return;
     const float scale = 0.5f * da * sid * sid;
 #pragma unroll
-    for (int k = 0; k < kBpSlices; ++k)
-        if (k < ns) img[(long long)(s0 + k) * g.nx * g.ny + (long long)j * g.nx + i] = acc[k] * scale;
+    for (int r = 0; r < R; ++r) {
+        const int j = j0 + r * kBpTy;
+        if (j >= g.ny) continue;
+#pragma unroll
+        for (int k = 0; k < S; ++k)
+            if (k < ns) img[(long long)(s0 + k) * g.nx * g.ny + (long long)j * g.nx + i] = acc[r][k] * scale;
+    }
 }
 
 // rho_e z with z = (Z / Z_w)^m (the photoelectric line-integral map)
@@ -348,14 +337,21 @@ int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float*
            long long* launches) {
     int rc = check_geom(g);
     if (rc) return rc;
-    if (g.n_views * 2 * sizeof(float) > 48 * 1024 ||
-        (size_t)fbp_filter_smem_floats(g.n_bins) * sizeof(float) > 48 * 1024 || n > 65535 * kBpSlices) {
+    if (g.n_views * 2 * sizeof(float) > 48 * 1024 || (3.5 * g.n_bins + 1) * sizeof(float) > 48 * 1024 ||
+        n > 65535) {
         set_error("too many views or bins");
         return RECON_EINVAL;
     }
-    k_fbp_filter<<<n * g.n_views, 256, fbp_filter_smem_floats(g.n_bins) * sizeof(float), st>>>(g, n, sino, scratch);
-    const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy - 1) / kBpTy, (n + kBpSlices - 1) / kBpSlices);
-    k_fbp_backproject<<<grid, dim3(kBpTx, kBpTy), 2 * g.n_views * sizeof(float), st>>>(g, n, scratch, img);
+    k_fbp_filter<<<n * g.n_views, 256, (3 * g.n_bins + (g.n_bins + 1) / 2) * sizeof(float), st>>>(g, n, sino,
+                                                                                                   scratch);
+    const size_t trig_bytes = 2 * g.n_views * sizeof(float);
+    if (n >= 2) {
+        const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy - 1) / kBpTy, (n + kBpGroup - 1) / kBpGroup);
+        k_fbp_backproject<kBpGroup, 1><<<grid, dim3(kBpTx, kBpTy), trig_bytes, st>>>(g, n, scratch, img);
+    } else {
+        const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + 2 * kBpTy - 1) / (2 * kBpTy), n);
+        k_fbp_backproject<1, 2><<<grid, dim3(kBpTx, kBpTy), trig_bytes, st>>>(g, n, scratch, img);
+    }
     if (launches) *launches += 2;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
