@@ -14,6 +14,7 @@
 //               normalised to 1 at mean(a^2)
 //   k_next_beta beta <- kappa beta, beta~ = tau beta
 // Sums for reductions are FP64 in a fixed order (deterministic).
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
@@ -2542,13 +2543,27 @@ __global__ void k_reset_state(int n, const SliceConst* C, SliceState* S) {
 }
 
 // --------------------------------------------------------------------------
-// Z = Z_w (Z^m / Z_w^m)^(1/m) in FP64 (Sec. II-D: Z is the m-th root of
-// Z^m); Z = 1 where z <= 0.
+// Z = Z_w z^(1/m), z = Z^m / Z_w^m (Sec. II-D: Z is the m-th root of Z^m);
+// Z = 1 where z <= 0.  Safeguarded FP64 Newton on phi(y) = m ln y - ln z,
+// y <- y (1 - (m ln y - ln z) / m), from the FP32 root.  That start is within
+// a few FP32 ulps (relative error e ~ 1e-7) and the step is quadratic (error
+// about e^2 / 2), so one step reaches FP64 working accuracy, far below the
+// rounding of the FP32 output.  Where z is outside the normal FP32 range the
+// start is not that close, and the closed form exp(ln z / m) is taken.
 // --------------------------------------------------------------------------
+
+__device__ __forceinline__ double mth_root_newton(double z, double m, double inv_m) {
+    const double lz = log(z);
+    const float zf = (float)z;
+    if (!(zf >= FLT_MIN) || isinf(zf)) return exp(lz * inv_m);
+    const double y0 = (double)powf(zf, (float)inv_m);
+    return y0 * (1.0 - (m * log(y0) - lz) * inv_m);
+}
 
 template <typename T>
 __global__ void k_extract(ItemList L, const SliceGeom* G, Ptrs<T> P, float* Z, float* rhoe, float* f1, float* f2,
-                          double zw, double inv_m) {
+                          double zw, double m) {
+    const double inv_m = 1.0 / m;
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
         const SliceGeom g = G[it.slice];
@@ -2559,7 +2574,7 @@ __global__ void k_extract(ItemList L, const SliceGeom* G, Ptrs<T> P, float* Z, f
             const long long e = g.ext_off + (long long)y * g.nx + x;
             if (Z) {
                 const double z = P.f[RECON_F_Z][d];
-                Z[e] = z > 0.0 ? (float)(zw * pow(z, inv_m)) : 1.0f;
+                Z[e] = z > 0.0 ? (float)(zw * mth_root_newton(z, m, inv_m)) : 1.0f;
             }
             if (rhoe) rhoe[e] = (float)P.f[RECON_F_RHO][d];
             if (f1) f1[e] = (float)P.f[RECON_F_F1][d];
@@ -3189,7 +3204,7 @@ int load_t(Ctx& c, const float* lo, const float* hi) {
 template <typename T>
 int extract_t(Ctx& c, float* Z, float* rhoe, float* f1, float* f2) {
     k_extract<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, ptrs<T>(c), Z,
-                                                                           rhoe, f1, f2, water_z(), 1.0 / z_exponent());
+                                                                           rhoe, f1, f2, water_z(), z_exponent());
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
@@ -4043,10 +4058,10 @@ int solver_extract_slots(Ctx& c, const std::vector<int>& slots, float* Z, float*
     const int grid = grid_for(c, L.n_items);
     if (c.precision == 1)
         k_extract<float><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, ptrs<float>(c), Z, rhoe, nullptr,
-                                                                 nullptr, water_z(), 1.0 / z_exponent());
+                                                                 nullptr, water_z(), z_exponent());
     else
         k_extract<double><<<grid, kStencilThreads, 0, c.stream>>>(L, c.d_geom, ptrs<double>(c), Z, rhoe, nullptr,
-                                                                  nullptr, water_z(), 1.0 / z_exponent());
+                                                                  nullptr, water_z(), z_exponent());
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;

@@ -229,3 +229,25 @@ def test_fft_solve_large_beta(rc):
     s.write("RHS_RHO", rhs32)
     s.op("SOLVE_RHO")
     close(s.read("RHO"), alg1.fft_solve(rhs32, 1.0, 1e5), 1e-5)
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_z_extraction_matches_closed_form(rc, precision):
+    """A6: Z = Z_w z^(1/m) from the stored z (Z = 1 where z <= 0), over z from
+    the FP32 subnormal range to 1e30 (the Newton start and its closed-form
+    safeguard), within one FP32 ulp of the FP64 closed form."""
+    nx, ny = 70, 9
+    s, _ = make(rc, nx, ny, precision=precision)
+    img = np.full((ny, nx), model.mu_mm(1.0, 7.45, 60.0), np.float32)
+    s.set_data(img, (img * 0.8).astype(np.float32))
+    rng = np.random.default_rng(11)
+    z = 10.0 ** rng.uniform(-6, 3, size=(ny, nx))
+    z.flat[:12] = [0.0, -1.0, -1e-30, 1e-40, 1e-38, 1.2e-38, 1e-20, 1.0, 1e10, 1e30, 3.4e38, 2.0 ** -126]
+    zs = as_stored(z, precision)
+    s.write("Z", zs)
+    Z = s.get_host()[0][0].astype(np.float64)
+    ref = model.z_from_ztilde(zs)
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    bad = np.abs(Z - ref) > ulp
+    assert not bad.any(), (zs[bad][:5], Z[bad][:5], ref[bad][:5])
+    assert np.all(Z[zs <= 0] == 1.0)
