@@ -133,20 +133,30 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
 
 // FBP step 1: cosine weight sid / sqrt(sid^2 + s^2) (s at the isocentre
 // plane) and Ram-Lak ramp h(0) = 1/(4 ds^2), h(odd m) = -1/(pi m ds)^2,
-// q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view).
+// q(n) = ds sum_k h(n - k) w(k).  One block per (slice, view).  A thread
+// forms the two outputs b, b + 1 (b even): the row sits at an odd offset in
+// shared memory, so for every odd m the taps b - m, b + 1 - m and b + m,
+// b + 1 + m are 8-byte aligned pairs, one vector load each; a warp's pairs are
+// consecutive, so the loads are free of bank conflicts.  Each output's sum
+// runs over m in increasing order as in a plain loop.
+__host__ __device__ inline int fbp_row_pad(int nb) { return nb | 1; }
+__host__ __device__ inline int fbp_row_len(int nb) { return 3 * nb + 4; }
+__host__ __device__ inline int fbp_filter_smem_floats(int nb) { return fbp_row_len(nb) + (nb + 1) / 2; }
+
 __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ sino, float* __restrict__ q) {
-    extern __shared__ float smem_f[];
+    extern __shared__ __align__(16) float smem_f[];
     const int nb = g.n_bins;
-    float* wrow = smem_f;          // weighted row, zero-padded by nb on both sides
-    float* hodd = smem_f + 3 * nb; // ds h(m) for odd m = 2t + 1
+    const int pad = fbp_row_pad(nb), len = fbp_row_len(nb);
+    float* wrow = smem_f;          // weighted row at the odd offset pad, zero-padded
+    float* hodd = smem_f + len;    // ds h(m) for odd m = 2t + 1
     const int sv = blockIdx.x;     // slice * n_views + view
     if (sv >= n * g.n_views) return;
     // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
     const float sid = (float)g.sid_mm;
     const float ds = (float)g.bin_mm * sid / (float)g.sdd_mm;
     const float* src = sino + (long long)sv * nb;
-    for (int b = threadIdx.x; b < 3 * nb; b += blockDim.x) {
-        const int k = b - nb;
+    for (int b = threadIdx.x; b < len; b += blockDim.x) {
+        const int k = b - pad;
         float v = 0.f;
         if (k >= 0 && k < nb) {
             const float s = ((float)k - 0.5f * (float)(nb - 1)) * ds;
@@ -161,12 +171,20 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
     }
     __syncthreads();
     const float h0 = 0.25f / ds;   // ds * 1/(4 ds^2)
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        float acc = 0.f;
-        const float* c = wrow + nb + b;
+    for (int b = 2 * threadIdx.x; b < nb; b += 2 * blockDim.x) {
+        float acc0 = 0.f, acc1 = 0.f;
+        const float* c = wrow + pad + b;   // odd index: c - m and c + m are even for odd m
         // odd offsets m = 2t + 1 on both sides (zero padding outside the row)
-        for (int t = 0; 2 * t + 1 < nb; ++t) acc = fmaf(hodd[t], c[-(2 * t + 1)] + c[2 * t + 1], acc);
-        q[(long long)sv * nb + b] = fmaf(h0, c[0], acc);
+        for (int t = 0; 2 * t + 1 < nb; ++t) {
+            const int m = 2 * t + 1;
+            const float h = hodd[t];
+            const float2 lf = *reinterpret_cast<const float2*>(c - m);
+            const float2 rt = *reinterpret_cast<const float2*>(c + m);
+            acc0 = fmaf(h, lf.x + rt.x, acc0);
+            acc1 = fmaf(h, lf.y + rt.y, acc1);
+        }
+        q[(long long)sv * nb + b] = fmaf(h0, c[0], acc0);
+        if (b + 1 < nb) q[(long long)sv * nb + b + 1] = fmaf(h0, c[1], acc1);
     }
 }
 
@@ -337,13 +355,12 @@ int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float*
            long long* launches) {
     int rc = check_geom(g);
     if (rc) return rc;
-    if (g.n_views * 2 * sizeof(float) > 48 * 1024 || (3.5 * g.n_bins + 1) * sizeof(float) > 48 * 1024 ||
-        n > 65535) {
+    if (g.n_views * 2 * sizeof(float) > 48 * 1024 ||
+        (size_t)fbp_filter_smem_floats(g.n_bins) * sizeof(float) > 48 * 1024 || n > 65535) {
         set_error("too many views or bins");
         return RECON_EINVAL;
     }
-    k_fbp_filter<<<n * g.n_views, 256, (3 * g.n_bins + (g.n_bins + 1) / 2) * sizeof(float), st>>>(g, n, sino,
-                                                                                                   scratch);
+    k_fbp_filter<<<n * g.n_views, 256, fbp_filter_smem_floats(g.n_bins) * sizeof(float), st>>>(g, n, sino, scratch);
     const size_t trig_bytes = 2 * g.n_views * sizeof(float);
     if (n >= 2) {
         const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy - 1) / kBpTy, (n + kBpGroup - 1) / kBpGroup);
