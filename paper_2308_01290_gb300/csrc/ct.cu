@@ -399,6 +399,8 @@ extern "C" int recon_fbp(const recon_geometry* geom, int32_t n, const float* sin
         set_error("recon_fbp: bad arguments");
         return RECON_EINVAL;
     }
+    // arguments are checked before any device call or allocation
+    if (int rc = check_geom(*geom)) return rc;
     float* scratch = nullptr;
     const size_t bytes = sizeof(float) * (size_t)n * geom->n_views * geom->n_bins;
     cudaError_t e = cudaMallocAsync((void**)&scratch, bytes, (cudaStream_t)stream);
@@ -424,8 +426,9 @@ extern "C" int recon_fbp_noalloc(const recon_geometry* geom, int32_t n, const fl
         set_error("recon_fbp_noalloc: bad arguments");
         return RECON_EINVAL;
     }
+    if (int rc = check_geom(*geom)) return rc;
     const long long need = (long long)n * geom->n_views * geom->n_bins;
-    if (geom->n_views < 1 || geom->n_bins < 1 || need > (long long)RECON_FBP_NOALLOC_MAX) {
+    if (need > (long long)RECON_FBP_NOALLOC_MAX) {
         set_error("recon_fbp_noalloc: n * n_views * n_bins exceeds RECON_FBP_NOALLOC_MAX floats of scratch");
         return RECON_EINVAL;
     }
@@ -455,6 +458,7 @@ extern "C" int recon_simulate(const recon_geometry* geom, const recon_params* pa
         set_error("recon_simulate: bad arguments");
         return RECON_EINVAL;
     }
+    if (int rc = check_geom(*geom)) return rc;
     const cudaStream_t st = (cudaStream_t)stream;
     const long long npx = (long long)n * geom->nx * geom->ny;
     const long long nrays = (long long)n * geom->n_views * geom->n_bins;
@@ -473,25 +477,32 @@ extern "C" int recon_simulate(const recon_geometry* geom, const recon_params* pa
     }
     float *rz = nullptr, *A1 = nullptr, *A2 = nullptr;
     double* dtab = nullptr;
-    RECON_CUDA(cudaMallocAsync((void**)&rz, sizeof(float) * npx, st));
-    RECON_CUDA(cudaMallocAsync((void**)&A1, sizeof(float) * nrays, st));
-    RECON_CUDA(cudaMallocAsync((void**)&A2, sizeof(float) * nrays, st));
-    RECON_CUDA(cudaMallocAsync((void**)&dtab, sizeof(double) * tab.size(), st));
-    RECON_CUDA(cudaMemcpyAsync(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st));
-    k_rho_z<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(npx, Z, rhoe, rz, (float)water_z(), (float)z_exponent());
-    int rc = ct_project(*geom, n, rz, A1, st, nullptr);
+    // on any failure the buffers already taken are released below
+    cudaError_t err = cudaMallocAsync((void**)&rz, sizeof(float) * npx, st);
+    if (err == cudaSuccess) err = cudaMallocAsync((void**)&A1, sizeof(float) * nrays, st);
+    if (err == cudaSuccess) err = cudaMallocAsync((void**)&A2, sizeof(float) * nrays, st);
+    if (err == cudaSuccess) err = cudaMallocAsync((void**)&dtab, sizeof(double) * tab.size(), st);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(dtab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) {
+        k_rho_z<<<(unsigned)((npx + 255) / 256), 256, 0, st>>>(npx, Z, rhoe, rz, (float)water_z(),
+                                                               (float)z_exponent());
+        err = cudaGetLastError();
+    }
+    int rc = err == cudaSuccess ? RECON_OK : cuda_fail(err, "recon_simulate");
+    if (!rc) rc = ct_project(*geom, n, rz, A1, st, nullptr);
     if (!rc) rc = ct_project(*geom, n, rhoe, A2, st, nullptr);
     if (!rc) {
         k_counts<<<(unsigned)((nrays + 255) / 256), 256, 0, st>>>(nrays, A1, A2, dtab, nbs[0], nbs[1], noise, i0,
                                                                   scale_per_mm(), sino_low, sino_high);
-        cudaError_t err = cudaGetLastError();
+        err = cudaGetLastError();
         if (err != cudaSuccess) rc = cuda_fail(err, "k_counts");
     }
     // the host table must outlive the async copy
     cudaStreamSynchronize(st);
-    cudaFreeAsync(rz, st);
-    cudaFreeAsync(A1, st);
-    cudaFreeAsync(A2, st);
-    cudaFreeAsync(dtab, st);
+    if (rz) cudaFreeAsync(rz, st);
+    if (A1) cudaFreeAsync(A1, st);
+    if (A2) cudaFreeAsync(A2, st);
+    if (dtab) cudaFreeAsync(dtab, st);
     return rc;
 }

@@ -76,3 +76,29 @@ def test_sinogram_domain_rejects_unsupported_configurations(rc):
     for geoms, params in bad:
         with pytest.raises(rc.ReconError):
             rc.Solver(geoms, params)
+
+
+def test_input_stage_rejects_bad_arguments_before_device_work(rc):
+    """recon_project / backproject / fbp / fbp_noalloc / simulate check their
+    arguments and the fan-beam geometry before any device call or
+    allocation, so each bad case returns RECON_EINVAL here without a GPU (the
+    buffer addresses are never touched)."""
+    from synthetic import phantoms as ph
+    acq = ph.acquisition("small", n=32)
+    good = dict(nx=acq.nx, ny=acq.ny, pixel_mm=acq.pixel_mm, n_views=acq.n_views, n_bins=acq.n_bins,
+                sid_mm=acq.sid_mm, sdd_mm=acq.sdd_mm, bin_mm=acq.bin_mm)
+    bad_geoms = [dict(good, n_views=0), dict(good, n_bins=0), dict(good, nx=0),
+                 dict(good, sdd_mm=acq.sid_mm),                            # detector on the source circle
+                 dict(good, pixel_mm=2.0 * acq.sid_mm),                    # image reaches the source
+                 dict(good, bin_mm=0.0)]
+    buf = 1 << 20   # an address that validation never dereferences
+    p = rc.default_params(low=acq.low, high=acq.high)
+    calls = [lambda g, n: rc.project(g, n, buf, buf), lambda g, n: rc.backproject(g, n, buf, buf),
+             lambda g, n: rc.fbp(g, n, buf, buf), lambda g, n: rc.fbp_noalloc(g, n, buf, buf),
+             lambda g, n: rc.simulate(g, p, n, buf, buf, None, 1e5, buf, buf)]
+    for call in calls:
+        for kw in bad_geoms:
+            with pytest.raises(rc.ReconError, match="invalid argument"):
+                call(rc.geometry(**kw), 1)
+        with pytest.raises(rc.ReconError, match="invalid argument"):
+            call(rc.geometry(**good), 0)
