@@ -31,6 +31,21 @@ bool same_geometry(const recon_geometry& a, const recon_geometry& b) {
            a.start_rad == b.start_rad && a.arc_rad == b.arc_rad;
 }
 
+void free_ctx(Ctx& c) {
+    solver_free_graph(c);
+    if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
+    for (cudaEvent_t e : c.graph_ev)
+        if (e) cudaEventDestroy(e);
+    c.graph_stream = nullptr;
+    for (void* p : c.allocations) cudaFree(p);
+    c.allocations.clear();
+    if (c.h_cg_pending) cudaFreeHost(c.h_cg_pending);
+    c.h_cg_pending = nullptr;
+}
+}  // namespace
+
+// Argument checks shared by the batch handle and the serving engine; they
+// touch no device state.
 int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
@@ -64,21 +79,12 @@ int check_geometry(const recon_geometry& g) {
         set_error("invalid fan-beam geometry");
         return RECON_EINVAL;
     }
+    if (g.n_views > 0 && 0.5 * g.pixel_mm * std::sqrt((double)g.nx * g.nx + (double)g.ny * g.ny) >= g.sid_mm) {
+        set_error("image reaches the source circle");
+        return RECON_EINVAL;
+    }
     return RECON_OK;
 }
-
-void free_ctx(Ctx& c) {
-    solver_free_graph(c);
-    if (c.graph_stream) cudaStreamDestroy(c.graph_stream);
-    for (cudaEvent_t e : c.graph_ev)
-        if (e) cudaEventDestroy(e);
-    c.graph_stream = nullptr;
-    for (void* p : c.allocations) cudaFree(p);
-    c.allocations.clear();
-    if (c.h_cg_pending) cudaFreeHost(c.h_cg_pending);
-    c.h_cg_pending = nullptr;
-}
-}  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 

@@ -10,6 +10,9 @@
 #include "ctx.h"
 
 namespace recon {
+int check_params(const recon_params& p);       // csrc/api.cu
+int check_geometry(const recon_geometry& g);   // csrc/api.cu
+
 namespace {
 
 double now_ms() {
@@ -136,6 +139,9 @@ int recon_submit(recon_server* s, const recon_request* r, uint64_t* ticket) {
         return RECON_EINVAL;
     }
     const recon_geometry& g = r->geom;
+    // a request is checked in full here, so a bad one never reaches a step shared with others
+    if (int rc = check_geometry(g)) return rc;
+    if (int rc = check_params(r->params)) return rc;
     if (g.nx < 1 || g.ny < 1 || g.nx > s->cfg.max_nx || g.ny > s->cfg.max_ny || !seven_smooth(g.nx) ||
         !seven_smooth(g.ny) || r->params.precision != s->cfg.precision || r->params.order != 0 ||
         r->params.domain != 0) {

@@ -102,3 +102,34 @@ def test_input_stage_rejects_bad_arguments_before_device_work(rc):
                 call(rc.geometry(**kw), 1)
         with pytest.raises(rc.ReconError, match="invalid argument"):
             call(rc.geometry(**good), 0)
+
+
+def bad_params(rc):
+    """Parameter sets that recon_init_batch and recon_submit must refuse."""
+    from synthetic import phantoms as ph
+    acq = ph.acquisition("small", n=32)
+    base = dict(low=acq.low, high=acq.high)
+    return [rc.default_params(**base, lam=-1.0), rc.default_params(**base, lam=0.0),
+            rc.default_params(**base, beta0=0.0), rc.default_params(**base, tau=-1.0),
+            rc.default_params(**base, iters=-1), rc.default_params(**base, cg_max_iters=-1),
+            rc.default_params(**base, cg_tol=-1.0), rc.default_params(**base, precision=2),
+            rc.default_params(**base, order=2), rc.default_params(**base, pcg_kernel=3),
+            rc.default_params(**base, e1_kev=50.0, e2_kev=50.0)]
+
+
+def test_batch_handle_rejects_bad_parameters_and_geometry(rc):
+    """recon_init_batch checks every slice's parameters and geometry before
+    any device work, so each bad case returns RECON_EINVAL without a GPU."""
+    from synthetic import phantoms as ph
+    acq = ph.acquisition("small", n=32)
+    g = rc.geometry(acq.nx, acq.ny)
+    for p in bad_params(rc):
+        with pytest.raises(rc.ReconError, match="invalid argument"):
+            rc.Solver(g, p)
+    p = rc.default_params(low=acq.low, high=acq.high)
+    reach = rc.geometry(acq.nx, acq.ny, 50.0, acq.n_views, acq.n_bins, acq.sid_mm, acq.sdd_mm, acq.bin_mm)
+    for geom in (rc.geometry(0, 8), rc.geometry(11, 8), rc.geometry(8, 8, 1.0, -1, 8), reach,
+                 rc.geometry(acq.nx, acq.ny, acq.pixel_mm, acq.n_views, acq.n_bins, acq.sid_mm, acq.sid_mm,
+                             acq.bin_mm)):
+        with pytest.raises(rc.ReconError, match="invalid argument"):
+            rc.Solver(geom, p)

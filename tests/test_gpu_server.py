@@ -97,3 +97,18 @@ def test_rejects_oversize_and_unknown(rc):
     with pytest.raises(rc.ReconError):
         srv.submit(g, p, L, H)
     assert rc.lib.recon_poll(srv.h, 12345, None, None, None) == -1   # RECON_EINVAL: unknown ticket
+
+
+def test_rejects_invalid_parameters_at_submission(rc):
+    """recon_submit checks a request's parameters and geometry as
+    recon_init_batch does, so a bad request is refused before it can join a
+    step that other requests share, and nothing is queued."""
+    srv = rc.Server(max_slots=1, max_nx=64, max_ny=64)
+    g, _, L, H = request(rc, 1, 64, 5, 1e-2)
+    acq = ph.acquisition("small")
+    base = dict(low=acq.low, high=acq.high)
+    for kw in (dict(lam=-1.0), dict(beta0=0.0), dict(tau=-1.0), dict(iters=-1), dict(cg_max_iters=-1),
+               dict(cg_tol=-1.0), dict(pcg_kernel=3), dict(e1_kev=50.0, e2_kev=50.0)):
+        with pytest.raises(rc.ReconError):
+            srv.submit(g, rc.default_params(**base, **kw), L, H)
+    assert srv.stats()["queued"] == 0
