@@ -273,8 +273,11 @@ int recon_step(recon_ctx* h, int32_t n_iters, recon_stats* stats) {
             const SliceState& x = st[s];
             o.k = x.k;
             o.cg_iters = x.cg_it;
+            // the beta factor of one iteration (none for a slice of zero iterations)
             const double kap = c.prm[s].kappa > 0 ? c.prm[s].kappa
-                                                 : std::pow(c.prm[s].beta_max / c.prm[s].beta0, 1.0 / c.prm[s].iters);
+                               : c.prm[s].iters > 0
+                                   ? std::pow(c.prm[s].beta_max / c.prm[s].beta0, 1.0 / c.prm[s].iters)
+                                   : 1.0;
             o.beta = n_iters > 0 ? x.beta / kap : x.beta;
             o.fid_low = x.stat[0];
             o.fid_high = x.stat[1];
