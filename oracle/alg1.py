@@ -35,7 +35,9 @@ of E(r); FFT solve = dense solve of the same periodic system; z solve = FFT
 solve when a^2 is constant, and = dense solve; every block update is the
 minimiser of its own subproblem (eq. obj_sub_f / rho / z) under random
 perturbations; a uniform material is a fixed point; noiseless uniform inputs
-recover (Z, rho_e) exactly.  The full multi-iteration trajectory on noisy
+recover (Z, rho_e) exactly.  The relaxed objective (eq. obj_unconstraint) is
+pinned to hand-computed values on 3 x 3 grids, to zero at an exact uniform
+material, and its f part to eq. obj_sub_f (tests/test_oracle_objective.py).  The full multi-iteration trajectory on noisy
 data has no independent pin beyond these (parity unpinned for whole runs).
 """
 from __future__ import annotations

@@ -22,9 +22,11 @@ fan-beam FBP.  Geometry (reading R14):
   1/U^2, U = (sid - x.(cos t, sin t)) / sid, linear interpolation, and a
   factor 1/2 for the full 360 degree scan.
 
-Pins: <A x, y> = <x, A^T y>; Joseph line integral of a uniform disc against the
-analytic chord 2 mu sqrt(R^2 - d^2); FBP of a uniform disc returns its value
-(tests/test_oracle_ct.py).
+Pins: <A x, y> = <x, A^T y>; Joseph line integrals of a Gaussian blob against
+their closed form; FBP of a uniform disc returns its value; the noiseless
+polyenergetic scan of a Gaussian blob of one material equals
+-ln sum_b w_b exp(-mu(E_b) chord) on the analytic chords, and the Kramers
+weights follow their law (tests/test_oracle_ct.py).
 """
 from __future__ import annotations
 
