@@ -266,8 +266,10 @@ int recon_fbp(const recon_geometry* geom, int32_t n, const float* sino, float* i
  * floats (8 MiB), which every GPU that loads the library holds until the
  * process exits; calls with n * n_views * n_bins above that return
  * RECON_EINVAL.  The first call on a device looks up the array's device
- * address (with that device current), so make that first call before any
- * stream capture.  Every call shares the one array: calls whose work
+ * address (with that device current) and keeps it for the life of the
+ * process, so make that first call before any stream capture; a device reset
+ * (cudaDeviceReset, or the primary context destroyed and created again)
+ * invalidates the kept address, so do not call this function after one.  Every call shares the one array: calls whose work
  * overlaps on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  Each call overwrites every scratch value it
  * reads, so nothing has to be cleared between calls. */

@@ -83,6 +83,9 @@ int check_geometry(const recon_geometry& g) {
         set_error("image reaches the source circle");
         return RECON_EINVAL;
     }
+    // sinogram inputs go through the FBP: its limits are checked here too,
+    // so a request that passes cannot fail later inside a shared step
+    if (g.n_views > 0) return ct_fbp_check(g, 1);
     return RECON_OK;
 }
 

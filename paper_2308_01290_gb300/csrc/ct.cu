@@ -351,15 +351,22 @@ int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img
     return ct_backproject_add(g, n, sino, img, g.nx, (long long)g.nx * g.ny, st, launches);
 }
 
-int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,
-           long long* launches) {
-    int rc = check_geom(g);
-    if (rc) return rc;
-    if (g.n_views * 2 * sizeof(float) > 48 * 1024 ||
-        (size_t)fbp_filter_smem_floats(g.n_bins) * sizeof(float) > 48 * 1024 || n > 65535) {
-        set_error("too many views or bins");
+int ct_fbp_check(const recon_geometry& g, int n) {
+    if (int rc = check_geom(g)) return rc;
+    // the filter keeps one weighted row and the odd ramp taps in shared
+    // memory, the backprojection the trigonometry of every view
+    if ((size_t)g.n_views * 2 * sizeof(float) > 48 * 1024 ||
+        (size_t)fbp_filter_smem_floats(g.n_bins) * sizeof(float) > 48 * 1024 || n < 1 || n > 65535 ||
+        (long long)n * g.n_views > 0x7fffffffLL) {
+        set_error("FBP: too many views or bins for the shared-memory tables, or too many slices");
         return RECON_EINVAL;
     }
+    return RECON_OK;
+}
+
+int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,
+           long long* launches) {
+    if (int rc = ct_fbp_check(g, n)) return rc;
     k_fbp_filter<<<n * g.n_views, 256, fbp_filter_smem_floats(g.n_bins) * sizeof(float), st>>>(g, n, sino, scratch);
     const size_t trig_bytes = 2 * g.n_views * sizeof(float);
     if (n >= 2) {
@@ -400,7 +407,7 @@ extern "C" int recon_fbp(const recon_geometry* geom, int32_t n, const float* sin
         return RECON_EINVAL;
     }
     // arguments are checked before any device call or allocation
-    if (int rc = check_geom(*geom)) return rc;
+    if (int rc = ct_fbp_check(*geom, n)) return rc;
     float* scratch = nullptr;
     const size_t bytes = sizeof(float) * (size_t)n * geom->n_views * geom->n_bins;
     cudaError_t e = cudaMallocAsync((void**)&scratch, bytes, (cudaStream_t)stream);
@@ -426,7 +433,7 @@ extern "C" int recon_fbp_noalloc(const recon_geometry* geom, int32_t n, const fl
         set_error("recon_fbp_noalloc: bad arguments");
         return RECON_EINVAL;
     }
-    if (int rc = check_geom(*geom)) return rc;
+    if (int rc = ct_fbp_check(*geom, n)) return rc;
     const long long need = (long long)n * geom->n_views * geom->n_bins;
     if (need > (long long)RECON_FBP_NOALLOC_MAX) {
         set_error("recon_fbp_noalloc: n * n_views * n_bins exceeds RECON_FBP_NOALLOC_MAX floats of scratch");

@@ -152,6 +152,9 @@ int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img
                    long long* launches);
 int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,
            long long* launches);
+// The checks ct_fbp makes before any launch (geometry, shared-memory tables of
+// the filter and the backprojection, slice count): RECON_OK or RECON_EINVAL.
+int ct_fbp_check(const recon_geometry& g, int n);
 
 // Records CUDA events around the launches of one kernel family when that
 // family is selected in Ctx::prof_mask.

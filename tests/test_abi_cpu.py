@@ -133,3 +133,31 @@ def test_batch_handle_rejects_bad_parameters_and_geometry(rc):
                              acq.bin_mm)):
         with pytest.raises(rc.ReconError, match="invalid argument"):
             rc.Solver(geom, p)
+
+
+def test_fbp_limits_checked_before_device_work(rc):
+    """Sinogram rows too long for the FBP's shared-memory tables (4000 bins)
+    or too many views for its trigonometry table are refused by every entry
+    point that reaches the FBP, before any device call: the input-stage
+    calls and a batch handle on sinogram inputs."""
+    from synthetic import phantoms as ph
+    acq = ph.acquisition("small", n=32)
+    buf = 1 << 20
+    for views, bins in ((40, 4000), (7000, 64)):
+        g = rc.geometry(acq.nx, acq.ny, acq.pixel_mm, views, bins, acq.sid_mm, acq.sdd_mm, 0.05)
+        for call in (lambda: rc.fbp(g, 1, buf, buf), lambda: rc.fbp_noalloc(g, 1, buf, buf)):
+            with pytest.raises(rc.ReconError, match="invalid argument"):
+                call()
+        with pytest.raises(rc.ReconError, match="invalid argument"):
+            rc.Solver(g, rc.default_params(low=acq.low, high=acq.high))
+
+
+def test_fbp_noalloc_limit_matches_header(rc):
+    """The binding's copy of RECON_FBP_NOALLOC_MAX equals the header's."""
+    src = open(os.path.join(ROOT, "include", "recon.h")).read()
+    m = re.search(r"#define RECON_FBP_NOALLOC_MAX \(([0-9 *]+)\)", src)
+    assert m is not None
+    val = 1
+    for f in m.group(1).split("*"):
+        val *= int(f)
+    assert rc.FBP_NOALLOC_MAX == val

@@ -112,3 +112,29 @@ def test_rejects_invalid_parameters_at_submission(rc):
         with pytest.raises(rc.ReconError):
             srv.submit(g, rc.default_params(**base, **kw), L, H)
     assert srv.stats()["queued"] == 0
+
+
+def test_rejects_sinogram_beyond_fbp_limits_and_keeps_stepping(rc):
+    """A sinogram request whose rows are too long for the FBP's shared-memory
+    tables (4000 bins) fits the slot's sinogram capacity, so only the FBP
+    limits can refuse it: recon_submit must do so, before it is queued,
+    while the solves in flight keep stepping to their results."""
+    acq = ph.acquisition("small", n=32)
+    srv = rc.Server(max_slots=2, max_nx=64, max_ny=64, max_views=64, max_bins=4000)
+    g, p, L, H = request(rc, 2, 64, 6, 1e-2)
+    t = srv.submit(g, p, L, H)
+    srv.step(2)
+    bad = rc.geometry(acq.nx, acq.ny, acq.pixel_mm, 40, 4000, acq.sid_mm, acq.sdd_mm, 0.05)
+    lo = np.zeros(40 * 4000, np.float32)
+    with pytest.raises(rc.ReconError):
+        srv.submit(bad, rc.default_params(low=acq.low, high=acq.high, iters=4), lo, lo)
+    assert srv.stats()["queued"] == 0
+    res = None
+    for _ in range(20):
+        srv.step(2)
+        res = srv.poll(t)
+        if res is not None:
+            break
+    assert res is not None and res[2].status == 0
+    Za, Ra = alone(rc, g, p, L, H)
+    assert np.array_equal(res[0], Za) and np.array_equal(res[1], Ra)

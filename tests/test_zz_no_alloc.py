@@ -4,10 +4,12 @@ start-up, or a service that reserves all its device memory up front).  It
 uses a fixed scratch array inside the library instead of allocating one.
 
 Checked through the C ABI against recon_fbp, which allocates its scratch:
-two calls in a row with different sinograms must give recon_fbp's images
-within the tolerance of the FBP parity test (1e-4 of the image's magnitude),
-and a request above the scratch size must be refused.  This file runs last
-(its name sorts last) and also passes alone in a fresh process."""
+the two run the same kernels on the same inputs, so two calls in a row with
+different sinograms must give recon_fbp's images bit for bit, both for a
+group of slices (the multi-slice backprojection) and for one slice (the
+single-slice one); a request above the scratch size must be refused.  This
+file runs last (its name sorts last) and also passes alone in a fresh
+process."""
 import numpy as np
 import pytest
 
@@ -23,16 +25,16 @@ def env():
     return recon, torch
 
 
-def test_fbp_noalloc_matches_fbp_twice(env):
+@pytest.mark.parametrize("n", [3, 1])
+def test_fbp_noalloc_matches_fbp_twice(env, n):
     rc, torch = env
     from synthetic import phantoms as ph
     acq = ph.acquisition("small")
     g = rc.geometry_from_acq(acq)
-    n = 3
     per = acq.n_views * acq.n_bins
     assert n * per <= rc.FBP_NOALLOC_MAX
     for call in range(2):
-        rng = np.random.default_rng(100 + call)
+        rng = np.random.default_rng(100 + 10 * n + call)
         sino = torch.from_numpy(rng.uniform(0.0, 4.0, size=n * per).astype(np.float32)).cuda()
         ref = torch.empty(n * acq.nx * acq.ny, device="cuda")
         out = torch.full_like(ref, float("nan"))
@@ -41,7 +43,7 @@ def test_fbp_noalloc_matches_fbp_twice(env):
         torch.cuda.synchronize()
         ref_h, out_h = ref.cpu().numpy(), out.cpu().numpy()
         assert np.isfinite(out_h).all()
-        assert np.abs(out_h - ref_h).max() <= 1e-4 * np.abs(ref_h).max(), call
+        assert np.array_equal(out_h, ref_h), (n, call, np.abs(out_h - ref_h).max())
 
 
 def test_fbp_noalloc_rejects_oversize(env):
