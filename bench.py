@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--workload", choices=["volume", "clinical", "uneven", "small", "serving"], default="volume")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: Poisson arrival rate (slices/s)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving leg of the default line")
+    ap.add_argument("--serving-requests", type=int, default=200, help="requests per rate of the serving leg")
     ap.add_argument("--graph", action="store_true",
                     help="run each iteration as one CUDA graph launch (roofline then from the profiling pass)")
     ap.add_argument("--domain", choices=["image", "sino"], default="image",
@@ -172,15 +173,13 @@ def read_traffic(kernel, alg_bytes_per_launch):
 # serving workload: Poisson arrivals into the continuous-batching engine
 # ---------------------------------------------------------------------------
 
-def serving_run(rc, torch, rate, n_req, seed, budget_bytes=150e9, steps_per_poll=4):
+def serving_requests(rc, torch, n_req, seed):
     """Requests of 256^2..512^2 slices (own seed, I0 log-uniform in [2e4, 2e5],
-    50..150 iterations) arrive as a Poisson process of ``rate`` slices/s;
-    returns latency percentiles (arrival -> result on the host) and
-    throughput."""
+    50..150 iterations, 720 x 736-scaled fan-beam sinograms simulated on the
+    GPU), as host arrays: (geometry, params, low, high, iterations)."""
     from synthetic import phantoms as ph
     rng = np.random.default_rng(seed)
     sizes = ph.uneven_sizes(seed, n_req)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     reqs = []
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
@@ -198,7 +197,22 @@ def serving_run(rc, torch, rate, n_req, seed, budget_bytes=150e9, steps_per_poll
                     torch.randn(2 * nr, device="cuda", generator=gen), acq.i0, lo, hi)
         reqs.append((g, p, lo.cpu().numpy(), hi.cpu().numpy(), acq.iters))
     torch.cuda.synchronize()
-    srv = rc.Server(max_slots=n_req, max_nx=512, max_ny=512, max_views=720, max_bins=736,
+    return reqs
+
+
+def poisson_arrivals(rate, n_req, seed):
+    return np.cumsum(np.random.default_rng(seed).exponential(1.0 / rate, size=n_req))
+
+
+def serving_run(rc, reqs, rate, seed, budget_bytes=150e9, max_slots=64, steps_per_poll=4):
+    """The requests arrive as a Poisson process of ``rate`` slices/s into the
+    continuous-batching engine (at most ``max_slots`` solves in flight,
+    admission gated by ``budget_bytes`` of HBM); returns latency percentiles
+    (arrival -> result on the host), throughput, and how often admission
+    waited for a slot or for the budget."""
+    n_req = len(reqs)
+    arrivals = poisson_arrivals(rate, n_req, seed)
+    srv = rc.Server(max_slots=max_slots, max_nx=512, max_ny=512, max_views=720, max_bins=736,
                     hbm_budget_bytes=budget_bytes)
     t0 = time.perf_counter()
     nxt = 0
@@ -206,6 +220,8 @@ def serving_run(rc, torch, rate, n_req, seed, budget_bytes=150e9, steps_per_poll
     lat = []
     done = 0
     iters_done = 0
+    waited_steps = 0
+    max_active = 0
     while done < n_req:
         now = time.perf_counter() - t0
         while nxt < n_req and arrivals[nxt] <= now:
@@ -213,6 +229,10 @@ def serving_run(rc, torch, rate, n_req, seed, budget_bytes=150e9, steps_per_poll
             tickets[srv.submit(g, p, lo, hi)] = (nxt, it)
             nxt += 1
         active = srv.step(steps_per_poll)
+        st = srv.stats()
+        max_active = max(max_active, st["active"])
+        if st["queued"] > 0:
+            waited_steps += 1
         t_now = time.perf_counter() - t0
         for t in list(tickets):
             r = srv.poll(t)
@@ -228,7 +248,65 @@ def serving_run(rc, torch, rate, n_req, seed, budget_bytes=150e9, steps_per_poll
     lat = np.array(lat)
     return dict(rate_slices_per_s=rate, requests=n_req, p50_ms=float(np.percentile(lat, 50)),
                 p99_ms=float(np.percentile(lat, 99)), throughput_slice_iters_per_s=iters_done / total,
-                wall_s=total, budget_gb=budget_bytes / 1e9)
+                wall_s=total, max_in_flight=max_active, steps_with_queue=waited_steps,
+                max_slots=max_slots, budget_gb=budget_bytes / 1e9)
+
+
+def fp64_service_times(rc, torch, reqs):
+    """Each request through the plain path, one solve at a time: an FP64
+    handle of its own geometry (created outside the timing), then FBP of its
+    host sinograms, its iterations and the maps back to the host, timed on
+    the host around the synchronous calls.  Returns seconds per request."""
+    out = []
+    for g, p, lo, hi, it in reqs:
+        p64 = rc.Params.from_buffer_copy(p)
+        p64.precision = 0
+        s = rc.Solver(g, p64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_data(lo, hi)
+        s.step(it)
+        s.get_host()
+        out.append(time.perf_counter() - t0)
+        s.close()
+    return np.array(out)
+
+
+def fifo_latencies(arrivals, service):
+    """Latency of each request through one server that takes requests in
+    arrival order, one at a time, each for its measured service time."""
+    lat = np.empty(len(arrivals))
+    free = 0.0
+    for k, (a, sv) in enumerate(zip(arrivals, service)):
+        start = max(a, free)
+        free = start + sv
+        lat[k] = free - a
+    return lat, free
+
+
+def serving_sweep(rc, torch, rates, n_req, seed):
+    """The config-5 serving measurement: one request stream, Poisson arrivals
+    at each rate, through the continuous-batching engine (FP32) and through
+    the plain FP64 path one solve at a time (its FIFO latencies from the
+    measured per-request service times and the same arrival times)."""
+    reqs = serving_requests(rc, torch, n_req, seed)
+    total_iters = sum(r[4] for r in reqs)
+    service = fp64_service_times(rc, torch, reqs)
+    table = []
+    for i, rate in enumerate(rates):
+        r = serving_run(rc, reqs, rate, seed + 1 + i)
+        arr = poisson_arrivals(rate, n_req, seed + 1 + i)
+        lat64, end64 = fifo_latencies(arr, service)
+        r["fp64_one_at_a_time"] = dict(p50_ms=float(np.percentile(lat64, 50) * 1000),
+                                       p99_ms=float(np.percentile(lat64, 99) * 1000),
+                                       throughput_slice_iters_per_s=total_iters / end64)
+        table.append(r)
+    return dict(requests=n_req, slice_iterations=int(total_iters),
+                fp64_service_ms=dict(mean=float(service.mean() * 1000), p50=float(np.median(service) * 1000),
+                                     total_s=float(service.sum())),
+                fp64_method="each request solved alone in FP64 (FBP + iterations + maps to host), its service "
+                            "time measured once; latencies of a one-at-a-time FIFO server on the same arrival times",
+                rates=table)
 
 
 # ---------------------------------------------------------------------------
@@ -414,15 +492,16 @@ def main():
     from paper_2308_01290_gb300 import recon as rc
 
     if args.workload == "serving":
-        r = serving_run(rc, torch, args.rate, args.slices or 64, 9000 + rank)
+        reqs = serving_requests(rc, torch, args.slices or 200, 9000 + rank)
+        r = serving_run(rc, reqs, args.rate, 9001 + rank)
         if rank == 0:
             line = dict(metric=METRIC, value=r["throughput_slice_iters_per_s"], unit="slice-iters/s", n_gpus=world,
                         steps=1, warmup=0, ms_per_step=1000.0 * r["wall_s"], higher_is_better=True, scaling="weak",
                         vs_baseline=None, dtype="f32", data="synthetic",
                         config=dict(workload=f"serving: Poisson arrivals at {args.rate:g} slices/s, 256^2..512^2, "
-                                             "I0 2e4..2e5, 50..150 iterations, 150 GB budget",
+                                             "I0 2e4..2e5, 50..150 iterations, 150 GB budget, 64 slots",
                                     requests=r["requests"]),
-                        latency_ms=dict(p50=r["p50_ms"], p99=r["p99_ms"]))
+                        latency_ms=dict(p50=r["p50_ms"], p99=r["p99_ms"]), serving=r)
             print(json.dumps(line), flush=True)
         return 0
     slices, iters, name = workload(args, rank)
@@ -556,30 +635,51 @@ def main():
 
     extra = {}
     if rank == 0 and not args.no_fp64 and args.domain == "image":
-        # plain FP64 path: same algorithm in double, one slice at a time
+        # plain FP64 path: the same algorithm in double, one 512^2 slice at a
+        # time, the same beta schedule and iteration count, and the same step
+        # boundaries as the line above (FBP of the device sinograms, the
+        # iterations, the maps to a device buffer)
         Zs, Rs, acq0 = slices[0]
         g0 = rc.geometry_from_acq(acq0)
-        it64 = min(iters, 20)
-        p64 = rc.default_params(low=acq0.low, high=acq0.high, iters=it64, precision=0)
+        p64 = rc.default_params(low=acq0.low, high=acq0.high, iters=iters, precision=0)
         s64 = rc.Solver(g0, p64)
         nr = acq0.n_views * acq0.n_bins
-        s64.set_data(sino_lo[:nr], sino_hi[:nr], on_device=True)
-        s64.step(2)
+        oZ = torch.empty(g0.nx * g0.ny, device="cuda")
+        oR = torch.empty(g0.nx * g0.ny, device="cuda")
+
+        def step64():
+            s64.set_data(sino_lo[:nr], sino_hi[:nr], on_device=True)
+            s64.step(iters)
+            s64.get(Z=oZ, rhoe=oR, on_device=True)
+
+        step64()
         torch.cuda.synchronize()
-        s64.set_data(sino_lo[:nr], sino_hi[:nr], on_device=True)
+        reps = 2
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        s64.step(it64)
+        for _ in range(reps):
+            step64()
         b.record()
         torch.cuda.synchronize()
-        v64 = it64 / (a.elapsed_time(b) / 1000.0)
-        extra["fp64_plain"] = dict(value=v64, unit="slice-iters/s",
-                                   sample=f"one {g0.nx}x{g0.ny} slice, {it64} iterations, precision FP64, "
-                                          "one slice per launch sequence")
+        v64 = reps * iters / (a.elapsed_time(b) / 1000.0)
+        s64.profile((1 << rc.KF_COUNT) - 1)
+        s64.profile_read()
+        step64()
+        prof64 = s64.profile_read()
+        s64.profile(0)
+        dom64 = max(prof64, key=lambda k: prof64[k][0])
+        t64, n64, b64 = prof64[dom64]
+        extra["fp64_plain"] = dict(
+            value=v64, unit="slice-iters/s", iters=iters, ratio_fp32_batched_over_fp64=value / v64,
+            sample=f"one {g0.nx}x{g0.ny} slice, {iters} iterations (the same beta schedule), precision FP64, one "
+                   f"slice per launch sequence, same step boundaries (FBP + iterations + maps out), mean of {reps}",
+            dominant_family=dict(kernel=dom64, share=t64 / sum(v[0] for v in prof64.values()),
+                                 achieved_gbs=b64 / (t64 / 1e3) / 1e9 if t64 > 0 else 0.0,
+                                 frac=(b64 / (t64 / 1e3) / 1e9) / read_peaks()["hbm_gbs"] if t64 > 0 else 0.0))
         s64.close()
     if rank == 0 and not args.no_serving and args.workload == "volume":
-        extra["serving"] = serving_run(rc, torch, args.rate, 48, 9000)
+        extra["serving"] = serving_sweep(rc, torch, (20.0, 50.0, 100.0, 200.0), args.serving_requests, 9000)
     cpu = None
     if rank == 0 and not args.no_cpu:
         big = slices[0][0].shape[1] >= 512

@@ -6,6 +6,7 @@ import hashlib
 import json
 import os
 
+import numpy as np
 import pytest
 
 import bench
@@ -56,3 +57,18 @@ def test_committed_traffic_record_is_well_formed():
     assert rec["algorithmic_bytes_per_launch"] == 160 * 512 * 512 * 4 * 29 // 4
     assert rec["dram_bytes_per_launch"] == rec["dram_read"] + rec["dram_write"]
     assert 0.5 < rec["dram_bytes_per_launch"] / rec["algorithmic_bytes_per_launch"] < 1.5
+
+
+def test_fifo_latencies_of_one_server():
+    """The one-at-a-time baseline of the serving leg: a request starts when it
+    arrives or when the previous one finishes, whichever is later."""
+    import bench
+    arr = np.array([0.0, 0.5, 0.6, 5.0])
+    svc = np.array([1.0, 1.0, 0.2, 0.5])
+    lat, end = bench.fifo_latencies(arr, svc)
+    # finishes: 1.0, 2.0, 2.2, 5.5
+    assert np.allclose(lat, [1.0, 1.5, 1.6, 0.5]) and end == 5.5
+    # Poisson arrival times are seeded and increasing
+    a = bench.poisson_arrivals(50.0, 200, 3)
+    assert np.all(np.diff(a) > 0) and np.array_equal(a, bench.poisson_arrivals(50.0, 200, 3))
+    assert 2.0 < a[-1] < 6.0
