@@ -3210,6 +3210,49 @@ int extract_t(Ctx& c, float* Z, float* rhoe, float* f1, float* f2) {
     return RECON_OK;
 }
 
+// Debug operator: q = [diag(a^2) + beta~ L] p for every slice, with p read
+// from CG_P0 and q written to CG_Q, by the kernel that forms q in that
+// slice's PCG (k_mg_pq on multigrid slices, k_pcg_inv on the others).  Each
+// slice is put in mid-solve state with beta_cg = 1, y = 0 and a zero
+// preconditioner spectrum, so both kernels form p = 0 + 1 * p_old exactly and
+// then q = M p.  The PCG scalars of the handle are left in that state.
+__global__ void k_zmv_state(int n, SliceState* S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    SliceState& st = S[s];
+    st.cg_it = 1;
+    st.cg_done = 0;
+    set_betacg(st, 1.0);
+}
+
+template <typename T>
+int op_z_matvec(Ctx& c) {
+    if (!c.cl_slices.empty()) {
+        set_error("recon_debug_op: the Z^m operator test needs the batched PCG (pcg_kernel 0 or 2)");
+        return RECON_EINVAL;
+    }
+    k_zmv_state<<<(c.n + 127) / 128, 128, 0, c.stream>>>(c.n, c.d_state);
+    c.launches += 1;
+    RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_CG_Y], 0, c.elem * (size_t)c.pool_elems, c.stream));
+    RECON_CUDA(cudaMemsetAsync(c.spec[0], 0, 2 * c.elem * (size_t)c.spec_elems, c.stream));
+    const Ptrs<T> P = ptrs<T>(c);
+    const bool mg = c.mg_max_lb > 0;
+    if (mg) {
+        const DevItemList& L0 = c.mg_tiles[0];
+        k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(L0.view(), c.d_geom,
+                                                                                              c.d_state, P, 0);
+        c.launches += 1;
+    }
+    const DevItemList& prow = mg ? c.pcg_rows : c.rows;
+    if (prow.n > 0) {
+        k_pcg_inv<T><<<grid_for(c, prow.n), kFftThreads, fft_smem_bytes<T>(c), c.stream>>>(
+            prow.view(), c.d_geom, c.d_state, P, static_cast<const cplx<T>*>(c.d_tw), fft_half_slots<T>(c), 0, 0);
+        c.launches += 1;
+    }
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
 template <typename T>
 int op_t(Ctx& c, int op) {
     switch (op) {
@@ -3224,6 +3267,7 @@ int op_t(Ctx& c, int op) {
         case RECON_OP_SOLVE_RHO: return fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2));
         case RECON_OP_SOLVE_Z: return op_solve_z<T>(c);
         case RECON_OP_NEXT_BETA: return op_next_beta<T>(c);
+        case RECON_OP_Z_MATVEC: return op_z_matvec<T>(c);
         default: set_error("unknown operator"); return RECON_EINVAL;
     }
 }

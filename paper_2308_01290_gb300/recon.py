@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "librecon.so")
 RECON_MAX_FILTERS = 4
 FIELDS = dict(F1=0, F2=1, RHO=2, Z=3, MUL=4, MUH=5, RHS_F1=6, RHS_F2=7, DIV_RHO=8, DIV_Z=9, RHS_RHO=10, A2=11,
               RHS_Z=12, CG_R=13, CG_P0=14, CG_P1=15, CG_Q=16, CG_Y=17, CG_R2=18)
-OPS = dict(INIT=0, THRESH_RHS=1, SOLVE_F=2, SYNTH=3, SOLVE_RHO=4, SOLVE_Z=5, NEXT_BETA=6)
+OPS = dict(INIT=0, THRESH_RHS=1, SOLVE_F=2, SYNTH=3, SOLVE_RHO=4, SOLVE_Z=5, NEXT_BETA=6, Z_MATVEC=7)
 
 
 class Geometry(C.Structure):

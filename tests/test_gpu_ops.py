@@ -251,3 +251,35 @@ def test_z_extraction_matches_closed_form(rc, precision):
     bad = np.abs(Z - ref) > ulp
     assert not bad.any(), (zs[bad][:5], Z[bad][:5], ref[bad][:5])
     assert np.all(Z[zs <= 0] == 1.0)
+
+
+@pytest.mark.parametrize("nx,ny,nb", [(63, 45, 1), (128, 128, 1), (512, 512, 4), (384, 320, 2), (96, 64, 1)])
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("beta0", [0.37, 1e3])
+def test_z_operator_matches_oracle(rc, nx, ny, nb, precision, beta0):
+    """The Z^m normal-equation operator q = [diag(a^2) + beta~ L] p (Alg. 1,
+    Z^m line, reading R5), element by element against the oracle's sparse
+    z_system, as the PCG forms it: on multigrid slices (128^2, 512^2,
+    384 x 320, 96 x 64) in k_mg_pq, on the 63 x 45 slice (FFT preconditioner)
+    in k_pcg_inv.  FP32 to 1e-5 of the magnitude of q, FP64 to 1e-12."""
+    if nb > 1 and precision == 0:
+        pytest.skip("FP64 path checked at the smaller sizes")
+    s, tab = make(rc, nx, ny, nb, precision, beta0=beta0)
+    imgs = [noisy_images(nx, ny, 3 + 5 * k) for k in range(nb)]
+    s.set_data(np.concatenate([i[0].ravel() for i in imgs]), np.concatenate([i[1].ravel() for i in imgs]))
+    bt = s.scalars()["beta_t"]
+    assert abs(bt / beta0 - 1) < 1e-12
+    ins = []
+    for k in range(nb):
+        a2 = as_stored(ph.random_field((ny, nx), 20 + k, 0.05, 3.0), precision)
+        p = as_stored(ph.random_field((ny, nx), 40 + k, -1.0, 1.0), precision)
+        s.write("A2", a2, k)
+        s.write("CG_P0", p, k)
+        ins.append((a2, p))
+    s.op("Z_MATVEC")
+    tol = 1e-5 if precision == 1 else 1e-12
+    for k in range(nb):
+        a2, p = ins[k]
+        ref = (alg1.z_system(a2, bt) @ p.ravel()).reshape(ny, nx)
+        close(s.read("CG_Q", k), ref, tol)
+        assert np.array_equal(s.read("CG_P1", k), p)   # p = 0 + 1 * p_old exactly
