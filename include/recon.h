@@ -334,9 +334,11 @@ int recon_debug_io(recon_ctx* ctx, int32_t field, int32_t slice, double* host, i
 #define RECON_OP_SOLVE_RHO 4   /* FFT solve of rho_e */
 #define RECON_OP_SOLVE_Z 5     /* PCG of Z^m */
 #define RECON_OP_NEXT_BETA 6   /* beta <- kappa beta, k <- k + 1 */
-#define RECON_OP_Z_MATVEC 7    /* q = [diag(a^2) + beta~ L] p (Alg. 1, Z^m line): p from CG_P0, q into CG_Q,
-                                  by the kernel that forms q inside each slice's PCG; leaves the PCG state
-                                  mid-solve */
+#define RECON_OP_Z_MATVEC 7    /* q = [diag(a^2) + beta~ L] p (Alg. 1, Z^m line): p from CG_P0, q into CG_Q
+                                  (and p into CG_P1), by the kernel that forms q inside each slice's PCG.
+                                  FP32 multigrid slices also run their update pass, which forms q again:
+                                  with alpha = 1 it leaves -q in CG_R and p in Z (CG_R2 cleared).  Leaves
+                                  the PCG state mid-solve */
 int recon_debug_op(recon_ctx* ctx, int32_t op);
 
 /* Per-slice scalars: out[0] beta, [1] beta~, [2] k, [3] mean a^2, [4] PCG

@@ -88,6 +88,8 @@ struct Ctx {
     int mg_block_smem = 0, mg_inv_smem = 0;
     void* mg_qinv = nullptr;                  // per slice: inverse of its coarsest operator (kMgCoarsePx^2)
     DevItemList pcg_rows, pcg_cols;           // row and column items of the slices on the FFT preconditioner
+    DevItemList mg_strips;                    // FP32: strip items of the fine level (k_mgs_*)
+    int mg_rb = 32;                           // rows a warp walks per strip item
     std::vector<SliceConst> hconst;
     // serving mode: every slot laid out at capacity; lists hold the active slots
     bool server_mode = false;

@@ -2083,6 +2083,10 @@ __global__ void __launch_bounds__(kStencilThreads, 4) k_mg_pq(ItemList L, const 
     pipeline_items(L, buf, make, issue, compute);
 }
 
+}  // namespace recon
+#include "mg_strip.cuh"
+namespace recon {
+
 // Sides of the in-block levels of a block level of bx x by pixels: halve while
 // both sides are even and the grid has more than kMgCoarsePx pixels.
 __host__ __device__ inline int mg_block_levels(int bx, int by, int* nx, int* ny) {
@@ -2777,11 +2781,52 @@ void mg_restrict_a2(Ctx& c, bool timed) {
 template <typename T, bool UPD>
 void mg_fwd(Ctx& c, int par, int rk, bool timed) {
     MaybeTimer t(c, KF_MG_FWD, timed);
-    const DevItemList& L = c.mg_tiles[0];
-    k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufFwd<T>), c.stream>>>(
-        L.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
-        mg_r<T>(c, rk ^ 1), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending);
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32: the register-streaming strip kernel over strips of the fine level
+        const DevItemList& S = c.mg_strips;
+        k_mgs_fwd<UPD><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
+            S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
+            mg_r<T>(c, rk ^ 1), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, c.mg_rb);
+    } else {
+        const DevItemList& L = c.mg_tiles[0];
+        k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufFwd<T>), c.stream>>>(
+            L.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
+            mg_r<T>(c, rk ^ 1), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending);
+    }
     c.launches += 1;
+}
+
+// Fine level of the cycle and the new direction: y (k_mgs_y / k_mg_y), then p
+// and p.q (k_mgs_pq / k_mg_pq).
+template <typename T>
+void mg_fine_tail(Ctx& c, int par, int rk, bool timed) {
+    T* pe = static_cast<T*>(c.mg_pool[2]);
+    if constexpr (std::is_same<T, float>::value) {
+        const DevItemList& S = c.mg_strips;
+        {
+            MaybeTimer t(c, KF_MG_Y, timed);
+            k_mgs_y<<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                S.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk), pe, c.mg_rb);
+        }
+        {
+            MaybeTimer t(c, KF_MG_PQ, timed);
+            k_mgs_pq<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                S.view(), c.d_geom, c.d_state, ptrs<T>(c), par, c.mg_rb);
+        }
+    } else {
+        const DevItemList& L0 = c.mg_tiles[0];
+        {
+            MaybeTimer t(c, KF_MG_Y, timed);
+            k_mg_y<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
+                L0.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk), pe);
+        }
+        {
+            MaybeTimer t(c, KF_MG_PQ, timed);
+            k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(
+                L0.view(), c.d_geom, c.d_state, ptrs<T>(c), par);
+        }
+    }
+    c.launches += 2;
 }
 
 // Rest of a multigrid PCG step for residual buffer rk: the V-cycle below the
@@ -2813,18 +2858,7 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
             c.launches += 1;
         }
     }
-    const DevItemList& L0 = c.mg_tiles[0];
-    {
-        MaybeTimer t(c, KF_MG_Y, timed);
-        k_mg_y<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
-            L0.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk), pe);
-    }
-    {
-        MaybeTimer t(c, KF_MG_PQ, timed);
-        k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(
-            L0.view(), c.d_geom, c.d_state, ptrs<T>(c), par);
-    }
-    c.launches += 2;
+    mg_fine_tail<T>(c, par, rk, timed);
 }
 
 template <typename T>
@@ -3225,6 +3259,13 @@ __global__ void k_zmv_state(int n, SliceState* S) {
     set_betacg(st, 1.0);
 }
 
+__global__ void k_zmv_alpha(int n, SliceState* S) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    S[s].cg_done = 0;
+    set_alpha(S[s], 1.0);
+}
+
 template <typename T>
 int op_z_matvec(Ctx& c) {
     if (!c.cl_slices.empty()) {
@@ -3238,10 +3279,26 @@ int op_z_matvec(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
     const bool mg = c.mg_max_lb > 0;
     if (mg) {
-        const DevItemList& L0 = c.mg_tiles[0];
-        k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(L0.view(), c.d_geom,
-                                                                                              c.d_state, P, 0);
-        c.launches += 1;
+        if constexpr (std::is_same<T, float>::value) {
+            // k_mgs_pq forms q for p.q (stored here); k_mgs_fwd forms it again for
+            // r' = r - alpha q: with alpha = 1, r = 0 and z = 0 it writes -q to
+            // CG_R and p to Z
+            RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_CG_R2], 0, c.elem * (size_t)c.pool_elems, c.stream));
+            RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_Z], 0, c.elem * (size_t)c.pool_elems, c.stream));
+            const DevItemList& S = c.mg_strips;
+            k_mgs_pq<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                S.view(), c.d_geom, c.d_state, P, 0, c.mg_rb);
+            k_zmv_alpha<<<(c.n + 127) / 128, 128, 0, c.stream>>>(c.n, c.d_state);
+            k_mgs_fwd<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
+                S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, P, 0, mg_r<T>(c, 1), mg_r<T>(c, 0),
+                static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, c.mg_rb);
+            c.launches += 3;
+        } else {
+            const DevItemList& L0 = c.mg_tiles[0];
+            k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(
+                L0.view(), c.d_geom, c.d_state, P, 0);
+            c.launches += 1;
+        }
     }
     const DevItemList& prow = mg ? c.pcg_rows : c.rows;
     if (prow.n > 0) {
@@ -3383,7 +3440,10 @@ void pcg_split_host(Ctx& c) {
 // (at most kMgBlockPx pixels); 0 when the slice takes the FFT preconditioner.
 // Each halving needs even sides, and the block level must halve on to at
 // most kMgCoarsePx pixels.
-int mg_tile_levels(int nx, int ny) {
+int mg_tile_levels(int nx, int ny, int precision) {
+    // the FP32 fine-level strip kernels take whole 16-byte vectors per lane and
+    // two lanes at least in a row's last strip
+    if (precision == 1 && nx % 8) return 0;
     int lb = 0;
     while ((long long)nx * ny > kMgBlockPx) {
         if (nx % 2 || ny % 2) return 0;
@@ -3415,6 +3475,29 @@ int mg_set_smem() {
 int fill_list(Ctx& c, DevItemList& L);
 int pcg_split_lists(Ctx& c);
 
+// Strip items of the fine level (k_mgs_*) of the slices that pass `take`:
+// 128-column strips, kStripWarps x mg_rb rows each, of every slice in
+// `slots` (every slice when empty).  Host lists only.
+template <typename F>
+void strip_items(Ctx& c, DevItemList& S, F take, const std::vector<int>& slots) {
+    S.h_items.clear();
+    S.h_lo.assign(c.n, 0);
+    S.h_cnt.assign(c.n, 0);
+    const int bh = kStripWarps * c.mg_rb;
+    auto add = [&](int s) {
+        S.h_lo[s] = (int)S.h_items.size();
+        if (!take(s)) return;
+        const SliceGeom& g = c.sg[s];
+        for (int y0 = 0; y0 < g.ny; y0 += bh)
+            for (int x0 = 0; x0 < g.nx; x0 += kStripW) S.h_items.push_back(Item{s, x0, y0, 0});
+        S.h_cnt[s] = (int)S.h_items.size() - S.h_lo[s];
+    };
+    if (slots.empty())
+        for (int s = 0; s < c.n; ++s) add(s);
+    else
+        for (int s : slots) add(s);
+}
+
 // Tiles of the multigrid levels 0 .. mg_max_lb - 1 of the given slots (a
 // slot's level l has tiles while mg_lb > l), uploaded.
 int mg_lists_for(Ctx& c, const std::vector<int>& slots) {
@@ -3434,6 +3517,10 @@ int mg_lists_for(Ctx& c, const std::vector<int>& slots) {
             T.h_cnt[s] = (int)T.h_items.size() - T.h_lo[s];
         }
         if ((rc = fill_list(c, T))) return rc;
+    }
+    if (c.precision == 1) {
+        strip_items(c, c.mg_strips, [&](int s) { return c.mg_lb[s] > 0; }, slots);
+        if ((rc = fill_list(c, c.mg_strips))) return rc;
     }
     return pcg_split_lists(c);
 }
@@ -3491,6 +3578,9 @@ int mg_setup_server(Ctx& c) {
         c.mg_tiles[l].h_cnt.assign(c.n, 0);
         if ((rc = upload_list(c, c.mg_tiles[l]))) return rc;
     }
+    c.mg_strips.h_lo.assign(c.n, 0);
+    c.mg_strips.h_cnt.assign(c.n, 0);
+    if ((rc = upload_list(c, c.mg_strips))) return rc;
     pcg_split_host(c);
     if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols))) return rc;
     return RECON_OK;
@@ -3504,7 +3594,7 @@ int mg_setup(Ctx& c) {
     if (c.prm[0].pcg_kernel == 2) return RECON_OK;
     for (int s = 0; s < c.n; ++s) {
         if (c.sg[s].cluster) continue;
-        c.mg_lb[s] = mg_tile_levels(c.sg[s].nx, c.sg[s].ny);
+        c.mg_lb[s] = mg_tile_levels(c.sg[s].nx, c.sg[s].ny, c.precision);
         c.mg_max_lb = c.mg_lb[s] > c.mg_max_lb ? c.mg_lb[s] : c.mg_max_lb;
     }
     if (c.mg_max_lb == 0) return RECON_OK;
@@ -3577,6 +3667,10 @@ int mg_setup(Ctx& c) {
             T.h_cnt[s] = (int)T.h_items.size() - T.h_lo[s];
         }
         if ((rc = upload_list(c, T))) return rc;
+    }
+    if (c.precision == 1) {
+        strip_items(c, c.mg_strips, [&](int s) { return c.mg_lb[s] > 0; }, std::vector<int>());
+        if ((rc = upload_list(c, c.mg_strips))) return rc;
     }
     // row and column items of the PCG on the slices that keep the FFT preconditioner
     pcg_split_host(c);
@@ -4039,7 +4133,7 @@ int solver_configure_slot(Ctx& c, int s, const recon_geometry& geo, const recon_
     c.hconst[s] = slice_const(p, c.tab[s]);
     if (c.mg_max_lb > 0) {
         // the request's multigrid levels inside the slot's capacity regions
-        const int lb = p.pcg_kernel == 2 ? 0 : mg_tile_levels(geo.nx, geo.ny);
+        const int lb = p.pcg_kernel == 2 ? 0 : mg_tile_levels(geo.nx, geo.ny, c.precision);
         c.mg_lb[s] = lb;
         for (int l = 1; l <= c.mg_max_lb; ++l) {
             SliceGeom& gl = c.mg_sg[l][s];

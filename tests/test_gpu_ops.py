@@ -260,8 +260,11 @@ def test_z_operator_matches_oracle(rc, nx, ny, nb, precision, beta0):
     """The Z^m normal-equation operator q = [diag(a^2) + beta~ L] p (Alg. 1,
     Z^m line, reading R5), element by element against the oracle's sparse
     z_system, as the PCG forms it: on multigrid slices (128^2, 512^2,
-    384 x 320, 96 x 64) in k_mg_pq, on the 63 x 45 slice (FFT preconditioner)
-    in k_pcg_inv.  FP32 to 1e-5 of the magnitude of q, FP64 to 1e-12."""
+    384 x 320, 96 x 64) in the direction pass (k_mgs_pq in FP32, k_mg_pq in
+    FP64), on the 63 x 45 slice (FFT preconditioner) in k_pcg_inv.  The FP32
+    multigrid update pass (k_mgs_fwd) forms q once more for r - alpha q; the
+    operator leaves -q of that pass in CG_R, which must equal the first q bit
+    for bit.  FP32 to 1e-5 of the magnitude of q, FP64 to 1e-12."""
     if nb > 1 and precision == 0:
         pytest.skip("FP64 path checked at the smaller sizes")
     s, tab = make(rc, nx, ny, nb, precision, beta0=beta0)
@@ -281,5 +284,8 @@ def test_z_operator_matches_oracle(rc, nx, ny, nb, precision, beta0):
     for k in range(nb):
         a2, p = ins[k]
         ref = (alg1.z_system(a2, bt) @ p.ravel()).reshape(ny, nx)
-        close(s.read("CG_Q", k), ref, tol)
+        q = s.read("CG_Q", k)
+        close(q, ref, tol)
         assert np.array_equal(s.read("CG_P1", k), p)   # p = 0 + 1 * p_old exactly
+        if precision == 1 and (nx, ny) != (63, 45):
+            assert np.array_equal(s.read("CG_R", k), -q)
