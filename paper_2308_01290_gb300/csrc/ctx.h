@@ -88,8 +88,9 @@ struct Ctx {
     int mg_block_smem = 0, mg_inv_smem = 0;
     void* mg_qinv = nullptr;                  // per slice: inverse of its coarsest operator (kMgCoarsePx^2)
     DevItemList pcg_rows, pcg_cols;           // row and column items of the slices on the FFT preconditioner
-    DevItemList mg_strips;                    // FP32: strip items of the fine level (k_mgs_*)
-    int mg_rb = 32;                           // rows a warp walks per strip item
+    std::vector<DevItemList> mg_strips;       // [l]: strip items of level l (k_mgs_*; FP32, width % 8 == 0)
+    std::vector<DevItemList> mg_tiles_rest;   // [l]: tile items of level l of the other slices (k_mg_down, k_mg_up)
+    int mg_rb = 32;                           // rows a warp walks per strip item on the fine level
     std::vector<SliceConst> hconst;
     // serving mode: every slot laid out at capacity; lists hold the active slots
     bool server_mode = false;

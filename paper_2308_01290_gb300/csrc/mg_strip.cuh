@@ -27,9 +27,13 @@
 //   k_mgs_fwd<UPD>  z += alpha p, r' = r - alpha q (q = M p), r'.r' and the
 //                   convergence test; pre-smoothing x1 = w r' / (a^2 + 4 bt)
 //                   and the 2x2-mean restriction of r' - M x1 to level 1
-//   k_mgs_y         x = w r / (a^2 + 4 bt) + e1 (prolonged), y = x + w (r -
+//   k_mgs_up<true>  x = w r / (a^2 + 4 bt) + e1 (prolonged), y = x + w (r -
 //                   M x) / (a^2 + 4 bt), r.y -> beta_cg
 //   k_mgs_pq        p = y + beta_cg p_old, q = M p, p.q -> alpha
+// The coarser tile levels l >= 1 whose width is a multiple of 8 run the same
+// kernels on their own grid (bt = beta~ / 4^l): k_mgs_fwd<false> is the
+// restriction of the level (pre-smoothing from zero, restricted residual),
+// k_mgs_up<false> the correction and post-smoothing (no reduction).
 #pragma once
 
 namespace recon {
@@ -161,8 +165,9 @@ __device__ __forceinline__ void strip_stream(int ta, int tb, FI issue, FC comput
 template <bool UPD>
 __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                               const SliceConst* C, SliceState* S, Ptrs<float> P,
-                                                              int par, const float* rin, float* rout, float* F1,
-                                                              int* pending, int rb) {
+                                                              int par, const float* rin, float* rout,
+                                                              const float* a2, float* F1, int* pending, int rb,
+                                                              int lvl) {
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -170,7 +175,6 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const 
     StripRing<4>& ring = reinterpret_cast<StripRing<4>*>(strip_dsm)[warp];
     float* z = P.f[RECON_F_Z];
     const float* p = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
-    const float* a2 = P.f[RECON_F_A2];
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
         const SliceState* sp = S + it.slice;
@@ -179,8 +183,8 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const 
         const SliceGeom* g1p = G1 + it.slice;
         const long long off1 = __ldg(&g1p->off);
         const int pitch1 = __ldg(&g1p->pitch);
-        account(P.acct, KF_MG_FWD, strip_item_px(s, it, rb) * (UPD ? 25 : 9));
-        const float bt = Sc<float>::beta_t(*sp), b4 = Sc<float>::b4(*sp);
+        account(P.acct, lvl ? KF_MG_LEVELS : KF_MG_FWD, strip_item_px(s, it, rb) * (UPD ? 25 : 9));
+        const float bt = mg_bt<float>(*sp, lvl), b4 = 4.f * bt;
         const float al = UPD ? Sc<float>::alpha(*sp) : 0.f;
         const int r0 = min(it.b + warp * rb, s.ny), r1 = min(r0 + rb, s.ny);
         const int es = s.es < 0 ? 0 : s.es;
@@ -323,17 +327,20 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const 
     }
 }
 
-// Fine level: y = B r (correction from level 1 and post-smoothing), r.y -> beta_cg.
-__global__ void __launch_bounds__(kStripThreads, 4) k_mgs_y(ItemList L, const SliceGeom* G, const SliceGeom* G1,
-                                                            SliceState* S, Ptrs<float> P, const float* r,
-                                                            const float* E1, int rb) {
+// Correction from level lvl + 1 and post-smoothing on level lvl: FINE (lvl
+// 0), y = B r into CG_Y and r.y -> beta_cg; else the level's correction e
+// into E (no reduction).  r: residual of the level, a2: its a^2.
+template <bool FINE>
+__global__ void __launch_bounds__(kStripThreads, 4) k_mgs_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                             SliceState* S, Ptrs<float> P, const float* r,
+                                                             const float* a2, const float* E1, float* out, int rb,
+                                                             int lvl) {
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // fields: 0 r, 1 a^2 (edge values), 2 e1 (.x, .y of the lane's vector: its two coarse cells; edge value)
     StripRing<3>& ring = reinterpret_cast<StripRing<3>*>(strip_dsm)[warp];
-    const float* a2 = P.f[RECON_F_A2];
-    float* y = P.f[RECON_F_CG_Y];
+    float* y = out;
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
         const SliceState* sp = S + it.slice;
@@ -342,8 +349,8 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_y(ItemList L, const Sl
         const SliceGeom* g1p = G1 + it.slice;
         const long long off1 = __ldg(&g1p->off);
         const int pitch1 = __ldg(&g1p->pitch);
-        account(P.acct, KF_MG_Y, strip_item_px(s, it, rb) * 13);
-        const float bt = Sc<float>::beta_t(*sp), b4 = Sc<float>::b4(*sp);
+        account(P.acct, FINE ? KF_MG_Y : KF_MG_LEVELS, strip_item_px(s, it, rb) * 13);
+        const float bt = mg_bt<float>(*sp, lvl), b4 = 4.f * bt;
         const int r0 = min(it.b + warp * rb, s.ny), r1 = min(r0 + rb, s.ny);
         const int es = s.es < 0 ? 0 : s.es;
         float acc = 0.f;
@@ -384,7 +391,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_y(ItemList L, const Sl
                     yv.w = __fadd_rn(xm1.w, jac(__fsub_rn(rm1.w, mx.w), am1.w, b4));
                     if (s.act) {
                         *reinterpret_cast<float4*>(y + strip_row(s, t - 1) + s.x) = yv;
-                        acc = dot4(rm1, yv, acc);
+                        if (FINE) acc = dot4(rm1, yv, acc);
                     }
                 }
                 xm2 = xm1;
@@ -395,14 +402,16 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_y(ItemList L, const Sl
             };
             strip_stream(r0 - 1, r1, issue, compute);
         }
-        const float part[1] = {acc};
-        double a[1];
-        block_sum_t<float, 1>(part, a, red);
-        double tot[1];
-        if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
-            SliceState& so = S[it.slice];
-            set_betacg(so, (so.cg_it == 0) ? 0.0 : tot[0] / so.ry);
-            so.ry = tot[0];
+        if (FINE) {
+            const float part[1] = {acc};
+            double a[1];
+            block_sum_t<float, 1>(part, a, red);
+            double tot[1];
+            if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
+                SliceState& so = S[it.slice];
+                set_betacg(so, (so.cg_it == 0) ? 0.0 : tot[0] / so.ry);
+                so.ry = tot[0];
+            }
         }
     }
 }

@@ -2758,6 +2758,13 @@ T* mg_r(Ctx& c, int k) {
     return field_t<T>(c, k ? RECON_F_CG_R2 : RECON_F_CG_R);
 }
 
+// Rows a warp walks per strip item on multigrid level l: mg_rb on the fine
+// level, halved per level (grids of a quarter of the pixels), at least 8.
+int strip_rows(const Ctx& c, int l) {
+    const int r = c.mg_rb >> l;
+    return r < 8 ? 8 : r;
+}
+
 // a^2 of every multigrid level from the fine a^2 (once per Z^m solve).
 template <typename T>
 void mg_restrict_a2(Ctx& c, bool timed) {
@@ -2783,10 +2790,11 @@ void mg_fwd(Ctx& c, int par, int rk, bool timed) {
     MaybeTimer t(c, KF_MG_FWD, timed);
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the register-streaming strip kernel over strips of the fine level
-        const DevItemList& S = c.mg_strips;
+        const DevItemList& S = c.mg_strips[0];
         k_mgs_fwd<UPD><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
             S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
-            mg_r<T>(c, rk ^ 1), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, c.mg_rb);
+            mg_r<T>(c, rk ^ 1), field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending,
+            strip_rows(c, 0), 0);
     } else {
         const DevItemList& L = c.mg_tiles[0];
         k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufFwd<T>), c.stream>>>(
@@ -2802,16 +2810,17 @@ template <typename T>
 void mg_fine_tail(Ctx& c, int par, int rk, bool timed) {
     T* pe = static_cast<T*>(c.mg_pool[2]);
     if constexpr (std::is_same<T, float>::value) {
-        const DevItemList& S = c.mg_strips;
+        const DevItemList& S = c.mg_strips[0];
         {
             MaybeTimer t(c, KF_MG_Y, timed);
-            k_mgs_y<<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
-                S.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk), pe, c.mg_rb);
+            k_mgs_up<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                S.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk),
+                field_t<T>(c, RECON_F_A2), pe, field_t<T>(c, RECON_F_CG_Y), strip_rows(c, 0), 0);
         }
         {
             MaybeTimer t(c, KF_MG_PQ, timed);
             k_mgs_pq<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
-                S.view(), c.d_geom, c.d_state, ptrs<T>(c), par, c.mg_rb);
+                S.view(), c.d_geom, c.d_state, ptrs<T>(c), par, strip_rows(c, 0));
         }
     } else {
         const DevItemList& L0 = c.mg_tiles[0];
@@ -2839,23 +2848,41 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
     {
         MaybeTimer t(c, KF_MG_LEVELS, timed);
         for (int l = 1; l < c.mg_max_lb; ++l) {
-            const DevItemList& L = c.mg_tiles[l];
-            k_mg_down<T><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
-                L.view(), c.d_mg_geom[l],
-                                                                             c.d_mg_geom[l + 1], c.d_state, pf, pa,
-                                                                             pf, c.d_acct);
-            c.launches += 1;
+            if constexpr (std::is_same<T, float>::value) {
+                const DevItemList& S = c.mg_strips[l];
+                if (S.n) {
+                    k_mgs_fwd<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
+                        S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_const, c.d_state, ptrs<T>(c), 0, pf,
+                        nullptr, pa, pf, c.d_cg_pending, strip_rows(c, l), l);
+                    c.launches += 1;
+                }
+            }
+            const DevItemList& L = c.mg_tiles_rest[l];
+            if (L.n) {
+                k_mg_down<T><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
+                    L.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_state, pf, pa, pf, c.d_acct);
+                c.launches += 1;
+            }
         }
         k_mg_block<T><<<c.n, kMgBlockThreads, c.mg_block_smem, c.stream>>>(
             c.d_mg_block, c.d_state, pf, pa, pe, static_cast<const T*>(c.mg_qinv), c.d_acct);
         c.launches += 1;
         for (int l = c.mg_max_lb - 1; l >= 1; --l) {
-            const DevItemList& L = c.mg_tiles[l];
-            k_mg_up<T><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
-                L.view(), c.d_mg_geom[l],
-                                                                           c.d_mg_geom[l + 1], c.d_state, pf, pa, pe,
-                                                                           pe, c.d_acct);
-            c.launches += 1;
+            if constexpr (std::is_same<T, float>::value) {
+                const DevItemList& S = c.mg_strips[l];
+                if (S.n) {
+                    k_mgs_up<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                        S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_state, ptrs<T>(c), pf, pa, pe, pe,
+                        strip_rows(c, l), l);
+                    c.launches += 1;
+                }
+            }
+            const DevItemList& L = c.mg_tiles_rest[l];
+            if (L.n) {
+                k_mg_up<T><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufHalo2<T>), c.stream>>>(
+                    L.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_state, pf, pa, pe, pe, c.d_acct);
+                c.launches += 1;
+            }
         }
     }
     mg_fine_tail<T>(c, par, rk, timed);
@@ -3285,13 +3312,13 @@ int op_z_matvec(Ctx& c) {
             // CG_R and p to Z
             RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_CG_R2], 0, c.elem * (size_t)c.pool_elems, c.stream));
             RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_Z], 0, c.elem * (size_t)c.pool_elems, c.stream));
-            const DevItemList& S = c.mg_strips;
+            const DevItemList& S = c.mg_strips[0];
             k_mgs_pq<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
-                S.view(), c.d_geom, c.d_state, P, 0, c.mg_rb);
+                S.view(), c.d_geom, c.d_state, P, 0, strip_rows(c, 0));
             k_zmv_alpha<<<(c.n + 127) / 128, 128, 0, c.stream>>>(c.n, c.d_state);
             k_mgs_fwd<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
                 S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, P, 0, mg_r<T>(c, 1), mg_r<T>(c, 0),
-                static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, c.mg_rb);
+                field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, strip_rows(c, 0), 0);
             c.launches += 3;
         } else {
             const DevItemList& L0 = c.mg_tiles[0];
@@ -3475,27 +3502,45 @@ int mg_set_smem() {
 int fill_list(Ctx& c, DevItemList& L);
 int pcg_split_lists(Ctx& c);
 
-// Strip items of the fine level (k_mgs_*) of the slices that pass `take`:
-// 128-column strips, kStripWarps x mg_rb rows each, of every slice in
-// `slots` (every slice when empty).  Host lists only.
-template <typename F>
-void strip_items(Ctx& c, DevItemList& S, F take, const std::vector<int>& slots) {
-    S.h_items.clear();
-    S.h_lo.assign(c.n, 0);
-    S.h_cnt.assign(c.n, 0);
-    const int bh = kStripWarps * c.mg_rb;
+// Multigrid level l of slice s runs on the strip kernels (FP32, width a
+// multiple of 8) rather than the tile kernels.
+bool mg_strip_level(const Ctx& c, int s, int l) {
+    return c.precision == 1 && c.mg_lb[s] > l && ((c.sg[s].nx >> l) % 8) == 0;
+}
+
+// Items of the multigrid level l of every slice in `slots` (every slice when
+// null): strips (128 columns, kStripWarps x strip_rows rows) where
+// mg_strip_level holds, and tiles (for the tile kernels) on the other slices
+// with that level.  Host lists only.
+void level_items(Ctx& c, int l, const std::vector<int>* slots) {
+    DevItemList& S = c.mg_strips[l];
+    DevItemList& T = c.mg_tiles_rest[l];
+    for (DevItemList* X : {&S, &T}) {
+        X->h_items.clear();
+        X->h_lo.assign(c.n, 0);
+        X->h_cnt.assign(c.n, 0);
+    }
+    const int bh = kStripWarps * strip_rows(c, l);
+    const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
     auto add = [&](int s) {
         S.h_lo[s] = (int)S.h_items.size();
-        if (!take(s)) return;
-        const SliceGeom& g = c.sg[s];
-        for (int y0 = 0; y0 < g.ny; y0 += bh)
-            for (int x0 = 0; x0 < g.nx; x0 += kStripW) S.h_items.push_back(Item{s, x0, y0, 0});
+        T.h_lo[s] = (int)T.h_items.size();
+        if (c.mg_lb[s] <= l) return;
+        const int nx = c.sg[s].nx >> l, ny = c.sg[s].ny >> l;
+        if (mg_strip_level(c, s, l)) {
+            for (int y0 = 0; y0 < ny; y0 += bh)
+                for (int x0 = 0; x0 < nx; x0 += kStripW) S.h_items.push_back(Item{s, x0, y0, 0});
+        } else {
+            for (int ty = 0; ty < ny; ty += th)
+                for (int tx = 0; tx < nx; tx += kTileW) T.h_items.push_back(Item{s, tx, ty, 0});
+        }
         S.h_cnt[s] = (int)S.h_items.size() - S.h_lo[s];
+        T.h_cnt[s] = (int)T.h_items.size() - T.h_lo[s];
     };
-    if (slots.empty())
+    if (!slots)
         for (int s = 0; s < c.n; ++s) add(s);
     else
-        for (int s : slots) add(s);
+        for (int s : *slots) add(s);
 }
 
 // Tiles of the multigrid levels 0 .. mg_max_lb - 1 of the given slots (a
@@ -3518,9 +3563,9 @@ int mg_lists_for(Ctx& c, const std::vector<int>& slots) {
         }
         if ((rc = fill_list(c, T))) return rc;
     }
-    if (c.precision == 1) {
-        strip_items(c, c.mg_strips, [&](int s) { return c.mg_lb[s] > 0; }, slots);
-        if ((rc = fill_list(c, c.mg_strips))) return rc;
+    for (int l = 0; l < c.mg_max_lb; ++l) {
+        level_items(c, l, &slots);
+        if ((rc = fill_list(c, c.mg_strips[l])) || (rc = fill_list(c, c.mg_tiles_rest[l]))) return rc;
     }
     return pcg_split_lists(c);
 }
@@ -3578,9 +3623,13 @@ int mg_setup_server(Ctx& c) {
         c.mg_tiles[l].h_cnt.assign(c.n, 0);
         if ((rc = upload_list(c, c.mg_tiles[l]))) return rc;
     }
-    c.mg_strips.h_lo.assign(c.n, 0);
-    c.mg_strips.h_cnt.assign(c.n, 0);
-    if ((rc = upload_list(c, c.mg_strips))) return rc;
+    c.mg_strips.assign(L, DevItemList{});
+    c.mg_tiles_rest.assign(L, DevItemList{});
+    for (int l = 0; l < L; ++l) {
+        const std::vector<int> none;
+        level_items(c, l, &none);
+        if ((rc = upload_list(c, c.mg_strips[l])) || (rc = upload_list(c, c.mg_tiles_rest[l]))) return rc;
+    }
     pcg_split_host(c);
     if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols))) return rc;
     return RECON_OK;
@@ -3668,9 +3717,11 @@ int mg_setup(Ctx& c) {
         }
         if ((rc = upload_list(c, T))) return rc;
     }
-    if (c.precision == 1) {
-        strip_items(c, c.mg_strips, [&](int s) { return c.mg_lb[s] > 0; }, std::vector<int>());
-        if ((rc = upload_list(c, c.mg_strips))) return rc;
+    c.mg_strips.assign(L, DevItemList{});
+    c.mg_tiles_rest.assign(L, DevItemList{});
+    for (int l = 0; l < L; ++l) {
+        level_items(c, l, nullptr);
+        if ((rc = upload_list(c, c.mg_strips[l])) || (rc = upload_list(c, c.mg_tiles_rest[l]))) return rc;
     }
     // row and column items of the PCG on the slices that keep the FFT preconditioner
     pcg_split_host(c);
