@@ -92,10 +92,9 @@ typedef struct recon_params {
     double cg_tol;                   /* relative residual of the Z^m PCG */
     double z_clip_max;               /* initial Z^m clipped to Z <= z_clip_max */
     double rho_air;                  /* initial Z^m set to water where rho_e < rho_air */
-    int32_t pcg_kernel;              /* Z^m solve.  0: batched kernels, multigrid-preconditioned PCG on slices
-                                        whose sides halve down to a small grid (below), FFT-preconditioned
-                                        elsewhere; 1: as 0, and cluster-resident where a slice fits;
-                                        2: batched kernels, FFT-preconditioned PCG on every slice */
+    int32_t pcg_kernel;              /* Z^m solve.  0: multigrid-preconditioned PCG on slices whose sides
+                                        halve down to a small grid (below), FFT-preconditioned elsewhere;
+                                        2: FFT-preconditioned PCG on every slice (1 is refused) */
     int32_t domain;                  /* data terms of the arms: 0 on the image pair (Sec. II-B, as printed);
                                         1 on the sinograms through the projector (below) */
 } recon_params;
@@ -109,7 +108,7 @@ typedef struct recon_params {
  * 2x2 means, corrections prolonged piecewise constant, beta~/4 per level),
  * an exact solve on the coarsest grid (its operator inverted once per Z^m
  * solve).  A slice takes the multigrid cycle
- * (pcg_kernel 0 or 1) when it has more than 4096 pixels and both sides stay
+ * (pcg_kernel 0) when it has more than 4096 pixels and both sides stay
  * even while it halves down to at most 4096 pixels and on to at most 64; the
  * choice is per slice, so a slice gives the same result alone and in a
  * batch. */
@@ -382,15 +381,14 @@ int64_t recon_kernel_launches(recon_ctx* ctx);
  * 4 synthesis, 5 PCG start (r = b - M z), and the three passes of a PCG
  * step: 6 update of z and r, convergence test and forward row transforms of
  * D^-1/2 r; 7 column transforms with the preconditioner's divide and r.y;
- * 8 inverse row transforms, new search direction p and q = M p.  9 the
- * cluster-resident PCG (whole Z^m solve of a slice per thread-block
- * cluster), 10 the CG of the sinogram-domain f updates (its pointwise,
- * stencil and preconditioner column passes), 11 projector and backprojector
- * inside the solve (domain 1); the multigrid-preconditioned PCG: 12 update of
- * z and r, convergence test and the first restriction, 13 fine-level
- * correction and smoothing with r.y, 14 new search direction p, q = M p and
- * p.q, 15 the coarse levels and the restriction of a^2; 16 other. */
-#define RECON_KF_COUNT 17
+ * 8 inverse row transforms, new search direction p and q = M p.  9 the CG of
+ * the sinogram-domain f updates (its pointwise, stencil and preconditioner
+ * column passes), 10 projector and backprojector inside the solve (domain
+ * 1); the multigrid-preconditioned PCG: 11 update of z and r, convergence
+ * test and the first restriction, 12 fine-level correction and smoothing
+ * with r.y, 13 new search direction p, q = M p and p.q, 14 the coarse levels
+ * and the restriction of a^2; 15 other. */
+#define RECON_KF_COUNT 16
 
 /* Time the launches of the kernel families whose bit is set in mask with
  * CUDA events on the handle's stream (0 = off).  Algorithmic bytes and launch

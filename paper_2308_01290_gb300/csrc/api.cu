@@ -49,7 +49,7 @@ void free_ctx(Ctx& c) {
 int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
-        (p.order != 0 && p.order != 1) || p.pcg_kernel < 0 || p.pcg_kernel > 2 ||
+        (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 2) ||
         (p.domain != 0 && p.domain != 1) || (p.domain == 1 && (p.precision != 1 || p.order != 0)) || !(p.e1_kev > 0) ||
         !(p.e2_kev > 0) || p.e1_kev == p.e2_kev) {
         set_error("invalid recon_params");
@@ -172,7 +172,6 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
     c.geo.assign(geoms, geoms + n);
     c.prm.assign(params, params + n);
     c.sino_input = geoms[0].n_views > 0;
-    c.use_cluster = params[0].pcg_kernel == 1;
     int rc = solver_setup(c);
     if (!rc && c.sino_input) {
         c.sino_off.resize(n);
@@ -495,10 +494,12 @@ int recon_profile_read(recon_ctx* h, double* ms, int64_t* launches, uint64_t* by
     return RECON_OK;
 }
 
+static_assert(KF_COUNT == RECON_KF_COUNT, "kernel families of the header and the solver");
+
 const char* recon_profile_name(int32_t f) {
     static const char* names[KF_COUNT] = {"thr_rhs",   "fft_rows_fwd", "fft_cols", "fft_rows_inv",
                                           "synth",     "pcg_start",    "pcg_fwd",  "pcg_cols",
-                                          "pcg_inv",   "pcg_cluster",  "fcg",      "project",
+                                          "pcg_inv",   "fcg",          "project",
                                           "mg_fwd",    "mg_y",         "mg_pq",    "mg_levels",
                                           "other"};
     return (f >= 0 && f < KF_COUNT) ? names[f] : "?";

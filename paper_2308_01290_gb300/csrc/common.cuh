@@ -34,7 +34,6 @@ struct SliceGeom {
     long long twx, twy;        // offsets of the twiddle tables exp(-2 pi i t/N) in the twiddle pool
     long long symx, symy;      // offsets of the tables 4 sin^2(pi t/N) in the symbol pool
     int rows_per_item, cols_per_item;
-    int cluster;               // 1: the Z^m solve of this slice runs in the cluster kernel
     float inv_n;               // 1 / (nx ny) rounded to float (spectral scale of the FP32 transforms)
     int lvl;                   // multigrid level of this grid (0: the slice's own grid)
 };
@@ -219,7 +218,6 @@ enum KFam {
     KF_PCG_FWD,
     KF_COLS_PRE,
     KF_PCG_INV,
-    KF_PCG_CLUSTER,
     KF_FCG,
     KF_PROJ,
     KF_MG_FWD,      // multigrid PCG: update, convergence test, first restriction

@@ -67,14 +67,6 @@ struct Ctx {
     long long fam_launches[KF_COUNT] = {};
     unsigned long long host_acct[KF_COUNT] = {};   // algorithmic bytes of launches accounted on the host
 
-    // cluster-resident PCG
-    std::vector<int> cl_slices;
-    int* d_cl_slices = nullptr;
-    int* d_cl_queue = nullptr;
-    int cl_smem_x = 0, cl_smem_s = 0, cl_max_clusters = 0;
-    size_t cl_bytes = 0;
-    bool use_cluster = true;
-
     DevItemList tiles, rows, cols;
     DevItemList tmp_tiles;       // per-slot operations of the serving engine
     // multigrid preconditioner of the Z^m PCG (slices with mg_lb > 0)

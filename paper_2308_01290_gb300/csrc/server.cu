@@ -95,7 +95,6 @@ int recon_server_create(const recon_server_config* cfg, void* stream, recon_serv
     c.server_mode = true;
     c.cap_nx = cfg->max_nx;
     c.cap_ny = cfg->max_ny;
-    c.use_cluster = false;
     recon_geometry g{};
     g.nx = cfg->max_nx;
     g.ny = cfg->max_ny;

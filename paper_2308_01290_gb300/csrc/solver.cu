@@ -23,7 +23,6 @@
 
 #include "ctx.h"
 #include "fft.cuh"
-#include "pcg_cluster.h"
 
 namespace recon {
 
@@ -1288,13 +1287,10 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_inv(ItemList
 // synthesis at E1/E2 from the new f, rho_e rhs, Z^m normal equations
 // --------------------------------------------------------------------------
 
-// REDUCE: also form mean(a^2) and ||rhs_z||^2 for the cluster-resident Z^m
-// solve; the batched PCG takes them from k_cg_init instead.
-template <typename T, bool REDUCE>
+template <typename T>
 __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const SliceGeom* G, const SliceConst* C,
                                                            SliceState* S, Ptrs<T> P) {
     constexpr int VN = TileDim<T>::VN;
-    __shared__ double red[2 * 32];
     __shared__ SliceGeom s_g;
     __shared__ SliceConst s_c;
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
@@ -1306,7 +1302,6 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
         const SliceGeom& g = s_g;
         const SliceConst& c = s_c;
         account(P.acct, KF_SYNTH, tile_px<T>(g, it) * 7 * (long long)sizeof(T));
-        T acc0 = T(0), acc1 = T(0);
         const T b00 = kc<T>(c, KC_B00), b10 = kc<T>(c, KC_B10), b01 = kc<T>(c, KC_B01), b11 = kc<T>(c, KC_B11);
         const T rr_ = kc<T>(c, KC_R), inv_crho = kc<T>(c, KC_INV_CRHO), inv_aw = kc<T>(c, KC_INV_AW);
         const T P1 = kc<T>(c, KC_P1), P2 = kc<T>(c, KC_P2), psi1 = kc<T>(c, KC_PSI1), psi2 = kc<T>(c, KC_PSI2);
@@ -1327,26 +1322,11 @@ __global__ void __launch_bounds__(kStencilThreads) k_synth(ItemList L, const Sli
                 orr.v[e] = rho_cf + dr.v[e];
                 oa2.v[e] = a * a;
                 orz.v[e] = a * b + dz.v[e];
-                if (REDUCE && e < cnt) {
-                    acc0 += oa2.v[e];
-                    acc1 = fma(orz.v[e], orz.v[e], acc1);
-                }
             }
             stv_n(P.f[RECON_F_RHS_RHO], d, orr, cnt);
             stv_n(P.f[RECON_F_A2], d, oa2, cnt);
             stv_n(P.f[RECON_F_RHS_Z], d, orz, cnt);
         });
-        if constexpr (REDUCE) {
-            const T part[2] = {acc0, acc1};
-            double acc[2];
-            block_sum_t<T, 2>(part, acc, red);
-            double tot[2];
-            if (item_reduce<2>(L, w, it.slice, acc, tot, red)) {
-                SliceState& so = S[it.slice];
-                set_abar2(so, tot[0] / ((double)g.nx * (double)g.ny));
-                so.bb = tot[1];
-            }
-        }
         __syncthreads();
     }
 }
@@ -1701,7 +1681,7 @@ __global__ void __launch_bounds__(kStencilThreads, 4) k_cg_init(ItemList L, cons
         PipeItem p;
         p.it = it;
         p.first = 0;
-        p.ok = __ldg(&S[it.slice].active) && !__ldg(&G[it.slice].cluster);
+        p.ok = __ldg(&S[it.slice].active);
         if (p.ok) p.g = tile_geo(G, it.slice);
         return p;
     };
@@ -2728,12 +2708,8 @@ int op_solve_f(Ctx& c) {
 template <typename T>
 int op_synth(Ctx& c) {
     FamTimer t(c, KF_SYNTH);
-    if (!c.cl_slices.empty())
-        k_synth<T, true><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
-                                                                                  c.d_const, c.d_state, ptrs<T>(c));
-    else
-        k_synth<T, false><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
-                                                                                   c.d_const, c.d_state, ptrs<T>(c));
+    k_synth<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+                                                                       c.d_state, ptrs<T>(c));
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
@@ -2891,11 +2867,6 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
 template <typename T>
 int op_solve_z(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
-    int rc;
-    if (!c.cl_slices.empty()) {
-        if ((rc = pcg_cluster_run(c))) return rc;
-        if ((int)c.cl_slices.size() == c.n) return RECON_OK;
-    }
     RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream));
     {
         FamTimer t0(c, KF_CG_INIT);
@@ -3295,10 +3266,6 @@ __global__ void k_zmv_alpha(int n, SliceState* S) {
 
 template <typename T>
 int op_z_matvec(Ctx& c) {
-    if (!c.cl_slices.empty()) {
-        set_error("recon_debug_op: the Z^m operator test needs the batched PCG (pcg_kernel 0 or 2)");
-        return RECON_EINVAL;
-    }
     k_zmv_state<<<(c.n + 127) / 128, 128, 0, c.stream>>>(c.n, c.d_state);
     c.launches += 1;
     RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_CG_Y], 0, c.elem * (size_t)c.pool_elems, c.stream));
@@ -3642,7 +3609,6 @@ int mg_setup(Ctx& c) {
     if (c.server_mode) return mg_setup_server(c);
     if (c.prm[0].pcg_kernel == 2) return RECON_OK;
     for (int s = 0; s < c.n; ++s) {
-        if (c.sg[s].cluster) continue;
         c.mg_lb[s] = mg_tile_levels(c.sg[s].nx, c.sg[s].ny, c.precision);
         c.mg_max_lb = c.mg_lb[s] > c.mg_max_lb ? c.mg_lb[s] : c.mg_max_lb;
     }
@@ -3892,7 +3858,6 @@ int solver_setup(Ctx& c) {
     if ((rc = alloc_dev(c, (void**)&c.d_acct, sizeof(unsigned long long) * KF_COUNT))) return rc;
     RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
     RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, sizeof(int)));
-    if (!c.server_mode && (rc = pcg_cluster_setup(c))) return rc;
     RECON_CUDA(cudaMemcpy(c.d_geom, c.sg.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
     if ((rc = mg_setup(c))) return rc;
     if (c.precision == 1)
@@ -4003,8 +3968,8 @@ void solver_free_graph(Ctx& c) {
 }
 
 int solver_set_graph(Ctx& c, bool on) {
-    if (on && (c.domain != 0 || c.use_cluster || c.server_mode)) {
-        set_error("graph capture needs domain 0, pcg_kernel 0 or 2 and a solve handle");
+    if (on && (c.domain != 0 || c.server_mode)) {
+        set_error("graph capture needs domain 0 and a solve handle");
         return RECON_EINVAL;
     }
     solver_free_graph(c);

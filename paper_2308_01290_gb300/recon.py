@@ -140,7 +140,7 @@ EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_
            "recon_set_autotune", "recon_tuning",
            "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name", "recon_server_create",
            "recon_submit", "recon_server_step", "recon_poll", "recon_server_stats", "recon_server_destroy")
-KF_COUNT = 17
+KF_COUNT = 16
 
 
 def _check(rc, what):

@@ -233,51 +233,6 @@ def test_invalid_sizes_rejected(rc):
         s.step(1)      # before set_data
 
 
-@pytest.mark.parametrize("shape", [(128, 128), (96, 160), (100, 70)])
-def test_cluster_pcg_matches_batched_pcg(rc, shape):
-    """The cluster-resident Z^m solve (one slice per thread-block cluster) and
-    the batched kernels solve the same normal equations, built by the oracle
-    from a noisy phantom: both reach the PCG tolerance and agree with the
-    oracle's exact solution."""
-    nx, ny = shape
-    acq = ph.acquisition("small")
-    tab = model.Tables(acq.low, acq.high)
-    P = ph.small_phantom(21, n=max(nx, ny))
-    Z, rho = P["Z"][:ny, :nx], P["rhoe"][:ny, :nx]
-    L = (model.mu_mm(rho, Z, 60.0) + 4e-4 * ph.normal_field((ny, nx), 22)).astype(np.float32)
-    H = (model.mu_mm(rho, Z, 90.0) + 4e-4 * ph.normal_field((ny, nx), 23)).astype(np.float32)
-    st = alg1.init_state(L.astype(np.float64) / model.S_MM, H.astype(np.float64) / model.S_MM, tab)
-    bt = 0.3
-    hv = alg1.thresholds(st, 1e-2 / bt)
-    m1, m2 = alg1.synthesize(st["f1"], st["f2"], tab)
-    a2, rz = alg1.z_terms(m1, m2, hv["zt"], bt, tab)
-    a2, rz, z0 = [np.asarray(v, np.float32).astype(np.float64) for v in (a2, rz, st["zt"])]
-    zx = alg1.z_solve(a2, rz, bt)
-    out = {}
-    for path in (1, 0):
-        p = rc.default_params(low=acq.low, high=acq.high, iters=50, pcg_kernel=path, beta0=bt)
-        s = rc.Solver(rc.geometry(nx, ny), p)
-        s.set_data(L, H)
-        s.write("A2", a2)
-        s.write("RHS_Z", rz)
-        s.write("Z", z0)
-        # the PCG reads mean(a^2) and ||rhs||^2 from the synthesis step: run it on
-        # oracle f and divergences so that they match a2 and rz above
-        s.write("F1", np.asarray(st["f1"], np.float32))
-        s.write("F2", np.asarray(st["f2"], np.float32))
-        s.write("DIV_Z", np.asarray(bt * alg1.adjoint_diff(*hv["zt"]), np.float32))
-        s.op("SYNTH")
-        s.write("A2", a2)
-        s.write("RHS_Z", rz)
-        s.op("SOLVE_Z")
-        z = s.read("Z")
-        res = np.linalg.norm(a2 * z + bt * alg1.laplacian(z) - rz) / np.linalg.norm(rz)
-        assert res < 3e-5, (path, res)
-        assert np.abs(z - zx).max() <= 1e-3 * np.abs(zx).max(), path
-        out[path] = z
-    assert np.abs(out[0] - out[1]).max() <= 2e-3 * np.abs(out[1]).max()
-
-
 @pytest.mark.parametrize("shape,precision", [((128, 128), 1), ((256, 192), 1), ((320, 320), 1), ((128, 128), 0)])
 def test_multigrid_pcg_matches_fft_pcg(rc, shape, precision):
     """The Z^m PCG with the multigrid V-cycle (pcg_kernel 0 on slices that
@@ -318,21 +273,6 @@ def test_multigrid_pcg_matches_fft_pcg(rc, shape, precision):
         assert np.abs(z - zx).max() <= 1e-3 * np.abs(zx).max(), path
         s.close()
     assert steps[0] < steps[2], steps
-
-
-def test_cluster_full_solve_matches_oracle(rc, small_case):
-    """Whole 128^2 solve with the cluster-resident Z^m solve (the default run
-    uses the batched kernels): within the final-map tolerance."""
-    c = small_case
-    acq = c["acq"]
-    p = rc.default_params(low=acq.low, high=acq.high, iters=acq.iters, pcg_kernel=1)
-    s = rc.Solver(rc.geometry(acq.nx, acq.ny), p)
-    s.set_data(c["muL"].astype(np.float32), c["muH"].astype(np.float32))
-    s.step(acq.iters)
-    Z, rho, _, _ = [x[0] for x in s.get_host()]
-    body = c["P"]["rhoe"] >= 0.1
-    r = report("cluster-pcg", Z, rho, c["ref"], body)
-    assert parity_ok(r), r
 
 
 def test_graph_iterations_equal_separate_launches(rc, small_case):
