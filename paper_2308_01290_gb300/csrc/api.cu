@@ -37,6 +37,13 @@ void free_ctx(Ctx& c) {
     for (cudaEvent_t e : c.graph_ev)
         if (e) cudaEventDestroy(e);
     c.graph_stream = nullptr;
+    if (c.side_stream) {
+        cudaStreamSynchronize(c.side_stream);
+        cudaStreamDestroy(c.side_stream);
+    }
+    for (cudaEvent_t e : c.side_ev)
+        if (e) cudaEventDestroy(e);
+    c.side_stream = nullptr;
     for (void* p : c.allocations) cudaFree(p);
     c.allocations.clear();
     if (c.h_cg_pending) cudaFreeHost(c.h_cg_pending);

@@ -94,6 +94,10 @@ struct Ctx {
     std::vector<std::pair<int, std::pair<long long, long long>>> tw_index;   // N -> (twiddle, symbol) offsets
     bool has_data = false;
     int cg_parity = 0;
+    // side stream of the rho_e FFT solve, which runs beside the Z^m PCG
+    // (ordered with `stream` by the two events)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t side_ev[2] = {nullptr, nullptr};
     // one iteration captured as a CUDA graph (recon_set_graph): the Z^m PCG
     // runs as a conditional WHILE node of two PCG steps per body
     bool graph_on = false;

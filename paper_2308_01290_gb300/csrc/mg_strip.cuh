@@ -1,15 +1,18 @@
 // Fine-level passes of the multigrid-preconditioned Z^m PCG for FP32 slices
 // (Alg. 1, Z^m line: [diag(a^2) + beta~ L] z = a b + beta~ div(h, v)),
 // written as register-streaming strip kernels.  Included by solver.cu after
-// the multigrid tile kernels, whose cycle (Jacobi weight, coarse grids,
-// restriction and prolongation) these passes share.
+// the multigrid tile kernels (the FP64 path), whose grids, restriction and
+// prolongation these kernels share.
 //
 // Work layout.  An item is one strip of kStripW = 128 columns (32 lanes of four
 // columns, 16-byte accesses) and kStripWarps x rb rows of one slice; warp w of
 // the block walks rows y0 + w rb .. y0 + (w + 1) rb - 1 from top to bottom.
 // * Horizontal neighbours come from the adjacent lanes by warp shuffles.  The
-//   column left of the strip (lane 0) and the column right of its last column
-//   (the last active lane) are fetched by those two lanes, with periodic wrap.
+//   four columns left of the strip (lane 0) and right of its last column (the
+//   last active lane) are fetched by those two lanes as a ghost vector, with
+//   periodic wrap; the edge lanes carry the values of the quantities the pass
+//   forms on the ghost columns they need (Row::g1..g3, nearest first), with
+//   the same rounding sequence as the lane that owns the column.
 // * Vertical neighbours are the rows above and below, kept in registers as the
 //   warp walks down the strip.
 // * Every row a warp reads arrives through a warp-private ring of
@@ -20,20 +23,31 @@
 // The slice width must be a multiple of 8 (every lane a whole 16-byte vector;
 // at least two active lanes in the last strip of a row).
 //
-// Per PCG step (rk: residual buffer, par: direction buffer), as in the tile
-// kernels but with q = M p no longer stored: k_mgs_fwd forms it again from p
-// on a two-pixel halo, and k_mgs_pq forms it only for p.q.  Both call the one
-// function m_op, so the two passes compute the same q bit for bit.
-//   k_mgs_fwd<UPD>  z += alpha p, r' = r - alpha q (q = M p), r'.r' and the
-//                   convergence test; pre-smoothing x1 = w r' / (a^2 + 4 bt)
-//                   and the 2x2-mean restriction of r' - M x1 to level 1
-//   k_mgs_up<true>  x = w r / (a^2 + 4 bt) + e1 (prolonged), y = x + w (r -
-//                   M x) / (a^2 + 4 bt), r.y -> beta_cg
-//   k_mgs_pq        p = y + beta_cg p_old, q = M p, p.q -> alpha
+// Smoothing.  The cycle takes two damped Jacobi sweeps (weight w = 0.8,
+// J f = w f / (a^2 + 4 bt)) before and after the coarse correction on every
+// strip level, as the in-block levels do:
+//   pre:  x1 = J f, x2 = x1 + J (f - M x1); restrict f - M x2
+//   post: x = x2 + P e, x' = x + J (f - M x), e_out = x' + J (f - M x')
+// x2 is formed again in the post-smoothing pass from the same f with the same
+// rounding sequence.  Two Jacobi sweeps from zero are a symmetric smoother
+// and the post-smoothing is its adjoint, so the cycle stays symmetric positive
+// definite as PCG needs.
+//
+// Per PCG step (rk: residual buffer, par: direction buffer), q = M p is not
+// stored: k_mgs_fwd forms it again from p on a three-pixel halo, and k_mgs_pq
+// forms it only for p.q.  Both call m_op, so the two passes form the same q
+// bit for bit.
+//   k_mgs_fwd<true>  z += alpha p, r' = r - alpha q, r'.r' and the
+//                    convergence test; pre-smoothing of r' and the 2x2-mean
+//                    restriction of r' - M x2 to level 1
+//   k_mgs_up<true>   y = B r (correction from level 1, post-smoothing), r.y
+//                    -> beta_cg
+//   k_mgs_pq         p = y + beta_cg p_old, q = M p, p.q -> alpha
 // The coarser tile levels l >= 1 whose width is a multiple of 8 run the same
 // kernels on their own grid (bt = beta~ / 4^l): k_mgs_fwd<false> is the
-// restriction of the level (pre-smoothing from zero, restricted residual),
-// k_mgs_up<false> the correction and post-smoothing (no reduction).
+// restriction of a level (pre-smoothing from zero, restricted residual; also
+// the fine level's first PCG step), k_mgs_up<false> its correction and
+// post-smoothing (no reduction).
 #pragma once
 
 namespace recon {
@@ -49,10 +63,11 @@ struct Lane {
     long long off;   // slice offset in the field pools
     int nx, ny, pitch;
     int x;           // first of the lane's four columns
-    int ex;          // this lane's edge column: lane 0 the column left of the strip, the last active lane the
-                     // column right of it (periodic)
-    int es;          // edge slot: 0 left, 1 right, -1 no edge
+    int gx;          // first column of this lane's ghost vector: lane 0 the four columns left of the strip, the
+                     // last active lane the four right of it (periodic)
+    int es;          // ghost slot: 0 left, 1 right, -1 no ghost
     bool act;        // x < nx
+    bool left;       // es == 0
 };
 
 __device__ __forceinline__ Lane strip_lane(const SliceGeom* G, const Item& it, int lane) {
@@ -67,7 +82,8 @@ __device__ __forceinline__ Lane strip_lane(const SliceGeom* G, const Item& it, i
     const int w = s.nx - it.a;
     const int last = w >= kStripW ? 31 : w / 4 - 1;   // >= 1 when nx % 8 == 0
     s.es = lane == 0 ? 0 : (lane == last ? 1 : -1);
-    s.ex = lane == 0 ? (it.a == 0 ? s.nx - 1 : it.a - 1) : (s.x + 4 == s.nx ? 0 : s.x + 4);
+    s.left = lane == 0;
+    s.gx = lane == 0 ? (it.a == 0 ? s.nx - 4 : it.a - 4) : (s.x + 4 == s.nx ? 0 : s.x + 4);
     return s;
 }
 
@@ -98,7 +114,12 @@ __device__ __forceinline__ float jac(float f, float a, float b4) {
 __device__ __forceinline__ float4 jac4(float4 f, float4 a, float b4) {
     return make_float4(jac(f.x, a.x, b4), jac(f.y, a.y, b4), jac(f.z, a.z, b4), jac(f.w, a.w, b4));
 }
-// Value at the column left of the lane's first column / right of its last.
+// One Jacobi sweep from x: x + J (f - m), m = M x.
+__device__ __forceinline__ float sweep(float x, float f, float m, float a, float b4) {
+    return __fadd_rn(x, jac(__fsub_rn(f, m), a, b4));
+}
+// Value at the column left of the lane's first column / right of its last
+// (e: the edge lane's nearest ghost value).
 __device__ __forceinline__ float from_left(const float4& v, float e, const Lane& s) {
     const float l = __shfl_up_sync(0xffffffffu, v.w, 1);
     return s.es == 0 ? e : l;
@@ -118,13 +139,54 @@ __device__ __forceinline__ float dot4(float4 a, float4 b, float acc) {
     return __fmaf_rn(a.w, b.w, acc);
 }
 
+// A row of one quantity as a lane holds it: its four columns, and in the two
+// edge lanes the values on the three ghost columns beyond the strip edge,
+// nearest first (other lanes carry unused values there).
+struct Row {
+    float4 v;
+    float g1, g2, g3;
+};
+
+// Row from a lane's vector and its ghost vector (left ghost: columns x0-4 ..
+// x0-1; right ghost: the four after the strip).
+__device__ __forceinline__ Row ld_row(const float4& v, const float4& g, const Lane& s) {
+    return Row{v, s.left ? g.w : g.x, s.left ? g.z : g.y, s.left ? g.y : g.z};
+}
+__device__ __forceinline__ Row jac_row(const Row& f, const Row& a, float b4) {
+    return Row{jac4(f.v, a.v, b4), jac(f.g1, a.g1, b4), jac(f.g2, a.g2, b4), jac(f.g3, a.g3, b4)};
+}
+// M c on a row (u, d: the rows above and below).  On the ghost columns the
+// neighbours are taken in the order of the owning lane (left neighbour first),
+// so the edge lane forms the owner's value bit for bit; valid one ghost column
+// less than c.
+__device__ __forceinline__ Row op_row(const Row& a, const Row& c, const Row& u, const Row& d, float bt,
+                                      const Lane& s) {
+    Row m;
+    m.v = m_op4(a.v, c.v, from_left(c.v, c.g1, s), from_right(c.v, c.g1, s), u.v, d.v, bt);
+    const float in = s.left ? c.v.x : c.v.w;   // the strip's own column next to the ghost
+    m.g1 = m_op(a.g1, c.g1, s.left ? c.g2 : in, s.left ? in : c.g2, u.g1, d.g1, bt);
+    m.g2 = m_op(a.g2, c.g2, s.left ? c.g3 : c.g1, s.left ? c.g1 : c.g3, u.g2, d.g2, bt);
+    m.g3 = 0.f;
+    return m;
+}
+// x + J (f - m) on a row.
+__device__ __forceinline__ Row sweep_row(const Row& x, const Row& f, const Row& m, const Row& a, float b4) {
+    Row o;
+    o.v = make_float4(sweep(x.v.x, f.v.x, m.v.x, a.v.x, b4), sweep(x.v.y, f.v.y, m.v.y, a.v.y, b4),
+                      sweep(x.v.z, f.v.z, m.v.z, a.v.z, b4), sweep(x.v.w, f.v.w, m.v.w, a.v.w, b4));
+    o.g1 = sweep(x.g1, f.g1, m.g1, a.g1, b4);
+    o.g2 = sweep(x.g2, f.g2, m.g2, a.g2, b4);
+    o.g3 = 0.f;
+    return o;
+}
+
 // Warp-private ring of NF fields: slot k holds one row of each field (the
-// lanes' vectors) and the two edge values of the row (slot e[k][f][0] left,
-// [1] right; a float2 for fields whose edge is a column pair).
+// lanes' vectors) and the two ghost vectors of the row (g[k][f][0] left,
+// [1] right).
 template <int NF>
 struct StripRing {
     float4 v[kStripDepth][NF][32];
-    float2 e[kStripDepth][NF][2];
+    float4 g[kStripDepth][NF][2];
 };
 
 template <int NF>
@@ -159,11 +221,27 @@ __device__ __forceinline__ void strip_stream(int ta, int tb, FI issue, FC comput
     __syncwarp();
 }
 
-// Fine level, start of a PCG step.  UPD: after the update with alpha; else the
-// first step (r from k_cg_init, no update).  r is read from rin and, updated,
-// written to rout: other items read the old r on their halo in the same launch.
+// Copies of one field of row offset ro into ring slot (k, f): the lane's
+// vector, and the ghost vector in the edge lanes.
+template <int NF>
+__device__ __forceinline__ void ring_copy(StripRing<NF>& ring, int k, int f, const float* src, long long ro,
+                                          const Lane& s, int lane) {
+    if (s.act) cp_async16(&ring.v[k][f][lane], src + ro + s.x);
+    if (s.es >= 0) cp_async16(&ring.g[k][f][s.es], src + ro + s.gx);
+}
+template <int NF>
+__device__ __forceinline__ Row ring_row(const StripRing<NF>& ring, int k, int f, const Lane& s, int lane) {
+    return ld_row(ring.v[k][f][lane], ring.g[k][f][s.es < 0 ? 0 : s.es], s);
+}
+
+// Start of a PCG step on the fine level (UPD: after the update with alpha),
+// or the restriction of a coarser tile level lvl (UPD false; also the fine
+// level's first step, r from k_cg_init).  The level's residual is read from
+// rin; with UPD the updated residual is written to rout (other items read the
+// old one on their halo in the same launch).  The pre-smoothed residual,
+// restricted as 2x2 means, goes to F1 on grid G1.
 template <bool UPD>
-__global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+__global__ void __launch_bounds__(kStripThreads, 3) k_mgs_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                               const SliceConst* C, SliceState* S, Ptrs<float> P,
                                                               int par, const float* rin, float* rout,
                                                               const float* a2, float* F1, int* pending, int rb,
@@ -171,7 +249,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const 
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // fields: 0 p (edge pair), 1 r, 2 a^2 (edge values), 3 z
+    // fields: 0 p, 1 r, 2 a^2, 3 z (lane vectors only)
     StripRing<4>& ring = reinterpret_cast<StripRing<4>*>(strip_dsm)[warp];
     float* z = P.f[RECON_F_Z];
     const float* p = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
@@ -187,124 +265,111 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const 
         const float bt = mg_bt<float>(*sp, lvl), b4 = 4.f * bt;
         const float al = UPD ? Sc<float>::alpha(*sp) : 0.f;
         const int r0 = min(it.b + warp * rb, s.ny), r1 = min(r0 + rb, s.ny);
-        const int es = s.es < 0 ? 0 : s.es;
-        const bool left = s.es == 0;
         float acc = 0.f;
-        // the restricted residual of rows (t - 1, t), t odd relative to r0
-        auto restrict_store = [&](const float4& e0, const float4& e1, int t) {
-            if (!s.act) return;
-            const float c0 = __fadd_rn(__fadd_rn(__fadd_rn(e0.x, e0.y), e1.x), e1.y);
-            const float c1 = __fadd_rn(__fadd_rn(__fadd_rn(e0.z, e0.w), e1.z), e1.w);
-            *reinterpret_cast<float2*>(F1 + off1 + (long long)(t >> 1) * pitch1 + (s.x >> 1)) =
-                make_float2(0.25f * c0, 0.25f * c1);
+        float4 res_prev = {};
+        // residual row w (of the restricted pair (w - 1, w) when w - r0 is odd)
+        auto restrict_row = [&](const float4& res, int wr) {
+            if ((wr - r0) & 1) {
+                if (s.act) {
+                    const float c0 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.x, res_prev.y), res.x), res.y);
+                    const float c1 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.z, res_prev.w), res.z), res.w);
+                    *reinterpret_cast<float2*>(F1 + off1 + (long long)(wr >> 1) * pitch1 + (s.x >> 1)) =
+                        make_float2(0.25f * c0, 0.25f * c1);
+                }
+            } else {
+                res_prev = res;
+            }
+        };
+        auto residual = [&](const Row& f, const Row& m) {
+            return make_float4(__fsub_rn(f.v.x, m.v.x), __fsub_rn(f.v.y, m.v.y), __fsub_rn(f.v.z, m.v.z),
+                               __fsub_rn(f.v.w, m.v.w));
         };
         if (r0 < r1) {
+            Row am1 = {}, am2 = {}, rm1 = {}, rm2 = {}, x1m1 = {}, x1m2 = {}, x2m1 = {}, x2m2 = {};
             if constexpr (UPD) {
-                // bundle t: p(t) for t in [r0-2, r1+1]; r, a^2 of row t-1 in [r0-1, r1]; z of row t-2 in [r0, r1-1]
+                // bundle t: p of row t in [r0-3, r1+2]; r, a^2 of row u = t-1 in [r0-2, r1+1]; z of u in [r0, r1)
                 auto issue = [&](int t, int k) {
-                    const long long ro = strip_row(s, t);
-                    if (s.act) cp_async16(&ring.v[k][0][lane], p + ro + s.x);
-                    if (s.es >= 0) cp_async_elem<8>(&ring.e[k][0][es], p + ro + (left ? s.ex - 1 : s.ex));
-                    if (t - 1 >= r0 - 1 && t - 1 <= r1) {
-                        const long long r1o = strip_row(s, t - 1);
-                        if (s.act) {
-                            cp_async16(&ring.v[k][1][lane], rin + r1o + s.x);
-                            cp_async16(&ring.v[k][2][lane], a2 + r1o + s.x);
-                        }
-                        if (s.es >= 0) {
-                            cp_async_elem<4>(&ring.e[k][1][es], rin + r1o + s.ex);
-                            cp_async_elem<4>(&ring.e[k][2][es], a2 + r1o + s.ex);
-                        }
+                    ring_copy(ring, k, 0, p, strip_row(s, t), s, lane);
+                    const int u = t - 1;
+                    if (u >= r0 - 2 && u <= r1 + 1) {
+                        const long long ro = strip_row(s, u);
+                        ring_copy(ring, k, 1, rin, ro, s, lane);
+                        ring_copy(ring, k, 2, a2, ro, s, lane);
+                        if (u >= r0 && u < r1 && s.act) cp_async16(&ring.v[k][3][lane], z + ro + s.x);
                     }
-                    if (t - 2 >= r0 && t - 2 < r1 && s.act)
-                        cp_async16(&ring.v[k][3][lane], z + strip_row(s, t - 2) + s.x);
                 };
-                float4 pm2 = {}, pm1 = {};      // p(t-2), p(t-1)
-                float2 em2 = {}, em1 = {};      // their edge pairs
-                float4 am2 = {};                // a^2(t-2)
-                float4 rm2 = {};                // r'(t-2)
-                float4 xm3 = {}, xm2 = {};      // x1(t-3), x1(t-2)
-                float xe2 = 0.f;                // edge value of x1(t-2)
-                float4 res_prev = {};           // residual of the even row of a pair
+                Row pm2 = {}, pm1 = {};   // p(t-2), p(t-1)
                 auto compute = [&](int t, int k) {
-                    const float4 pt = ring.v[k][0][lane];
-                    const float2 et = ring.e[k][0][es];
-                    if (t >= r0) {
-                        // q, r', x1 on row t-1
-                        const float4 r_ = ring.v[k][1][lane], a_ = ring.v[k][2][lane];
-                        const float re_ = ring.e[k][1][es].x, ae_ = ring.e[k][2][es].x;
-                        const float pc_e = left ? em1.y : em1.x;   // p(t-1) at the edge column
-                        const float pl = from_left(pm1, pc_e, s), pr = from_right(pm1, pc_e, s);
-                        const float4 q = m_op4(a_, pm1, pl, pr, pm2, pt, bt);
-                        // q at the edge column: neighbours in the same order as its own lane forms them
-                        const float ql = left ? em1.x : pm1.w, qr = left ? pm1.x : em1.y;
-                        const float qe = m_op(ae_, pc_e, ql, qr, left ? em2.y : em2.x, left ? et.y : et.x, bt);
-                        const float4 rn = fma4(-al, q, r_);
-                        const float rne = __fmaf_rn(-al, qe, re_);
-                        const float4 x1 = jac4(rn, a_, b4);
-                        const float x1e = jac(rne, ae_, b4);
-                        if (t >= r0 + 2) {
-                            // row t-2: residual, z and r' out, r'.r', restriction
-                            const float4 zt = ring.v[k][3][lane];
-                            const float xl = from_left(xm2, xe2, s), xr = from_right(xm2, xe2, s);
-                            const float4 mx = m_op4(am2, xm2, xl, xr, xm3, x1, bt);
-                            const float4 res = make_float4(__fsub_rn(rm2.x, mx.x), __fsub_rn(rm2.y, mx.y),
-                                                           __fsub_rn(rm2.z, mx.z), __fsub_rn(rm2.w, mx.w));
-                            if (s.act) {
-                                const long long ro = strip_row(s, t - 2) + s.x;
-                                *reinterpret_cast<float4*>(z + ro) = fma4(al, pm2, zt);
-                                *reinterpret_cast<float4*>(rout + ro) = rm2;
-                                acc = dot4(rm2, rm2, acc);
+                    const Row pt = ring_row(ring, k, 0, s, lane);
+                    if (t >= r0 - 1) {
+                        // row u = t-1: q = M p, r' = r - alpha q, x1 = J r' (and z += alpha p)
+                        const int u = t - 1;
+                        const Row au = ring_row(ring, k, 2, s, lane);
+                        const Row ru = ring_row(ring, k, 1, s, lane);
+                        const Row q = op_row(au, pm1, pm2, pt, bt, s);
+                        Row rn;
+                        rn.v = fma4(-al, q.v, ru.v);
+                        rn.g1 = __fmaf_rn(-al, q.g1, ru.g1);
+                        rn.g2 = __fmaf_rn(-al, q.g2, ru.g2);
+                        rn.g3 = 0.f;
+                        const Row x1 = jac_row(rn, au, b4);
+                        if (u >= r0 && u < r1 && s.act)
+                            *reinterpret_cast<float4*>(z + strip_row(s, u) + s.x) = fma4(al, pm1.v, ring.v[k][3][lane]);
+                        if (t >= r0 + 1) {
+                            // row v = t-2: second pre-smoothing sweep
+                            const Row x2 = sweep_row(x1m1, rm1, op_row(am1, x1m1, x1m2, x1, bt, s), am1, b4);
+                            if (t >= r0 + 3) {
+                                // row w = t-3: residual after pre-smoothing, r' out, r'.r', restriction
+                                const int wr = t - 3;
+                                const float4 res = residual(rm2, op_row(am2, x2m1, x2m2, x2, bt, s));
+                                if (s.act) {
+                                    *reinterpret_cast<float4*>(rout + strip_row(s, wr) + s.x) = rm2.v;
+                                    acc = dot4(rm2.v, rm2.v, acc);
+                                }
+                                restrict_row(res, wr);
                             }
-                            if ((t - 2 - r0) & 1) restrict_store(res_prev, res, t - 2);
-                            res_prev = res;
+                            x2m2 = x2m1;
+                            x2m1 = x2;
                         }
-                        xm3 = xm2;
-                        xm2 = x1;
-                        xe2 = x1e;
-                        rm2 = rn;
-                        am2 = a_;
+                        x1m2 = x1m1;
+                        x1m1 = x1;
+                        rm2 = rm1;
+                        rm1 = rn;
+                        am2 = am1;
+                        am1 = au;
                     }
                     pm2 = pm1;
-                    em2 = em1;
                     pm1 = pt;
-                    em1 = et;
                 };
-                strip_stream(r0 - 2, r1 + 1, issue, compute);
+                strip_stream(r0 - 3, r1 + 2, issue, compute);
             } else {
-                // bundle t: r, a^2 of row t in [r0-1, r1]
+                // bundle t: r, a^2 of row t in [r0-2, r1+1]
                 auto issue = [&](int t, int k) {
                     const long long ro = strip_row(s, t);
-                    if (s.act) {
-                        cp_async16(&ring.v[k][1][lane], rin + ro + s.x);
-                        cp_async16(&ring.v[k][2][lane], a2 + ro + s.x);
-                    }
-                    if (s.es >= 0) {
-                        cp_async_elem<4>(&ring.e[k][1][es], rin + ro + s.ex);
-                        cp_async_elem<4>(&ring.e[k][2][es], a2 + ro + s.ex);
-                    }
+                    ring_copy(ring, k, 1, rin, ro, s, lane);
+                    ring_copy(ring, k, 2, a2, ro, s, lane);
                 };
-                float4 rm1 = {}, am1 = {}, xm2 = {}, xm1 = {}, res_prev = {};
-                float xe1 = 0.f;
                 auto compute = [&](int t, int k) {
-                    const float4 r_ = ring.v[k][1][lane], a_ = ring.v[k][2][lane];
-                    const float4 x1 = jac4(r_, a_, b4);
-                    const float x1e = jac(ring.e[k][1][es].x, ring.e[k][2][es].x, b4);
-                    if (t >= r0 + 1) {
-                        const float xl = from_left(xm1, xe1, s), xr = from_right(xm1, xe1, s);
-                        const float4 mx = m_op4(am1, xm1, xl, xr, xm2, x1, bt);
-                        const float4 res = make_float4(__fsub_rn(rm1.x, mx.x), __fsub_rn(rm1.y, mx.y),
-                                                       __fsub_rn(rm1.z, mx.z), __fsub_rn(rm1.w, mx.w));
-                        if ((t - 1 - r0) & 1) restrict_store(res_prev, res, t - 1);
-                        res_prev = res;
+                    const Row rt = ring_row(ring, k, 1, s, lane), at = ring_row(ring, k, 2, s, lane);
+                    const Row x1 = jac_row(rt, at, b4);
+                    if (t >= r0) {
+                        // row v = t-1: second pre-smoothing sweep
+                        const Row x2 = sweep_row(x1m1, rm1, op_row(am1, x1m1, x1m2, x1, bt, s), am1, b4);
+                        if (t >= r0 + 2) {
+                            // row w = t-2: residual after pre-smoothing, restriction
+                            restrict_row(residual(rm2, op_row(am2, x2m1, x2m2, x2, bt, s)), t - 2);
+                        }
+                        x2m2 = x2m1;
+                        x2m1 = x2;
                     }
-                    xm2 = xm1;
-                    xm1 = x1;
-                    xe1 = x1e;
-                    rm1 = r_;
-                    am1 = a_;
+                    x1m2 = x1m1;
+                    x1m1 = x1;
+                    rm2 = rm1;
+                    rm1 = rt;
+                    am2 = am1;
+                    am1 = at;
                 };
-                strip_stream(r0 - 1, r1, issue, compute);
+                strip_stream(r0 - 2, r1 + 1, issue, compute);
             }
         }
         if (UPD) {
@@ -328,19 +393,19 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_fwd(ItemList L, const 
 }
 
 // Correction from level lvl + 1 and post-smoothing on level lvl: FINE (lvl
-// 0), y = B r into CG_Y and r.y -> beta_cg; else the level's correction e
-// into E (no reduction).  r: residual of the level, a2: its a^2.
+// 0), y = B r into `out` (CG_Y) and r.y -> beta_cg; else the level's
+// correction into `out` (no reduction).  r: residual of the level, a2: its
+// a^2, E1: the correction of level lvl + 1 on grid G1.
 template <bool FINE>
-__global__ void __launch_bounds__(kStripThreads, 4) k_mgs_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+__global__ void __launch_bounds__(kStripThreads, 3) k_mgs_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
                                                              SliceState* S, Ptrs<float> P, const float* r,
                                                              const float* a2, const float* E1, float* out, int rb,
                                                              int lvl) {
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // fields: 0 r, 1 a^2 (edge values), 2 e1 (.x, .y of the lane's vector: its two coarse cells; edge value)
+    // fields: 0 r, 1 a^2, 2 e1 (.x, .y: the lane's two coarse cells; ghost .x: the coarse cell next to the strip)
     StripRing<3>& ring = reinterpret_cast<StripRing<3>*>(strip_dsm)[warp];
-    float* y = out;
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
         const SliceState* sp = S + it.slice;
@@ -352,55 +417,65 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_up(ItemList L, const S
         account(P.acct, FINE ? KF_MG_Y : KF_MG_LEVELS, strip_item_px(s, it, rb) * 13);
         const float bt = mg_bt<float>(*sp, lvl), b4 = 4.f * bt;
         const int r0 = min(it.b + warp * rb, s.ny), r1 = min(r0 + rb, s.ny);
-        const int es = s.es < 0 ? 0 : s.es;
+        // the coarse cell next to the strip: the two ghost columns nearest the strip lie in it
+        const int ecx = (s.left ? s.gx + 3 : s.gx) >> 1;
         float acc = 0.f;
         if (r0 < r1) {
+            // bundle t: r, a^2 of row t in [r0-3, r1+2]; e1 under row u = t-1 in [r0-2, r1+1]
             auto issue = [&](int t, int k) {
-                const int yy = wrap_near(t, s.ny);
-                const long long ro = s.off + (long long)yy * s.pitch;
-                const long long co = off1 + (long long)(yy >> 1) * pitch1;
-                if (s.act) {
-                    cp_async16(&ring.v[k][0][lane], r + ro + s.x);
-                    cp_async16(&ring.v[k][1][lane], a2 + ro + s.x);
-                    cp_async_elem<8>(&ring.v[k][2][lane], E1 + co + (s.x >> 1));
-                }
-                if (s.es >= 0) {
-                    cp_async_elem<4>(&ring.e[k][0][es], r + ro + s.ex);
-                    cp_async_elem<4>(&ring.e[k][1][es], a2 + ro + s.ex);
-                    cp_async_elem<4>(&ring.e[k][2][es], E1 + co + (s.ex >> 1));
+                const long long ro = strip_row(s, t);
+                ring_copy(ring, k, 0, r, ro, s, lane);
+                ring_copy(ring, k, 1, a2, ro, s, lane);
+                const int u = t - 1;
+                if (u >= r0 - 2 && u <= r1 + 1) {
+                    const long long co = off1 + (long long)(wrap_near(u, s.ny) >> 1) * pitch1;
+                    if (s.act) cp_async_elem<8>(&ring.v[k][2][lane], E1 + co + (s.x >> 1));
+                    if (s.es >= 0) cp_async_elem<4>(&ring.g[k][2][s.es], E1 + co + ecx);
                 }
             };
-            float4 rm1 = {}, am1 = {}, xm2 = {}, xm1 = {};
-            float xe1 = 0.f;
+            Row rm1 = {}, rm2 = {}, rm3 = {}, am1 = {}, am2 = {}, am3 = {};
+            Row x1m1 = {}, x1m2 = {}, xm1 = {}, xm2 = {}, xpm1 = {}, xpm2 = {};
             auto compute = [&](int t, int k) {
-                const float4 r_ = ring.v[k][0][lane], a_ = ring.v[k][1][lane], e_ = ring.v[k][2][lane];
-                float4 x = jac4(r_, a_, b4);
-                x.x = __fadd_rn(x.x, e_.x);
-                x.y = __fadd_rn(x.y, e_.x);
-                x.z = __fadd_rn(x.z, e_.y);
-                x.w = __fadd_rn(x.w, e_.y);
-                const float xe = __fadd_rn(jac(ring.e[k][0][es].x, ring.e[k][1][es].x, b4), ring.e[k][2][es].x);
-                if (t >= r0 + 1) {
-                    // row t-1: post-smoothing, r.y, y out
-                    const float xl = from_left(xm1, xe1, s), xr = from_right(xm1, xe1, s);
-                    const float4 mx = m_op4(am1, xm1, xl, xr, xm2, x, bt);
-                    float4 yv;
-                    yv.x = __fadd_rn(xm1.x, jac(__fsub_rn(rm1.x, mx.x), am1.x, b4));
-                    yv.y = __fadd_rn(xm1.y, jac(__fsub_rn(rm1.y, mx.y), am1.y, b4));
-                    yv.z = __fadd_rn(xm1.z, jac(__fsub_rn(rm1.z, mx.z), am1.z, b4));
-                    yv.w = __fadd_rn(xm1.w, jac(__fsub_rn(rm1.w, mx.w), am1.w, b4));
-                    if (s.act) {
-                        *reinterpret_cast<float4*>(y + strip_row(s, t - 1) + s.x) = yv;
-                        if (FINE) acc = dot4(rm1, yv, acc);
+                const Row rt = ring_row(ring, k, 0, s, lane), at = ring_row(ring, k, 1, s, lane);
+                const Row x1 = jac_row(rt, at, b4);
+                if (t >= r0 - 1) {
+                    // row u = t-1: second pre-smoothing sweep, then the prolonged correction
+                    Row x = sweep_row(x1m1, rm1, op_row(am1, x1m1, x1m2, x1, bt, s), am1, b4);
+                    const float4 e = ring.v[k][2][lane];
+                    const float eg = ring.g[k][2][s.es < 0 ? 0 : s.es].x;
+                    x.v.x = __fadd_rn(x.v.x, e.x);
+                    x.v.y = __fadd_rn(x.v.y, e.x);
+                    x.v.z = __fadd_rn(x.v.z, e.y);
+                    x.v.w = __fadd_rn(x.v.w, e.y);
+                    x.g1 = __fadd_rn(x.g1, eg);
+                    x.g2 = __fadd_rn(x.g2, eg);
+                    if (t >= r0 + 1) {
+                        // row v = t-2: first post-smoothing sweep
+                        const Row xp = sweep_row(xm1, rm2, op_row(am2, xm1, xm2, x, bt, s), am2, b4);
+                        if (t >= r0 + 3) {
+                            // row w = t-3: second post-smoothing sweep, out (and r.y)
+                            const Row y = sweep_row(xpm1, rm3, op_row(am3, xpm1, xpm2, xp, bt, s), am3, b4);
+                            if (s.act) {
+                                *reinterpret_cast<float4*>(out + strip_row(s, t - 3) + s.x) = y.v;
+                                if (FINE) acc = dot4(rm3.v, y.v, acc);
+                            }
+                        }
+                        xpm2 = xpm1;
+                        xpm1 = xp;
                     }
+                    xm2 = xm1;
+                    xm1 = x;
                 }
-                xm2 = xm1;
-                xm1 = x;
-                xe1 = xe;
-                rm1 = r_;
-                am1 = a_;
+                x1m2 = x1m1;
+                x1m1 = x1;
+                rm3 = rm2;
+                rm2 = rm1;
+                rm1 = rt;
+                am3 = am2;
+                am2 = am1;
+                am1 = at;
             };
-            strip_stream(r0 - 1, r1, issue, compute);
+            strip_stream(r0 - 3, r1 + 2, issue, compute);
         }
         if (FINE) {
             const float part[1] = {acc};
@@ -425,7 +500,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_pq(ItemList L, const S
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // fields: 0 y, 1 p_old (edge values), 2 a^2
+    // fields: 0 y, 1 p_old, 2 a^2 (lane vectors only)
     StripRing<3>& ring = reinterpret_cast<StripRing<3>*>(strip_dsm)[warp];
     const float* yf = P.f[RECON_F_CG_Y];
     const float* pold = P.f[par ? RECON_F_CG_P1 : RECON_F_CG_P0];
@@ -441,45 +516,36 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgs_pq(ItemList L, const S
         account(P.acct, KF_MG_PQ, strip_item_px(s, it, rb) * (first ? 12 : 16));
         const float bc = first ? 0.f : Sc<float>::betacg(*sp), bt = Sc<float>::beta_t(*sp);
         const int r0 = min(it.b + warp * rb, s.ny), r1 = min(r0 + rb, s.ny);
-        const int es = s.es < 0 ? 0 : s.es;
         float acc = 0.f;
         if (r0 < r1) {
             // bundle t: y, p_old of row t in [r0-1, r1]; a^2 of row t-1 in [r0, r1-1]
             auto issue = [&](int t, int k) {
                 const long long ro = strip_row(s, t);
-                if (s.act) {
-                    cp_async16(&ring.v[k][0][lane], yf + ro + s.x);
-                    if (!first) cp_async16(&ring.v[k][1][lane], pold + ro + s.x);
-                    if (t - 1 >= r0 && t - 1 < r1) cp_async16(&ring.v[k][2][lane], a2 + strip_row(s, t - 1) + s.x);
-                }
-                if (s.es >= 0) {
-                    cp_async_elem<4>(&ring.e[k][0][es], yf + ro + s.ex);
-                    if (!first) cp_async_elem<4>(&ring.e[k][1][es], pold + ro + s.ex);
-                }
+                ring_copy(ring, k, 0, yf, ro, s, lane);
+                if (!first) ring_copy(ring, k, 1, pold, ro, s, lane);
+                if (t - 1 >= r0 && t - 1 < r1 && s.act) cp_async16(&ring.v[k][2][lane], a2 + strip_row(s, t - 1) + s.x);
             };
-            float4 pm2 = {}, pm1 = {};
-            float em1 = 0.f;
+            Row pm2 = {}, pm1 = {};
             auto compute = [&](int t, int k) {
-                float4 pt = ring.v[k][0][lane];
-                float et = ring.e[k][0][es].x;
+                Row pt = ring_row(ring, k, 0, s, lane);
                 if (!first) {
-                    pt = fma4(bc, ring.v[k][1][lane], pt);
-                    et = __fmaf_rn(bc, ring.e[k][1][es].x, et);
+                    const Row po = ring_row(ring, k, 1, s, lane);
+                    pt.v = fma4(bc, po.v, pt.v);
+                    pt.g1 = __fmaf_rn(bc, po.g1, pt.g1);
                 }
-                if (t >= r0 && t < r1 && s.act) *reinterpret_cast<float4*>(pnew + strip_row(s, t) + s.x) = pt;
+                if (t >= r0 && t < r1 && s.act) *reinterpret_cast<float4*>(pnew + strip_row(s, t) + s.x) = pt.v;
                 if (t >= r0 + 1) {
                     // row t-1: q = M p, p.q
                     const float4 a_ = ring.v[k][2][lane];
-                    const float pl = from_left(pm1, em1, s), pr = from_right(pm1, em1, s);
-                    const float4 q = m_op4(a_, pm1, pl, pr, pm2, pt, bt);
+                    const float4 q = m_op4(a_, pm1.v, from_left(pm1.v, pm1.g1, s), from_right(pm1.v, pm1.g1, s),
+                                           pm2.v, pt.v, bt);
                     if (s.act) {
-                        acc = dot4(pm1, q, acc);
+                        acc = dot4(pm1.v, q, acc);
                         if (STOREQ) *reinterpret_cast<float4*>(qo + strip_row(s, t - 1) + s.x) = q;
                     }
                 }
                 pm2 = pm1;
                 pm1 = pt;
-                em1 = et;
             };
             strip_stream(r0 - 1, r1, issue, compute);
         }

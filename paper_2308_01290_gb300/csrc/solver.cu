@@ -3208,8 +3208,29 @@ int iterate_t(Ctx& c, bool stats) {
     if ((rc = op_thr_rhs<T>(c, stats))) return rc;
     if ((rc = c.domain == 1 ? op_solve_f_sino<T>(c) : op_solve_f<T>(c))) return rc;
     if ((rc = op_synth<T>(c))) return rc;
-    if ((rc = fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2)))) return rc;
-    if ((rc = op_solve_z<T>(c))) return rc;
+    const FftJobs rho = jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2);
+    if (!c.side_stream) {
+        if ((rc = fft_solve<T>(c, rho))) return rc;
+        if ((rc = op_solve_z<T>(c))) return rc;
+        return op_next_beta<T>(c);
+    }
+    // The rho_e and Z^m updates of an iteration read only what the synthesis
+    // wrote (Alg. 1, reading R1) and touch disjoint fields and spectra: the FFT
+    // solve of rho_e (instruction-bound) runs on the side stream while the Z^m
+    // PCG (bound by HBM) runs on the handle's stream.
+    RECON_CUDA(cudaEventRecord(c.side_ev[0], c.stream));
+    RECON_CUDA(cudaStreamWaitEvent(c.side_stream, c.side_ev[0], 0));
+    const cudaStream_t main_stream = c.stream;
+    c.stream = c.side_stream;
+    rc = fft_solve<T>(c, rho);
+    const cudaError_t e = cudaEventRecord(c.side_ev[1], c.side_stream);
+    c.stream = main_stream;
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventRecord (side stream)");
+    rc = op_solve_z<T>(c);
+    // the handle's stream waits for the side stream even when the PCG failed
+    RECON_CUDA(cudaStreamWaitEvent(c.stream, c.side_ev[1], 0));
+    if (rc) return rc;
     return op_next_beta<T>(c);
 }
 
@@ -3858,6 +3879,9 @@ int solver_setup(Ctx& c) {
     if ((rc = alloc_dev(c, (void**)&c.d_acct, sizeof(unsigned long long) * KF_COUNT))) return rc;
     RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
     RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, sizeof(int)));
+    RECON_CUDA(cudaStreamCreateWithFlags(&c.side_stream, cudaStreamNonBlocking));
+    RECON_CUDA(cudaEventCreateWithFlags(&c.side_ev[0], cudaEventDisableTiming));
+    RECON_CUDA(cudaEventCreateWithFlags(&c.side_ev[1], cudaEventDisableTiming));
     RECON_CUDA(cudaMemcpy(c.d_geom, c.sg.data(), sizeof(SliceGeom) * c.n, cudaMemcpyHostToDevice));
     if ((rc = mg_setup(c))) return rc;
     if (c.precision == 1)
