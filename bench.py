@@ -634,6 +634,27 @@ def main():
                d2h_bytes_per_step=int(h_Z.numel() + h_R.numel()) * 4)
 
     extra = {}
+    if rank == 0:
+        # image quality against the truth maps, inside the body (Sec. III):
+        # Algorithm 1 and the two-step image-based comparator, mean over slices
+        truth_Z = torch.from_numpy(np.concatenate([np.asarray(Z, np.float32).ravel() for Z, _, _ in slices])).cuda()
+        truth_R = torch.from_numpy(np.concatenate([np.asarray(r, np.float32).ravel() for _, r, _ in slices])).cuda()
+        body = (truth_R >= 0.1).to(torch.uint8)
+        dZ = torch.empty(npx, device="cuda")
+        dR = torch.empty(npx, device="cuda")
+        solver.direct(Z=dZ, rhoe=dR, on_device=True)
+        solver.get(Z=outZ, rhoe=outR, on_device=True)
+        torch.cuda.synchronize()
+        g0 = geoms[0]
+        if all(g.nx == g0.nx and g.ny == g0.ny for g in geoms):
+            def metrics(x, ref):
+                m = rc.iqa(len(geoms), g0.nx, g0.ny, x, ref, body).mean(axis=0)
+                return dict(psnr=float(m[0]), nmad=float(m[1]), ssim=float(m[2]))
+            extra["iqa"] = dict(
+                what="mean over slices of PSNR (dB), NMAD and SSIM against the truth maps, PSNR and NMAD inside the "
+                     "body (truth rho_e >= 0.1)",
+                rhoe=dict(one_step=metrics(outR, truth_R), two_step=metrics(dR, truth_R)),
+                Z=dict(one_step=metrics(outZ, truth_Z), two_step=metrics(dZ, truth_Z)))
     if rank == 0 and not args.no_fp64 and args.domain == "image":
         # plain FP64 path: the same algorithm in double, one 512^2 slice at a
         # time, the same beta schedule and iteration count, and the same step

@@ -96,7 +96,8 @@ typedef struct recon_params {
                                         halve down to a small grid (below), FFT-preconditioned elsewhere;
                                         2: FFT-preconditioned PCG on every slice (1 is refused) */
     int32_t domain;                  /* data terms of the arms: 0 on the image pair (Sec. II-B, as printed);
-                                        1 on the sinograms through the projector (below) */
+                                        1 on the sinograms through the projector, linear model (below);
+                                        2 on the sinograms, polyenergetic model by Gauss-Newton (below) */
 } recon_params;
 
 /* Preconditioners of the Z^m PCG (Alg. 1, Z^m step: [diag(a^2) + beta~ L] z =
@@ -126,7 +127,22 @@ typedef struct recon_params {
  * Requires sinogram inputs (n_views > 0), the same geometry for every slice
  * of a batch, precision 1 and order 0.  A^T adds with atomics, so results
  * may differ in the last bits between runs.  The solve starts from the FBP
- * image pair; recon_stats.fid_low/fid_high are 0 in this mode. */
+ * image pair; recon_stats.fid_low/fid_high are 0 in this mode.
+ *
+ * domain = 2 (polyenergetic sinogram fidelity, linearised by Gauss-Newton).
+ * With polyenergetic arms the -log sinogram of a ray is the nonlinear
+ *     h_i(l1, l2) = -ln sum_b w_ib exp(-S (mu1(E_b) l1 + mu2(E_b) l2)) / S
+ * of the basis line integrals l_k = A f_k (w_ib the arm's normalised
+ * detected spectrum; two basis materials span the photoelectric / Compton
+ * model at every energy, Sec. II-B).  Each iteration linearises the data term
+ * (1/gamma) sum_i ||h_i(A f1, A f2) - s_i / S||^2 at the iterate: with
+ * J_ik = dh_i/dl_k (the spectrum reweighted by the ray's attenuation),
+ * W_kl = sum_i J_ik J_il and d_i = s_i / S - h_i + J_i1 l1 + J_i2 l2, the f_k
+ * normal equations are those of domain 1 with A^T diag(W_kk) A / gamma in
+ * place of sum_i mu_k(E_i)^2 A^T A / gamma and A^T (sum_i J_ik d_i - W_ko l_o)
+ * / gamma as the data image.  With monoenergetic arms this is domain 1.  Same
+ * requirements as domain 1, and the same spectra and basis materials for every
+ * slice of a batch. */
 
 /* Per-slice statistics of the last iteration run by recon_step.  The
  * objective terms are those of eq. obj_unconstraint at the iterate the
@@ -181,6 +197,36 @@ int recon_get(recon_ctx* ctx, float* Z, float* rhoe, float* f1, float* f2, int o
 
 /* Blocks until the handle's queued work is done. */
 int recon_sync(recon_ctx* ctx);
+
+/* Outputs of the comparison the paper's Sec. III makes (they do not change
+ * the solve's state):
+ * recon_direct: Z and rho_e of the two-step image-based method -- the
+ *   decomposition of the loaded image pair (eq. lac_EL/EH), the synthesis at
+ *   E1, E2 (eq. mac_E1/E2) and the closed forms eq. rho_e, eq. Z_m with no
+ *   regularisation, i.e. the maps of iteration 0 of Algorithm 1.  Z, rho_e:
+ *   caller-owned buffers of the total pixel count (slices unpadded, in order),
+ *   host or device as on_device says.  RECON_ESTATE before recon_set_data.
+ * recon_mono: monoenergetic images at n_e energies kev[0..n_e-1] (keV > 0,
+ *   1 <= n_e <= 16), mu(E) = S (f1 mu_1(E) + f2 mu_2(E)) in
+ *   1/mm from the current basis fractions (eq. mac_E1/E2 at E).  out holds
+ *   n_e blocks of the total pixel count, energy-major.  The slices must share
+ *   their basis materials (RECON_EINVAL otherwise). */
+int recon_direct(recon_ctx* ctx, float* Z, float* rhoe, int on_device);
+int recon_mono(recon_ctx* ctx, int32_t n_e, const double* kev, float* out, int on_device);
+
+/* Image-quality metrics of Sec. III for n slices of nx x ny pixels (both at
+ * least 11): out[3 s + 0..2] = PSNR, NMAD and SSIM of slice s of x against
+ * slice s of ref.  x, ref: device, n * nx * ny floats, slice-major; mask:
+ * device, n * nx * ny bytes (nonzero: pixel counted by PSNR and NMAD) or NULL
+ * for every pixel; out: host, 3 n doubles.  The paper prints no definitions;
+ * the library takes PSNR = 10 log10(max|ref|^2 / MSE), NMAD = sum|x - ref| /
+ * sum|ref|, both over the mask, and SSIM (Wang et al. 2004) as the mean over
+ * the pixels whose 11 x 11 Gaussian window (sigma 1.5) fits in the slice,
+ * with C1 = (0.01 L)^2, C2 = (0.03 L)^2, L = max(ref) - min(ref).  Scratch
+ * is allocated on the stream (stream-ordered); the call returns once out is
+ * written. */
+int recon_iqa(int32_t n, int32_t nx, int32_t ny, const float* x, const float* ref, const uint8_t* mask,
+              double* out, void* stream);
 
 void recon_destroy(recon_ctx* ctx);
 
@@ -386,9 +432,11 @@ int64_t recon_kernel_launches(recon_ctx* ctx);
  * column passes), 10 projector and backprojector inside the solve (domain
  * 1); the multigrid-preconditioned PCG: 11 update of z and r, convergence
  * test and the first restriction, 12 fine-level correction and smoothing
- * with r.y, 13 new search direction p, q = M p and p.q, 14 the coarse levels
- * and the restriction of a^2; 15 other. */
-#define RECON_KF_COUNT 16
+ * with r.y, 13 new search direction p, q = M p and p.q, 14 the coarse tile
+ * levels (restriction and correction passes), 15 the in-block levels of
+ * each slice and its coarsest solve, 16 a^2 of the levels and the coarsest
+ * inverse (once per Z^m solve); 17 other. */
+#define RECON_KF_COUNT 18
 
 /* Time the launches of the kernel families whose bit is set in mask with
  * CUDA events on the handle's stream (0 = off).  Algorithmic bytes and launch

@@ -18,6 +18,9 @@ FP64:
 * ``l0``     -- plain gradient-L0 smoothing (Sec. II-C), the building block.
 * ``ct``     -- fan-beam Joseph projector, its exact transpose, flat-detector
   FBP and the data simulation that turns phantoms into DECT image pairs.
+* ``modeb``  -- the sinogram-domain data terms of the f updates.
+* ``iqa``    -- monoenergetic images at any energy, the two-step image-based
+  comparator of Sec. III and the image-quality metrics PSNR, NMAD, SSIM.
 
 Parity status of every function is given in its docstring; functions with no
 independent pin say "parity unpinned".

@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "librecon.so")
-SOURCES = ["model_tables.cpp", "solver.cu", "ct.cu", "api.cu", "server.cu"]
+SOURCES = ["model_tables.cpp", "solver.cu", "ct.cu", "api.cu", "server.cu", "iqa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

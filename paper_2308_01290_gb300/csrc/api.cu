@@ -25,6 +25,20 @@ bool seven_smooth(int n) {
 
 constexpr int kFbpGroup = 8;   // slices per FBP launch pair in recon_set_data
 
+bool same_spectrum(const recon_spectrum& a, const recon_spectrum& b) {
+    if (a.kind != b.kind || a.kev != b.kev || a.kvp != b.kvp || a.n_filters != b.n_filters) return false;
+    for (int i = 0; i < a.n_filters && i < RECON_MAX_FILTERS; ++i)
+        if (a.filters[i].Z != b.filters[i].Z || a.filters[i].rhoe != b.filters[i].rhoe ||
+            a.filters[i].thickness_mm != b.filters[i].thickness_mm)
+            return false;
+    return true;
+}
+
+bool same_spectra(const recon_params& a, const recon_params& b) {
+    return same_spectrum(a.low, b.low) && same_spectrum(a.high, b.high) && a.basis_z[0] == b.basis_z[0] &&
+           a.basis_z[1] == b.basis_z[1] && a.basis_rhoe[0] == b.basis_rhoe[0] && a.basis_rhoe[1] == b.basis_rhoe[1];
+}
+
 bool same_geometry(const recon_geometry& a, const recon_geometry& b) {
     return a.nx == b.nx && a.ny == b.ny && a.pixel_mm == b.pixel_mm && a.n_views == b.n_views &&
            a.n_bins == b.n_bins && a.sid_mm == b.sid_mm && a.sdd_mm == b.sdd_mm && a.bin_mm == b.bin_mm &&
@@ -57,7 +71,7 @@ int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
         (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 2) ||
-        (p.domain != 0 && p.domain != 1) || (p.domain == 1 && (p.precision != 1 || p.order != 0)) || !(p.e1_kev > 0) ||
+        (p.domain < 0 || p.domain > 2) || (p.domain != 0 && (p.precision != 1 || p.order != 0)) || !(p.e1_kev > 0) ||
         !(p.e2_kev > 0) || p.e1_kev == p.e2_kev) {
         set_error("invalid recon_params");
         return RECON_EINVAL;
@@ -159,15 +173,19 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
             set_error("all slices of a batch take images, or all take sinograms");
             return RECON_EINVAL;
         }
-        if (params[0].domain == 1) {
+        if (params[0].domain != 0) {
             const recon_geometry& a = geoms[s];
             const recon_geometry& b = geoms[0];
             if (a.n_views < 1 || a.nx != b.nx || a.ny != b.ny || a.n_views != b.n_views || a.n_bins != b.n_bins ||
                 a.pixel_mm != b.pixel_mm || a.sid_mm != b.sid_mm || a.sdd_mm != b.sdd_mm || a.bin_mm != b.bin_mm ||
                 a.start_rad != b.start_rad || a.arc_rad != b.arc_rad) {
-                set_error("domain 1 needs sinogram inputs and one geometry for every slice of the batch");
+                set_error("domains 1 and 2 need sinogram inputs and one geometry for every slice of the batch");
                 return RECON_EINVAL;
             }
+        }
+        if (params[0].domain == 2 && !same_spectra(params[s], params[0])) {
+            set_error("domain 2 needs the same spectra and basis materials for every slice of the batch");
+            return RECON_EINVAL;
         }
     }
     recon_ctx* h = new (std::nothrow) recon_ctx();
@@ -203,7 +221,7 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
             else c.allocations.push_back(c.d_filt);
         }
     }
-    if (!rc && params[0].domain == 1) rc = solver_setup_sino(c);
+    if (!rc && params[0].domain != 0) rc = solver_setup_sino(c);
     if (rc) {
         free_ctx(c);
         delete h;
@@ -327,6 +345,44 @@ int recon_get(recon_ctx* h, float* Z, float* rhoe, float* f1, float* f2, int on_
         if (a) RECON_CUDA(cudaMemcpyAsync(outs[k], a, sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
         if (b)
             RECON_CUDA(cudaMemcpyAsync(outs[k + 1], b, sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
+        RECON_CUDA(cudaStreamSynchronize(c.stream));
+    }
+    return RECON_OK;
+}
+
+int recon_direct(recon_ctx* h, float* Z, float* rhoe, int on_device) {
+    if (!h || !Z || !rhoe) return RECON_EINVAL;
+    Ctx& c = h->c;
+    if (!c.has_data) {
+        set_error("recon_direct before recon_set_data");
+        return RECON_ESTATE;
+    }
+    if (on_device) return solver_direct(c, Z, rhoe);
+    int rc;
+    if ((rc = solver_direct(c, c.d_stage[0], c.d_stage[1]))) return rc;
+    RECON_CUDA(cudaMemcpyAsync(Z, c.d_stage[0], sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
+    RECON_CUDA(cudaMemcpyAsync(rhoe, c.d_stage[1], sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
+    RECON_CUDA(cudaStreamSynchronize(c.stream));
+    return RECON_OK;
+}
+
+int recon_mono(recon_ctx* h, int32_t n_e, const double* kev, float* out, int on_device) {
+    if (!h || !kev || !out || n_e < 1 || n_e > 16) {
+        set_error("recon_mono: bad arguments (1 to 16 energies per call)");
+        return RECON_EINVAL;
+    }
+    Ctx& c = h->c;
+    if (!c.has_data) {
+        set_error("recon_mono before recon_set_data");
+        return RECON_ESTATE;
+    }
+    if (on_device) return solver_mono(c, n_e, kev, out);
+    // host output: one energy at a time through the unpadded staging buffer
+    for (int k = 0; k < n_e; ++k) {
+        int rc;
+        if ((rc = solver_mono(c, 1, kev + k, c.d_stage[0]))) return rc;
+        RECON_CUDA(cudaMemcpyAsync(out + (size_t)k * c.ext_elems, c.d_stage[0], sizeof(float) * c.ext_elems,
+                                   cudaMemcpyDeviceToHost, c.stream));
         RECON_CUDA(cudaStreamSynchronize(c.stream));
     }
     return RECON_OK;
@@ -508,7 +564,7 @@ const char* recon_profile_name(int32_t f) {
                                           "synth",     "pcg_start",    "pcg_fwd",  "pcg_cols",
                                           "pcg_inv",   "fcg",          "project",
                                           "mg_fwd",    "mg_y",         "mg_pq",    "mg_levels",
-                                          "other"};
+                                          "mg_block",  "mg_setup",     "other"};
     return (f >= 0 && f < KF_COUNT) ? names[f] : "?";
 }
 

@@ -69,6 +69,7 @@ struct SliceConst {
     // c'_k = sum_j b[k][j]^2, cross = sum_i a[0][i] a[1][i], 1/gamma
     double fa0, fa1, fcp0, fcp1, fcross, inv_gamma;
     int iters, order, cg_max, domain;
+    int gn;                       // domain 2: per-ray Gauss-Newton weights replace alpha_k and the cross term
     float fk[KC_N];               // kc_value(*this, i) rounded to float (set by finish_const)
 };
 
@@ -93,12 +94,12 @@ __host__ __device__ inline double kc_value(const SliceConst& c, int id) {
         case KC_INV_AW: return 1.0 / c.a_w;
         case KC_CF1: return c.c_f1;
         case KC_CF2: return c.c_f2;
-        case KC_SINO_AG: return c.fcross * c.inv_gamma;
+        case KC_SINO_AG: return c.gn ? 0.0 : c.fcross * c.inv_gamma;
         case KC_SINO_BC: return c.c12 - c.fcross;
         case KC_SINO_D0: return c.fa0 + c.fcp0;
         case KC_SINO_D1: return c.fa1 + c.fcp1;
-        case KC_SINO_AL0: return c.fa0 * c.inv_gamma;
-        case KC_SINO_AL1: return c.fa1 * c.inv_gamma;
+        case KC_SINO_AL0: return c.gn ? c.inv_gamma : c.fa0 * c.inv_gamma;
+        case KC_SINO_AL1: return c.gn ? c.inv_gamma : c.fa1 * c.inv_gamma;
         case KC_SINO_CP0: return c.fcp0;
         case KC_SINO_CP1: return c.fcp1;
         default: return 0.0;
@@ -223,7 +224,9 @@ enum KFam {
     KF_MG_FWD,      // multigrid PCG: update, convergence test, first restriction
     KF_MG_Y,        // multigrid PCG: fine-level correction and smoothing, r.y
     KF_MG_PQ,       // multigrid PCG: new direction p, q = M p, p.q
-    KF_MG_LEVELS,   // multigrid PCG: the coarse levels (and the a^2 restriction)
+    KF_MG_LEVELS,   // multigrid PCG: the coarse tile levels (restriction and correction passes)
+    KF_MG_BLOCK,    // multigrid PCG: the in-block levels of every slice and the coarsest solve
+    KF_MG_SETUP,    // multigrid PCG: a^2 of the levels and the coarsest inverse (once per Z^m solve)
     KF_OTHER,
     KF_COUNT
 };

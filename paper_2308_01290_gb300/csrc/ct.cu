@@ -96,9 +96,10 @@ __global__ void k_project(recon_geometry g, int n, const float* __restrict__ img
 }
 
 // exact transpose of k_project (same samples, scattered with atomics)
-// Adds A^T sino into img (layout as k_project).
+// Adds A^T (wt o sino) into img (layout as k_project; wt: per-ray weights
+// laid out as sino, or null for none).
 __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__ sino, float* img, long long pitch,
-                              long long stride) {
+                              long long stride, const float* __restrict__ wt) {
     const long long nr = (long long)g.n_views * g.n_bins;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= nr * n) return;
@@ -107,7 +108,7 @@ __global__ void k_backproject(recon_geometry g, int n, const float* __restrict__
     const int view = ray / g.n_bins, bin = ray - view * g.n_bins;
     const RaySetup r = ray_setup(g, view, bin);
     float* im = img + (long long)sl * stride;
-    const float v = sino[tid] * r.w;
+    const float v = (wt ? sino[tid] * wt[tid] : sino[tid]) * r.w;
     if (v == 0.f) return;
     if (r.xmajor) {
         for (int i = 0; i < g.nx; ++i) {
@@ -334,10 +335,10 @@ int ct_project_pitched(const recon_geometry& g, int n, const float* img, long lo
 }
 
 int ct_backproject_add(const recon_geometry& g, int n, const float* sino, float* img, long long pitch,
-                       long long stride, cudaStream_t st, long long* launches) {
+                       long long stride, cudaStream_t st, long long* launches, const float* wt) {
     const long long total = (long long)n * g.n_views * g.n_bins;
     if (total <= 0) return RECON_OK;
-    k_backproject<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, sino, img, pitch, stride);
+    k_backproject<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(g, n, sino, img, pitch, stride, wt);
     if (launches) *launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;

@@ -90,6 +90,12 @@ struct Ctx {
     int domain = 0;
     double gamma = 0.0;             // ||A 1||^2 / (nx ny)
     float* d_sino_tmp = nullptr;    // one sinogram per slice (A p)
+    // domain 2 (polyenergetic Gauss-Newton): per ray and slice l1 = A f1, l2 = A f2,
+    // W11, W22, v1 / gamma, v2 / gamma (kGnArrays sinograms of n slices each), and
+    // the detected spectra of both arms (bins x (w, mu_hat_1, mu_hat_2), float)
+    float* d_gn = nullptr;
+    float* d_spec = nullptr;
+    int spec_nb[2] = {0, 0};
     int cap_nx = 0, cap_ny = 0;
     std::vector<std::pair<int, std::pair<long long, long long>>> tw_index;   // N -> (twiddle, symbol) offsets
     bool has_data = false;
@@ -131,6 +137,8 @@ int solver_modeb_data(Ctx& c);                 // domain 1: data images t_k from
 int solver_iterate(Ctx& c, bool stats);        // one iteration of Algorithm 1
 int solver_op(Ctx& c, int op);
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int on_device);
+int solver_direct(Ctx& c, float* Z, float* rhoe);                // two-step comparator maps (device, unpadded)
+int solver_mono(Ctx& c, int n_e, const double* kev, float* out); // monoenergetic images (device, unpadded)
 int solver_read_state(Ctx& c, std::vector<SliceState>& out);
 int solver_profile_read(Ctx& c, double* ms, long long* launches, unsigned long long* bytes);
 // serving engine (slots of a capacity-sized handle)
@@ -146,7 +154,7 @@ int ct_project(const recon_geometry& g, int n, const float* img, float* sino, cu
 int ct_project_pitched(const recon_geometry& g, int n, const float* img, long long pitch, long long stride,
                        float* sino, cudaStream_t st, long long* launches);
 int ct_backproject_add(const recon_geometry& g, int n, const float* sino, float* img, long long pitch,
-                       long long stride, cudaStream_t st, long long* launches);
+                       long long stride, cudaStream_t st, long long* launches, const float* wt = nullptr);
 int ct_backproject(const recon_geometry& g, int n, const float* sino, float* img, cudaStream_t st,
                    long long* launches);
 int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,

@@ -133,6 +133,25 @@ __global__ void k_load(ItemList L, const SliceGeom* G, const SliceConst* C, cons
     }
 }
 
+// The per-pixel initialisation of Algorithm 1 from the normalised image pair
+// (uL, uH), in FP64: f by Cramer's rule on eq. lac_EL / lac_EH, the synthesis
+// eq. mac_E1 / mac_E2, and the closed forms eq. rho_e and eq. Z_m
+// (normalised, reading R3; z set to water where a = 0 or rho_e < rho_air and
+// clipped to the Z range, reading R16).  This is also the two-step
+// image-based comparator of Sec. III.
+__device__ __forceinline__ void init_pixel(const SliceConst& c, double uL, double uH, double& f1, double& f2,
+                                           double& rho, double& z) {
+    f1 = (c.a11 * uL - c.a10 * uH) / c.det;
+    f2 = (c.a00 * uH - c.a01 * uL) / c.det;
+    const double m1 = c.b00 * f1 + c.b10 * f2;
+    const double m2 = c.b01 * f1 + c.b11 * f2;
+    rho = (m1 * c.r - m2) / c.c_rho;
+    const double a = (m1 * c.P2 - m2 * c.P1) / c.a_w;
+    const double b = (m2 * c.psi1 - m1 * c.psi2) / c.a_w;
+    z = 1.0;
+    if (a != 0.0 && rho >= c.rho_air) z = fmin(fmax(b / a, 0.0), c.zclip_hi);
+}
+
 template <typename T>
 __global__ void k_init(ItemList L, const SliceGeom* G, const SliceConst* C, Ptrs<T> P) {
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
@@ -143,19 +162,8 @@ __global__ void k_init(ItemList L, const SliceGeom* G, const SliceConst* C, Ptrs
             const int x = it.a + (q & (kTileW - 1)), y = it.b + q / kTileW;
             if (x >= g.nx || y >= g.ny) continue;
             const long long d = g.off + (long long)y * g.pitch + x;
-            const double uL = P.f[RECON_F_MUL][d], uH = P.f[RECON_F_MUH][d];
-            // Cramer on eq. lac_EL / lac_EH
-            const double f1 = (c.a11 * uL - c.a10 * uH) / c.det;
-            const double f2 = (c.a00 * uH - c.a01 * uL) / c.det;
-            // eq. mac_E1 / mac_E2
-            const double m1 = c.b00 * f1 + c.b10 * f2;
-            const double m2 = c.b01 * f1 + c.b11 * f2;
-            // eq. rho_e, eq. Z_m (normalised)
-            const double rho = (m1 * c.r - m2) / c.c_rho;
-            const double a = (m1 * c.P2 - m2 * c.P1) / c.a_w;
-            const double b = (m2 * c.psi1 - m1 * c.psi2) / c.a_w;
-            double z = 1.0;
-            if (a != 0.0 && rho >= c.rho_air) z = fmin(fmax(b / a, 0.0), c.zclip_hi);
+            double f1, f2, rho, z;
+            init_pixel(c, P.f[RECON_F_MUL][d], P.f[RECON_F_MUH][d], f1, f2, rho, z);
             P.f[RECON_F_F1][d] = T(f1);
             P.f[RECON_F_F2][d] = T(f2);
             P.f[RECON_F_RHO][d] = T(rho);
@@ -395,7 +403,7 @@ __global__ void __launch_bounds__(kStencilThreads, 4) k_thr_rhs(ItemList L, cons
         double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         // image domain: uL, uH = mu_hat(E_L), mu_hat(E_H).  Sinogram domain
         // (domain 1): uL, uH = t_1, t_2 and G1, G2 = A^T A f1, A^T A f2
-        const bool sino = c.domain == 1;
+        const bool sino = c.domain != 0;
         struct In {
             Pack<T> uL, uH, G1, G2;
         };
@@ -1518,7 +1526,7 @@ __global__ void __launch_bounds__(kStencilThreads) k_mg_restrict(ItemList L, con
         const Item it = L.items[w];
         if (!__ldg(&S[it.slice].active)) continue;
         const SliceGeom g = G[it.slice], g1 = G1[it.slice];
-        account(acct, KF_MG_LEVELS, tile_px<T>(g, it) * 5 * (long long)sizeof(T) / 4);
+        account(acct, KF_MG_SETUP, tile_px<T>(g, it) * 5 * (long long)sizeof(T) / 4);
         for (int q = threadIdx.x; q < CW * CH; q += blockDim.x) {
             const int cy = q / CW, cx = q - cy * CW;
             const int x = it.a + 2 * cx, y = it.b + 2 * cy;
@@ -2215,7 +2223,7 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* G
     T* a = sh + tot;       // a^2
     T* x = sh + 2 * tot;   // correction
     T* r = sh + 3 * tot;   // residual of a smoothing sweep (size of the first level)
-    if (threadIdx.x == 0) atomicAdd(acct + KF_MG_LEVELS, (unsigned long long)(g.nx * g.ny) * 3ull * sizeof(T));
+    if (threadIdx.x == 0) atomicAdd(acct + KF_MG_BLOCK, (unsigned long long)(g.nx * g.ny) * 3ull * sizeof(T));
     const T om = mg_omega<T>();
     T bt[kMgMaxBlockLevels];
     bt[0] = mg_bt<T>(S[s], g.lvl);
@@ -2544,6 +2552,59 @@ __device__ __forceinline__ double mth_root_newton(double z, double m, double inv
     return y0 * (1.0 - (m * log(y0) - lz) * inv_m);
 }
 
+// The two-step comparator's maps of every slice from the loaded image pair:
+// the initialisation (init_pixel) with rho_e and z rounded to the map
+// precision as k_init stores them, then Z as k_extract forms it -- the maps
+// recon_get returns right after recon_set_data -- into unpadded Z, rho_e,
+// without touching the solve's state.
+template <typename T>
+__global__ void k_direct(ItemList L, const SliceGeom* G, const SliceConst* C, Ptrs<T> P, float* Z, float* rhoe,
+                         double zw, double m) {
+    const double inv_m = 1.0 / m;
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceGeom g = G[it.slice];
+        const SliceConst c = C[it.slice];
+        for (int q = threadIdx.x; q < kTileW * TileH<T>::v; q += blockDim.x) {
+            const int x = it.a + (q & (kTileW - 1)), y = it.b + q / kTileW;
+            if (x >= g.nx || y >= g.ny) continue;
+            const long long d = g.off + (long long)y * g.pitch + x;
+            const long long e = g.ext_off + (long long)y * g.nx + x;
+            double f1, f2, rho, z;
+            init_pixel(c, P.f[RECON_F_MUL][d], P.f[RECON_F_MUH][d], f1, f2, rho, z);
+            const double zs = (double)T(z);
+            Z[e] = zs > 0.0 ? (float)(zw * mth_root_newton(zs, m, inv_m)) : 1.0f;
+            rhoe[e] = (float)T(rho);
+        }
+    }
+}
+
+// Monoenergetic images (eq. mac_E1/E2 at any energy): for energy k,
+// out[k * n_ext + e] = f1 c[k][0] + f2 c[k][1] with c[k][j] = S mu_hat_j(E_k)
+// of basis j (1/mm), from the current basis fractions, in the map precision.
+constexpr int kMonoMax = 16;
+struct MonoCoef {
+    int n;
+    double c[kMonoMax][2];
+};
+
+template <typename T>
+__global__ void k_mono(ItemList L, const SliceGeom* G, Ptrs<T> P, MonoCoef mc, float* out, long long n_ext) {
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceGeom g = G[it.slice];
+        for (int q = threadIdx.x; q < kTileW * TileH<T>::v; q += blockDim.x) {
+            const int x = it.a + (q & (kTileW - 1)), y = it.b + q / kTileW;
+            if (x >= g.nx || y >= g.ny) continue;
+            const long long d = g.off + (long long)y * g.pitch + x;
+            const long long e = g.ext_off + (long long)y * g.nx + x;
+            const T f1 = P.f[RECON_F_F1][d], f2 = P.f[RECON_F_F2][d];
+            for (int k = 0; k < mc.n; ++k)
+                out[k * n_ext + e] = (float)(f1 * T(mc.c[k][0]) + f2 * T(mc.c[k][1]));
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_extract(ItemList L, const SliceGeom* G, Ptrs<T> P, float* Z, float* rhoe, float* f1, float* f2,
                           double zw, double m) {
@@ -2744,7 +2805,7 @@ int strip_rows(const Ctx& c, int l) {
 // a^2 of every multigrid level from the fine a^2 (once per Z^m solve).
 template <typename T>
 void mg_restrict_a2(Ctx& c, bool timed) {
-    MaybeTimer t(c, KF_MG_LEVELS, timed);
+    MaybeTimer t(c, KF_MG_SETUP, timed);
     T* pa = static_cast<T*>(c.mg_pool[1]);
     for (int l = 0; l < c.mg_max_lb; ++l) {
         const DevItemList& L = c.mg_tiles[l];
@@ -2840,9 +2901,15 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
                 c.launches += 1;
             }
         }
+    }
+    {
+        MaybeTimer t(c, KF_MG_BLOCK, timed);
         k_mg_block<T><<<c.n, kMgBlockThreads, c.mg_block_smem, c.stream>>>(
             c.d_mg_block, c.d_state, pf, pa, pe, static_cast<const T*>(c.mg_qinv), c.d_acct);
         c.launches += 1;
+    }
+    {
+        MaybeTimer t(c, KF_MG_LEVELS, timed);
         for (int l = c.mg_max_lb - 1; l >= 1; --l) {
             if constexpr (std::is_same<T, float>::value) {
                 const DevItemList& S = c.mg_strips[l];
@@ -2958,16 +3025,103 @@ T* field_base(Ctx& c, int f) {
 // out (cleared) = A^T A x over all slices.  Algorithmic HBM bytes: the image
 // read and the sinogram written by A, the sinogram read and the image added
 // to by A^T (the gathers themselves hit the L2-resident image).
-int gram_all(Ctx& c, const float* x, float* out) {
+int gram_all(Ctx& c, const float* x, float* out, const float* wt = nullptr) {
     const recon_geometry& g = c.geo[0];
     const long long pitch = c.sg[0].pitch, stride = (long long)c.sg[0].ny * pitch;
     FamTimer t(c, KF_PROJ);
     c.host_acct[KF_PROJ] += 4ull * (unsigned long long)c.n *
-                            (3ull * g.nx * g.ny + 2ull * (unsigned long long)g.n_views * g.n_bins);
+                            (3ull * g.nx * g.ny + (wt ? 3ull : 2ull) * (unsigned long long)g.n_views * g.n_bins);
     int rc;
     if ((rc = ct_project_pitched(g, c.n, x, pitch, stride, c.d_sino_tmp, c.stream, &c.launches))) return rc;
     RECON_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * stride * c.n, c.stream));
-    return ct_backproject_add(g, c.n, c.d_sino_tmp, out, pitch, stride, c.stream, &c.launches);
+    return ct_backproject_add(g, c.n, c.d_sino_tmp, out, pitch, stride, c.stream, &c.launches, wt);
+}
+
+// ---- domain 2: polyenergetic sinogram fidelity linearised by Gauss-Newton ----
+//
+// Per ray of every slice, at l = (A f1, A f2) of the iterate (Jacobi, reading
+// R1): the polyenergetic -log h_i(l) = -ln sum_b w_ib exp(-S (mu_1b l1 +
+// mu_2b l2)) / S of each arm (w_ib its normalised detected spectrum; the
+// photoelectric / Compton model is spanned by the two basis materials at every
+// energy, Sec. II-B), its derivatives J_ik = sum_b om_ib mu_kb (om: the
+// spectrum reweighted by the ray's attenuation), d_i = s_i / S - h_i + J_i1 l1
+// + J_i2 l2, W_kl = sum_i J_ik J_il and v_k = sum_i J_ik d_i - W_ko l_o.  The
+// f_k normal equations become [A^T diag(W_kk) A / gamma + c'_k + beta L] f_k
+// = A^T v_k / gamma + (model terms) + beta div(h, v): the linear mode's with
+// per-ray weights.  Sums over the bins start from the smallest exponent, so
+// no term underflows.
+constexpr int kGnArrays = 6;   // per ray: l1, l2, W11, W22, v1 / gamma, v2 / gamma
+__global__ void k_gn_rays(long long n_rays, const float* __restrict__ sL, const float* __restrict__ sH,
+                          const float* __restrict__ spec, int nb0, int nb1, float S, float inv_gamma, float* gn) {
+    extern __shared__ float tab[];   // (nb0 + nb1) x (w, mu_hat_1, mu_hat_2)
+    for (int i = threadIdx.x; i < 3 * (nb0 + nb1); i += blockDim.x) tab[i] = spec[i];
+    __syncthreads();
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rays) return;
+    const float l1 = gn[r], l2 = gn[n_rays + r];
+    float W11 = 0.f, W22 = 0.f, W12 = 0.f, u1 = 0.f, u2 = 0.f;
+    for (int arm = 0; arm < 2; ++arm) {
+        const float* t = tab + (arm ? 3 * nb0 : 0);
+        const int nb = arm ? nb1 : nb0;
+        float tmin = INFINITY;
+        for (int b = 0; b < nb; ++b) tmin = fminf(tmin, fmaf(t[3 * b + 1], l1, t[3 * b + 2] * l2));
+        float se = 0.f, s1 = 0.f, s2 = 0.f;
+        for (int b = 0; b < nb; ++b) {
+            const float m1 = t[3 * b + 1], m2 = t[3 * b + 2];
+            const float e = t[3 * b] * expf(-S * (fmaf(m1, l1, m2 * l2) - tmin));
+            se += e;
+            s1 = fmaf(e, m1, s1);
+            s2 = fmaf(e, m2, s2);
+        }
+        const float J1 = s1 / se, J2 = s2 / se;
+        const float h = tmin - logf(se) / S;
+        const float d = (arm ? sH : sL)[r] / S - h + fmaf(J1, l1, J2 * l2);
+        W11 = fmaf(J1, J1, W11);
+        W22 = fmaf(J2, J2, W22);
+        W12 = fmaf(J1, J2, W12);
+        u1 = fmaf(J1, d, u1);
+        u2 = fmaf(J2, d, u2);
+    }
+    gn[2 * n_rays + r] = W11;
+    gn[3 * n_rays + r] = W22;
+    gn[4 * n_rays + r] = (u1 - W12 * l2) * inv_gamma;
+    gn[5 * n_rays + r] = (u2 - W12 * l1) * inv_gamma;
+}
+
+// The Gauss-Newton terms of the iterate: t_k = A^T v_k / gamma into MUL (k = 0)
+// and MUH (k = 1), the weighted Gram images A^T (W_kk o A f_k) into A2 and
+// RHS_Z (read by the right-hand sides and by the starts of the two CG solves).
+int op_gn_terms(Ctx& c) {
+    const recon_geometry& g = c.geo[0];
+    const long long nr = (long long)g.n_views * g.n_bins, n_rays = nr * c.n;
+    const long long pitch = c.sg[0].pitch, stride = (long long)c.sg[0].ny * pitch;
+    FamTimer t(c, KF_PROJ);
+    c.host_acct[KF_PROJ] += 4ull * (unsigned long long)c.n *
+                            (6ull * g.nx * g.ny + 18ull * (unsigned long long)nr);
+    int rc;
+    float* l1 = c.d_gn;
+    float* l2 = c.d_gn + n_rays;
+    if ((rc = ct_project_pitched(g, c.n, field_base<float>(c, RECON_F_F1), pitch, stride, l1, c.stream,
+                                 &c.launches)))
+        return rc;
+    if ((rc = ct_project_pitched(g, c.n, field_base<float>(c, RECON_F_F2), pitch, stride, l2, c.stream,
+                                 &c.launches)))
+        return rc;
+    const int smem = 3 * (c.spec_nb[0] + c.spec_nb[1]) * (int)sizeof(float);
+    k_gn_rays<<<(unsigned)((n_rays + 255) / 256), 256, smem, c.stream>>>(
+        n_rays, c.d_sino[0], c.d_sino[1], c.d_spec, c.spec_nb[0], c.spec_nb[1], (float)scale_per_mm(),
+        (float)c.hconst[0].inv_gamma, c.d_gn);
+    c.launches += 1;
+    RECON_CUDA(cudaGetLastError());
+    const int out[4] = {RECON_F_MUL, RECON_F_MUH, RECON_F_A2, RECON_F_RHS_Z};
+    const float* src[4] = {c.d_gn + 4 * n_rays, c.d_gn + 5 * n_rays, l1, l2};
+    const float* wt[4] = {nullptr, nullptr, c.d_gn + 2 * n_rays, c.d_gn + 3 * n_rays};
+    for (int k = 0; k < 4; ++k) {
+        float* o = field_base<float>(c, out[k]);
+        RECON_CUDA(cudaMemsetAsync(o, 0, sizeof(float) * stride * c.n, c.stream));
+        if ((rc = ct_backproject_add(g, c.n, src[k], o, pitch, stride, c.stream, &c.launches, wt[k]))) return rc;
+    }
+    return RECON_OK;
 }
 
 // A^T A f1 into A2 and A^T A f2 into RHS_Z (read by the right-hand sides
@@ -3010,7 +3164,9 @@ int op_solve_f_sino(Ctx& c) {
                     k_fcg_p<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
                                                                                         c.d_state, P);
                 }
-                if ((rc = gram_all(c, field_base<float>(c, RECON_F_CG_P0), field_base<float>(c, RECON_F_CG_P1))))
+                const float* wt = c.domain == 2 ? c.d_gn + (long long)(2 + k) * c.n * c.geo[0].n_views * c.geo[0].n_bins
+                                                : nullptr;
+                if ((rc = gram_all(c, field_base<float>(c, RECON_F_CG_P0), field_base<float>(c, RECON_F_CG_P1), wt)))
                     return rc;
                 {
                     FamTimer t(c, KF_FCG);
@@ -3205,8 +3361,9 @@ template <typename T>
 int iterate_t(Ctx& c, bool stats) {
     int rc;
     if (c.domain == 1 && (rc = op_modeb_gram<T>(c))) return rc;
+    if (c.domain == 2 && (rc = op_gn_terms(c))) return rc;
     if ((rc = op_thr_rhs<T>(c, stats))) return rc;
-    if ((rc = c.domain == 1 ? op_solve_f_sino<T>(c) : op_solve_f<T>(c))) return rc;
+    if ((rc = c.domain != 0 ? op_solve_f_sino<T>(c) : op_solve_f<T>(c))) return rc;
     if ((rc = op_synth<T>(c))) return rc;
     const FftJobs rho = jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2);
     if (!c.side_stream) {
@@ -3332,9 +3489,10 @@ int op_t(Ctx& c, int op) {
         case RECON_OP_THRESH_RHS: {
             int rc;
             if (c.domain == 1 && (rc = op_modeb_gram<T>(c))) return rc;
+            if (c.domain == 2 && (rc = op_gn_terms(c))) return rc;
             return op_thr_rhs<T>(c, false);
         }
-        case RECON_OP_SOLVE_F: return c.domain == 1 ? op_solve_f_sino<T>(c) : op_solve_f<T>(c);
+        case RECON_OP_SOLVE_F: return c.domain != 0 ? op_solve_f_sino<T>(c) : op_solve_f<T>(c);
         case RECON_OP_SYNTH: return op_synth<T>(c);
         case RECON_OP_SOLVE_RHO: return fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2));
         case RECON_OP_SOLVE_Z: return op_solve_z<T>(c);
@@ -3925,12 +4083,33 @@ int solver_setup_sino(Ctx& c) {
         set_error("domain 1: the projector misses the image (gamma = 0)");
         return RECON_EINVAL;
     }
+    const int domain = c.prm[0].domain;
     for (int s = 0; s < c.n; ++s) {
         c.hconst[s].inv_gamma = 1.0 / c.gamma;
+        c.hconst[s].gn = domain == 2;
         finish_const(c.hconst[s]);
     }
     RECON_CUDA(cudaMemcpy(c.d_const, c.hconst.data(), sizeof(SliceConst) * c.n, cudaMemcpyHostToDevice));
-    c.domain = 1;
+    if (domain == 2) {
+        // per-ray arrays, and the spectra of both arms with the basis values per bin
+        if ((rc = alloc_dev(c, (void**)&c.d_gn, sizeof(float) * kGnArrays * nr * c.n))) return rc;
+        const recon_params& p = c.prm[0];
+        std::vector<float> tab;
+        const recon_spectrum* arms[2] = {&p.low, &p.high};
+        for (int a = 0; a < 2; ++a) {
+            std::vector<double> E, w;
+            spectrum_bins(*arms[a], E, w);
+            c.spec_nb[a] = (int)E.size();
+            for (size_t b = 0; b < E.size(); ++b) {
+                tab.push_back((float)w[b]);
+                tab.push_back((float)mu_norm(p.basis_z[0], p.basis_rhoe[0], E[b]));
+                tab.push_back((float)mu_norm(p.basis_z[1], p.basis_rhoe[1], E[b]));
+            }
+        }
+        if ((rc = alloc_dev(c, (void**)&c.d_spec, sizeof(float) * tab.size()))) return rc;
+        RECON_CUDA(cudaMemcpy(c.d_spec, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
+    }
+    c.domain = domain;
     return RECON_OK;
 }
 
@@ -4127,6 +4306,53 @@ int solver_op(Ctx& c, int op) { return c.precision == 1 ? op_t<float>(c, op) : o
 
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int /*on_device*/) {
     return c.precision == 1 ? extract_t<float>(c, Z, rhoe, f1, f2) : extract_t<double>(c, Z, rhoe, f1, f2);
+}
+
+int solver_direct(Ctx& c, float* Z, float* rhoe) {
+    const int grid = grid_for(c, c.tiles.n);
+    if (c.precision == 1)
+        k_direct<float><<<grid, kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const, ptrs<float>(c),
+                                                                Z, rhoe, water_z(), z_exponent());
+    else
+        k_direct<double><<<grid, kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
+                                                                 ptrs<double>(c), Z, rhoe, water_z(), z_exponent());
+    c.launches += 1;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
+}
+
+int solver_mono(Ctx& c, int n_e, const double* kev, float* out) {
+    if (n_e < 1 || n_e > kMonoMax) {
+        set_error("recon_mono: 1 to 16 energies per call");
+        return RECON_EINVAL;
+    }
+    MonoCoef mc{};
+    mc.n = n_e;
+    const recon_params& p = c.prm[0];
+    for (const recon_params& q : c.prm)
+        if (q.basis_z[0] != p.basis_z[0] || q.basis_z[1] != p.basis_z[1] || q.basis_rhoe[0] != p.basis_rhoe[0] ||
+            q.basis_rhoe[1] != p.basis_rhoe[1]) {
+            set_error("recon_mono: the slices of the handle have different basis materials");
+            return RECON_EINVAL;
+        }
+    for (int k = 0; k < n_e; ++k) {
+        if (!(kev[k] > 0)) {
+            set_error("recon_mono: energies must be positive (keV)");
+            return RECON_EINVAL;
+        }
+        // every slice of a handle shares the basis materials (checked at init)
+        for (int j = 0; j < 2; ++j) mc.c[k][j] = scale_per_mm() * mu_norm(p.basis_z[j], p.basis_rhoe[j], kev[k]);
+    }
+    const int grid = grid_for(c, c.tiles.n);
+    if (c.precision == 1)
+        k_mono<float><<<grid, kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, ptrs<float>(c), mc, out,
+                                                              c.ext_elems);
+    else
+        k_mono<double><<<grid, kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, ptrs<double>(c), mc, out,
+                                                               c.ext_elems);
+    c.launches += 1;
+    RECON_CUDA(cudaGetLastError());
+    return RECON_OK;
 }
 
 __global__ void k_reset_slots(const int* slots, int n, const SliceConst* C, SliceState* S) {

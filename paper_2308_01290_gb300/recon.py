@@ -85,6 +85,9 @@ def _load():
         "recon_step": (I, [VP, C.c_int32, P(Stats)]),
         "recon_get": (I, [VP, VP, VP, VP, VP, I]),
         "recon_sync": (I, [VP]),
+        "recon_direct": (I, [VP, VP, VP, I]),
+        "recon_mono": (I, [VP, C.c_int32, P(D), VP, I]),
+        "recon_iqa": (I, [C.c_int32, C.c_int32, C.c_int32, VP, VP, VP, P(D), VP]),
         "recon_destroy": (None, [VP]),
         "recon_solve": (I, [VP, VP, P(Geometry), D, D, C.c_int32, VP, VP]),
         "recon_strerror": (C.c_char_p, [I]),
@@ -139,8 +142,9 @@ EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_
            "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches", "recon_set_graph",
            "recon_set_autotune", "recon_tuning",
            "recon_abi_sizes", "recon_profile", "recon_profile_read", "recon_profile_name", "recon_server_create",
-           "recon_submit", "recon_server_step", "recon_poll", "recon_server_stats", "recon_server_destroy")
-KF_COUNT = 16
+           "recon_submit", "recon_server_step", "recon_poll", "recon_server_stats", "recon_server_destroy",
+           "recon_direct", "recon_mono", "recon_iqa")
+KF_COUNT = 18
 
 
 def _check(rc, what):
@@ -277,6 +281,41 @@ class Solver:
 
     def sync(self):
         _check(lib.recon_sync(self.h), "recon_sync")
+
+    def direct(self, Z=None, rhoe=None, on_device=None):
+        """Z and rho_e of the two-step image-based method (recon_direct); with
+        no buffers, host arrays per slice."""
+        if Z is None:
+            tot = sum(g.nx * g.ny for g in self.geoms)
+            Z, rhoe = np.empty(tot, np.float32), np.empty(tot, np.float32)
+            _check(lib.recon_direct(self.h, _ptr(Z), _ptr(rhoe), 0), "recon_direct")
+            return self._split(Z), self._split(rhoe)
+        if on_device is None:
+            on_device = not isinstance(Z, np.ndarray)
+        _check(lib.recon_direct(self.h, _ptr(Z), _ptr(rhoe), int(on_device)), "recon_direct")
+        return None
+
+    def mono(self, kev, out=None, on_device=None):
+        """Monoenergetic images at the energies kev (recon_mono); with no
+        buffer, a list (per energy) of per-slice host arrays."""
+        e = np.ascontiguousarray(np.atleast_1d(np.asarray(kev, np.float64)))
+        ep = e.ctypes.data_as(C.POINTER(C.c_double))
+        if out is None:
+            tot = sum(g.nx * g.ny for g in self.geoms)
+            buf = np.empty(len(e) * tot, np.float32)
+            _check(lib.recon_mono(self.h, len(e), ep, _ptr(buf), 0), "recon_mono")
+            return [self._split(buf[k * tot:(k + 1) * tot]) for k in range(len(e))]
+        if on_device is None:
+            on_device = not isinstance(out, np.ndarray)
+        _check(lib.recon_mono(self.h, len(e), ep, _ptr(out), int(on_device)), "recon_mono")
+        return None
+
+    def _split(self, flat):
+        parts, off = [], 0
+        for g in self.geoms:
+            parts.append(flat[off:off + g.nx * g.ny].reshape(g.ny, g.nx))
+            off += g.nx * g.ny
+        return parts
 
     def field(self, name, slice_=0):
         p = C.c_void_p()
@@ -431,3 +470,12 @@ class Server:
         out = (C.c_int64 * 4)()
         _check(lib.recon_server_stats(self.h, out), "recon_server_stats")
         return dict(queued=out[0], active=out[1], finished=out[2], footprint=out[3])
+
+
+def iqa(n, nx, ny, x, ref, mask=None, stream=None):
+    """(PSNR, NMAD, SSIM) per slice of device maps x against ref (recon_iqa);
+    an (n, 3) array."""
+    out = np.empty(3 * int(n), np.float64)
+    _check(lib.recon_iqa(int(n), int(nx), int(ny), _ptr(x), _ptr(ref), _ptr(mask) if mask is not None else None,
+                         out.ctypes.data_as(C.POINTER(C.c_double)), stream), "recon_iqa")
+    return out.reshape(int(n), 3)

@@ -108,3 +108,105 @@ def test_uniform_water_is_a_fixed_point():
     new, _ = modeb.iterate(st, 0.5, 0.5, 1e-2, t, geom, tab, g, z_method="dense")
     for key in ("f1", "f2", "rhoe", "zt"):
         assert np.max(np.abs(new[key] - st[key])) <= 1e-8, key
+
+
+# --- polyenergetic fidelity linearised by Gauss-Newton ----------------------
+
+def tiny_poly():
+    geom, _ = tiny()
+    acq = ph.acquisition("clinical", n=16)
+    return geom, model.Tables(acq.low, acq.high)
+
+
+def test_poly_jacobian_matches_finite_differences():
+    _, tab = tiny_poly()
+    rng = np.random.default_rng(7)
+    l1 = rng.uniform(0.0, 40.0, 9)
+    l2 = rng.uniform(0.0, 300.0, 9)
+    for arm in modeb.spectrum_rows(tab):
+        h, J1, J2 = modeb.poly_log(l1, l2, arm)
+        eps = 1e-4
+        d1 = (modeb.poly_log(l1 + eps, l2, arm)[0] - modeb.poly_log(l1 - eps, l2, arm)[0]) / (2 * eps)
+        d2 = (modeb.poly_log(l1, l2 + eps, arm)[0] - modeb.poly_log(l1, l2 - eps, arm)[0]) / (2 * eps)
+        assert np.allclose(J1, d1, rtol=1e-7) and np.allclose(J2, d2, rtol=1e-7)
+        # h is the -log of the spectrum-weighted transmission, written out bin by bin
+        w, m1, m2 = arm
+        ref = np.array([-np.log(np.sum(w * np.exp(-model.S_MM * (m1 * a + m2 * b)))) / model.S_MM
+                        for a, b in zip(l1, l2)])
+        assert np.allclose(h, ref, rtol=1e-12)
+
+
+def test_gauss_newton_reduces_to_the_linear_mode_for_mono_arms():
+    """Monoenergetic arms: J_ik = a_ki, so W_kk = alpha_k, W_12 = cross and
+    A^T v_k / gamma + the cross term of the linear mode agree."""
+    geom, tab = tiny()
+    g = modeb.gamma(geom)
+    rng = np.random.default_rng(8)
+    shape = (geom["ny"], geom["nx"])
+    st, hv = random_state(shape, 9)
+    sL = rng.uniform(0.0, 3.0, (geom["n_views"], geom["n_bins"]))
+    sH = rng.uniform(0.0, 2.5, (geom["n_views"], geom["n_bins"]))
+    l1, l2 = modeb.project(st["f1"], geom), modeb.project(st["f2"], geom)
+    W11, W22, W12, v1, v2 = modeb.gn_terms(l1, l2, sL, sH, tab)
+    for k, W in ((0, W11), (1, W22)):
+        alpha, _, cross = modeb.coefficients(k, tab)
+        assert np.allclose(W, alpha, rtol=1e-13)
+        assert np.allclose(W12, cross, rtol=1e-12)
+    t = modeb.data_images(sL, sH, geom, tab, g)
+    for k, v in ((0, v1), (1, v2)):
+        lin = modeb.rhs(k, st, hv, 0.4, t, geom, tab, g)
+        gn = modeb.rhs_gn(k, st, hv, 0.4, v, geom, tab, g)
+        assert np.allclose(gn, lin, rtol=1e-10, atol=1e-10 * np.abs(lin).max())
+
+
+def test_gauss_newton_solve_is_dense_solve_and_minimiser():
+    geom, tab = tiny_poly()
+    g = modeb.gamma(geom)
+    shape = (geom["ny"], geom["nx"])
+    n = shape[0] * shape[1]
+    st, hv = random_state(shape, 10)
+    rng = np.random.default_rng(11)
+    sL = rng.uniform(0.5, 3.0, (geom["n_views"], geom["n_bins"]))
+    sH = rng.uniform(0.4, 2.5, (geom["n_views"], geom["n_bins"]))
+    l1, l2 = modeb.project(st["f1"], geom), modeb.project(st["f2"], geom)
+    W11, W22, W12, v1, v2 = modeb.gn_terms(l1, l2, sL, sH, tab)
+    beta = 0.3
+    for k, W, v in ((0, W11, v1), (1, W22, v2)):
+        # dense A^T diag(W) A / gamma + c' + beta L from the projector's columns
+        Q = np.empty((n, n))
+        for c in range(n):
+            e = np.zeros(n)
+            e[c] = 1.0
+            Q[:, c] = modeb.normal_op(e.reshape(shape), k, beta, geom, tab, g, W).ravel()
+        b = modeb.rhs_gn(k, st, hv, beta, v, geom, tab, g)
+        ref = np.linalg.solve(Q, b.ravel()).reshape(shape)
+        got = modeb.f_solve(b, k, beta, geom, tab, g, np.zeros(shape), W=W)
+        assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref))
+        e0 = modeb.sub_objective_gn(got, k, st, hv, beta, l1, l2, sL, sH, geom, tab, g)
+        for s in range(3):
+            d = 1e-2 * rng.standard_normal(shape)
+            e1 = modeb.sub_objective_gn(got + d, k, st, hv, beta, l1, l2, sL, sH, geom, tab, g)
+            dqd = float(np.sum(d * modeb.normal_op(d, k, beta, geom, tab, g, W)))
+            assert e1 > e0 and abs((e1 - e0) - dqd) <= 1e-7 * dqd
+
+
+def test_uniform_material_is_a_gauss_newton_fixed_point():
+    """Noiseless polyenergetic sinograms (Kramers 80 / 140 kVp, Al, Sn) of a
+    uniform bone-like material: the exact state is kept by a whole iteration
+    of the Gauss-Newton mode (the linear mode would move it: beam hardening)."""
+    acq = ph.acquisition("clinical", n=16)
+    geom = ct.geometry(acq)
+    tab = model.Tables(acq.low, acq.high)
+    shape = (acq.ny, acq.nx)
+    Zv, rv = 11.0, 1.4
+    sL, sH = ct.simulate(np.full(shape, Zv), np.full(shape, rv), acq, seed=None)
+    st = alg1.init_state(np.full(shape, model.effective(model.mu_hat(rv, Zv, tab.arms[0][0]), tab.arms[0][1])),
+                         np.full(shape, model.effective(model.mu_hat(rv, Zv, tab.arms[1][0]), tab.arms[1][1])), tab)
+    assert np.allclose(model.z_from_ztilde(st["zt"]), Zv, rtol=1e-10)
+    g = modeb.gamma(geom)
+    new, _ = modeb.iterate_gn(st, 0.5, 0.5, 1e-2, sL, sH, geom, tab, g, z_method="dense")
+    for key in ("f1", "f2", "rhoe", "zt"):
+        assert np.max(np.abs(new[key] - st[key])) <= 1e-7 * max(1.0, np.abs(st[key]).max()), key
+    lin, _ = modeb.iterate(st, 0.5, 0.5, 1e-2, modeb.data_images(sL, sH, geom, tab, g), geom, tab, g,
+                           z_method="dense")
+    assert np.max(np.abs(lin["f1"] - st["f1"])) > 1e-3
