@@ -45,8 +45,9 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=200, help="requests per rate of the serving leg")
     ap.add_argument("--graph", action="store_true",
                     help="run each iteration as one CUDA graph launch (roofline then from the profiling pass)")
-    ap.add_argument("--domain", choices=["image", "sino"], default="image",
-                    help="data terms on the FBP image pair (as printed) or on the sinograms through the projector")
+    ap.add_argument("--domain", choices=["image", "sino", "poly"], default="image",
+                    help="data terms on the FBP image pair (as printed), on the sinograms through the projector "
+                         "(linear), or on the sinograms through the polyenergetic model linearised by Gauss-Newton")
     ap.add_argument("--slices", type=int, default=None)
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--precision", type=int, default=1)
@@ -59,6 +60,14 @@ def parse():
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
+
+DOMAIN_ID = {"image": 0, "sino": 1, "poly": 2}
+DOMAIN_NAME = {"image": "", "sino": ", sinogram-domain data terms",
+               "poly": ", polyenergetic sinogram-domain data terms (Gauss-Newton)"}
+DOMAIN_SAMPLE = {"image": "image-domain inputs from the oracle's model",
+                 "sino": "noisy sinograms from the oracle's scan model, sinogram-domain f updates",
+                 "poly": "noisy sinograms from the oracle's scan model, Gauss-Newton polyenergetic f updates"}
+
 
 def workload(args, rank):
     """Truth maps, acquisitions and iteration count of this rank's batch."""
@@ -370,20 +379,21 @@ class ClockSampler:
 def oracle_sample(slices, iters_sample, domain="image"):
     """Time the oracle on one slice of the workload for a bounded number of
     iterations (image-domain inputs made by the oracle's own model; with
-    domain "sino", noisy sinograms from the oracle's scan model and the
-    sinogram-domain f updates)."""
+    domain "sino" or "poly", noisy sinograms from the oracle's scan model and
+    the linear or Gauss-Newton sinogram-domain f updates)."""
     from oracle import alg1, model
     from synthetic import phantoms as ph
     Z, rho, acq = slices[0]
     Z = np.asarray(Z, np.float64)
     rho = np.asarray(rho, np.float64)
     ny, nx = Z.shape
-    if domain == "sino":
+    if domain in ("sino", "poly"):
         from oracle import ct, modeb
         sL, sH = ct.simulate(Z, rho, acq, seed=77)
         tab = model.Tables(acq.low, acq.high)
         t0 = time.perf_counter()
-        modeb.solve(sL, sH, ct.geometry(acq), tab, alg1.Params(iters=iters_sample))
+        (modeb.solve if domain == "sino" else modeb.solve_gn)(sL, sH, ct.geometry(acq), tab,
+                                                               alg1.Params(iters=iters_sample))
         dt = time.perf_counter() - t0
         return dict(value=iters_sample / dt, seconds=dt, nx=nx, ny=ny, iters=iters_sample)
     E = [model.spectrum_bins(s) for s in (acq.low, acq.high)]
@@ -455,8 +465,7 @@ def run_reference(args, rank, world):
     rounds = oracle_all_cores(slices, it, args.domain, cores, steps=args.steps, warmup=min(args.warmup, 1))
     value = float(sum(v for v, _ in rounds) / len(rounds))
     dt = sum(w for _, w in rounds)
-    what = ("noisy sinograms from the oracle's scan model, sinogram-domain f updates" if args.domain == "sino"
-            else "image-domain inputs from the oracle's model")
+    what = DOMAIN_SAMPLE[args.domain]
     line = dict(metric=METRIC, value=value, unit="slice-iters/s", n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000 * dt / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
@@ -508,7 +517,7 @@ def main():
     sino_lo, sino_hi = make_scans(rc, torch, slices, seed=4242 + rank)
     geoms = [rc.geometry_from_acq(acq) for _, _, acq in slices]
     params = [rc.default_params(low=acq.low, high=acq.high, iters=iters, precision=args.precision,
-                                domain=1 if args.domain == "sino" else 0)
+                                domain=DOMAIN_ID[args.domain])
               for _, _, acq in slices]
     solver = rc.Solver(geoms, params)
     if args.graph:
@@ -707,8 +716,7 @@ def main():
         r = oracle_sample(slices, 3 if not big else 1, args.domain)
         n_proc = os.cpu_count() or 1
         (v_all, wall), = oracle_all_cores(slices, 3 if not big else 1, args.domain, n_proc, steps=1, warmup=0)
-        what = ("noisy sinograms from the oracle's scan model, sinogram-domain f updates" if args.domain == "sino"
-                else "image-domain inputs from the oracle's model")
+        what = DOMAIN_SAMPLE[args.domain]
         cpu = dict(value=v_all, unit="slice-iters/s", cores=n_proc, kind="oracle",
                    sample=f"{n_proc} processes at once (spawn pool, math libraries single-threaded), each one "
                           f"{r['nx']}x{r['ny']} slice of the workload for {r['iters']} iteration(s), "
@@ -718,7 +726,7 @@ def main():
         line = dict(metric=METRIC, value=value, unit="slice-iters/s", n_gpus=world, steps=args.steps,
                     warmup=args.warmup, ms_per_step=ms / args.steps, higher_is_better=True, scaling="weak",
                     vs_baseline=None, dtype="f32" if args.precision == 1 else "f64", data="synthetic",
-                    config=dict(workload=name + (", sinogram-domain data terms" if args.domain == "sino" else ""),
+                    config=dict(workload=name + DOMAIN_NAME[args.domain],
                                 slices=len(slices), iters=iters, precision=args.precision,
                                 **({"slice_iters_per_s_512sq_equivalent": value * npx / (len(slices) * 512 * 512)}
                                    if args.workload == "uneven" else {}),

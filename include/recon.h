@@ -203,7 +203,9 @@ int recon_sync(recon_ctx* ctx);
  * recon_direct: Z and rho_e of the two-step image-based method -- the
  *   decomposition of the loaded image pair (eq. lac_EL/EH), the synthesis at
  *   E1, E2 (eq. mac_E1/E2) and the closed forms eq. rho_e, eq. Z_m with no
- *   regularisation, i.e. the maps of iteration 0 of Algorithm 1.  Z, rho_e:
+ *   regularisation, i.e. the maps of iteration 0 of Algorithm 1.  With the
+ *   sinogram-domain data terms (domain 1 or 2) the pair is the FBP of the
+ *   staged sinograms, formed again by this call.  Z, rho_e:
  *   caller-owned buffers of the total pixel count (slices unpadded, in order),
  *   host or device as on_device says.  RECON_ESTATE before recon_set_data.
  * recon_mono: monoenergetic images at n_e energies kev[0..n_e-1] (keV > 0,

@@ -235,6 +235,24 @@ int recon_init(const recon_geometry* geom, const recon_params* params, void* str
     return recon_init_batch(1, geom, params, stream, out);
 }
 
+// The FBP of both staged sinograms of every slice into the unpadded image
+// staging buffers d_stage[0], d_stage[1].  Consecutive slices of one geometry
+// go through the FBP together, up to kFbpGroup at a time (their sinograms and
+// images are contiguous).
+static int fbp_pair(Ctx& c) {
+    for (int s = 0; s < c.n;) {
+        int k = 1;
+        while (k < kFbpGroup && s + k < c.n && same_geometry(c.geo[s + k], c.geo[s])) ++k;
+        for (int a = 0; a < 2; ++a) {
+            const int rc = ct_fbp(c.geo[s], k, c.d_sino[a] + c.sino_off[s], c.d_stage[a] + c.sg[s].ext_off, c.d_filt,
+                                  c.stream, &c.launches);
+            if (rc) return rc;
+        }
+        s += k;
+    }
+    return RECON_OK;
+}
+
 int recon_set_data(recon_ctx* h, const float* low, const float* high, int on_device) {
     if (!h || !low || !high) {
         set_error("recon_set_data: bad arguments");
@@ -248,18 +266,7 @@ int recon_set_data(recon_ctx* h, const float* low, const float* high, int on_dev
         const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         RECON_CUDA(cudaMemcpyAsync(c.d_sino[0], low, sizeof(float) * c.sino_elems, kind, c.stream));
         RECON_CUDA(cudaMemcpyAsync(c.d_sino[1], high, sizeof(float) * c.sino_elems, kind, c.stream));
-        // consecutive slices of one geometry go through the FBP together, up to
-        // kFbpGroup at a time (their sinograms and images are contiguous)
-        for (int s = 0; s < c.n;) {
-            int k = 1;
-            while (k < kFbpGroup && s + k < c.n && same_geometry(c.geo[s + k], c.geo[s])) ++k;
-            for (int a = 0; a < 2; ++a) {
-                rc = ct_fbp(c.geo[s], k, c.d_sino[a] + c.sino_off[s], c.d_stage[a] + c.sg[s].ext_off, c.d_filt,
-                            c.stream, &c.launches);
-                if (rc) return rc;
-            }
-            s += k;
-        }
+        if ((rc = fbp_pair(c))) return rc;
         lo = c.d_stage[0];
         hi = c.d_stage[1];
     } else if (!on_device) {
@@ -357,9 +364,18 @@ int recon_direct(recon_ctx* h, float* Z, float* rhoe, int on_device) {
         set_error("recon_direct before recon_set_data");
         return RECON_ESTATE;
     }
-    if (on_device) return solver_direct(c, Z, rhoe);
+    // in the sinogram domains the loaded fields hold the data images of the f
+    // updates, so the FBP pair is formed again from the staged sinograms
     int rc;
-    if ((rc = solver_direct(c, c.d_stage[0], c.d_stage[1]))) return rc;
+    const float* lo = nullptr;
+    const float* hi = nullptr;
+    if (c.domain != 0) {
+        if ((rc = fbp_pair(c))) return rc;
+        lo = c.d_stage[0];
+        hi = c.d_stage[1];
+    }
+    if (on_device) return solver_direct(c, lo, hi, Z, rhoe);
+    if ((rc = solver_direct(c, lo, hi, c.d_stage[0], c.d_stage[1]))) return rc;
     RECON_CUDA(cudaMemcpyAsync(Z, c.d_stage[0], sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
     RECON_CUDA(cudaMemcpyAsync(rhoe, c.d_stage[1], sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
     RECON_CUDA(cudaStreamSynchronize(c.stream));

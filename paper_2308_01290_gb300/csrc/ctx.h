@@ -137,7 +137,9 @@ int solver_modeb_data(Ctx& c);                 // domain 1: data images t_k from
 int solver_iterate(Ctx& c, bool stats);        // one iteration of Algorithm 1
 int solver_op(Ctx& c, int op);
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int on_device);
-int solver_direct(Ctx& c, float* Z, float* rhoe);                // two-step comparator maps (device, unpadded)
+// two-step comparator maps (device, unpadded) from the loaded pair, or from
+// the unpadded images lo, hi (1/mm) when set
+int solver_direct(Ctx& c, const float* lo, const float* hi, float* Z, float* rhoe);
 int solver_mono(Ctx& c, int n_e, const double* kev, float* out); // monoenergetic images (device, unpadded)
 int solver_read_state(Ctx& c, std::vector<SliceState>& out);
 int solver_profile_read(Ctx& c, double* ms, long long* launches, unsigned long long* bytes);

@@ -2556,10 +2556,13 @@ __device__ __forceinline__ double mth_root_newton(double z, double m, double inv
 // the initialisation (init_pixel) with rho_e and z rounded to the map
 // precision as k_init stores them, then Z as k_extract forms it -- the maps
 // recon_get returns right after recon_set_data -- into unpadded Z, rho_e,
-// without touching the solve's state.
+// without touching the solve's state.  With lo, hi set, the image pair is read
+// from those unpadded images (in 1/mm, normalised and rounded as k_load does)
+// instead of the loaded fields; Z may alias lo and rhoe hi (each thread reads
+// its pixel's pair before it writes that pixel).
 template <typename T>
-__global__ void k_direct(ItemList L, const SliceGeom* G, const SliceConst* C, Ptrs<T> P, float* Z, float* rhoe,
-                         double zw, double m) {
+__global__ void k_direct(ItemList L, const SliceGeom* G, const SliceConst* C, Ptrs<T> P, const float* lo,
+                         const float* hi, float* Z, float* rhoe, double zw, double m) {
     const double inv_m = 1.0 / m;
     for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
         const Item it = L.items[w];
@@ -2571,7 +2574,9 @@ __global__ void k_direct(ItemList L, const SliceGeom* G, const SliceConst* C, Pt
             const long long d = g.off + (long long)y * g.pitch + x;
             const long long e = g.ext_off + (long long)y * g.nx + x;
             double f1, f2, rho, z;
-            init_pixel(c, P.f[RECON_F_MUL][d], P.f[RECON_F_MUH][d], f1, f2, rho, z);
+            const T uL = lo ? T((double)lo[e] * c.inv_S) : P.f[RECON_F_MUL][d];
+            const T uH = hi ? T((double)hi[e] * c.inv_S) : P.f[RECON_F_MUH][d];
+            init_pixel(c, uL, uH, f1, f2, rho, z);
             const double zs = (double)T(z);
             Z[e] = zs > 0.0 ? (float)(zw * mth_root_newton(zs, m, inv_m)) : 1.0f;
             rhoe[e] = (float)T(rho);
@@ -4308,14 +4313,15 @@ int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int /*on
     return c.precision == 1 ? extract_t<float>(c, Z, rhoe, f1, f2) : extract_t<double>(c, Z, rhoe, f1, f2);
 }
 
-int solver_direct(Ctx& c, float* Z, float* rhoe) {
+int solver_direct(Ctx& c, const float* lo, const float* hi, float* Z, float* rhoe) {
     const int grid = grid_for(c, c.tiles.n);
     if (c.precision == 1)
         k_direct<float><<<grid, kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const, ptrs<float>(c),
-                                                                Z, rhoe, water_z(), z_exponent());
+                                                                lo, hi, Z, rhoe, water_z(), z_exponent());
     else
         k_direct<double><<<grid, kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
-                                                                 ptrs<double>(c), Z, rhoe, water_z(), z_exponent());
+                                                                 ptrs<double>(c), lo, hi, Z, rhoe, water_z(),
+                                                                 z_exponent());
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
