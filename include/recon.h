@@ -94,7 +94,9 @@ typedef struct recon_params {
     double rho_air;                  /* initial Z^m set to water where rho_e < rho_air */
     int32_t pcg_kernel;              /* Z^m solve.  0: multigrid-preconditioned PCG on slices whose sides
                                         halve down to a small grid (below), FFT-preconditioned elsewhere;
-                                        2: FFT-preconditioned PCG on every slice (1 is refused) */
+                                        2: FFT-preconditioned PCG on every slice; 3: as 0, with every
+                                        FP32 strip level on the ghost-column strip kernels, which the
+                                        band kernels match bit for bit (a check; slower; 1 is refused) */
     int32_t domain;                  /* data terms of the arms: 0 on the image pair (Sec. II-B, as printed);
                                         1 on the sinograms through the projector, linear model (below);
                                         2 on the sinograms, polyenergetic model by Gauss-Newton (below) */
@@ -104,8 +106,8 @@ typedef struct recon_params {
  * rhs, L = dx'dx + dy'dy periodic).  Both stop at the relative residual
  * cg_tol.  FFT: D^-1/2 (mean(a^2) + beta~ L)^-1 D^-1/2 with D = diag((a^2 +
  * 4 beta~) / (mean(a^2) + 4 beta~)), applied by real FFTs.  Multigrid: one
- * V(1,1)-cycle, a damped Jacobi step (weight 0.8) before and after the
- * coarse correction, grids of half the sides (residual and a^2 restricted as
+ * V-cycle, two damped Jacobi steps (weight 0.8) before and after the coarse
+ * correction on every level, grids of half the sides (residual and a^2 restricted as
  * 2x2 means, corrections prolonged piecewise constant, beta~/4 per level),
  * an exact solve on the coarsest grid (its operator inverted once per Z^m
  * solve).  A slice takes the multigrid cycle
@@ -417,7 +419,7 @@ int recon_tuning(recon_ctx* ctx, int32_t* out2);
  * stream of the handle, ordered after earlier and before later work of the
  * handle's stream; the iteration that fills recon_stats, and iterations
  * while recon_profile is on, still run as separate launches.  Needs domain 0
- * and pcg_kernel 0 or 2 (RECON_EINVAL otherwise). */
+ * (RECON_EINVAL otherwise). */
 int recon_set_graph(recon_ctx* ctx, int32_t on);
 
 /* Number of kernels this handle has launched since creation (counting

@@ -70,7 +70,7 @@ void free_ctx(Ctx& c) {
 int check_params(const recon_params& p) {
     if (!(p.lambda > 0) || !(p.beta0 > 0) || !(p.beta_max > 0) || !(p.tau > 0) || p.iters < 0 ||
         p.cg_max_iters < 0 || !(p.cg_tol >= 0) || (p.precision != 0 && p.precision != 1) ||
-        (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 2) ||
+        (p.order != 0 && p.order != 1) || (p.pcg_kernel != 0 && p.pcg_kernel != 2 && p.pcg_kernel != 3) ||
         (p.domain < 0 || p.domain > 2) || (p.domain != 0 && (p.precision != 1 || p.order != 0)) || !(p.e1_kev > 0) ||
         !(p.e2_kev > 0) || p.e1_kev == p.e2_kev) {
         set_error("invalid recon_params");

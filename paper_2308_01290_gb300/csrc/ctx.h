@@ -55,8 +55,9 @@ struct Ctx {
     float* d_filt = nullptr;     // filtered sinogram scratch (one slice)
     void* d_tw = nullptr;        // FFT twiddle tables (map precision)
     void* d_sym = nullptr;       // |F dx|^2 symbol tables 4 sin^2(pi t/N) (map precision)
-    int* d_cg_pending = nullptr;
+    int* d_cg_pending = nullptr; // [0] slices whose Z^m PCG runs, [1] most steps a finished slice took
     int* h_cg_pending = nullptr; // pinned
+    int cg_pred = 0;             // steps of the last Z^m solve: when the host first checks the next one
 
     // accounting: algorithmic bytes per kernel family (device counters) and
     // optional CUDA-event timing of the families in prof_mask
@@ -80,7 +81,8 @@ struct Ctx {
     int mg_block_smem = 0, mg_inv_smem = 0;
     void* mg_qinv = nullptr;                  // per slice: inverse of its coarsest operator (kMgCoarsePx^2)
     DevItemList pcg_rows, pcg_cols;           // row and column items of the slices on the FFT preconditioner
-    std::vector<DevItemList> mg_strips;       // [l]: strip items of level l (k_mgs_*; FP32, width % 8 == 0)
+    std::vector<DevItemList> mg_strips;       // [l]: band items of level l (k_mgb_*; FP32, width % 8 == 0, <= 512)
+    std::vector<DevItemList> mg_wide;         // [l]: strip items of the wider such levels (k_mgs_*)
     std::vector<DevItemList> mg_tiles_rest;   // [l]: tile items of level l of the other slices (k_mg_down, k_mg_up)
     int mg_rb = 32;                           // rows a warp walks per strip item on the fine level
     std::vector<SliceConst> hconst;

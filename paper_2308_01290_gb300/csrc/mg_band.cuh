@@ -1,0 +1,455 @@
+// Fine-level passes of the multigrid-preconditioned Z^m PCG for FP32 slices
+// up to kBandMaxW columns wide (Alg. 1, Z^m line), as register-streaming band
+// kernels: the strip kernels' arithmetic (mg_strip.cuh: same rounding
+// sequence, same smoothing, same fusion of q = M p into the update pass, so
+// every value is the strip kernels' bit for bit) without ghost columns.
+// Included by solver.cu after mg_strip.cuh.
+//
+// Work layout.  A row of a level nx columns wide is covered by G = nx / 128
+// (rounded up) warps of one block, lanes of four columns (16-byte accesses).
+// Those G warps walk one band of rb rows together from top to bottom; a block
+// of kStripWarps warps holds 4 / G such groups (one when G = 3: the fourth
+// warp idles), so an item is 4 / G bands of one slice stacked vertically.
+// * Horizontal neighbours come from the adjacent lanes by warp shuffles.  Each
+//   warp's first column and last (active) column are published in shared
+//   memory, and after a barrier of the group the two edge lanes take their
+//   outer neighbour from there: the chunk to the left (the last chunk for the
+//   first column) and the chunk to the right (the first chunk for column
+//   nx - 1).  The whole row sits in one group, so the periodic boundary
+//   (reading R6) needs no ghost columns, and every quantity is formed once per
+//   column: no lane carries another lane's values.
+// * Vertical neighbours and the cp.async row rings are as in the strip
+//   kernels: a warp-private ring of kStripDepth slots per field.
+// The edge values alternate between two shared-memory buffers: between two
+// uses of one buffer every warp of the group passes the barrier of the other,
+// so no warp overwrites an edge that another has still to read.
+#pragma once
+
+namespace recon {
+
+constexpr int kBandMaxW = kStripWarps * kStripW;   // widest level the band kernels take (512)
+
+// Warps per row (G) of a level nx columns wide, and row bands per item.
+__host__ __device__ __forceinline__ int band_warps(int nx) { return (nx + kStripW - 1) / kStripW; }
+__host__ __device__ __forceinline__ int band_groups(int nx) {
+    const int g = band_warps(nx);
+    return g == 3 ? 1 : kStripWarps / g;
+}
+
+// One lane of a band item.
+struct BandLane {
+    long long off;
+    int nx, ny, pitch;
+    int x;       // first of the lane's four columns
+    int G;       // warps per row
+    int grp;     // the warp's row band within the item (>= band_groups: idle warp)
+    int wg;      // the warp's chunk of the row (columns wg * 128 ..)
+    int lastw;   // last lane of this warp holding columns
+    int lsrc;    // chunk whose last column lies left of column wg * 128
+    int rsrc;    // chunk whose first column lies right of the warp's last column
+    bool act;    // x < nx
+    bool idle;
+};
+
+__device__ __forceinline__ BandLane band_lane(const SliceGeom* G, int lane, int warp, int slice) {
+    const SliceGeom* g = G + slice;
+    BandLane b;
+    b.off = __ldg(&g->off);
+    b.nx = __ldg(&g->nx);
+    b.ny = __ldg(&g->ny);
+    b.pitch = __ldg(&g->pitch);
+    b.G = band_warps(b.nx);
+    b.grp = warp / b.G;
+    b.wg = warp - b.grp * b.G;
+    b.idle = b.grp >= band_groups(b.nx);
+    b.x = b.wg * kStripW + 4 * lane;
+    b.act = b.x < b.nx;
+    const int w = b.nx - b.wg * kStripW;   // columns from this chunk on (>= 8: widths are multiples of 8)
+    b.lastw = w >= kStripW ? 31 : w / 4 - 1;
+    b.lsrc = b.wg == 0 ? b.G - 1 : b.wg - 1;
+    b.rsrc = b.wg == b.G - 1 ? 0 : b.wg + 1;
+    return b;
+}
+
+__device__ __forceinline__ long long band_row(const BandLane& b, int t) {
+    return b.off + (long long)wrap_near(t, b.ny) * b.pitch;
+}
+
+// Pixels of a band item (all groups).
+__device__ __forceinline__ long long band_item_px(const BandLane& b, const Item& it, int rb) {
+    const int h = min(it.b + band_groups(b.nx) * rb, b.ny) - it.b;
+    return (long long)h * b.nx;
+}
+
+// Barrier of row-band group grp (named barriers 1 .. kStripWarps; immediate
+// ids, so that the kernels reserve only those).
+__device__ __forceinline__ void band_bar(int grp, int count) {
+    switch (grp) {
+        case 0: asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory"); break;
+        case 1: asm volatile("bar.sync 2, %0;" ::"r"(count) : "memory"); break;
+        case 2: asm volatile("bar.sync 3, %0;" ::"r"(count) : "memory"); break;
+        default: asm volatile("bar.sync 4, %0;" ::"r"(count) : "memory"); break;
+    }
+}
+
+// Edge values of one item: [buffer][group][chunk], .x the chunk's first
+// column, .y its last.
+struct BandEdges {
+    float2 e[2][kStripWarps][kStripWarps];
+};
+
+// Left and right neighbours of a lane's four columns of c (the values in the
+// columns x - 1 and x + 4).  Every warp of the group calls it at the same
+// point of its row walk.
+__device__ __forceinline__ float2 band_lr(const float4& c, const BandLane& b, int lane, BandEdges& E, int& buf) {
+    float2(&e)[kStripWarps] = E.e[buf][b.grp];
+    if (lane == 0) e[b.wg].x = c.x;
+    if (lane == b.lastw) e[b.wg].y = c.w;
+    band_bar(b.grp, 32 * b.G);
+    const float up = __shfl_up_sync(0xffffffffu, c.w, 1);
+    const float dn = __shfl_down_sync(0xffffffffu, c.x, 1);
+    const float l = lane == 0 ? e[b.lsrc].y : up;
+    const float r = lane == b.lastw ? e[b.rsrc].x : dn;
+    buf ^= 1;
+    return make_float2(l, r);
+}
+
+__device__ __forceinline__ float4 band_op(const float4& a, const float4& c, const float4& u, const float4& d, float bt,
+                                          const BandLane& b, int lane, BandEdges& E, int& buf) {
+    const float2 lr = band_lr(c, b, lane, E, buf);
+    return m_op4(a, c, lr.x, lr.y, u, d, bt);
+}
+__device__ __forceinline__ float4 sweep4(const float4& x, const float4& f, const float4& m, const float4& a, float b4) {
+    return make_float4(sweep(x.x, f.x, m.x, a.x, b4), sweep(x.y, f.y, m.y, a.y, b4), sweep(x.z, f.z, m.z, a.z, b4),
+                       sweep(x.w, f.w, m.w, a.w, b4));
+}
+
+template <int NF>
+struct BandRing {
+    float4 v[kStripDepth][NF][32];
+};
+
+template <int NF>
+constexpr int band_smem_bytes() {
+    return kStripWarps * (int)sizeof(BandRing<NF>);
+}
+
+// k_mgs_fwd on band items (see mg_strip.cuh for the pass).
+template <bool UPD>
+__global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                              const SliceConst* C, SliceState* S, Ptrs<float> P,
+                                                              int par, const float* rin, float* rout,
+                                                              const float* a2, float* F1, int* pending, int rb,
+                                                              int lvl) {
+    extern __shared__ __align__(16) unsigned char strip_dsm[];
+    __shared__ double red[32];
+    __shared__ BandEdges E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // fields: 0 p, 1 r, 2 a^2, 3 z
+    BandRing<4>& ring = reinterpret_cast<BandRing<4>*>(strip_dsm)[warp];
+    float* z = P.f[RECON_F_Z];
+    const float* p = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        const BandLane b = band_lane(G, lane, warp, it.slice);
+        const SliceGeom* g1p = G1 + it.slice;
+        const long long off1 = __ldg(&g1p->off);
+        const int pitch1 = __ldg(&g1p->pitch);
+        account(P.acct, lvl ? KF_MG_LEVELS : KF_MG_FWD, band_item_px(b, it, rb) * (UPD ? 25 : 9));
+        const float bt = mg_bt<float>(*sp, lvl), b4 = 4.f * bt;
+        const float al = UPD ? Sc<float>::alpha(*sp) : 0.f;
+        const int r0 = min(it.b + b.grp * rb, b.ny), r1 = min(r0 + rb, b.ny);
+        float acc = 0.f;
+        float4 res_prev = {};
+        int buf = 0;
+        auto restrict_row = [&](const float4& res, int wr) {
+            if ((wr - r0) & 1) {
+                if (b.act) {
+                    const float c0 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.x, res_prev.y), res.x), res.y);
+                    const float c1 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.z, res_prev.w), res.z), res.w);
+                    *reinterpret_cast<float2*>(F1 + off1 + (long long)(wr >> 1) * pitch1 + (b.x >> 1)) =
+                        make_float2(0.25f * c0, 0.25f * c1);
+                }
+            } else {
+                res_prev = res;
+            }
+        };
+        auto sub4 = [](const float4& f, const float4& m) {
+            return make_float4(__fsub_rn(f.x, m.x), __fsub_rn(f.y, m.y), __fsub_rn(f.z, m.z), __fsub_rn(f.w, m.w));
+        };
+        if (!b.idle && r0 < r1) {
+            float4 am1 = {}, am2 = {}, rm1 = {}, rm2 = {}, x1m1 = {}, x1m2 = {}, x2m1 = {}, x2m2 = {};
+            if constexpr (UPD) {
+                // bundle t: p of row t in [r0-3, r1+2]; r, a^2 of row u = t-1 in [r0-2, r1+1]; z of u in [r0, r1)
+                auto issue = [&](int t, int k) {
+                    if (b.act) cp_async16(&ring.v[k][0][lane], p + band_row(b, t) + b.x);
+                    const int u = t - 1;
+                    if (u >= r0 - 2 && u <= r1 + 1 && b.act) {
+                        const long long ro = band_row(b, u);
+                        cp_async16(&ring.v[k][1][lane], rin + ro + b.x);
+                        cp_async16(&ring.v[k][2][lane], a2 + ro + b.x);
+                        if (u >= r0 && u < r1) cp_async16(&ring.v[k][3][lane], z + ro + b.x);
+                    }
+                };
+                float4 pm2 = {}, pm1 = {};
+                auto compute = [&](int t, int k) {
+                    const float4 pt = ring.v[k][0][lane];
+                    if (t >= r0 - 1) {
+                        // row u = t-1: q = M p, r' = r - alpha q, x1 = J r' (and z += alpha p)
+                        const int u = t - 1;
+                        const float4 au = ring.v[k][2][lane];
+                        const float4 q = band_op(au, pm1, pm2, pt, bt, b, lane, E, buf);
+                        const float4 rn = fma4(-al, q, ring.v[k][1][lane]);
+                        const float4 x1 = jac4(rn, au, b4);
+                        if (u >= r0 && u < r1 && b.act)
+                            *reinterpret_cast<float4*>(z + band_row(b, u) + b.x) = fma4(al, pm1, ring.v[k][3][lane]);
+                        if (t >= r0 + 1) {
+                            // row v = t-2: second pre-smoothing sweep
+                            const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
+                                                     am1, b4);
+                            if (t >= r0 + 3) {
+                                // row w = t-3: residual after pre-smoothing, r' out, r'.r', restriction
+                                const int wr = t - 3;
+                                const float4 res = sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf));
+                                if (b.act) {
+                                    *reinterpret_cast<float4*>(rout + band_row(b, wr) + b.x) = rm2;
+                                    acc = dot4(rm2, rm2, acc);
+                                }
+                                restrict_row(res, wr);
+                            }
+                            x2m2 = x2m1;
+                            x2m1 = x2;
+                        }
+                        x1m2 = x1m1;
+                        x1m1 = x1;
+                        rm2 = rm1;
+                        rm1 = rn;
+                        am2 = am1;
+                        am1 = au;
+                    }
+                    pm2 = pm1;
+                    pm1 = pt;
+                };
+                strip_stream(r0 - 3, r1 + 2, issue, compute);
+            } else {
+                // bundle t: r, a^2 of row t in [r0-2, r1+1]
+                auto issue = [&](int t, int k) {
+                    if (b.act) {
+                        const long long ro = band_row(b, t);
+                        cp_async16(&ring.v[k][1][lane], rin + ro + b.x);
+                        cp_async16(&ring.v[k][2][lane], a2 + ro + b.x);
+                    }
+                };
+                auto compute = [&](int t, int k) {
+                    const float4 rt = ring.v[k][1][lane], at = ring.v[k][2][lane];
+                    const float4 x1 = jac4(rt, at, b4);
+                    if (t >= r0) {
+                        // row v = t-1: second pre-smoothing sweep
+                        const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
+                                                 am1, b4);
+                        if (t >= r0 + 2) {
+                            // row w = t-2: residual after pre-smoothing, restriction
+                            restrict_row(sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf)), t - 2);
+                        }
+                        x2m2 = x2m1;
+                        x2m1 = x2;
+                    }
+                    x1m2 = x1m1;
+                    x1m1 = x1;
+                    rm2 = rm1;
+                    rm1 = rt;
+                    am2 = am1;
+                    am1 = at;
+                };
+                strip_stream(r0 - 2, r1 + 1, issue, compute);
+            }
+        }
+        if (UPD) {
+            const float part[1] = {b.act && !b.idle ? acc : 0.f};
+            double a[1];
+            block_sum_t<float, 1>(part, a, red);
+            double tot[1];
+            if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
+                SliceState& so = S[it.slice];
+                const SliceConst& cs = C[it.slice];
+                so.rr = tot[0];
+                so.cg_it += 1;
+                const bool conv = !(tot[0] > cs.cg_tol * cs.cg_tol * so.bb);
+                if (conv || so.cg_it >= cs.cg_max) {
+                    so.cg_done = 1;
+                    atomicSub(pending, 1);
+                    atomicMax(pending + 1, so.cg_it);
+                }
+            }
+        } else {
+            __syncthreads();   // the next item's edges reuse E
+        }
+    }
+}
+
+// k_mgs_up on band items (see mg_strip.cuh for the pass).
+template <bool FINE>
+__global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const SliceGeom* G, const SliceGeom* G1,
+                                                             SliceState* S, Ptrs<float> P, const float* r,
+                                                             const float* a2, const float* E1, float* out, int rb,
+                                                             int lvl) {
+    extern __shared__ __align__(16) unsigned char strip_dsm[];
+    __shared__ double red[32];
+    __shared__ BandEdges E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // fields: 0 r, 1 a^2, 2 e1 (.x, .y: the lane's two coarse cells)
+    BandRing<3>& ring = reinterpret_cast<BandRing<3>*>(strip_dsm)[warp];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        const BandLane b = band_lane(G, lane, warp, it.slice);
+        const SliceGeom* g1p = G1 + it.slice;
+        const long long off1 = __ldg(&g1p->off);
+        const int pitch1 = __ldg(&g1p->pitch);
+        account(P.acct, FINE ? KF_MG_Y : KF_MG_LEVELS, band_item_px(b, it, rb) * 13);
+        const float bt = mg_bt<float>(*sp, lvl), b4 = 4.f * bt;
+        const int r0 = min(it.b + b.grp * rb, b.ny), r1 = min(r0 + rb, b.ny);
+        float acc = 0.f;
+        int buf = 0;
+        if (!b.idle && r0 < r1) {
+            // bundle t: r, a^2 of row t in [r0-3, r1+2]; e1 under row u = t-1 in [r0-2, r1+1]
+            auto issue = [&](int t, int k) {
+                if (b.act) {
+                    const long long ro = band_row(b, t);
+                    cp_async16(&ring.v[k][0][lane], r + ro + b.x);
+                    cp_async16(&ring.v[k][1][lane], a2 + ro + b.x);
+                    const int u = t - 1;
+                    if (u >= r0 - 2 && u <= r1 + 1) {
+                        const long long co = off1 + (long long)(wrap_near(u, b.ny) >> 1) * pitch1;
+                        cp_async_elem<8>(&ring.v[k][2][lane], E1 + co + (b.x >> 1));
+                    }
+                }
+            };
+            float4 rm1 = {}, rm2 = {}, rm3 = {}, am1 = {}, am2 = {}, am3 = {};
+            float4 x1m1 = {}, x1m2 = {}, xm1 = {}, xm2 = {}, xpm1 = {}, xpm2 = {};
+            auto compute = [&](int t, int k) {
+                const float4 rt = ring.v[k][0][lane], at = ring.v[k][1][lane];
+                const float4 x1 = jac4(rt, at, b4);
+                if (t >= r0 - 1) {
+                    // row u = t-1: second pre-smoothing sweep, then the prolonged correction
+                    float4 x = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf), am1, b4);
+                    const float4 e = ring.v[k][2][lane];
+                    x.x = __fadd_rn(x.x, e.x);
+                    x.y = __fadd_rn(x.y, e.x);
+                    x.z = __fadd_rn(x.z, e.y);
+                    x.w = __fadd_rn(x.w, e.y);
+                    if (t >= r0 + 1) {
+                        // row v = t-2: first post-smoothing sweep
+                        const float4 xp = sweep4(xm1, rm2, band_op(am2, xm1, xm2, x, bt, b, lane, E, buf), am2, b4);
+                        if (t >= r0 + 3) {
+                            // row w = t-3: second post-smoothing sweep, out (and r.y)
+                            const float4 y =
+                                sweep4(xpm1, rm3, band_op(am3, xpm1, xpm2, xp, bt, b, lane, E, buf), am3, b4);
+                            if (b.act) {
+                                *reinterpret_cast<float4*>(out + band_row(b, t - 3) + b.x) = y;
+                                if (FINE) acc = dot4(rm3, y, acc);
+                            }
+                        }
+                        xpm2 = xpm1;
+                        xpm1 = xp;
+                    }
+                    xm2 = xm1;
+                    xm1 = x;
+                }
+                x1m2 = x1m1;
+                x1m1 = x1;
+                rm3 = rm2;
+                rm2 = rm1;
+                rm1 = rt;
+                am3 = am2;
+                am2 = am1;
+                am1 = at;
+            };
+            strip_stream(r0 - 3, r1 + 2, issue, compute);
+        }
+        if (FINE) {
+            const float part[1] = {b.act && !b.idle ? acc : 0.f};
+            double a[1];
+            block_sum_t<float, 1>(part, a, red);
+            double tot[1];
+            if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
+                SliceState& so = S[it.slice];
+                set_betacg(so, (so.cg_it == 0) ? 0.0 : tot[0] / so.ry);
+                so.ry = tot[0];
+            }
+        } else {
+            __syncthreads();   // the next item's edges reuse E
+        }
+    }
+}
+
+// k_mgs_pq on band items (see mg_strip.cuh for the pass).
+template <bool STOREQ>
+__global__ void __launch_bounds__(kStripThreads, 4) k_mgb_pq(ItemList L, const SliceGeom* G, SliceState* S,
+                                                             Ptrs<float> P, int par, int rb) {
+    extern __shared__ __align__(16) unsigned char strip_dsm[];
+    __shared__ double red[32];
+    __shared__ BandEdges E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // fields: 0 y, 1 p_old, 2 a^2
+    BandRing<3>& ring = reinterpret_cast<BandRing<3>*>(strip_dsm)[warp];
+    const float* yf = P.f[RECON_F_CG_Y];
+    const float* pold = P.f[par ? RECON_F_CG_P1 : RECON_F_CG_P0];
+    float* pnew = P.f[par ? RECON_F_CG_P0 : RECON_F_CG_P1];
+    const float* a2 = P.f[RECON_F_A2];
+    float* qo = P.f[RECON_F_CG_Q];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active) || __ldg(&sp->cg_done)) continue;
+        const BandLane b = band_lane(G, lane, warp, it.slice);
+        const bool first = __ldg(&sp->cg_it) == 0;
+        account(P.acct, KF_MG_PQ, band_item_px(b, it, rb) * (first ? 12 : 16));
+        const float bc = first ? 0.f : Sc<float>::betacg(*sp), bt = Sc<float>::beta_t(*sp);
+        const int r0 = min(it.b + b.grp * rb, b.ny), r1 = min(r0 + rb, b.ny);
+        float acc = 0.f;
+        int buf = 0;
+        if (!b.idle && r0 < r1) {
+            // bundle t: y, p_old of row t in [r0-1, r1]; a^2 of row t-1 in [r0, r1-1]
+            auto issue = [&](int t, int k) {
+                if (b.act) {
+                    const long long ro = band_row(b, t);
+                    cp_async16(&ring.v[k][0][lane], yf + ro + b.x);
+                    if (!first) cp_async16(&ring.v[k][1][lane], pold + ro + b.x);
+                    if (t - 1 >= r0 && t - 1 < r1) cp_async16(&ring.v[k][2][lane], a2 + band_row(b, t - 1) + b.x);
+                }
+            };
+            float4 pm2 = {}, pm1 = {};
+            auto compute = [&](int t, int k) {
+                float4 pt = ring.v[k][0][lane];
+                if (!first) pt = fma4(bc, ring.v[k][1][lane], pt);
+                if (t >= r0 && t < r1 && b.act) *reinterpret_cast<float4*>(pnew + band_row(b, t) + b.x) = pt;
+                if (t >= r0 + 1) {
+                    // row t-1: q = M p, p.q
+                    const float4 q = band_op(ring.v[k][2][lane], pm1, pm2, pt, bt, b, lane, E, buf);
+                    if (b.act) {
+                        acc = dot4(pm1, q, acc);
+                        if (STOREQ) *reinterpret_cast<float4*>(qo + band_row(b, t - 1) + b.x) = q;
+                    }
+                }
+                pm2 = pm1;
+                pm1 = pt;
+            };
+            strip_stream(r0 - 1, r1, issue, compute);
+        }
+        const float part[1] = {b.act && !b.idle ? acc : 0.f};
+        double a[1];
+        block_sum_t<float, 1>(part, a, red);
+        double tot[1];
+        if (item_reduce<1>(L, w, it.slice, a, tot, red)) {
+            SliceState& so = S[it.slice];
+            so.pq = tot[0];
+            set_alpha(so, tot[0] > 0.0 ? so.ry / tot[0] : 0.0);
+        }
+    }
+}
+
+}  // namespace recon

@@ -386,6 +386,7 @@ __global__ void __launch_bounds__(kStripThreads, 3) k_mgs_fwd(ItemList L, const 
                 if (conv || so.cg_it >= cs.cg_max) {
                     so.cg_done = 1;
                     atomicSub(pending, 1);
+                    atomicMax(pending + 1, so.cg_it);
                 }
             }
         }

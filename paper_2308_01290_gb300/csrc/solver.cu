@@ -1053,6 +1053,7 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_pcg_fwd(ItemList
                 if (conv || so.cg_it >= c.cg_max) {
                     so.cg_done = 1;
                     atomicSub(pending, 1);
+                    atomicMax(pending + 1, so.cg_it);
                 }
             }
         }
@@ -1900,6 +1901,7 @@ __global__ void __launch_bounds__(kStencilThreads, 3) k_mg_fwd(ItemList L, const
                 if (conv || so.cg_it >= cs.cg_max) {
                     so.cg_done = 1;
                     atomicSub(pending, 1);
+                    atomicMax(pending + 1, so.cg_it);
                 }
             }
         }
@@ -2073,6 +2075,7 @@ __global__ void __launch_bounds__(kStencilThreads, 4) k_mg_pq(ItemList L, const 
 
 }  // namespace recon
 #include "mg_strip.cuh"
+#include "mg_band.cuh"
 namespace recon {
 
 // Sides of the in-block levels of a block level of bx x by pixels: halve while
@@ -2807,6 +2810,21 @@ int strip_rows(const Ctx& c, int l) {
     return r < 8 ? 8 : r;
 }
 
+// One pass of the strip family on level l: the band kernel over the band items
+// (levels up to kBandMaxW wide), the ghost-column strip kernel over the strip
+// items of wider levels.
+template <typename FB, typename FS>
+void strip_pass(Ctx& c, int l, FB band, FS wide) {
+    if (c.mg_strips[l].n) {
+        band(c.mg_strips[l]);
+        c.launches += 1;
+    }
+    if (c.mg_wide[l].n) {
+        wide(c.mg_wide[l]);
+        c.launches += 1;
+    }
+}
+
 // a^2 of every multigrid level from the fine a^2 (once per Z^m solve).
 template <typename T>
 void mg_restrict_a2(Ctx& c, bool timed) {
@@ -2831,19 +2849,29 @@ template <typename T, bool UPD>
 void mg_fwd(Ctx& c, int par, int rk, bool timed) {
     MaybeTimer t(c, KF_MG_FWD, timed);
     if constexpr (std::is_same<T, float>::value) {
-        // FP32: the register-streaming strip kernel over strips of the fine level
-        const DevItemList& S = c.mg_strips[0];
-        k_mgs_fwd<UPD><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
-            S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
-            mg_r<T>(c, rk ^ 1), field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending,
-            strip_rows(c, 0), 0);
+        // FP32: the register-streaming band / strip kernels over the fine level
+        const int rb = strip_rows(c, 0);
+        strip_pass(
+            c, 0,
+            [&](const DevItemList& S) {
+                k_mgb_fwd<UPD><<<grid_for(c, S.n), kStripThreads, band_smem_bytes<4>(), c.stream>>>(
+                    S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
+                    mg_r<T>(c, rk ^ 1), field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, rb,
+                    0);
+            },
+            [&](const DevItemList& S) {
+                k_mgs_fwd<UPD><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
+                    S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
+                    mg_r<T>(c, rk ^ 1), field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, rb,
+                    0);
+            });
     } else {
         const DevItemList& L = c.mg_tiles[0];
         k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufFwd<T>), c.stream>>>(
             L.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
             mg_r<T>(c, rk ^ 1), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending);
+        c.launches += 1;
     }
-    c.launches += 1;
 }
 
 // Fine level of the cycle and the new direction: y (k_mgs_y / k_mg_y), then p
@@ -2852,17 +2880,34 @@ template <typename T>
 void mg_fine_tail(Ctx& c, int par, int rk, bool timed) {
     T* pe = static_cast<T*>(c.mg_pool[2]);
     if constexpr (std::is_same<T, float>::value) {
-        const DevItemList& S = c.mg_strips[0];
+        const int rb = strip_rows(c, 0);
         {
             MaybeTimer t(c, KF_MG_Y, timed);
-            k_mgs_up<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
-                S.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk),
-                field_t<T>(c, RECON_F_A2), pe, field_t<T>(c, RECON_F_CG_Y), strip_rows(c, 0), 0);
+            strip_pass(
+                c, 0,
+                [&](const DevItemList& S) {
+                    k_mgb_up<true><<<grid_for(c, S.n), kStripThreads, band_smem_bytes<3>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk),
+                        field_t<T>(c, RECON_F_A2), pe, field_t<T>(c, RECON_F_CG_Y), rb, 0);
+                },
+                [&](const DevItemList& S) {
+                    k_mgs_up<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_mg_geom[1], c.d_state, ptrs<T>(c), mg_r<T>(c, rk),
+                        field_t<T>(c, RECON_F_A2), pe, field_t<T>(c, RECON_F_CG_Y), rb, 0);
+                });
         }
         {
             MaybeTimer t(c, KF_MG_PQ, timed);
-            k_mgs_pq<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
-                S.view(), c.d_geom, c.d_state, ptrs<T>(c), par, strip_rows(c, 0));
+            strip_pass(
+                c, 0,
+                [&](const DevItemList& S) {
+                    k_mgb_pq<false><<<grid_for(c, S.n), kStripThreads, band_smem_bytes<3>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_state, ptrs<T>(c), par, rb);
+                },
+                [&](const DevItemList& S) {
+                    k_mgs_pq<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_state, ptrs<T>(c), par, rb);
+                });
         }
     } else {
         const DevItemList& L0 = c.mg_tiles[0];
@@ -2876,8 +2921,8 @@ void mg_fine_tail(Ctx& c, int par, int rk, bool timed) {
             k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(
                 L0.view(), c.d_geom, c.d_state, ptrs<T>(c), par);
         }
+        c.launches += 2;
     }
-    c.launches += 2;
 }
 
 // Rest of a multigrid PCG step for residual buffer rk: the V-cycle below the
@@ -2891,13 +2936,19 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
         MaybeTimer t(c, KF_MG_LEVELS, timed);
         for (int l = 1; l < c.mg_max_lb; ++l) {
             if constexpr (std::is_same<T, float>::value) {
-                const DevItemList& S = c.mg_strips[l];
-                if (S.n) {
-                    k_mgs_fwd<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
-                        S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_const, c.d_state, ptrs<T>(c), 0, pf,
-                        nullptr, pa, pf, c.d_cg_pending, strip_rows(c, l), l);
-                    c.launches += 1;
-                }
+                const int rb = strip_rows(c, l);
+                strip_pass(
+                    c, l,
+                    [&](const DevItemList& S) {
+                        k_mgb_fwd<false><<<grid_for(c, S.n), kStripThreads, band_smem_bytes<4>(), c.stream>>>(
+                            S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_const, c.d_state, ptrs<T>(c), 0, pf,
+                            nullptr, pa, pf, c.d_cg_pending, rb, l);
+                    },
+                    [&](const DevItemList& S) {
+                        k_mgs_fwd<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
+                            S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_const, c.d_state, ptrs<T>(c), 0, pf,
+                            nullptr, pa, pf, c.d_cg_pending, rb, l);
+                    });
             }
             const DevItemList& L = c.mg_tiles_rest[l];
             if (L.n) {
@@ -2917,13 +2968,19 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
         MaybeTimer t(c, KF_MG_LEVELS, timed);
         for (int l = c.mg_max_lb - 1; l >= 1; --l) {
             if constexpr (std::is_same<T, float>::value) {
-                const DevItemList& S = c.mg_strips[l];
-                if (S.n) {
-                    k_mgs_up<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
-                        S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_state, ptrs<T>(c), pf, pa, pe, pe,
-                        strip_rows(c, l), l);
-                    c.launches += 1;
-                }
+                const int rb = strip_rows(c, l);
+                strip_pass(
+                    c, l,
+                    [&](const DevItemList& S) {
+                        k_mgb_up<false><<<grid_for(c, S.n), kStripThreads, band_smem_bytes<3>(), c.stream>>>(
+                            S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_state, ptrs<T>(c), pf, pa, pe, pe, rb,
+                            l);
+                    },
+                    [&](const DevItemList& S) {
+                        k_mgs_up<false><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                            S.view(), c.d_mg_geom[l], c.d_mg_geom[l + 1], c.d_state, ptrs<T>(c), pf, pa, pe, pe, rb,
+                            l);
+                    });
             }
             const DevItemList& L = c.mg_tiles_rest[l];
             if (L.n) {
@@ -2939,7 +2996,7 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
 template <typename T>
 int op_solve_z(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
-    RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream));
+    RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, 2 * sizeof(int), c.stream));
     {
         FamTimer t0(c, KF_CG_INIT);
         k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 2 * sizeof(CgInitBuf<T>), c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
@@ -2976,6 +3033,12 @@ int op_solve_z(Ctx& c) {
     }
     int cap = 0;
     for (const auto& p : c.prm) cap = p.cg_max_iters > cap ? p.cg_max_iters : cap;
+    // The host learns that every slice has converged by reading the pending
+    // count, which costs a synchronisation.  The first read comes after as
+    // many steps as the previous Z^m solve took (its slowest slice; the warm
+    // started solves of consecutive iterations take similar counts), then
+    // every two steps.
+    const int first_check = c.cg_pred > 0 ? c.cg_pred : 4;
     for (int it = 0; it < cap; ++it) {
         if (fft) {
             {
@@ -3006,11 +3069,15 @@ int op_solve_z(Ctx& c) {
         }
         RECON_CUDA(cudaGetLastError());
         par ^= 1;
-        if ((it & 3) == 3 || it == cap - 1) {
-            RECON_CUDA(cudaMemcpyAsync(c.h_cg_pending, c.d_cg_pending, sizeof(int), cudaMemcpyDeviceToHost,
+        const int done = it + 1;   // updating steps launched
+        if ((done >= first_check && (done - first_check) % 2 == 0) || it == cap - 1) {
+            RECON_CUDA(cudaMemcpyAsync(c.h_cg_pending, c.d_cg_pending, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                        c.stream));
             RECON_CUDA(cudaStreamSynchronize(c.stream));
-            if (*c.h_cg_pending <= 0) break;
+            if (c.h_cg_pending[0] <= 0) {
+                c.cg_pred = c.h_cg_pending[1];
+                break;
+            }
         }
     }
     c.cg_parity = par;
@@ -3462,14 +3529,31 @@ int op_z_matvec(Ctx& c) {
             // CG_R and p to Z
             RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_CG_R2], 0, c.elem * (size_t)c.pool_elems, c.stream));
             RECON_CUDA(cudaMemsetAsync(c.field[RECON_F_Z], 0, c.elem * (size_t)c.pool_elems, c.stream));
-            const DevItemList& S = c.mg_strips[0];
-            k_mgs_pq<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
-                S.view(), c.d_geom, c.d_state, P, 0, strip_rows(c, 0));
+            const int rb = strip_rows(c, 0);
+            strip_pass(
+                c, 0,
+                [&](const DevItemList& S) {
+                    k_mgb_pq<true><<<grid_for(c, S.n), kStripThreads, band_smem_bytes<3>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_state, P, 0, rb);
+                },
+                [&](const DevItemList& S) {
+                    k_mgs_pq<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<3>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_state, P, 0, rb);
+                });
             k_zmv_alpha<<<(c.n + 127) / 128, 128, 0, c.stream>>>(c.n, c.d_state);
-            k_mgs_fwd<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
-                S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, P, 0, mg_r<T>(c, 1), mg_r<T>(c, 0),
-                field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, strip_rows(c, 0), 0);
-            c.launches += 3;
+            c.launches += 1;
+            strip_pass(
+                c, 0,
+                [&](const DevItemList& S) {
+                    k_mgb_fwd<true><<<grid_for(c, S.n), kStripThreads, band_smem_bytes<4>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, P, 0, mg_r<T>(c, 1), mg_r<T>(c, 0),
+                        field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, rb, 0);
+                },
+                [&](const DevItemList& S) {
+                    k_mgs_fwd<true><<<grid_for(c, S.n), kStripThreads, strip_smem_bytes<4>(), c.stream>>>(
+                        S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, P, 0, mg_r<T>(c, 1), mg_r<T>(c, 0),
+                        field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, rb, 0);
+                });
         } else {
             const DevItemList& L0 = c.mg_tiles[0];
             k_mg_pq<T><<<grid_for(c, L0.n), kStencilThreads, 2 * sizeof(MgBufPq<T>), c.stream>>>(
@@ -3664,29 +3748,33 @@ bool mg_strip_level(const Ctx& c, int s, int l) {
 // mg_strip_level holds, and tiles (for the tile kernels) on the other slices
 // with that level.  Host lists only.
 void level_items(Ctx& c, int l, const std::vector<int>* slots) {
-    DevItemList& S = c.mg_strips[l];
+    DevItemList& B = c.mg_strips[l];
+    DevItemList& W = c.mg_wide[l];
     DevItemList& T = c.mg_tiles_rest[l];
-    for (DevItemList* X : {&S, &T}) {
+    for (DevItemList* X : {&B, &W, &T}) {
         X->h_items.clear();
         X->h_lo.assign(c.n, 0);
         X->h_cnt.assign(c.n, 0);
     }
-    const int bh = kStripWarps * strip_rows(c, l);
+    const int rb = strip_rows(c, l);
     const int th = c.precision == 1 ? kTileHFloat : kTileHDouble;
     auto add = [&](int s) {
-        S.h_lo[s] = (int)S.h_items.size();
-        T.h_lo[s] = (int)T.h_items.size();
-        if (c.mg_lb[s] <= l) return;
-        const int nx = c.sg[s].nx >> l, ny = c.sg[s].ny >> l;
-        if (mg_strip_level(c, s, l)) {
-            for (int y0 = 0; y0 < ny; y0 += bh)
-                for (int x0 = 0; x0 < nx; x0 += kStripW) S.h_items.push_back(Item{s, x0, y0, 0});
-        } else {
-            for (int ty = 0; ty < ny; ty += th)
-                for (int tx = 0; tx < nx; tx += kTileW) T.h_items.push_back(Item{s, tx, ty, 0});
+        for (DevItemList* X : {&B, &W, &T}) X->h_lo[s] = (int)X->h_items.size();
+        if (c.mg_lb[s] > l) {
+            const int nx = c.sg[s].nx >> l, ny = c.sg[s].ny >> l;
+            if (mg_strip_level(c, s, l) && nx <= kBandMaxW && c.prm[s].pcg_kernel != 3) {
+                const int bh = band_groups(nx) * rb;
+                for (int y0 = 0; y0 < ny; y0 += bh) B.h_items.push_back(Item{s, 0, y0, 0});
+            } else if (mg_strip_level(c, s, l)) {
+                const int bh = kStripWarps * rb;
+                for (int y0 = 0; y0 < ny; y0 += bh)
+                    for (int x0 = 0; x0 < nx; x0 += kStripW) W.h_items.push_back(Item{s, x0, y0, 0});
+            } else {
+                for (int ty = 0; ty < ny; ty += th)
+                    for (int tx = 0; tx < nx; tx += kTileW) T.h_items.push_back(Item{s, tx, ty, 0});
+            }
         }
-        S.h_cnt[s] = (int)S.h_items.size() - S.h_lo[s];
-        T.h_cnt[s] = (int)T.h_items.size() - T.h_lo[s];
+        for (DevItemList* X : {&B, &W, &T}) X->h_cnt[s] = (int)X->h_items.size() - X->h_lo[s];
     };
     if (!slots)
         for (int s = 0; s < c.n; ++s) add(s);
@@ -3716,7 +3804,9 @@ int mg_lists_for(Ctx& c, const std::vector<int>& slots) {
     }
     for (int l = 0; l < c.mg_max_lb; ++l) {
         level_items(c, l, &slots);
-        if ((rc = fill_list(c, c.mg_strips[l])) || (rc = fill_list(c, c.mg_tiles_rest[l]))) return rc;
+        if ((rc = fill_list(c, c.mg_strips[l])) || (rc = fill_list(c, c.mg_wide[l])) ||
+            (rc = fill_list(c, c.mg_tiles_rest[l])))
+            return rc;
     }
     return pcg_split_lists(c);
 }
@@ -3775,11 +3865,14 @@ int mg_setup_server(Ctx& c) {
         if ((rc = upload_list(c, c.mg_tiles[l]))) return rc;
     }
     c.mg_strips.assign(L, DevItemList{});
+    c.mg_wide.assign(L, DevItemList{});
     c.mg_tiles_rest.assign(L, DevItemList{});
     for (int l = 0; l < L; ++l) {
         const std::vector<int> none;
         level_items(c, l, &none);
-        if ((rc = upload_list(c, c.mg_strips[l])) || (rc = upload_list(c, c.mg_tiles_rest[l]))) return rc;
+        if ((rc = upload_list(c, c.mg_strips[l])) || (rc = upload_list(c, c.mg_wide[l])) ||
+            (rc = upload_list(c, c.mg_tiles_rest[l])))
+            return rc;
     }
     pcg_split_host(c);
     if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols))) return rc;
@@ -3868,10 +3961,13 @@ int mg_setup(Ctx& c) {
         if ((rc = upload_list(c, T))) return rc;
     }
     c.mg_strips.assign(L, DevItemList{});
+    c.mg_wide.assign(L, DevItemList{});
     c.mg_tiles_rest.assign(L, DevItemList{});
     for (int l = 0; l < L; ++l) {
         level_items(c, l, nullptr);
-        if ((rc = upload_list(c, c.mg_strips[l])) || (rc = upload_list(c, c.mg_tiles_rest[l]))) return rc;
+        if ((rc = upload_list(c, c.mg_strips[l])) || (rc = upload_list(c, c.mg_wide[l])) ||
+            (rc = upload_list(c, c.mg_tiles_rest[l])))
+            return rc;
     }
     // row and column items of the PCG on the slices that keep the FFT preconditioner
     pcg_split_host(c);
@@ -4038,10 +4134,10 @@ int solver_setup(Ctx& c) {
         if ((rc = alloc_dev(c, &c.spec[f], 2 * c.elem * c.spec_elems))) return rc;
     for (int i = 0; i < 2; ++i)
         if ((rc = alloc_dev(c, (void**)&c.d_stage[i], sizeof(float) * c.ext_elems))) return rc;
-    if ((rc = alloc_dev(c, (void**)&c.d_cg_pending, sizeof(int)))) return rc;
+    if ((rc = alloc_dev(c, (void**)&c.d_cg_pending, 2 * sizeof(int)))) return rc;
     if ((rc = alloc_dev(c, (void**)&c.d_acct, sizeof(unsigned long long) * KF_COUNT))) return rc;
     RECON_CUDA(cudaMemset(c.d_acct, 0, sizeof(unsigned long long) * KF_COUNT));
-    RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, sizeof(int)));
+    RECON_CUDA(cudaMallocHost((void**)&c.h_cg_pending, 2 * sizeof(int)));
     RECON_CUDA(cudaStreamCreateWithFlags(&c.side_stream, cudaStreamNonBlocking));
     RECON_CUDA(cudaEventCreateWithFlags(&c.side_ev[0], cudaEventDisableTiming));
     RECON_CUDA(cudaEventCreateWithFlags(&c.side_ev[1], cudaEventDisableTiming));

@@ -113,7 +113,7 @@ def bad_params(rc):
             rc.default_params(**base, beta0=0.0), rc.default_params(**base, tau=-1.0),
             rc.default_params(**base, iters=-1), rc.default_params(**base, cg_max_iters=-1),
             rc.default_params(**base, cg_tol=-1.0), rc.default_params(**base, precision=2),
-            rc.default_params(**base, order=2), rc.default_params(**base, pcg_kernel=3),
+            rc.default_params(**base, order=2), rc.default_params(**base, pcg_kernel=4),
             rc.default_params(**base, pcg_kernel=1),
             rc.default_params(**base, e1_kev=50.0, e2_kev=50.0)]
 

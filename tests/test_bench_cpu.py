@@ -48,13 +48,13 @@ def test_traffic_record_without_file_is_none(tmp_path, monkeypatch):
 def test_committed_traffic_record_is_well_formed():
     """The committed record names sources that exist, and its algorithmic
     bytes are the kernel's own count for the captured launch: 160 slices of
-    512^2, 7.25 FP32 maps per pixel (z, p, r, q, a^2 in; z, r out; a quarter
-    map of level-1 residual out)."""
+    512^2, 6.25 FP32 maps per pixel (z, p, r, a^2 in; z, r out; a quarter map
+    of level-1 residual out; q = M p is formed again from p)."""
     with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
         rec = json.load(f)["mg_fwd"]
     assert rec["sources"] and all(os.path.isfile(os.path.join(ROOT, s)) for s in rec["sources"])
     assert "paper_2308_01290_gb300/csrc/solver.cu" in rec["sources"]
-    assert rec["algorithmic_bytes_per_launch"] == 160 * 512 * 512 * 4 * 29 // 4
+    assert rec["algorithmic_bytes_per_launch"] == 160 * 512 * 512 * 4 * 25 // 4
     assert rec["dram_bytes_per_launch"] == rec["dram_read"] + rec["dram_write"]
     assert 0.5 < rec["dram_bytes_per_launch"] / rec["algorithmic_bytes_per_launch"] < 1.5
 

@@ -233,19 +233,24 @@ def test_invalid_sizes_rejected(rc):
         s.step(1)      # before set_data
 
 
-@pytest.mark.parametrize("shape,precision", [((128, 128), 1), ((256, 192), 1), ((320, 320), 1), ((128, 128), 0)])
+@pytest.mark.parametrize("shape,precision", [((128, 128), 1), ((256, 192), 1), ((320, 320), 1), ((640, 96), 1),
+                                            ((128, 128), 0)])
 def test_multigrid_pcg_matches_fft_pcg(rc, shape, precision):
     """The Z^m PCG with the multigrid V-cycle (pcg_kernel 0 on slices that
     halve down to a small grid) and with the FFT preconditioner (pcg_kernel
     2) on the same normal equations, built by the oracle from a noisy
     phantom, with a step cap high enough for both: both reach the PCG
     tolerance and the oracle's exact solution, and the multigrid cycle takes
-    fewer steps."""
+    fewer steps.  The FP32 widths take every layout of the fine and strip
+    levels: one to four warps per row (128, 256, 320 with an idle warp) and
+    ghost-column strips (640, whose level 1 is 320 wide)."""
     nx, ny = shape
     acq = ph.acquisition("small")
     tab = model.Tables(acq.low, acq.high)
-    P = ph.small_phantom(31, n=max(nx, ny))
-    Z, rho = P["Z"][:ny, :nx], P["rhoe"][:ny, :nx]
+    n = max(nx, ny)
+    P = ph.small_phantom(31, n=n)
+    y0, x0 = (n - ny) // 2, (n - nx) // 2   # the middle of the phantom
+    Z, rho = P["Z"][y0:y0 + ny, x0:x0 + nx], P["rhoe"][y0:y0 + ny, x0:x0 + nx]
     L = (model.mu_mm(rho, Z, 60.0) + 4e-4 * ph.normal_field((ny, nx), 32)).astype(np.float32)
     H = (model.mu_mm(rho, Z, 90.0) + 4e-4 * ph.normal_field((ny, nx), 33)).astype(np.float32)
     st = alg1.init_state(L.astype(np.float64) / model.S_MM, H.astype(np.float64) / model.S_MM, tab)
@@ -273,6 +278,34 @@ def test_multigrid_pcg_matches_fft_pcg(rc, shape, precision):
         assert np.abs(z - zx).max() <= 1e-3 * np.abs(zx).max(), path
         s.close()
     assert steps[0] < steps[2], steps
+
+
+def test_band_kernels_equal_strip_kernels(rc):
+    """The band kernels (a row of up to 512 columns across the warps of one
+    block) form every value of the ghost-column strip kernels' cycle with the
+    same rounding sequence: a batch of slices 128, 256 x 192, 320 (an idle
+    warp per block) and 512 wide, 10 iterations, gives bitwise the same maps
+    with pcg_kernel 0 (band kernels) and 3 (strip kernels on every level)."""
+    acq = ph.acquisition("small")
+    shapes = [(128, 128), (256, 192), (320, 320), (512, 512)]
+    lo, hi = [], []
+    for k, (nx, ny) in enumerate(shapes):
+        n = max(nx, ny)
+        P = ph.small_phantom(40 + k, n=n)
+        Z, rho = P["Z"][:ny, :nx], P["rhoe"][:ny, :nx]
+        lo.append((model.mu_mm(rho, Z, 60.0) + 4e-4 * ph.normal_field((ny, nx), 50 + k)).astype(np.float32).ravel())
+        hi.append((model.mu_mm(rho, Z, 90.0) + 4e-4 * ph.normal_field((ny, nx), 60 + k)).astype(np.float32).ravel())
+    out = {}
+    for path in (0, 3):
+        p = rc.default_params(low=acq.low, high=acq.high, iters=10, pcg_kernel=path)
+        s = rc.Solver([rc.geometry(nx, ny) for nx, ny in shapes], [p] * len(shapes))
+        s.set_data(np.concatenate(lo), np.concatenate(hi))
+        s.step(10)
+        out[path] = s.get_host()
+        s.close()
+    for a, b in zip(out[0], out[3]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
 
 
 def test_graph_iterations_equal_separate_launches(rc, small_case):
