@@ -81,6 +81,8 @@ struct Ctx {
     int mg_block_smem = 0, mg_inv_smem = 0;
     void* mg_qinv = nullptr;                  // per slice: inverse of its coarsest operator (kMgCoarsePx^2)
     DevItemList pcg_rows, pcg_cols;           // row and column items of the slices on the FFT preconditioner
+    DevItemList cg_tiles;                     // k_cg_init tiles: slices without a band fine level
+    DevItemList thr_band, thr_tiles;          // threshold pass: band items (FP32, width % 4 == 0, <= 512), tiles of the rest
     std::vector<DevItemList> mg_strips;       // [l]: band items of level l (k_mgb_*; FP32, width % 8 == 0, <= 512)
     std::vector<DevItemList> mg_wide;         // [l]: strip items of the wider such levels (k_mgs_*)
     std::vector<DevItemList> mg_tiles_rest;   // [l]: tile items of level l of the other slices (k_mg_down, k_mg_up)

@@ -134,6 +134,58 @@ constexpr int band_smem_bytes() {
     return kStripWarps * (int)sizeof(BandRing<NF>);
 }
 
+template <int K>
+using Slot = std::integral_constant<int, K>;
+using Full = std::true_type;
+using Edge = std::false_type;
+
+// Streams rows ta .. tb of a warp through its ring as strip_stream does, with
+// compute(t, slot, full).  Rows sa .. sb are the steady part of the walk,
+// where every condition of compute on t holds: there the rows go four at a
+// time with the ring slots and `full` as compile-time constants, so compute
+// drops its tests and indexes the ring with immediate offsets.  Elsewhere
+// slot is a run-time int and full is false.
+template <typename FI, typename FC>
+__device__ __forceinline__ void band_stream(int ta, int tb, int sa, int sb, FI issue, FC compute) {
+    constexpr int D = kStripDepth;
+    static_assert(D == 4, "four rows per steady round");
+#pragma unroll
+    for (int i = 0; i < D - 1; ++i) {
+        if (ta + i <= tb) issue(ta + i, i);
+        cp_async_commit();
+    }
+    auto step = [&](int t, auto k, auto full) {
+        __syncwarp();
+        if (t + D - 1 <= tb) issue(t + D - 1, (k + D - 1) % D);
+        cp_async_commit();
+        cp_async_wait<D - 1>();
+        __syncwarp();
+        compute(t, k, full);
+    };
+    int t = ta, slot = 0;
+    while (t <= tb) {
+        if (slot == 0 && t >= sa && t + D - 1 <= sb) {
+            step(t, Slot<0>{}, Full{});
+            step(t + 1, Slot<1>{}, Full{});
+            step(t + 2, Slot<2>{}, Full{});
+            step(t + 3, Slot<3>{}, Full{});
+            t += D;
+        } else {
+            step(t, slot, Edge{});
+            ++t;
+            slot = slot == D - 1 ? 0 : slot + 1;
+        }
+    }
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+// Offset of row t (full: a row inside the slice, no wrap).
+template <typename F>
+__device__ __forceinline__ long long band_row_at(const BandLane& b, int t, F full) {
+    return full ? b.off + (long long)t * b.pitch : band_row(b, t);
+}
+
 // k_mgs_fwd on band items (see mg_strip.cuh for the pass).
 template <bool UPD>
 __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const SliceGeom* G, const SliceGeom* G1,
@@ -164,8 +216,9 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
         float acc = 0.f;
         float4 res_prev = {};
         int buf = 0;
-        auto restrict_row = [&](const float4& res, int wr) {
-            if ((wr - r0) & 1) {
+        // odd: wr - r0 is odd (the second row of a restricted pair)
+        auto restrict_row = [&](const float4& res, int wr, bool odd) {
+            if (odd) {
                 if (b.act) {
                     const float c0 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.x, res_prev.y), res.x), res.y);
                     const float c1 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.z, res_prev.w), res.z), res.w);
@@ -194,30 +247,33 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                     }
                 };
                 float4 pm2 = {}, pm1 = {};
-                auto compute = [&](int t, int k) {
+                // steady rows t in [r0+3, r1]: slot k holds bundle t with t - r0 + 3 = k (mod 4), so
+                // wr - r0 = t - 3 - r0 has the parity of k
+                auto compute = [&](int t, auto k, auto full) {
                     const float4 pt = ring.v[k][0][lane];
-                    if (t >= r0 - 1) {
+                    if (full || t >= r0 - 1) {
                         // row u = t-1: q = M p, r' = r - alpha q, x1 = J r' (and z += alpha p)
                         const int u = t - 1;
                         const float4 au = ring.v[k][2][lane];
                         const float4 q = band_op(au, pm1, pm2, pt, bt, b, lane, E, buf);
                         const float4 rn = fma4(-al, q, ring.v[k][1][lane]);
                         const float4 x1 = jac4(rn, au, b4);
-                        if (u >= r0 && u < r1 && b.act)
-                            *reinterpret_cast<float4*>(z + band_row(b, u) + b.x) = fma4(al, pm1, ring.v[k][3][lane]);
-                        if (t >= r0 + 1) {
+                        if ((full || (u >= r0 && u < r1)) && b.act)
+                            *reinterpret_cast<float4*>(z + band_row_at(b, u, full) + b.x) =
+                                fma4(al, pm1, ring.v[k][3][lane]);
+                        if (full || t >= r0 + 1) {
                             // row v = t-2: second pre-smoothing sweep
                             const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
                                                      am1, b4);
-                            if (t >= r0 + 3) {
+                            if (full || t >= r0 + 3) {
                                 // row w = t-3: residual after pre-smoothing, r' out, r'.r', restriction
                                 const int wr = t - 3;
                                 const float4 res = sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf));
                                 if (b.act) {
-                                    *reinterpret_cast<float4*>(rout + band_row(b, wr) + b.x) = rm2;
+                                    *reinterpret_cast<float4*>(rout + band_row_at(b, wr, full) + b.x) = rm2;
                                     acc = dot4(rm2, rm2, acc);
                                 }
-                                restrict_row(res, wr);
+                                restrict_row(res, wr, full ? (k & 1) != 0 : ((wr - r0) & 1) != 0);
                             }
                             x2m2 = x2m1;
                             x2m1 = x2;
@@ -232,7 +288,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                     pm2 = pm1;
                     pm1 = pt;
                 };
-                strip_stream(r0 - 3, r1 + 2, issue, compute);
+                band_stream(r0 - 3, r1 + 2, r0 + 3, r1, issue, compute);
             } else {
                 // bundle t: r, a^2 of row t in [r0-2, r1+1]
                 auto issue = [&](int t, int k) {
@@ -242,16 +298,20 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                         cp_async16(&ring.v[k][2][lane], a2 + ro + b.x);
                     }
                 };
-                auto compute = [&](int t, int k) {
+                // steady rows t in [r0+2, r1+1]: slot k holds bundle t with t - r0 + 2 = k (mod 4), so
+                // w - r0 = t - 2 - r0 has the parity of k
+                auto compute = [&](int t, auto k, auto full) {
                     const float4 rt = ring.v[k][1][lane], at = ring.v[k][2][lane];
                     const float4 x1 = jac4(rt, at, b4);
-                    if (t >= r0) {
+                    if (full || t >= r0) {
                         // row v = t-1: second pre-smoothing sweep
                         const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
                                                  am1, b4);
-                        if (t >= r0 + 2) {
+                        if (full || t >= r0 + 2) {
                             // row w = t-2: residual after pre-smoothing, restriction
-                            restrict_row(sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf)), t - 2);
+                            const int wr = t - 2;
+                            restrict_row(sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf)), wr,
+                                         full ? (k & 1) != 0 : ((wr - r0) & 1) != 0);
                         }
                         x2m2 = x2m1;
                         x2m1 = x2;
@@ -263,7 +323,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                     am2 = am1;
                     am1 = at;
                 };
-                strip_stream(r0 - 2, r1 + 1, issue, compute);
+                band_stream(r0 - 2, r1 + 1, r0 + 2, r1 + 1, issue, compute);
             }
         }
         if (UPD) {
@@ -285,6 +345,135 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
             }
         } else {
             __syncthreads();   // the next item's edges reuse E
+        }
+    }
+}
+
+// Start of a Z^m solve on the band items of the fine level: k_cg_init and the
+// first step's k_mgb_fwd<false> in one pass.  r = rhs - M z (the operator in
+// the stencil kernels' rounding sequence, so r equals k_cg_init's bit for
+// bit), r out to CG_R, its two pre-smoothing sweeps and the restriction of the
+// smoothed residual to level 1 (into F1 on grid G1), and per slice the sums
+// r.r, sum a^2 and ||rhs||^2 that initialise the PCG scalars and the
+// convergence test as k_cg_init does.  Every active slice takes part: the
+// previous solve's cg_done is reset here.
+__global__ void __launch_bounds__(kStripThreads, 4) k_mgb_start(ItemList L, const SliceGeom* G,
+                                                                const SliceGeom* G1, const SliceConst* C,
+                                                                SliceState* S, Ptrs<float> P, float* F1,
+                                                                int* pending, int rb) {
+    extern __shared__ __align__(16) unsigned char strip_dsm[];
+    __shared__ double red[3 * 32];
+    __shared__ BandEdges E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // fields: 0 z, 1 rhs, 2 a^2
+    BandRing<3>& ring = reinterpret_cast<BandRing<3>*>(strip_dsm)[warp];
+    const float* z = P.f[RECON_F_Z];
+    const float* rz = P.f[RECON_F_RHS_Z];
+    const float* a2 = P.f[RECON_F_A2];
+    float* rout = P.f[RECON_F_CG_R];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        const SliceState* sp = S + it.slice;
+        if (!__ldg(&sp->active)) continue;
+        const BandLane b = band_lane(G, lane, warp, it.slice);
+        const SliceGeom* g1p = G1 + it.slice;
+        const long long off1 = __ldg(&g1p->off);
+        const int pitch1 = __ldg(&g1p->pitch);
+        account(P.acct, KF_CG_INIT, band_item_px(b, it, rb) * 17);
+        const float bt = Sc<float>::beta_t(*sp), b4 = 4.f * bt;
+        const int r0 = min(it.b + b.grp * rb, b.ny), r1 = min(r0 + rb, b.ny);
+        float acc_r = 0.f, acc_a = 0.f, acc_b = 0.f;
+        float4 res_prev = {};
+        int buf = 0;
+        auto restrict_row = [&](const float4& res, int wr, bool odd) {
+            if (odd) {
+                if (b.act) {
+                    const float c0 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.x, res_prev.y), res.x), res.y);
+                    const float c1 = __fadd_rn(__fadd_rn(__fadd_rn(res_prev.z, res_prev.w), res.z), res.w);
+                    *reinterpret_cast<float2*>(F1 + off1 + (long long)(wr >> 1) * pitch1 + (b.x >> 1)) =
+                        make_float2(0.25f * c0, 0.25f * c1);
+                }
+            } else {
+                res_prev = res;
+            }
+        };
+        auto sub4 = [](const float4& f, const float4& m) {
+            return make_float4(__fsub_rn(f.x, m.x), __fsub_rn(f.y, m.y), __fsub_rn(f.z, m.z), __fsub_rn(f.w, m.w));
+        };
+        if (!b.idle && r0 < r1) {
+            float4 am1 = {}, am2 = {}, rm1 = {}, rm2 = {}, x1m1 = {}, x1m2 = {}, x2m1 = {}, x2m2 = {};
+            float4 zm2 = {}, zm1 = {};
+            // bundle t: z of row t in [r0-3, r1+2]; rhs, a^2 of row u = t-1 in [r0-2, r1+1]
+            auto issue = [&](int t, int k) {
+                if (b.act) {
+                    cp_async16(&ring.v[k][0][lane], z + band_row(b, t) + b.x);
+                    const int u = t - 1;
+                    if (u >= r0 - 2 && u <= r1 + 1) {
+                        const long long ro = band_row(b, u);
+                        cp_async16(&ring.v[k][1][lane], rz + ro + b.x);
+                        cp_async16(&ring.v[k][2][lane], a2 + ro + b.x);
+                    }
+                }
+            };
+            // steady rows t in [r0+3, r1]: slot k holds bundle t with t - r0 + 3 = k (mod 4)
+            auto compute = [&](int t, auto k, auto full) {
+                const float4 zt = ring.v[k][0][lane];
+                if (full || t >= r0 - 1) {
+                    // row u = t-1: r = rhs - M z, x1 = J r
+                    const int u = t - 1;
+                    const float4 au = ring.v[k][2][lane], bu = ring.v[k][1][lane];
+                    const float4 rn = sub4(bu, band_op(au, zm1, zm2, zt, bt, b, lane, E, buf));
+                    const float4 x1 = jac4(rn, au, b4);
+                    if ((full || (u >= r0 && u < r1)) && b.act) {
+                        acc_a = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(acc_a, au.x), au.y), au.z), au.w);
+                        acc_b = dot4(bu, bu, acc_b);
+                    }
+                    if (full || t >= r0 + 1) {
+                        // row v = t-2: second pre-smoothing sweep
+                        const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
+                                                 am1, b4);
+                        if (full || t >= r0 + 3) {
+                            // row w = t-3: r out, r.r, residual after pre-smoothing, restriction
+                            const int wr = t - 3;
+                            const float4 res = sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf));
+                            if (b.act) {
+                                *reinterpret_cast<float4*>(rout + band_row_at(b, wr, full) + b.x) = rm2;
+                                acc_r = dot4(rm2, rm2, acc_r);
+                            }
+                            restrict_row(res, wr, full ? (k & 1) != 0 : ((wr - r0) & 1) != 0);
+                        }
+                        x2m2 = x2m1;
+                        x2m1 = x2;
+                    }
+                    x1m2 = x1m1;
+                    x1m1 = x1;
+                    rm2 = rm1;
+                    rm1 = rn;
+                    am2 = am1;
+                    am1 = au;
+                }
+                zm2 = zm1;
+                zm1 = zt;
+            };
+            band_stream(r0 - 3, r1 + 2, r0 + 3, r1, issue, compute);
+        }
+        const bool own = b.act && !b.idle;
+        const float part[3] = {own ? acc_r : 0.f, own ? acc_a : 0.f, own ? acc_b : 0.f};
+        double a[3];
+        block_sum_t<float, 3>(part, a, red);
+        double tot[3];
+        if (item_reduce<3>(L, w, it.slice, a, tot, red)) {
+            SliceState& so = S[it.slice];
+            const double tol2 = C[it.slice].cg_tol * C[it.slice].cg_tol;
+            set_abar2(so, tot[1] / ((double)b.nx * (double)b.ny));
+            so.bb = tot[2];
+            so.rr = tot[0];
+            so.rr0 = tot[0];
+            so.cg_it = 0;
+            so.ry = 0.0;
+            set_betacg(so, 0.0);
+            so.cg_done = (so.bb == 0.0 || !(tot[0] > tol2 * so.bb)) ? 1 : 0;
+            if (!so.cg_done) atomicAdd(pending, 1);
         }
     }
 }
@@ -330,10 +519,11 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const S
             };
             float4 rm1 = {}, rm2 = {}, rm3 = {}, am1 = {}, am2 = {}, am3 = {};
             float4 x1m1 = {}, x1m2 = {}, xm1 = {}, xm2 = {}, xpm1 = {}, xpm2 = {};
-            auto compute = [&](int t, int k) {
+            // steady rows t in [r0+3, r1+2]
+            auto compute = [&](int t, auto k, auto full) {
                 const float4 rt = ring.v[k][0][lane], at = ring.v[k][1][lane];
                 const float4 x1 = jac4(rt, at, b4);
-                if (t >= r0 - 1) {
+                if (full || t >= r0 - 1) {
                     // row u = t-1: second pre-smoothing sweep, then the prolonged correction
                     float4 x = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf), am1, b4);
                     const float4 e = ring.v[k][2][lane];
@@ -341,15 +531,15 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const S
                     x.y = __fadd_rn(x.y, e.x);
                     x.z = __fadd_rn(x.z, e.y);
                     x.w = __fadd_rn(x.w, e.y);
-                    if (t >= r0 + 1) {
+                    if (full || t >= r0 + 1) {
                         // row v = t-2: first post-smoothing sweep
                         const float4 xp = sweep4(xm1, rm2, band_op(am2, xm1, xm2, x, bt, b, lane, E, buf), am2, b4);
-                        if (t >= r0 + 3) {
+                        if (full || t >= r0 + 3) {
                             // row w = t-3: second post-smoothing sweep, out (and r.y)
                             const float4 y =
                                 sweep4(xpm1, rm3, band_op(am3, xpm1, xpm2, xp, bt, b, lane, E, buf), am3, b4);
                             if (b.act) {
-                                *reinterpret_cast<float4*>(out + band_row(b, t - 3) + b.x) = y;
+                                *reinterpret_cast<float4*>(out + band_row_at(b, t - 3, full) + b.x) = y;
                                 if (FINE) acc = dot4(rm3, y, acc);
                             }
                         }
@@ -368,7 +558,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const S
                 am2 = am1;
                 am1 = at;
             };
-            strip_stream(r0 - 3, r1 + 2, issue, compute);
+            band_stream(r0 - 3, r1 + 2, r0 + 3, r1 + 2, issue, compute);
         }
         if (FINE) {
             const float part[1] = {b.act && !b.idle ? acc : 0.f};
@@ -423,22 +613,24 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_pq(ItemList L, const S
                 }
             };
             float4 pm2 = {}, pm1 = {};
-            auto compute = [&](int t, int k) {
+            // steady rows t in [r0+1, r1-1]
+            auto compute = [&](int t, auto k, auto full) {
                 float4 pt = ring.v[k][0][lane];
                 if (!first) pt = fma4(bc, ring.v[k][1][lane], pt);
-                if (t >= r0 && t < r1 && b.act) *reinterpret_cast<float4*>(pnew + band_row(b, t) + b.x) = pt;
-                if (t >= r0 + 1) {
+                if ((full || (t >= r0 && t < r1)) && b.act)
+                    *reinterpret_cast<float4*>(pnew + band_row_at(b, t, full) + b.x) = pt;
+                if (full || t >= r0 + 1) {
                     // row t-1: q = M p, p.q
                     const float4 q = band_op(ring.v[k][2][lane], pm1, pm2, pt, bt, b, lane, E, buf);
                     if (b.act) {
                         acc = dot4(pm1, q, acc);
-                        if (STOREQ) *reinterpret_cast<float4*>(qo + band_row(b, t - 1) + b.x) = q;
+                        if (STOREQ) *reinterpret_cast<float4*>(qo + band_row_at(b, t - 1, full) + b.x) = q;
                     }
                 }
                 pm2 = pm1;
                 pm1 = pt;
             };
-            strip_stream(r0 - 1, r1, issue, compute);
+            band_stream(r0 - 1, r1, r0 + 1, r1 - 1, issue, compute);
         }
         const float part[1] = {b.act && !b.idle ? acc : 0.f};
         double a[1];

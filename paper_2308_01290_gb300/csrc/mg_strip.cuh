@@ -97,12 +97,6 @@ __device__ __forceinline__ long long strip_item_px(const Lane& s, const Item& it
     return (long long)h * min(kStripW, s.nx - it.a);
 }
 
-// The Z^m operator at one pixel, a c + bt ((4c - l - r) - (u + d)): the one
-// rounding sequence every strip kernel uses.
-__device__ __forceinline__ float m_op(float a, float c, float l, float r, float u, float d, float bt) {
-    const float lap = __fsub_rn(__fsub_rn(__fsub_rn(__fmul_rn(4.f, c), l), r), __fadd_rn(u, d));
-    return __fmaf_rn(a, c, __fmul_rn(bt, lap));
-}
 __device__ __forceinline__ float4 m_op4(float4 a, float4 c, float l, float r, float4 u, float4 d, float bt) {
     return make_float4(m_op(a.x, c.x, l, c.y, u.x, d.x, bt), m_op(a.y, c.y, c.x, c.z, u.y, d.y, bt),
                        m_op(a.z, c.z, c.y, c.w, u.z, d.z, bt), m_op(a.w, c.w, c.z, r, u.w, d.w, bt));

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <type_traits>
 #include <memory>
+#include <tuple>
 #include <vector>
 
 #include "ctx.h"
@@ -1450,6 +1451,14 @@ __device__ __forceinline__ void for_halo_vec(FV fv, FS fs) {
 
 // (a^2 x + bt L x) for the VN pixels of row ry from column c0 (x in sx with
 // its halo), given a^2 there.
+// The Z^m operator at one pixel in FP32, a c + bt ((4c - l - r) - (u + d)):
+// the one rounding sequence of every FP32 kernel that forms it (k_cg_init and
+// the strip and band kernels), so that they agree bit for bit.
+__device__ __forceinline__ float m_op(float a, float c, float l, float r, float u, float d, float bt) {
+    const float lap = __fsub_rn(__fsub_rn(__fsub_rn(__fmul_rn(4.f, c), l), r), __fadd_rn(u, d));
+    return __fmaf_rn(a, c, __fmul_rn(bt, lap));
+}
+
 template <typename T>
 __device__ __forceinline__ Pack<T> mx_pack(const T (*sx)[TileDim<T>::SW], int ry, int c0, const Pack<T>& a, T bt,
                                            Pack<T>& xc) {
@@ -1462,8 +1471,12 @@ __device__ __forceinline__ Pack<T> mx_pack(const T (*sx)[TileDim<T>::SW], int ry
     for (int e = 0; e < VN; ++e) {
         const T l = e == 0 ? xl : xc.v[e - 1];
         const T r = e == VN - 1 ? xr : xc.v[e + 1];
-        const T lap = (T(4) * xc.v[e] - l - r) - (xu.v[e] + xd.v[e]);
-        o.v[e] = a.v[e] * xc.v[e] + bt * lap;
+        if constexpr (std::is_same<T, float>::value) {
+            o.v[e] = m_op(a.v[e], xc.v[e], l, r, xu.v[e], xd.v[e], bt);
+        } else {
+            const T lap = (T(4) * xc.v[e] - l - r) - (xu.v[e] + xd.v[e]);
+            o.v[e] = a.v[e] * xc.v[e] + bt * lap;
+        }
     }
     return o;
 }
@@ -1717,7 +1730,7 @@ __global__ void __launch_bounds__(kStencilThreads, 4) k_cg_init(ItemList L, cons
             Pack<T> rv;
 #pragma unroll
             for (int e = 0; e < VN; ++e) {
-                rv.v[e] = bv.v[e] - m.v[e];
+                rv.v[e] = sub_rn(bv.v[e], m.v[e]);
                 if (e < cnt) {
                     accT = fma(rv.v[e], rv.v[e], accT);
                     acc_a2 += av.v[e];
@@ -2076,6 +2089,7 @@ __global__ void __launch_bounds__(kStencilThreads, 4) k_mg_pq(ItemList L, const 
 }  // namespace recon
 #include "mg_strip.cuh"
 #include "mg_band.cuh"
+#include "thr_band.cuh"
 namespace recon {
 
 // Sides of the in-block levels of a block level of bx x by pixels: halve while
@@ -2746,13 +2760,31 @@ template <typename T>
 int op_thr_rhs(Ctx& c, bool stats) {
     const Ptrs<T> P = ptrs<T>(c);
     FamTimer t(c, KF_THR_RHS);
-    if (stats)
+    if (stats) {
         k_thr_rhs<T, true><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
                                                                                      c.d_const, c.d_state, P);
-    else
-        k_thr_rhs<T, false><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom,
-                                                                                      c.d_const, c.d_state, P);
-    c.launches += 1;
+        c.launches += 1;
+    } else {
+        // FP32 slices up to kBandMaxW wide on the band kernel, the others on tiles
+        if constexpr (std::is_same<T, float>::value) {
+            const DevItemList& B = c.thr_band;
+            if (B.n) {
+                if (c.domain != 0)
+                    k_thr_band<true><<<grid_for(c, B.n), kStripThreads, band_smem_bytes<8>(), c.stream>>>(
+                        B.view(), c.d_geom, c.d_const, c.d_state, P, kThrRows);
+                else
+                    k_thr_band<false><<<grid_for(c, B.n), kStripThreads, band_smem_bytes<6>(), c.stream>>>(
+                        B.view(), c.d_geom, c.d_const, c.d_state, P, kThrRows);
+                c.launches += 1;
+            }
+        }
+        const DevItemList& L = std::is_same<T, float>::value ? c.thr_tiles : c.tiles;
+        if (L.n) {
+            k_thr_rhs<T, false><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(L.view(), c.d_geom, c.d_const,
+                                                                                   c.d_state, P);
+            c.launches += 1;
+        }
+    }
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
 }
@@ -2814,8 +2846,8 @@ int strip_rows(const Ctx& c, int l) {
 // (levels up to kBandMaxW wide), the ghost-column strip kernel over the strip
 // items of wider levels.
 template <typename FB, typename FS>
-void strip_pass(Ctx& c, int l, FB band, FS wide) {
-    if (c.mg_strips[l].n) {
+void strip_pass(Ctx& c, int l, FB band, FS wide, bool with_band = true) {
+    if (with_band && c.mg_strips[l].n) {
         band(c.mg_strips[l]);
         c.launches += 1;
     }
@@ -2850,6 +2882,7 @@ void mg_fwd(Ctx& c, int par, int rk, bool timed) {
     MaybeTimer t(c, KF_MG_FWD, timed);
     if constexpr (std::is_same<T, float>::value) {
         // FP32: the register-streaming band / strip kernels over the fine level
+        // (the first step of the band slices is part of k_mgb_start)
         const int rb = strip_rows(c, 0);
         strip_pass(
             c, 0,
@@ -2864,7 +2897,8 @@ void mg_fwd(Ctx& c, int par, int rk, bool timed) {
                     S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, ptrs<T>(c), par, mg_r<T>(c, rk),
                     mg_r<T>(c, rk ^ 1), field_t<T>(c, RECON_F_A2), static_cast<T*>(c.mg_pool[0]), c.d_cg_pending, rb,
                     0);
-            });
+            },
+            UPD);
     } else {
         const DevItemList& L = c.mg_tiles[0];
         k_mg_fwd<T, UPD><<<grid_for(c, L.n), kStencilThreads, 2 * sizeof(MgBufFwd<T>), c.stream>>>(
@@ -2993,16 +3027,35 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
     mg_fine_tail<T>(c, par, rk, timed);
 }
 
+// Start of a Z^m solve: the pending count cleared, r = rhs - M z and the PCG
+// scalars of every slice (k_cg_init), and on the FP32 band slices also the
+// first multigrid step (k_mgb_start does both there).
+template <typename T>
+void pcg_begin(Ctx& c, bool timed) {
+    const Ptrs<T> P = ptrs<T>(c);
+    cudaMemsetAsync(c.d_cg_pending, 0, 2 * sizeof(int), c.stream);
+    MaybeTimer t0(c, KF_CG_INIT, timed);
+    const DevItemList& ct = c.mg_max_lb > 0 ? c.cg_tiles : c.tiles;
+    if (ct.n) {
+        k_cg_init<T><<<grid_for(c, ct.n), kStencilThreads, 2 * sizeof(CgInitBuf<T>), c.stream>>>(
+            ct.view(), c.d_geom, c.d_const, c.d_state, P, c.d_cg_pending);
+        c.launches += 1;
+    }
+    if constexpr (std::is_same<T, float>::value) {
+        const DevItemList& S = c.mg_max_lb > 0 ? c.mg_strips[0] : c.tiles;
+        if (c.mg_max_lb > 0 && S.n) {
+            k_mgb_start<<<grid_for(c, S.n), kStripThreads, band_smem_bytes<3>(), c.stream>>>(
+                S.view(), c.d_geom, c.d_mg_geom[1], c.d_const, c.d_state, P, static_cast<float*>(c.mg_pool[0]),
+                c.d_cg_pending, strip_rows(c, 0));
+            c.launches += 1;
+        }
+    }
+}
+
 template <typename T>
 int op_solve_z(Ctx& c) {
     const Ptrs<T> P = ptrs<T>(c);
-    RECON_CUDA(cudaMemsetAsync(c.d_cg_pending, 0, 2 * sizeof(int), c.stream));
-    {
-        FamTimer t0(c, KF_CG_INIT);
-        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 2 * sizeof(CgInitBuf<T>), c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
-                                                                              c.d_state, P, c.d_cg_pending);
-    }
-    c.launches += 1;
+    pcg_begin<T>(c, true);
     // slices on the FFT preconditioner (the row and column items of the PCG)
     // and slices on the multigrid cycle run side by side, step by step
     const bool mg = c.mg_max_lb > 0;
@@ -3328,10 +3381,7 @@ int graph_build_t(Ctx& c) {
     if (!rc) rc = op_synth<T>(c);
     if (!rc) rc = fft_solve<T>(c, jobs1(RECON_F_RHS_RHO, 2, RECON_F_RHO, 2));
     if (!rc) {
-        cudaMemsetAsync(c.d_cg_pending, 0, sizeof(int), c.stream);
-        k_cg_init<T><<<grid_for(c, c.tiles.n), kStencilThreads, 2 * sizeof(CgInitBuf<T>), c.stream>>>(c.tiles.view(), c.d_geom, c.d_const,
-                                                                              c.d_state, P, c.d_cg_pending);
-        c.launches += 1;
+        pcg_begin<T>(c, false);
         if (fft) {
             k_pcg_fwd<T, false><<<grid_for(c, prow.n), kFftThreads, smem, c.stream>>>(
                 prow.view(), c.d_geom, c.d_const, c.d_state, P, tw, half, 0, c.d_cg_pending, 1);
@@ -3681,17 +3731,23 @@ int upload_list(Ctx& c, DevItemList& L) {
 }
 
 // Row and column items of the FFT-preconditioned PCG: those of c.rows and
-// c.cols on the slices without multigrid levels (host vectors).
+// c.cols on the slices without multigrid levels; and the tiles of k_cg_init:
+// those of c.tiles on the slices whose fine level has no band items
+// (k_mgb_start starts the others).  Host vectors.
 void pcg_split_host(Ctx& c) {
-    for (auto pr : {std::make_pair(&c.rows, &c.pcg_rows), std::make_pair(&c.cols, &c.pcg_cols)}) {
-        const DevItemList& A = *pr.first;
-        DevItemList& B = *pr.second;
+    const std::vector<int>& band = c.mg_strips.empty() ? std::vector<int>() : c.mg_strips[0].h_cnt;
+    const std::tuple<const DevItemList*, DevItemList*, int> parts[3] = {
+        {&c.rows, &c.pcg_rows, 0}, {&c.cols, &c.pcg_cols, 0}, {&c.tiles, &c.cg_tiles, 1}};
+    for (const auto& pr : parts) {
+        const DevItemList& A = *std::get<0>(pr);
+        DevItemList& B = *std::get<1>(pr);
+        const bool tiles = std::get<2>(pr) != 0;
         B.h_items.clear();
         B.h_lo.assign(c.n, 0);
         B.h_cnt.assign(c.n, 0);
         for (int s = 0; s < c.n; ++s) {
             B.h_lo[s] = (int)B.h_items.size();
-            if (c.mg_lb[s]) continue;
+            if (tiles ? (!band.empty() && band[s] > 0) : c.mg_lb[s] != 0) continue;
             for (int i = 0; i < A.h_cnt[s]; ++i) B.h_items.push_back(A.h_items[A.h_lo[s] + i]);
             B.h_cnt[s] = A.h_cnt[s];
         }
@@ -3736,6 +3792,32 @@ int mg_set_smem() {
 // and column items of the slices that keep the FFT preconditioner.
 int fill_list(Ctx& c, DevItemList& L);
 int pcg_split_lists(Ctx& c);
+
+// Items of the threshold pass: band items (kThrRows rows per band) of the
+// FP32 slices whose width is a multiple of 4 and at most kBandMaxW, and the
+// tiles of c.tiles on the other slices.  Host vectors.
+void thr_split_host(Ctx& c) {
+    DevItemList& B = c.thr_band;
+    DevItemList& T = c.thr_tiles;
+    for (DevItemList* X : {&B, &T}) {
+        X->h_items.clear();
+        X->h_lo.assign(c.n, 0);
+        X->h_cnt.assign(c.n, 0);
+    }
+    for (int s = 0; s < c.n; ++s) {
+        B.h_lo[s] = (int)B.h_items.size();
+        T.h_lo[s] = (int)T.h_items.size();
+        const int nx = c.sg[s].nx, ny = c.sg[s].ny;
+        if (c.tiles.h_cnt[s] > 0 && c.precision == 1 && nx % 4 == 0 && nx <= kBandMaxW) {
+            const int bh = band_groups(nx) * kThrRows;
+            for (int y0 = 0; y0 < ny; y0 += bh) B.h_items.push_back(Item{s, 0, y0, 0});
+        } else {
+            for (int i = 0; i < c.tiles.h_cnt[s]; ++i) T.h_items.push_back(c.tiles.h_items[c.tiles.h_lo[s] + i]);
+        }
+        B.h_cnt[s] = (int)B.h_items.size() - B.h_lo[s];
+        T.h_cnt[s] = (int)T.h_items.size() - T.h_lo[s];
+    }
+}
 
 // Multigrid level l of slice s runs on the strip kernels (FP32, width a
 // multiple of 8) rather than the tile kernels.
@@ -3875,7 +3957,8 @@ int mg_setup_server(Ctx& c) {
             return rc;
     }
     pcg_split_host(c);
-    if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols))) return rc;
+    if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols)) || (rc = upload_list(c, c.cg_tiles)))
+        return rc;
     return RECON_OK;
 }
 
@@ -3971,7 +4054,8 @@ int mg_setup(Ctx& c) {
     }
     // row and column items of the PCG on the slices that keep the FFT preconditioner
     pcg_split_host(c);
-    if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols))) return rc;
+    if ((rc = upload_list(c, c.pcg_rows)) || (rc = upload_list(c, c.pcg_cols)) || (rc = upload_list(c, c.cg_tiles)))
+        return rc;
     return RECON_OK;
 }
 
@@ -4105,6 +4189,14 @@ int solver_setup(Ctx& c) {
         }
     }
     if ((rc = upload_list(c, c.tiles)) || (rc = upload_list(c, c.rows)) || (rc = upload_list(c, c.cols))) return rc;
+    thr_split_host(c);
+    if ((rc = upload_list(c, c.thr_band)) || (rc = upload_list(c, c.thr_tiles))) return rc;
+    if (c.precision == 1) {
+        RECON_CUDA(cudaFuncSetAttribute(k_thr_band<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        band_smem_bytes<6>()));
+        RECON_CUDA(cudaFuncSetAttribute(k_thr_band<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        band_smem_bytes<8>()));
+    }
     if (c.server_mode) {
         c.tmp_tiles.h_items = c.tiles.h_items;
         c.tmp_tiles.h_lo = c.tiles.h_lo;
@@ -4325,7 +4417,8 @@ int pcg_split_lists(Ctx& c) {
     if (c.mg_max_lb == 0) return RECON_OK;
     pcg_split_host(c);
     int rc;
-    if ((rc = fill_list(c, c.pcg_rows)) || (rc = fill_list(c, c.pcg_cols))) return rc;
+    if ((rc = fill_list(c, c.pcg_rows)) || (rc = fill_list(c, c.pcg_cols)) || (rc = fill_list(c, c.cg_tiles)))
+        return rc;
     return RECON_OK;
 }
 
@@ -4373,6 +4466,8 @@ int solver_autotune(Ctx& c) {
         c.row_budget = b;
         lists_for(c, all, &c.tiles, &c.rows, &c.cols);
         if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+        thr_split_host(c);
+        if ((rc = fill_list(c, c.thr_band)) || (rc = fill_list(c, c.thr_tiles))) return rc;
         if ((rc = pcg_split_lists(c))) return rc;
         if ((rc = c.precision == 1 ? set_fft_smem<float>(c) : set_fft_smem<double>(c))) return rc;
         for (int m : {16, 32, 64}) {
@@ -4390,6 +4485,8 @@ int solver_autotune(Ctx& c) {
     c.row_budget = best_b;
     lists_for(c, all, &c.tiles, &c.rows, &c.cols);
     if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+    thr_split_host(c);
+    if ((rc = fill_list(c, c.thr_band)) || (rc = fill_list(c, c.thr_tiles))) return rc;
     if ((rc = pcg_split_lists(c))) return rc;
     if ((rc = c.precision == 1 ? set_fft_smem<float>(c) : set_fft_smem<double>(c))) return rc;
     c.tuned = true;
@@ -4522,6 +4619,8 @@ int solver_rebuild_lists(Ctx& c, const std::vector<int>& active) {
     lists_for(c, active, &c.tiles, &c.rows, &c.cols);
     int rc;
     if ((rc = fill_list(c, c.tiles)) || (rc = fill_list(c, c.rows)) || (rc = fill_list(c, c.cols))) return rc;
+    thr_split_host(c);
+    if ((rc = fill_list(c, c.thr_band)) || (rc = fill_list(c, c.thr_tiles))) return rc;
     if (c.mg_max_lb > 0 && (rc = mg_lists_for(c, active))) return rc;
     return RECON_OK;
 }

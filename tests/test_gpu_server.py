@@ -108,7 +108,7 @@ def test_rejects_invalid_parameters_at_submission(rc):
     acq = ph.acquisition("small")
     base = dict(low=acq.low, high=acq.high)
     for kw in (dict(lam=-1.0), dict(beta0=0.0), dict(tau=-1.0), dict(iters=-1), dict(cg_max_iters=-1),
-               dict(cg_tol=-1.0), dict(pcg_kernel=3), dict(e1_kev=50.0, e2_kev=50.0)):
+               dict(cg_tol=-1.0), dict(pcg_kernel=4), dict(e1_kev=50.0, e2_kev=50.0)):
         with pytest.raises(rc.ReconError):
             srv.submit(g, rc.default_params(**base, **kw), L, H)
     assert srv.stats()["queued"] == 0
