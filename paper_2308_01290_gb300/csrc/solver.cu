@@ -579,6 +579,24 @@ __device__ __forceinline__ bool p2_fast(int n) {
 
 // Split the transforms of np row pairs (natural order in `res`) into the two
 // half spectra of each pair: A = (Z_k + conj Z_-k)/2, B = (Z_k - conj Z_-k)/(2i).
+// ---- asynchronous tile copies (cp.async: global -> shared, no registers) ----
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+// 16 bytes; both addresses 16-byte aligned
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+// one element of B = 4 or 8 bytes
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <typename T>
 __device__ __forceinline__ void rows_to_half_spectra(const cplx<T>* res, int ld, int N, int nh, int np, int rows,
                                                      cplx<T>* spr, int cpitch) {
@@ -636,7 +654,21 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_fwd(ItemLis
         bool fast = false;
         if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
         if (fast) {
-            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw + NN, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+            // the item's rows land in buf2 first, all copies in flight at once (rows x N reals, which fit:
+            // the item's transforms take (np + 1) padded sequences of N complex slots)
+            T* stg = reinterpret_cast<T*>(buf2);
+            const int nv = N / 4;   // 16-byte vectors per row (N >= 64)
+            for (int q = threadIdx.x; q < rows * nv; q += blockDim.x) {
+                const int rr = q / nv, v4 = q - rr * nv;
+                cp_async16(stg + rr * N + 4 * v4, inr + (long long)rr * g.pitch + 4 * v4);
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            auto selem = [&](int b, int n) -> cplx<T> {
+                return {stg[2 * b * N + n], 2 * b + 1 < rows ? stg[(2 * b + 1) * N + n] : T(0)};
+            };
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, -1, false, 1>(np, tw + NN, fn_load<T>(selem), SmemSeq<T>{buf, ld});
                               __syncthreads();
                               res = p2_smem_stages<T, NN, -1, 1, P2Plan<NN>::S - 1>(buf, buf2, ld, np, tw + NN));
         } else {
@@ -686,8 +718,28 @@ __device__ __forceinline__ void cols_item_p2(cplx<T>* spc, int cpitch, int nc, i
     constexpr int E = FftBudget<T>::E / N;
     constexpr int CB = E > 16 ? 16 : (E < 1 ? 1 : E);
     const int ld = col_ld(N);
-    auto gload = [&](int b, int y) -> cplx<T> { return spc[(long long)y * cpitch + b]; };
-    p2_stage<T, N, 0, -1, true, CB>(nc, tw + N, fn_load<T>(gload), SmemSeq<T>{buf0, ld});
+    // the item's columns land in buf1 first, row-major (N rows of CB slots), all copies in flight at
+    // once.  With CB and col0 even (the power-of-two sizes) a copy moves a pair of columns, 16-byte
+    // aligned on both sides (the spectrum's offsets and pitch are multiples of 16 slots), and the last
+    // pair of an odd count reads one padding column of the row (nh odd, so the pitch exceeds it).
+    // Otherwise (CB = 9 or col0 odd for N = 448) one column per copy.
+    if (((CB | col0) & 1) == 0) {
+        const int nv = (nc + 1) / 2;
+        for (int q = threadIdx.x; q < N * nv; q += blockDim.x) {
+            const int y = q / nv, v2 = q - y * nv;
+            cp_async16(buf1 + y * CB + 2 * v2, spc + (long long)y * cpitch + 2 * v2);
+        }
+    } else {
+        for (int q = threadIdx.x; q < N * nc; q += blockDim.x) {
+            const int y = q / nc, b = q - y * nc;
+            cp_async_elem<sizeof(cplx<T>)>(buf1 + y * CB + b, spc + (long long)y * cpitch + b);
+        }
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    auto sload = [&](int b, int y) -> cplx<T> { return buf1[y * CB + b]; };
+    p2_stage<T, N, 0, -1, true, CB>(nc, tw + N, fn_load<T>(sload), SmemSeq<T>{buf0, ld});
     __syncthreads();
     cplx<T>* cur = p2_smem_stages<T, N, -1, 1, S - 2>(buf0, buf1, ld, nc, tw + N);
     cplx<T>* oth = cur == buf0 ? buf1 : buf0;
@@ -859,7 +911,22 @@ __global__ void __launch_bounds__(kFftThreads, kFftMinBlocks) k_rows_inv(ItemLis
         bool fast = false;
         if constexpr (std::is_same<T, float>::value) fast = p2_fast(N);
         if (fast) {
-            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np, tw + NN, fn_load<T>(elem), SmemSeq<T>{buf, ld});
+            // the item's half-spectrum rows land in buf2 first (rows x sw complex, sw = nh rounded up to
+            // even, which fits beside the (np + 1) padded sequences of the item's transforms)
+            cplx<T>* stg = buf2;
+            const int sw = (g.nh + 1) & ~1, nv = sw / 2;
+            for (int q = threadIdx.x; q < rows * nv; q += blockDim.x) {
+                const int rr = q / nv, v2 = q - rr * nv;
+                cp_async16(stg + rr * sw + 2 * v2, spr + (long long)rr * g.cpitch + 2 * v2);
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncthreads();
+            auto selem = [&](int b, int n) -> cplx<T> {
+                const cplx<T>* ra = stg + 2 * b * sw;
+                return row_pair_from_half_spectra<T>(ra, 2 * b + 1 < rows ? ra + sw : nullptr, N, g.nh, n);
+            };
+            RECON_P2_DISPATCH(N, p2_stage<T, NN, 0, +1, false, 1>(np, tw + NN, fn_load<T>(selem), SmemSeq<T>{buf, ld});
                               __syncthreads();
                               cplx<T>* cur = p2_smem_stages<T, NN, +1, 1, P2Plan<NN>::S - 2>(buf, buf2, ld, np, tw + NN);
                               p2_stage<T, NN, P2Plan<NN>::S - 1, +1, false, 1>(np, tw + NN, SmemSeq<T>{cur, ld},
@@ -1550,24 +1617,6 @@ __global__ void __launch_bounds__(kStencilThreads) k_mg_restrict(ItemList L, con
                 T(0.25) * ((a[d] + a[d + 1]) + (a[d + g.pitch] + a[d + g.pitch + 1]));
         }
     }
-}
-
-// ---- asynchronous tile copies (cp.async: global -> shared, no registers) ----
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-// 16 bytes; both addresses 16-byte aligned
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-// one element of B = 4 or 8 bytes
-template <int B>
-__device__ __forceinline__ void cp_async_elem(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // Start the copies of NM maps of the tile at (tx0, ty0) with its one-pixel
