@@ -18,6 +18,11 @@
 //   nx - 1).  The whole row sits in one group, so the periodic boundary
 //   (reading R6) needs no ghost columns, and every quantity is formed once per
 //   column: no lane carries another lane's values.
+// * A pass forms its stencils on rows that lag one step behind each other
+//   (q on row t-1 from p, the next sweep on row t-2 from the first, ...), so
+//   every stencil of a step takes neighbours of values formed in the step
+//   before.  Those are exchanged together at the end of each step: one barrier
+//   per row, and the stencils of a step are independent of each other.
 // * Vertical neighbours and the cp.async row rings are as in the strip
 //   kernels: a warp-private ring of kStripDepth slots per field.
 // The edge values alternate between two shared-memory buffers: between two
@@ -92,33 +97,43 @@ __device__ __forceinline__ void band_bar(int grp, int count) {
     }
 }
 
-// Edge values of one item: [buffer][group][chunk], .x the chunk's first
-// column, .y its last.
-struct BandEdges {
-    float2 e[2][kStripWarps][kStripWarps];
+// Edge values of up to four quantities of one item: [buffer][group][chunk]
+// [0: the chunk's first column, 1: its last column].
+struct BandEdges4 {
+    float4 e[2][kStripWarps][kStripWarps][2];
 };
 
-// Left and right neighbours of a lane's four columns of c (the values in the
-// columns x - 1 and x + 4).  Every warp of the group calls it at the same
-// point of its row walk.
-__device__ __forceinline__ float2 band_lr(const float4& c, const BandLane& b, int lane, BandEdges& E, int& buf) {
-    float2(&e)[kStripWarps] = E.e[buf][b.grp];
-    if (lane == 0) e[b.wg].x = c.x;
-    if (lane == b.lastw) e[b.wg].y = c.w;
-    band_bar(b.grp, 32 * b.G);
-    const float up = __shfl_up_sync(0xffffffffu, c.w, 1);
-    const float dn = __shfl_down_sync(0xffffffffu, c.x, 1);
-    const float l = lane == 0 ? e[b.lsrc].y : up;
-    const float r = lane == b.lastw ? e[b.rsrc].x : dn;
-    buf ^= 1;
-    return make_float2(l, r);
+__device__ __forceinline__ float f4_get(const float4& v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
-__device__ __forceinline__ float4 band_op(const float4& a, const float4& c, const float4& u, const float4& d, float bt,
-                                          const BandLane& b, int lane, BandEdges& E, int& buf) {
-    const float2 lr = band_lr(c, b, lane, E, buf);
-    return m_op4(a, c, lr.x, lr.y, u, d, bt);
+// Left and right neighbours (lr[k].x: column x - 1, lr[k].y: column x + 4) of
+// the lane's four columns of each of c[0 .. N-1], through one barrier of the
+// band's warps.  Every warp of the band calls it at the same point of its walk.
+template <int N>
+__device__ __forceinline__ void band_xchg(const float4 (&c)[N], const BandLane& b, int lane, BandEdges4& E,
+                                          int& buf, float2 (&lr)[N]) {
+    static_assert(N >= 1 && N <= 4, "up to four quantities");
+    float4(&e)[kStripWarps][2] = E.e[buf][b.grp];
+    float fv[4] = {0.f, 0.f, 0.f, 0.f}, lv[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        fv[k] = c[k].x;
+        lv[k] = c[k].w;
+    }
+    if (lane == 0) e[b.wg][0] = make_float4(fv[0], fv[1], fv[2], fv[3]);
+    if (lane == b.lastw) e[b.wg][1] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    band_bar(b.grp, 32 * b.G);
+    const float4 Lv = e[b.lsrc][1], Rv = e[b.rsrc][0];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const float up = __shfl_up_sync(0xffffffffu, c[k].w, 1);
+        const float dn = __shfl_down_sync(0xffffffffu, c[k].x, 1);
+        lr[k] = make_float2(lane == 0 ? f4_get(Lv, k) : up, lane == b.lastw ? f4_get(Rv, k) : dn);
+    }
+    buf ^= 1;
 }
+
 __device__ __forceinline__ float4 sweep4(const float4& x, const float4& f, const float4& m, const float4& a, float b4) {
     return make_float4(sweep(x.x, f.x, m.x, a.x, b4), sweep(x.y, f.y, m.y, a.y, b4), sweep(x.z, f.z, m.z, a.z, b4),
                        sweep(x.w, f.w, m.w, a.w, b4));
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                                                               int lvl) {
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
-    __shared__ BandEdges E;
+    __shared__ BandEdges4 E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // fields: 0 p, 1 r, 2 a^2, 3 z
     BandRing<4>& ring = reinterpret_cast<BandRing<4>*>(strip_dsm)[warp];
@@ -247,6 +262,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                     }
                 };
                 float4 pm2 = {}, pm1 = {};
+                float2 lr[3] = {};   // neighbours of pm1, x1m1, x2m1 (exchanged at the end of the step before)
                 // steady rows t in [r0+3, r1]: slot k holds bundle t with t - r0 + 3 = k (mod 4), so
                 // wr - r0 = t - 3 - r0 has the parity of k
                 auto compute = [&](int t, auto k, auto full) {
@@ -255,7 +271,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                         // row u = t-1: q = M p, r' = r - alpha q, x1 = J r' (and z += alpha p)
                         const int u = t - 1;
                         const float4 au = ring.v[k][2][lane];
-                        const float4 q = band_op(au, pm1, pm2, pt, bt, b, lane, E, buf);
+                        const float4 q = m_op4(au, pm1, lr[0].x, lr[0].y, pm2, pt, bt);
                         const float4 rn = fma4(-al, q, ring.v[k][1][lane]);
                         const float4 x1 = jac4(rn, au, b4);
                         if ((full || (u >= r0 && u < r1)) && b.act)
@@ -263,12 +279,12 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                                 fma4(al, pm1, ring.v[k][3][lane]);
                         if (full || t >= r0 + 1) {
                             // row v = t-2: second pre-smoothing sweep
-                            const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
-                                                     am1, b4);
+                            const float4 x2 =
+                                sweep4(x1m1, rm1, m_op4(am1, x1m1, lr[1].x, lr[1].y, x1m2, x1, bt), am1, b4);
                             if (full || t >= r0 + 3) {
                                 // row w = t-3: residual after pre-smoothing, r' out, r'.r', restriction
                                 const int wr = t - 3;
-                                const float4 res = sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf));
+                                const float4 res = sub4(rm2, m_op4(am2, x2m1, lr[2].x, lr[2].y, x2m2, x2, bt));
                                 if (b.act) {
                                     *reinterpret_cast<float4*>(rout + band_row_at(b, wr, full) + b.x) = rm2;
                                     acc = dot4(rm2, rm2, acc);
@@ -287,6 +303,9 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                     }
                     pm2 = pm1;
                     pm1 = pt;
+                    // p(t), x1(t-1), x2(t-2): their neighbours serve the next step
+                    const float4 ex[3] = {pm1, x1m1, x2m1};
+                    band_xchg<3>(ex, b, lane, E, buf, lr);
                 };
                 band_stream(r0 - 3, r1 + 2, r0 + 3, r1, issue, compute);
             } else {
@@ -298,6 +317,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                         cp_async16(&ring.v[k][2][lane], a2 + ro + b.x);
                     }
                 };
+                float2 lr[2] = {};   // neighbours of x1m1, x2m1 (exchanged at the end of the step before)
                 // steady rows t in [r0+2, r1+1]: slot k holds bundle t with t - r0 + 2 = k (mod 4), so
                 // w - r0 = t - 2 - r0 has the parity of k
                 auto compute = [&](int t, auto k, auto full) {
@@ -305,12 +325,12 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                     const float4 x1 = jac4(rt, at, b4);
                     if (full || t >= r0) {
                         // row v = t-1: second pre-smoothing sweep
-                        const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
-                                                 am1, b4);
+                        const float4 x2 =
+                            sweep4(x1m1, rm1, m_op4(am1, x1m1, lr[0].x, lr[0].y, x1m2, x1, bt), am1, b4);
                         if (full || t >= r0 + 2) {
                             // row w = t-2: residual after pre-smoothing, restriction
                             const int wr = t - 2;
-                            restrict_row(sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf)), wr,
+                            restrict_row(sub4(rm2, m_op4(am2, x2m1, lr[1].x, lr[1].y, x2m2, x2, bt)), wr,
                                          full ? (k & 1) != 0 : ((wr - r0) & 1) != 0);
                         }
                         x2m2 = x2m1;
@@ -322,6 +342,9 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_fwd(ItemList L, const 
                     rm1 = rt;
                     am2 = am1;
                     am1 = at;
+                    // x1(t), x2(t-1): their neighbours serve the next step
+                    const float4 ex[2] = {x1m1, x2m1};
+                    band_xchg<2>(ex, b, lane, E, buf, lr);
                 };
                 band_stream(r0 - 2, r1 + 1, r0 + 2, r1 + 1, issue, compute);
             }
@@ -363,7 +386,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_start(ItemList L, cons
                                                                 int* pending, int rb) {
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[3 * 32];
-    __shared__ BandEdges E;
+    __shared__ BandEdges4 E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // fields: 0 z, 1 rhs, 2 a^2
     BandRing<3>& ring = reinterpret_cast<BandRing<3>*>(strip_dsm)[warp];
@@ -403,6 +426,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_start(ItemList L, cons
         if (!b.idle && r0 < r1) {
             float4 am1 = {}, am2 = {}, rm1 = {}, rm2 = {}, x1m1 = {}, x1m2 = {}, x2m1 = {}, x2m2 = {};
             float4 zm2 = {}, zm1 = {};
+            float2 lr[3] = {};   // neighbours of zm1, x1m1, x2m1 (exchanged at the end of the step before)
             // bundle t: z of row t in [r0-3, r1+2]; rhs, a^2 of row u = t-1 in [r0-2, r1+1]
             auto issue = [&](int t, int k) {
                 if (b.act) {
@@ -422,7 +446,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_start(ItemList L, cons
                     // row u = t-1: r = rhs - M z, x1 = J r
                     const int u = t - 1;
                     const float4 au = ring.v[k][2][lane], bu = ring.v[k][1][lane];
-                    const float4 rn = sub4(bu, band_op(au, zm1, zm2, zt, bt, b, lane, E, buf));
+                    const float4 rn = sub4(bu, m_op4(au, zm1, lr[0].x, lr[0].y, zm2, zt, bt));
                     const float4 x1 = jac4(rn, au, b4);
                     if ((full || (u >= r0 && u < r1)) && b.act) {
                         acc_a = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(acc_a, au.x), au.y), au.z), au.w);
@@ -430,12 +454,12 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_start(ItemList L, cons
                     }
                     if (full || t >= r0 + 1) {
                         // row v = t-2: second pre-smoothing sweep
-                        const float4 x2 = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf),
-                                                 am1, b4);
+                        const float4 x2 =
+                            sweep4(x1m1, rm1, m_op4(am1, x1m1, lr[1].x, lr[1].y, x1m2, x1, bt), am1, b4);
                         if (full || t >= r0 + 3) {
                             // row w = t-3: r out, r.r, residual after pre-smoothing, restriction
                             const int wr = t - 3;
-                            const float4 res = sub4(rm2, band_op(am2, x2m1, x2m2, x2, bt, b, lane, E, buf));
+                            const float4 res = sub4(rm2, m_op4(am2, x2m1, lr[2].x, lr[2].y, x2m2, x2, bt));
                             if (b.act) {
                                 *reinterpret_cast<float4*>(rout + band_row_at(b, wr, full) + b.x) = rm2;
                                 acc_r = dot4(rm2, rm2, acc_r);
@@ -454,6 +478,9 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_start(ItemList L, cons
                 }
                 zm2 = zm1;
                 zm1 = zt;
+                // z(t), x1(t-1), x2(t-2): their neighbours serve the next step
+                const float4 ex[3] = {zm1, x1m1, x2m1};
+                band_xchg<3>(ex, b, lane, E, buf, lr);
             };
             band_stream(r0 - 3, r1 + 2, r0 + 3, r1, issue, compute);
         }
@@ -486,7 +513,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const S
                                                              int lvl) {
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
-    __shared__ BandEdges E;
+    __shared__ BandEdges4 E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // fields: 0 r, 1 a^2, 2 e1 (.x, .y: the lane's two coarse cells)
     BandRing<3>& ring = reinterpret_cast<BandRing<3>*>(strip_dsm)[warp];
@@ -519,13 +546,14 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const S
             };
             float4 rm1 = {}, rm2 = {}, rm3 = {}, am1 = {}, am2 = {}, am3 = {};
             float4 x1m1 = {}, x1m2 = {}, xm1 = {}, xm2 = {}, xpm1 = {}, xpm2 = {};
+            float2 lr[3] = {};   // neighbours of x1m1, xm1, xpm1 (exchanged at the end of the step before)
             // steady rows t in [r0+3, r1+2]
             auto compute = [&](int t, auto k, auto full) {
                 const float4 rt = ring.v[k][0][lane], at = ring.v[k][1][lane];
                 const float4 x1 = jac4(rt, at, b4);
                 if (full || t >= r0 - 1) {
                     // row u = t-1: second pre-smoothing sweep, then the prolonged correction
-                    float4 x = sweep4(x1m1, rm1, band_op(am1, x1m1, x1m2, x1, bt, b, lane, E, buf), am1, b4);
+                    float4 x = sweep4(x1m1, rm1, m_op4(am1, x1m1, lr[0].x, lr[0].y, x1m2, x1, bt), am1, b4);
                     const float4 e = ring.v[k][2][lane];
                     x.x = __fadd_rn(x.x, e.x);
                     x.y = __fadd_rn(x.y, e.x);
@@ -533,11 +561,11 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const S
                     x.w = __fadd_rn(x.w, e.y);
                     if (full || t >= r0 + 1) {
                         // row v = t-2: first post-smoothing sweep
-                        const float4 xp = sweep4(xm1, rm2, band_op(am2, xm1, xm2, x, bt, b, lane, E, buf), am2, b4);
+                        const float4 xp = sweep4(xm1, rm2, m_op4(am2, xm1, lr[1].x, lr[1].y, xm2, x, bt), am2, b4);
                         if (full || t >= r0 + 3) {
                             // row w = t-3: second post-smoothing sweep, out (and r.y)
                             const float4 y =
-                                sweep4(xpm1, rm3, band_op(am3, xpm1, xpm2, xp, bt, b, lane, E, buf), am3, b4);
+                                sweep4(xpm1, rm3, m_op4(am3, xpm1, lr[2].x, lr[2].y, xpm2, xp, bt), am3, b4);
                             if (b.act) {
                                 *reinterpret_cast<float4*>(out + band_row_at(b, t - 3, full) + b.x) = y;
                                 if (FINE) acc = dot4(rm3, y, acc);
@@ -557,6 +585,9 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_up(ItemList L, const S
                 am3 = am2;
                 am2 = am1;
                 am1 = at;
+                // x1(t), x(t-1), xp(t-2): their neighbours serve the next step
+                const float4 ex[3] = {x1m1, xm1, xpm1};
+                band_xchg<3>(ex, b, lane, E, buf, lr);
             };
             band_stream(r0 - 3, r1 + 2, r0 + 3, r1 + 2, issue, compute);
         }
@@ -582,7 +613,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_pq(ItemList L, const S
                                                              Ptrs<float> P, int par, int rb) {
     extern __shared__ __align__(16) unsigned char strip_dsm[];
     __shared__ double red[32];
-    __shared__ BandEdges E;
+    __shared__ BandEdges4 E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // fields: 0 y, 1 p_old, 2 a^2
     BandRing<3>& ring = reinterpret_cast<BandRing<3>*>(strip_dsm)[warp];
@@ -613,6 +644,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_pq(ItemList L, const S
                 }
             };
             float4 pm2 = {}, pm1 = {};
+            float2 lr[1] = {};   // neighbours of pm1 (exchanged at the end of the step before)
             // steady rows t in [r0+1, r1-1]
             auto compute = [&](int t, auto k, auto full) {
                 float4 pt = ring.v[k][0][lane];
@@ -621,7 +653,7 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_pq(ItemList L, const S
                     *reinterpret_cast<float4*>(pnew + band_row_at(b, t, full) + b.x) = pt;
                 if (full || t >= r0 + 1) {
                     // row t-1: q = M p, p.q
-                    const float4 q = band_op(ring.v[k][2][lane], pm1, pm2, pt, bt, b, lane, E, buf);
+                    const float4 q = m_op4(ring.v[k][2][lane], pm1, lr[0].x, lr[0].y, pm2, pt, bt);
                     if (b.act) {
                         acc = dot4(pm1, q, acc);
                         if (STOREQ) *reinterpret_cast<float4*>(qo + band_row_at(b, t - 1, full) + b.x) = q;
@@ -629,6 +661,9 @@ __global__ void __launch_bounds__(kStripThreads, 4) k_mgb_pq(ItemList L, const S
                 }
                 pm2 = pm1;
                 pm1 = pt;
+                // p(t): its neighbours serve the next step
+                const float4 ex[1] = {pm1};
+                band_xchg<1>(ex, b, lane, E, buf, lr);
             };
             band_stream(r0 - 1, r1, r0 + 1, r1 - 1, issue, compute);
         }

@@ -21,15 +21,6 @@ namespace recon {
 
 constexpr int kThrRows = 32;   // rows a warp walks per band item of the threshold pass
 
-// Edges of four quantities at once: [buffer][group][chunk][0 first column, 1 last].
-struct BandEdges4 {
-    float4 e[2][kStripWarps][kStripWarps][2];
-};
-
-__device__ __forceinline__ float f4_get(const float4& v, int k) {
-    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
-}
-
 // Left (l) and right (r) neighbours of the lane's four columns of each of
 // c[0..3], one barrier.  LEFT / RIGHT: which sides are needed.
 template <bool LEFT, bool RIGHT>
