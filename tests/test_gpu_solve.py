@@ -234,7 +234,7 @@ def test_invalid_sizes_rejected(rc):
 
 
 @pytest.mark.parametrize("shape,precision", [((128, 128), 1), ((256, 192), 1), ((320, 320), 1), ((640, 96), 1),
-                                            ((128, 128), 0)])
+                                            ((512, 512), 1), ((128, 128), 0)])
 def test_multigrid_pcg_matches_fft_pcg(rc, shape, precision):
     """The Z^m PCG with the multigrid V-cycle (pcg_kernel 0 on slices that
     halve down to a small grid) and with the FFT preconditioner (pcg_kernel
@@ -243,7 +243,9 @@ def test_multigrid_pcg_matches_fft_pcg(rc, shape, precision):
     tolerance and the oracle's exact solution, and the multigrid cycle takes
     fewer steps.  The FP32 widths take every layout of the fine and strip
     levels: one to four warps per row (128, 256, 320 with an idle warp) and
-    ghost-column strips (640, whose level 1 is 320 wide)."""
+    ghost-column strips (640, whose level 1 is 320 wide); 512^2 runs the
+    FFT preconditioner's column pass with its r.y reduction on 512-point
+    columns (257 columns: 32 items of 8 and one of 1)."""
     nx, ny = shape
     acq = ph.acquisition("small")
     tab = model.Tables(acq.low, acq.high)
