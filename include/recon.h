@@ -184,7 +184,12 @@ int recon_init_batch(int32_t n, const recon_geometry* geoms, const recon_params*
  * (Cramer decomposition, synthesis, closed-form rho_e and Z^m).  low/high:
  * mu images (1/mm) when the geometry has n_views = 0, else -log sinograms
  * which are reconstructed by FBP; host or device (on_device = 1) buffers.
- * Resets the iteration counter and beta. */
+ * Host sinograms are copied one FBP group (up to 8 slices of one geometry)
+ * at a time on a copy stream of the handle, beside the FBP of the groups
+ * before.  Reads of host buffers are asynchronous for pinned memory (keep it
+ * unchanged until recon_step or recon_sync returns) and finish before the
+ * call returns for pageable memory.  Resets the iteration counter and
+ * beta. */
 int recon_set_data(recon_ctx* ctx, const float* low, const float* high, int on_device);
 
 /* Run n_iters iterations of Algorithm 1 on every slice that has not yet done

@@ -58,6 +58,13 @@ void free_ctx(Ctx& c) {
     for (cudaEvent_t e : c.side_ev)
         if (e) cudaEventDestroy(e);
     c.side_stream = nullptr;
+    if (c.copy_stream) {
+        cudaStreamSynchronize(c.copy_stream);
+        cudaStreamDestroy(c.copy_stream);
+    }
+    for (cudaEvent_t e : c.copy_ev)
+        if (e) cudaEventDestroy(e);
+    c.copy_stream = nullptr;
     for (void* p : c.allocations) cudaFree(p);
     c.allocations.clear();
     if (c.h_cg_pending) cudaFreeHost(c.h_cg_pending);
@@ -238,11 +245,40 @@ int recon_init(const recon_geometry* geom, const recon_params* params, void* str
 // The FBP of both staged sinograms of every slice into the unpadded image
 // staging buffers d_stage[0], d_stage[1].  Consecutive slices of one geometry
 // go through the FBP together, up to kFbpGroup at a time (their sinograms and
-// images are contiguous).
-static int fbp_pair(Ctx& c) {
+// images are contiguous).  With host sinograms (hlo, hhi), each group's two
+// sinograms are copied on the copy stream and the group's FBP waits for that
+// copy only, so every copy after the first runs beside the FBP of the groups
+// before it.
+static int copy_stream_ready(Ctx& c) {
+    if (!c.copy_stream) {
+        RECON_CUDA(cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : c.copy_ev) RECON_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    return RECON_OK;
+}
+
+static int fbp_pair(Ctx& c, const float* hlo = nullptr, const float* hhi = nullptr) {
+    if (hlo) {
+        int rc;
+        if ((rc = copy_stream_ready(c))) return rc;
+        // the copies overwrite d_sino: after everything already queued on the stream
+        RECON_CUDA(cudaEventRecord(c.copy_ev[0], c.stream));
+        RECON_CUDA(cudaStreamWaitEvent(c.copy_stream, c.copy_ev[0], 0));
+    }
     for (int s = 0; s < c.n;) {
         int k = 1;
         while (k < kFbpGroup && s + k < c.n && same_geometry(c.geo[s + k], c.geo[s])) ++k;
+        if (hlo) {
+            const long long end = s + k < c.n ? c.sino_off[s + k] : c.sino_elems;
+            const size_t bytes = sizeof(float) * (size_t)(end - c.sino_off[s]);
+            RECON_CUDA(cudaMemcpyAsync(c.d_sino[0] + c.sino_off[s], hlo + c.sino_off[s], bytes, cudaMemcpyHostToDevice,
+                                       c.copy_stream));
+            RECON_CUDA(cudaMemcpyAsync(c.d_sino[1] + c.sino_off[s], hhi + c.sino_off[s], bytes, cudaMemcpyHostToDevice,
+                                       c.copy_stream));
+            // a wait takes the record before it, so the one event serves every group
+            RECON_CUDA(cudaEventRecord(c.copy_ev[1], c.copy_stream));
+            RECON_CUDA(cudaStreamWaitEvent(c.stream, c.copy_ev[1], 0));
+        }
         for (int a = 0; a < 2; ++a) {
             const int rc = ct_fbp(c.geo[s], k, c.d_sino[a] + c.sino_off[s], c.d_stage[a] + c.sg[s].ext_off, c.d_filt,
                                   c.stream, &c.launches);
@@ -263,10 +299,15 @@ int recon_set_data(recon_ctx* h, const float* low, const float* high, int on_dev
     const float* hi = high;
     int rc;
     if (c.sino_input) {
-        const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        RECON_CUDA(cudaMemcpyAsync(c.d_sino[0], low, sizeof(float) * c.sino_elems, kind, c.stream));
-        RECON_CUDA(cudaMemcpyAsync(c.d_sino[1], high, sizeof(float) * c.sino_elems, kind, c.stream));
-        if ((rc = fbp_pair(c))) return rc;
+        if (on_device) {
+            RECON_CUDA(cudaMemcpyAsync(c.d_sino[0], low, sizeof(float) * c.sino_elems, cudaMemcpyDeviceToDevice,
+                                       c.stream));
+            RECON_CUDA(cudaMemcpyAsync(c.d_sino[1], high, sizeof(float) * c.sino_elems, cudaMemcpyDeviceToDevice,
+                                       c.stream));
+            if ((rc = fbp_pair(c))) return rc;
+        } else if ((rc = fbp_pair(c, low, high))) {
+            return rc;
+        }
         lo = c.d_stage[0];
         hi = c.d_stage[1];
     } else if (!on_device) {
@@ -340,20 +381,33 @@ int recon_get(recon_ctx* h, float* Z, float* rhoe, float* f1, float* f2, int on_
     }
     int rc;
     if (on_device) return solver_extract(c, Z, rhoe, f1, f2, 1);
+    if ((rc = copy_stream_ready(c))) return rc;
     float* outs[4] = {Z, rhoe, f1, f2};
-    // stage through the two unpadded buffers, two outputs at a time
+    // Two outputs at a time through the two unpadded staging buffers, in
+    // groups of kFbpGroup slices: a group is copied out on the copy stream
+    // while the stream extracts the next one.
     for (int k = 0; k < 4; k += 2) {
         float* a = outs[k] ? c.d_stage[0] : nullptr;
         float* b = outs[k + 1] ? c.d_stage[1] : nullptr;
         if (!a && !b) continue;
-        if (k == 0) rc = solver_extract(c, a, b, nullptr, nullptr, 1);
-        else rc = solver_extract(c, nullptr, nullptr, a, b, 1);
-        if (rc) return rc;
-        if (a) RECON_CUDA(cudaMemcpyAsync(outs[k], a, sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
-        if (b)
-            RECON_CUDA(cudaMemcpyAsync(outs[k + 1], b, sizeof(float) * c.ext_elems, cudaMemcpyDeviceToHost, c.stream));
-        RECON_CUDA(cudaStreamSynchronize(c.stream));
+        for (int s0 = 0; s0 < c.n; s0 += kFbpGroup) {
+            const int s1 = s0 + kFbpGroup < c.n ? s0 + kFbpGroup : c.n;
+            if (k == 0) rc = solver_extract_range(c, s0, s1, a, b, nullptr, nullptr);
+            else rc = solver_extract_range(c, s0, s1, nullptr, nullptr, a, b);
+            if (rc) return rc;
+            RECON_CUDA(cudaEventRecord(c.copy_ev[1], c.stream));
+            RECON_CUDA(cudaStreamWaitEvent(c.copy_stream, c.copy_ev[1], 0));
+            const long long e0 = c.sg[s0].ext_off, e1 = s1 < c.n ? c.sg[s1].ext_off : c.ext_elems;
+            const size_t bytes = sizeof(float) * (size_t)(e1 - e0);
+            if (a) RECON_CUDA(cudaMemcpyAsync(outs[k] + e0, a + e0, bytes, cudaMemcpyDeviceToHost, c.copy_stream));
+            if (b)
+                RECON_CUDA(cudaMemcpyAsync(outs[k + 1] + e0, b + e0, bytes, cudaMemcpyDeviceToHost, c.copy_stream));
+        }
+        // the next pair (or the next call) reuses the staging buffers: after these copies
+        RECON_CUDA(cudaEventRecord(c.copy_ev[0], c.copy_stream));
+        RECON_CUDA(cudaStreamWaitEvent(c.stream, c.copy_ev[0], 0));
     }
+    RECON_CUDA(cudaStreamSynchronize(c.copy_stream));
     return RECON_OK;
 }
 

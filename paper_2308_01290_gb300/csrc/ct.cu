@@ -189,6 +189,81 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
     }
 }
 
+// The same filter for groups of 8 slices of one geometry, one block per
+// (group, view), writing the group's filtered rows slice-interleaved:
+// q8[(v nb + b) 8 + k] for slice k of the group, so that the backprojection
+// reads the 8 slices of a bin as two 16-byte loads.  The block takes the
+// group's 8 rows one after another through the one-row shared buffer and
+// keeps each output in a register until all 8 are formed; every output is
+// the same sum in the same order as in k_fbp_filter.  A thread holds up to
+// kFilt8Pairs bin pairs (nb <= 2 * 256 * kFilt8Pairs).
+constexpr int kFilt8Pairs = 2;
+
+__global__ void __launch_bounds__(256) k_fbp_filter8(recon_geometry g, int n_groups, const float* __restrict__ sino,
+                                                     float* __restrict__ q) {
+    extern __shared__ __align__(16) float smem_f[];
+    const int nb = g.n_bins, nv = g.n_views;
+    const int pad = fbp_row_pad(nb), len = fbp_row_len(nb);
+    float* wrow = smem_f;
+    float* hodd = smem_f + len;
+    const int gv = blockIdx.x;   // group * n_views + view
+    if (gv >= n_groups * nv) return;
+    const int grp = gv / nv, v = gv - grp * nv;
+    const float sid = (float)g.sid_mm;
+    const float ds = (float)g.bin_mm * sid / (float)g.sdd_mm;
+    const float inv_pi2 = (float)(1.0 / (M_PI * M_PI));
+    for (int t = threadIdx.x; t < (nb + 1) / 2; t += blockDim.x) {
+        const float m = 2.f * (float)t + 1.f;
+        hodd[t] = -inv_pi2 / (ds * m * m);
+    }
+    const float h0 = 0.25f / ds;
+    float out[kFilt8Pairs][8][2];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const float* src = sino + ((long long)(grp * 8 + k) * nv + v) * nb;
+        __syncthreads();   // the previous row's taps are read
+        for (int b = threadIdx.x; b < len; b += blockDim.x) {
+            const int kk = b - pad;
+            float x = 0.f;
+            if (kk >= 0 && kk < nb) {
+                const float s = ((float)kk - 0.5f * (float)(nb - 1)) * ds;
+                x = src[kk] * sid / sqrtf(fmaf(s, s, sid * sid));
+            }
+            wrow[b] = x;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kFilt8Pairs; ++j) {
+            const int b = 2 * (threadIdx.x + j * blockDim.x);
+            if (b >= nb) continue;
+            float acc0 = 0.f, acc1 = 0.f;
+            const float* c = wrow + pad + b;
+            for (int t = 0; 2 * t + 1 < nb; ++t) {
+                const int m = 2 * t + 1;
+                const float h = hodd[t];
+                const float2 lf = *reinterpret_cast<const float2*>(c - m);
+                const float2 rt = *reinterpret_cast<const float2*>(c + m);
+                acc0 = fmaf(h, lf.x + rt.x, acc0);
+                acc1 = fmaf(h, lf.y + rt.y, acc1);
+            }
+            out[j][k][0] = fmaf(h0, c[0], acc0);
+            out[j][k][1] = fmaf(h0, c[1], acc1);
+        }
+    }
+    float4* q8 = reinterpret_cast<float4*>(q + (long long)grp * 8 * nv * nb + (long long)v * nb * 8);
+#pragma unroll
+    for (int j = 0; j < kFilt8Pairs; ++j) {
+        const int b = 2 * (threadIdx.x + j * blockDim.x);
+        if (b >= nb) continue;
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            if (b + e >= nb) continue;
+            q8[2 * (b + e)] = make_float4(out[j][0][e], out[j][1][e], out[j][2][e], out[j][3][e]);
+            q8[2 * (b + e) + 1] = make_float4(out[j][4][e], out[j][5][e], out[j][6][e], out[j][7][e]);
+        }
+    }
+}
+
 // FBP step 2: pixel-driven backprojection of the filtered rows with weight
 // 1/U^2, U = (sid - x cos t - y sin t) / sid, detector coordinate at the
 // isocentre s' = sid (-x sin t + y cos t) / (U sid), linear interpolation,
@@ -199,12 +274,14 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
 // once for all S slices.  Groups of several slices of one geometry run with
 // S = 8, R = 1; single slices with S = 1, R = 2.  Every product that could
 // be contracted is written as an explicit FMA or kept apart, so a pixel's
-// value is the same in both forms, bit for bit.
+// value is the same in both forms, bit for bit.  The first il_groups groups
+// (full groups of 8) come slice-interleaved from k_fbp_filter8, the 8 values
+// of a bin in two 16-byte loads; a partial last group comes row by row.
 constexpr int kBpTx = 16, kBpTy = 16, kBpGroup = 8;
 
 template <int S, int R>
-__global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q,
-                                                                  float* __restrict__ img) {
+__global__ void __launch_bounds__(kBpTx * kBpTy, 8)
+    k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q, float* __restrict__ img, int il_groups) {
     // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
     extern __shared__ float trig[];   // cos, sin per view
     const float a0 = (float)g.start_rad, da = (float)(g.arc_rad / g.n_views);
@@ -228,7 +305,8 @@ __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometr
 #pragma unroll
     for (int r = 0; r < R; ++r) y[r] = fmaf(-0.5f, (float)(g.ny - 1), (float)(j0 + r * kBpTy)) * pix;
     const long long sstride = (long long)g.n_views * g.n_bins;
-    const float* qs = q + s0 * sstride;
+    const float* qs = q + s0 * sstride;   // a full group's interleaved rows start there too
+    const bool il = S == 8 && (int)blockIdx.z < il_groups;
     const float kb = sid * inv_ds;
     const unsigned nb = (unsigned)g.n_bins;
     float acc[R][S];
@@ -255,6 +333,19 @@ __global__ void __launch_bounds__(kBpTx * kBpTy) k_fbp_backproject(recon_geometr
             const bool in0 = (unsigned)b0 < nb, in1 = (unsigned)(b0 + 1) < nb;
             const float e0 = in0 ? w0 * u2 : 0.f, e1 = in1 ? w1 * u2 : 0.f;
             const int o0 = in0 ? b0 : 0, o1 = in1 ? b0 + 1 : 0;
+            if constexpr (S == 8) {
+                if (il) {
+                    // the 8 slices of bin o: two 16-byte loads
+                    const float4* r4 = reinterpret_cast<const float4*>(qs + (long long)v * g.n_bins * 8);
+                    const float4 a0 = __ldg(r4 + 2 * o0), a1 = __ldg(r4 + 2 * o0 + 1);
+                    const float4 c0 = __ldg(r4 + 2 * o1), c1 = __ldg(r4 + 2 * o1 + 1);
+                    const float qa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float qb[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) acc[r][k] = fmaf(e0, qa[k], fmaf(e1, qb[k], acc[r][k]));
+                    continue;
+                }
+            }
 #pragma unroll
             for (int k = 0; k < S; ++k)
                 if (k < ns) {
@@ -368,16 +459,30 @@ int ct_fbp_check(const recon_geometry& g, int n) {
 int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float* scratch, cudaStream_t st,
            long long* launches) {
     if (int rc = ct_fbp_check(g, n)) return rc;
-    k_fbp_filter<<<n * g.n_views, 256, fbp_filter_smem_floats(g.n_bins) * sizeof(float), st>>>(g, n, sino, scratch);
+    const size_t fsm = fbp_filter_smem_floats(g.n_bins) * sizeof(float);
+    // full groups of 8 slices: filtered slice-interleaved (bins up to 2 * 256 * kFilt8Pairs); the rest row by row
+    const int il_groups = (n >= 8 && g.n_bins <= 2 * 256 * kFilt8Pairs) ? n / kBpGroup : 0;
+    const long long sstride = (long long)g.n_views * g.n_bins;
+    int k = 0;
+    if (il_groups > 0) {
+        k_fbp_filter8<<<il_groups * g.n_views, 256, fsm, st>>>(g, il_groups, sino, scratch);
+        ++k;
+    }
+    const int rest = n - kBpGroup * il_groups;
+    if (rest > 0) {
+        const long long o = (long long)kBpGroup * il_groups * sstride;
+        k_fbp_filter<<<rest * g.n_views, 256, fsm, st>>>(g, rest, sino + o, scratch + o);
+        ++k;
+    }
     const size_t trig_bytes = 2 * g.n_views * sizeof(float);
     if (n >= 2) {
         const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + kBpTy - 1) / kBpTy, (n + kBpGroup - 1) / kBpGroup);
-        k_fbp_backproject<kBpGroup, 1><<<grid, dim3(kBpTx, kBpTy), trig_bytes, st>>>(g, n, scratch, img);
+        k_fbp_backproject<kBpGroup, 1><<<grid, dim3(kBpTx, kBpTy), trig_bytes, st>>>(g, n, scratch, img, il_groups);
     } else {
         const dim3 grid((g.nx + kBpTx - 1) / kBpTx, (g.ny + 2 * kBpTy - 1) / (2 * kBpTy), n);
-        k_fbp_backproject<1, 2><<<grid, dim3(kBpTx, kBpTy), trig_bytes, st>>>(g, n, scratch, img);
+        k_fbp_backproject<1, 2><<<grid, dim3(kBpTx, kBpTy), trig_bytes, st>>>(g, n, scratch, img, 0);
     }
-    if (launches) *launches += 2;
+    if (launches) *launches += k + 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
 }

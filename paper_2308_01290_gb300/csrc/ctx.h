@@ -108,6 +108,10 @@ struct Ctx {
     // (ordered with `stream` by the two events)
     cudaStream_t side_stream = nullptr;
     cudaEvent_t side_ev[2] = {nullptr, nullptr};
+    // host sinograms come in on this stream, one FBP group at a time, while
+    // `stream` filters and backprojects the groups before (recon_set_data)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ev[2] = {nullptr, nullptr};
     // one iteration captured as a CUDA graph (recon_set_graph): the Z^m PCG
     // runs as a conditional WHILE node of two PCG steps per body
     bool graph_on = false;
@@ -141,6 +145,8 @@ int solver_modeb_data(Ctx& c);                 // domain 1: data images t_k from
 int solver_iterate(Ctx& c, bool stats);        // one iteration of Algorithm 1
 int solver_op(Ctx& c, int op);
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int on_device);
+// the maps of slices s0 .. s1-1 only (outputs indexed as for the whole handle)
+int solver_extract_range(Ctx& c, int s0, int s1, float* Z, float* rhoe, float* f1, float* f2);
 // two-step comparator maps (device, unpadded) from the loaded pair, or from
 // the unpadded images lo, hi (1/mm) when set
 int solver_direct(Ctx& c, const float* lo, const float* hi, float* Z, float* rhoe);

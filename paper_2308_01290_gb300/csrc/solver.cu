@@ -3583,9 +3583,15 @@ int load_t(Ctx& c, const float* lo, const float* hi) {
 }
 
 template <typename T>
-int extract_t(Ctx& c, float* Z, float* rhoe, float* f1, float* f2) {
-    k_extract<T><<<grid_for(c, c.tiles.n), kStencilThreads, 0, c.stream>>>(c.tiles.view(), c.d_geom, ptrs<T>(c), Z,
-                                                                           rhoe, f1, f2, water_z(), z_exponent());
+int extract_t(Ctx& c, int s0, int s1, float* Z, float* rhoe, float* f1, float* f2) {
+    // the tiles of slices s0 .. s1-1 (the list is in slice order; k_extract reads only the items)
+    ItemList L = c.tiles.view();
+    const int i0 = c.tiles.h_lo[s0], i1 = s1 < c.n ? c.tiles.h_lo[s1] : c.tiles.n;
+    L.items += i0;
+    L.n_items = i1 - i0;
+    if (L.n_items <= 0) return RECON_OK;
+    k_extract<T><<<grid_for(c, L.n_items), kStencilThreads, 0, c.stream>>>(L, c.d_geom, ptrs<T>(c), Z, rhoe, f1, f2,
+                                                                           water_z(), z_exponent());
     c.launches += 1;
     RECON_CUDA(cudaGetLastError());
     return RECON_OK;
@@ -4552,7 +4558,12 @@ int solver_iterate(Ctx& c, bool stats) {
 int solver_op(Ctx& c, int op) { return c.precision == 1 ? op_t<float>(c, op) : op_t<double>(c, op); }
 
 int solver_extract(Ctx& c, float* Z, float* rhoe, float* f1, float* f2, int /*on_device*/) {
-    return c.precision == 1 ? extract_t<float>(c, Z, rhoe, f1, f2) : extract_t<double>(c, Z, rhoe, f1, f2);
+    return solver_extract_range(c, 0, c.n, Z, rhoe, f1, f2);
+}
+
+int solver_extract_range(Ctx& c, int s0, int s1, float* Z, float* rhoe, float* f1, float* f2) {
+    return c.precision == 1 ? extract_t<float>(c, s0, s1, Z, rhoe, f1, f2)
+                            : extract_t<double>(c, s0, s1, Z, rhoe, f1, f2);
 }
 
 int solver_direct(Ctx& c, const float* lo, const float* hi, float* Z, float* rhoe) {
