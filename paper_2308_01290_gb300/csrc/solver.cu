@@ -1449,6 +1449,12 @@ constexpr int kMgCoarsePx = 64;        // the coarsest grid has at most this man
 constexpr int kMgMaxBlockLevels = 8;
 constexpr int kMgBlockSweeps = 2;      // Jacobi sweeps before and after the correction on the block's levels
 constexpr int kMgBlockThreads = 256;
+// k_mg_block: its passes stride over a level by the block size and hold no
+// per-thread state across pixels, so the result does not depend on it; 512
+// threads hide the shared-memory latency of a pass better, and two blocks
+// still fit an SM (registers and the 64^2 levels' shared memory), so one
+// block per slice runs in one wave for up to twice the SM count.
+constexpr int kMgBlockRunThreads = 512;
 
 // x / y for the Jacobi weights of the cycle: any fixed positive diagonal
 // keeps the cycle symmetric, so FP32 kernels use the fast reciprocal.
@@ -2270,9 +2276,9 @@ __global__ void __launch_bounds__(kMgBlockThreads) k_mg_coarse_inv(const SliceGe
 // The levels of one slice that fit one block (grid: one block per slice):
 // f and a^2 of the slice's block level in, its correction e out.
 template <typename T>
-__global__ void __launch_bounds__(kMgBlockThreads) k_mg_block(const SliceGeom* GB, const SliceState* S, const T* F,
-                                                              const T* A, T* E, const T* Qinv,
-                                                              unsigned long long* acct) {
+__global__ void __launch_bounds__(kMgBlockRunThreads)
+    k_mg_block(const SliceGeom* GB, const SliceState* S, const T* F, const T* A, T* E, const T* Qinv,
+               unsigned long long* acct) {
     extern __shared__ __align__(16) unsigned char mg_smem[];
     T* sh = reinterpret_cast<T*>(mg_smem);
     const int s = blockIdx.x;
@@ -3043,7 +3049,7 @@ void mg_tail(Ctx& c, int par, int rk, bool timed) {
     }
     {
         MaybeTimer t(c, KF_MG_BLOCK, timed);
-        k_mg_block<T><<<c.n, kMgBlockThreads, c.mg_block_smem, c.stream>>>(
+        k_mg_block<T><<<c.n, kMgBlockRunThreads, c.mg_block_smem, c.stream>>>(
             c.d_mg_block, c.d_state, pf, pa, pe, static_cast<const T*>(c.mg_qinv), c.d_acct);
         c.launches += 1;
     }
