@@ -189,78 +189,120 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
     }
 }
 
-// The same filter for groups of 8 slices of one geometry, one block per
-// (group, view), writing the group's filtered rows slice-interleaved:
-// q8[(v nb + b) 8 + k] for slice k of the group, so that the backprojection
-// reads the 8 slices of a bin as two 16-byte loads.  The block takes the
-// group's 8 rows one after another through the one-row shared buffer and
-// keeps each output in a register until all 8 are formed; every output is
-// the same sum in the same order as in k_fbp_filter.  A thread holds up to
-// kFilt8Pairs bin pairs (nb <= 2 * 256 * kFilt8Pairs).
-constexpr int kFilt8Pairs = 2;
+// The same filter for groups of 8 slices of one geometry, writing the
+// group's filtered rows slice-interleaved: q8[(v nb + b) 8 + k] for slice k
+// of the group, so that the backprojection reads the 8 slices of a bin as
+// two 16-byte loads.  Two blocks per (group, view), one per half of the group
+// (slices 4h .. 4h + 3, the 16-byte half h of each bin), filter8_tpr(nb)
+// threads per row.  A thread forms 8 consecutive outputs b0 .. b0 + 7 of one
+// row and keeps, for each side of the ramp, a window of 16 consecutive
+// weighted inputs in registers: four taps move a window by 8, so every four
+// taps a thread loads one new group of 8 inputs per side.  The weighted row
+// sits in shared memory in 8 phases (element e at (e mod 8) P + e / 8, from
+// an offset pad = 1 mod 8), so such a group is 8 loads at fixed offsets from
+// one address, and the threads of a warp (consecutive b0 / 8) read
+// consecutive words of each phase.  Every output is the same sum in the same
+// order as in k_fbp_filter (taps by increasing m, left input plus right).
+__host__ __device__ inline int filt8_pad(int nb) { return ((nb + 22) & ~7) + 1; }   // = 1 mod 8, >= nb + 16
+__host__ __device__ inline int filt8_phase(int nb) {
+    int p = (filt8_pad(nb) + 2 * nb + 40 + 7) / 8;   // the row and the reach of the last windows
+    return p + ((4 - p % 32) + 32) % 32;                // = 4 mod 32: conflict-free row fill
+}
+__host__ __device__ inline int filt8_tpr(int nb) { return ((nb + 7) / 8 + 31) / 32 * 32; }
+__host__ __device__ inline int filt8_taps(int nb) { return (nb / 2 + 3) / 4 * 4; }   // ramp taps, padded to 4
+__host__ __device__ inline int filt8_smem_floats(int nb) { return filt8_taps(nb) + 32 * filt8_phase(nb); }
 
-__global__ void __launch_bounds__(256) k_fbp_filter8(recon_geometry g, int n_groups, const float* __restrict__ sino,
+// The 8 inputs of group q of a phase-layout row.
+__device__ __forceinline__ void filt8_group(const float* ph, int P, int q, float* x) {
+#pragma unroll
+    for (int p = 0; p < 8; ++p) x[p] = ph[p * P + q];
+}
+
+__global__ void __launch_bounds__(512) k_fbp_filter8(recon_geometry g, int n_groups, const float* __restrict__ sino,
                                                      float* __restrict__ q) {
     extern __shared__ __align__(16) float smem_f[];
     const int nb = g.n_bins, nv = g.n_views;
-    const int pad = fbp_row_pad(nb), len = fbp_row_len(nb);
-    float* wrow = smem_f;
-    float* hodd = smem_f + len;
-    const int gv = blockIdx.x;   // group * n_views + view
+    const int pad = filt8_pad(nb), P = filt8_phase(nb), tpr = filt8_tpr(nb), T = nb / 2;
+    const int hl = filt8_taps(nb);
+    float* hodd = smem_f;        // ds h(m) for odd m = 2t + 1, zero from t = T
+    float* rows = smem_f + hl;   // the half group's 4 weighted rows, 8 P floats each, phase layout
+    const int gv = blockIdx.x >> 1, hf = blockIdx.x & 1;   // (group * n_views + view, half)
     if (gv >= n_groups * nv) return;
     const int grp = gv / nv, v = gv - grp * nv;
     const float sid = (float)g.sid_mm;
     const float ds = (float)g.bin_mm * sid / (float)g.sdd_mm;
     const float inv_pi2 = (float)(1.0 / (M_PI * M_PI));
-    for (int t = threadIdx.x; t < (nb + 1) / 2; t += blockDim.x) {
+    for (int t = threadIdx.x; t < hl; t += blockDim.x) {
         const float m = 2.f * (float)t + 1.f;
-        hodd[t] = -inv_pi2 / (ds * m * m);
+        hodd[t] = t < T ? -inv_pi2 / (ds * m * m) : 0.f;
     }
+    const int len = 8 * P;
+    for (int qq = threadIdx.x; qq < 4 * len; qq += blockDim.x) {
+        const int k = qq / len, e = qq - k * len, kk = e - pad;
+        float x = 0.f;
+        if (kk >= 0 && kk < nb) {
+            const float* src = sino + ((long long)(grp * 8 + 4 * hf + k) * nv + v) * nb;
+            const float s = ((float)kk - 0.5f * (float)(nb - 1)) * ds;
+            x = src[kk] * sid / sqrtf(fmaf(s, s, sid * sid));
+        }
+        rows[k * len + (e & 7) * P + (e >> 3)] = x;
+    }
+    __syncthreads();
     const float h0 = 0.25f / ds;
-    float out[kFilt8Pairs][8][2];
+    const int k = threadIdx.x / tpr, j = threadIdx.x - k * tpr;
+    float acc[8];
+    const bool on = 8 * j < nb;
+    if (on) {
+        const float* ph = rows + k * len;
+        const int base = pad + 8 * j, Jb = base >> 3;   // base = 8 Jb + 1
+        // windows: left inputs 8 (Jb - u - 1) .. 8 (Jb - u) + 7 in (lp, lc), right 8 (Jb + u) .. + 15 in (rc, rn)
+        float lp[8], lc[8], rc[8], rn[8];
+        filt8_group(ph, P, Jb, lc);
+        filt8_group(ph, P, Jb - 1, lp);
+        filt8_group(ph, P, Jb, rc);
+        filt8_group(ph, P, Jb + 1, rn);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const float* src = sino + ((long long)(grp * 8 + k) * nv + v) * nb;
-        __syncthreads();   // the previous row's taps are read
-        for (int b = threadIdx.x; b < len; b += blockDim.x) {
-            const int kk = b - pad;
-            float x = 0.f;
-            if (kk >= 0 && kk < nb) {
-                const float s = ((float)kk - 0.5f * (float)(nb - 1)) * ds;
-                x = src[kk] * sid / sqrtf(fmaf(s, s, sid * sid));
-            }
-            wrow[b] = x;
-        }
-        __syncthreads();
+        for (int i = 0; i < 8; ++i) acc[i] = 0.f;
+        const int nblk = T >> 2;
+        for (int u = 0; u < nblk; ++u) {
+            const float4 h4 = *reinterpret_cast<const float4*>(hodd + 4 * u);
+            const float hs[4] = {h4.x, h4.y, h4.z, h4.w};
 #pragma unroll
-        for (int j = 0; j < kFilt8Pairs; ++j) {
-            const int b = 2 * (threadIdx.x + j * blockDim.x);
-            if (b >= nb) continue;
-            float acc0 = 0.f, acc1 = 0.f;
-            const float* c = wrow + pad + b;
-            for (int t = 0; 2 * t + 1 < nb; ++t) {
-                const int m = 2 * t + 1;
-                const float h = hodd[t];
-                const float2 lf = *reinterpret_cast<const float2*>(c - m);
-                const float2 rt = *reinterpret_cast<const float2*>(c + m);
-                acc0 = fmaf(h, lf.x + rt.x, acc0);
-                acc1 = fmaf(h, lf.y + rt.y, acc1);
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    // tap t = 4u + s: input b0 + i - m at window offset i - 2s + 8, b0 + i + m at i + 2s + 2
+                    const int li = i - 2 * s + 8, ri = i + 2 * s + 2;
+                    const float L = li < 8 ? lp[li] : lc[li - 8];
+                    const float R = ri < 8 ? rc[ri] : rn[ri - 8];
+                    acc[i] = fmaf(hs[s], L + R, acc[i]);
+                }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                lc[i] = lp[i];
+                rc[i] = rn[i];
             }
-            out[j][k][0] = fmaf(h0, c[0], acc0);
-            out[j][k][1] = fmaf(h0, c[1], acc1);
+            filt8_group(ph, P, Jb - u - 2, lp);
+            filt8_group(ph, P, Jb + u + 2, rn);
         }
+        auto el = [&](int e) { return ph[(e & 7) * P + (e >> 3)]; };
+        for (int t = 4 * nblk; t < T; ++t)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                acc[i] = fmaf(hodd[t], el(base + i - 2 * t - 1) + el(base + i + 2 * t + 1), acc[i]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = fmaf(h0, el(base + i), acc[i]);
     }
-    float4* q8 = reinterpret_cast<float4*>(q + (long long)grp * 8 * nv * nb + (long long)v * nb * 8);
+    // out through shared memory (over the rows): slot (k, i, j) at k 8 Q + i Q + j, Q = P
+    __syncthreads();
+    if (on)
 #pragma unroll
-    for (int j = 0; j < kFilt8Pairs; ++j) {
-        const int b = 2 * (threadIdx.x + j * blockDim.x);
-        if (b >= nb) continue;
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            if (b + e >= nb) continue;
-            q8[2 * (b + e)] = make_float4(out[j][0][e], out[j][1][e], out[j][2][e], out[j][3][e]);
-            q8[2 * (b + e) + 1] = make_float4(out[j][4][e], out[j][5][e], out[j][6][e], out[j][7][e]);
-        }
+        for (int i = 0; i < 8; ++i) rows[k * len + i * P + j] = acc[i];
+    __syncthreads();
+    float4* q8 = reinterpret_cast<float4*>(q + (long long)grp * 8 * nv * nb);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int o = (b & 7) * P + (b >> 3);
+        q8[((long long)v * nb + b) * 2 + hf] = make_float4(rows[o], rows[len + o], rows[2 * len + o], rows[3 * len + o]);
     }
 }
 
@@ -460,12 +502,14 @@ int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float*
            long long* launches) {
     if (int rc = ct_fbp_check(g, n)) return rc;
     const size_t fsm = fbp_filter_smem_floats(g.n_bins) * sizeof(float);
-    // full groups of 8 slices: filtered slice-interleaved (bins up to 2 * 256 * kFilt8Pairs); the rest row by row
-    const int il_groups = (n >= 8 && g.n_bins <= 2 * 256 * kFilt8Pairs) ? n / kBpGroup : 0;
+    const size_t fsm8 = filt8_smem_floats(g.n_bins) * sizeof(float);
+    // full groups of 8 slices: filtered slice-interleaved (where the 4 rows of a half group fit 48 KB of shared
+    // memory, up to about 880 bins); the rest row by row
+    const int il_groups = (n >= 8 && fsm8 <= 48 * 1024) ? n / kBpGroup : 0;
     const long long sstride = (long long)g.n_views * g.n_bins;
     int k = 0;
     if (il_groups > 0) {
-        k_fbp_filter8<<<il_groups * g.n_views, 256, fsm, st>>>(g, il_groups, sino, scratch);
+        k_fbp_filter8<<<2 * il_groups * g.n_views, 4 * filt8_tpr(g.n_bins), fsm8, st>>>(g, il_groups, sino, scratch);
         ++k;
     }
     const int rest = n - kBpGroup * il_groups;

@@ -121,6 +121,25 @@ def test_fbp_batch_of_slices_equals_one_by_one(rc):
         assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max(), k
 
 
+@pytest.mark.parametrize("nb", [83, 191, 736])
+def test_fbp_interleaved_groups_equal_one_by_one(rc, nb):
+    """17 slices of random sinograms: two full groups of 8, filtered
+    slice-interleaved with a sliding window of 8 outputs per thread, and one
+    slice filtered row by row.  Bin counts whose last window is ragged (83,
+    191: not a multiple of 8) and whose tap count is not a multiple of 4 (83:
+    41 taps, 191: 95) give each slice's single-slice result bit for bit."""
+    g = geom_dict(nx=72, ny=64, nv=48, nb=nb)
+    G = to_rc(rc, g)
+    n, nr, npx = 17, g["n_views"] * nb, g["nx"] * g["ny"]
+    allv = dev(np.concatenate([ph.random_field((g["n_views"], nb), 70 + k).ravel() for k in range(n)]))
+    img = torch.zeros(n * npx, device="cuda")
+    rc.fbp(G, n, allv, img)
+    for k in range(n):
+        one = torch.zeros(npx, device="cuda")
+        rc.fbp(G, 1, allv[k * nr:(k + 1) * nr], one)
+        assert torch.equal(one, img[k * npx:(k + 1) * npx]), k
+
+
 @pytest.mark.parametrize("kind", ["small", "clinical"])
 def test_simulate_noiseless_matches_oracle(rc, kind):
     acq = ph.acquisition(kind, n=64)
