@@ -87,6 +87,8 @@ struct Ctx {
     std::vector<DevItemList> mg_wide;         // [l]: strip items of the wider such levels (k_mgs_*)
     std::vector<DevItemList> mg_tiles_rest;   // [l]: tile items of level l of the other slices (k_mg_down, k_mg_up)
     int mg_rb = 32;                           // rows a warp walks per strip item on the fine level
+    std::vector<int> mg_level_rb;             // per coarse level l >= 1: rows a warp walks per item (0: default)
+    int band_res = 0;                         // resident blocks of the coarse band kernels on the device
     std::vector<SliceConst> hconst;
     // serving mode: every slot laid out at capacity; lists hold the active slots
     bool server_mode = false;

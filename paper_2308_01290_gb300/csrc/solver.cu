@@ -2891,8 +2891,11 @@ T* mg_r(Ctx& c, int k) {
 }
 
 // Rows a warp walks per strip item on multigrid level l: mg_rb on the fine
-// level, halved per level (grids of a quarter of the pixels), at least 8.
+// level; on a coarse level the count level_items chose for the handle's
+// items, else mg_rb halved per level (grids of a quarter of the pixels), at
+// least 8.
 int strip_rows(const Ctx& c, int l) {
+    if (l >= 1 && l < (int)c.mg_level_rb.size() && c.mg_level_rb[l] > 0) return c.mg_level_rb[l];
     const int r = c.mg_rb >> l;
     return r < 8 ? 8 : r;
 }
@@ -3890,7 +3893,62 @@ bool mg_strip_level(const Ctx& c, int s, int l) {
 // null): strips (128 columns, kStripWarps x strip_rows rows) where
 // mg_strip_level holds, and tiles (for the tile kernels) on the other slices
 // with that level.  Host lists only.
+// Resident blocks of the coarse band kernels over the device's SMs.
+int band_resident(Ctx& c) {
+    if (c.band_res > 0) return c.band_res;
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_mgb_fwd<false>, kStripThreads, band_smem_bytes<4>()) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_mgb_up<false>, kStripThreads, band_smem_bytes<3>()) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        a = b = 4;   // the kernels' launch bounds
+    }
+    const int m = a < b ? a : b;
+    c.band_res = (m > 0 ? m : 1) * c.sm_count;
+    return c.band_res;
+}
+
+// Rows a warp walks per band item on a coarse level l >= 1 for the band
+// items of `slots` (every slice when null).  The coarse passes form no
+// reductions and every row's values come out the same whichever item forms
+// them, so the count is free; it stays even (the restriction pairs rows from
+// a band's first row).  The walks are bound by the latency of their row
+// steps, so the count taken is the even one in [8, 32] that minimises the
+// waves of resident blocks the items need times the rows one walks (its rows
+// plus about 6 rows of halo and start); 0 (the default) without band items.
+int coarse_band_rows(Ctx& c, int l, const std::vector<int>* slots) {
+    const long long res = band_resident(c);
+    int best = 0;
+    long long best_cost = 0;
+    for (int rb = 8; rb <= 32; rb += 2) {
+        long long items = 0;
+        auto count = [&](int s) {
+            const int nx = c.sg[s].nx >> l;
+            if (c.mg_lb[s] > l && mg_strip_level(c, s, l) && nx <= kBandMaxW && c.prm[s].pcg_kernel != 3) {
+                const int bh = band_groups(nx) * rb;
+                items += ((c.sg[s].ny >> l) + bh - 1) / bh;
+            }
+        };
+        if (!slots)
+            for (int s = 0; s < c.n; ++s) count(s);
+        else
+            for (int s : *slots) count(s);
+        if (items == 0) return 0;
+        const long long cost = (items + res - 1) / res * (rb + 6);
+        if (!best || cost <= best_cost) {   // ties: the longer walk (fewer items)
+            best = rb;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
 void level_items(Ctx& c, int l, const std::vector<int>* slots) {
+    if (l >= 1) {
+        if ((int)c.mg_level_rb.size() <= l) c.mg_level_rb.resize(l + 1, 0);
+        c.mg_level_rb[l] = c.precision == 1 ? coarse_band_rows(c, l, slots) : 0;
+    }
     DevItemList& B = c.mg_strips[l];
     DevItemList& W = c.mg_wide[l];
     DevItemList& T = c.mg_tiles_rest[l];
