@@ -14,7 +14,6 @@
 // Per-ray set-up is FP64; the marching is FP32 with the fractional index
 // evaluated as start + i * slope from FP64-rounded start and slope.
 #include <cmath>
-#include <cstdint>
 #include <mutex>
 #include <vector>
 
@@ -192,8 +191,8 @@ __global__ void k_fbp_filter(recon_geometry g, int n, const float* __restrict__ 
 
 // The same filter for groups of 8 slices of one geometry, writing the
 // group's filtered rows slice-interleaved: q8[(v nb + b) 8 + k] for slice k
-// of the group, so that the backprojection reads the 8 slices of a bin in
-// one 32-byte load.  Two blocks per (group, view), one per half of the group
+// of the group, so that the backprojection reads the 8 slices of a bin as
+// two 16-byte loads.  Two blocks per (group, view), one per half of the group
 // (slices 4h .. 4h + 3, the 16-byte half h of each bin), filter8_tpr(nb)
 // threads per row.  A thread forms 8 consecutive outputs b0 .. b0 + 7 of one
 // row and keeps, for each side of the ramp, a window of 16 consecutive
@@ -319,20 +318,11 @@ __global__ void __launch_bounds__(512) k_fbp_filter8(recon_geometry g, int n_gro
 // be contracted is written as an explicit FMA or kept apart, so a pixel's
 // value is the same in both forms, bit for bit.  The first il_groups groups
 // (full groups of 8) come slice-interleaved from k_fbp_filter8, the 8 values
-// of a bin in one 32-byte load (each bin starts on a 32-byte boundary: the
-// scratch is 256-byte aligned and a group spans 8 n_views n_bins floats); a
-// partial last group comes row by row.
+// of a bin in two 16-byte loads; a partial last group comes row by row.
 constexpr int kBpTx = 16, kBpTy = 16, kBpGroup = 8;
 
-// v[0..7] = p[0..7] through the read-only path in one 32-byte load (p 32-byte aligned).
-__device__ __forceinline__ void ldg_v8(const float* p, float* v) {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
-        : "l"(p));
-}
-
 template <int S, int R>
-__global__ void __launch_bounds__(kBpTx * kBpTy, 6)
+__global__ void __launch_bounds__(kBpTx * kBpTy, 8)
     k_fbp_backproject(recon_geometry g, int n, const float* __restrict__ q, float* __restrict__ img, int il_groups) {
     // FP32 throughout: GB300 issues FP64 at a small fraction of its FP32 rate
     extern __shared__ float trig[];   // cos, sin per view
@@ -387,11 +377,12 @@ __global__ void __launch_bounds__(kBpTx * kBpTy, 6)
             const int o0 = in0 ? b0 : 0, o1 = in1 ? b0 + 1 : 0;
             if constexpr (S == 8) {
                 if (il) {
-                    // the 8 slices of bin o: one 32-byte load
-                    const float* r8 = qs + (long long)v * g.n_bins * 8;
-                    float qa[8], qb[8];
-                    ldg_v8(r8 + 8 * o0, qa);
-                    ldg_v8(r8 + 8 * o1, qb);
+                    // the 8 slices of bin o: two 16-byte loads
+                    const float4* r4 = reinterpret_cast<const float4*>(qs + (long long)v * g.n_bins * 8);
+                    const float4 a0 = __ldg(r4 + 2 * o0), a1 = __ldg(r4 + 2 * o0 + 1);
+                    const float4 c0 = __ldg(r4 + 2 * o1), c1 = __ldg(r4 + 2 * o1 + 1);
+                    const float qa[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                    const float qb[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
 #pragma unroll
                     for (int k = 0; k < 8; ++k) acc[r][k] = fmaf(e0, qa[k], fmaf(e1, qb[k], acc[r][k]));
                     continue;
@@ -514,9 +505,7 @@ int ct_fbp(const recon_geometry& g, int n, const float* sino, float* img, float*
     const size_t fsm8 = filt8_smem_floats(g.n_bins) * sizeof(float);
     // full groups of 8 slices: filtered slice-interleaved (where the 4 rows of a half group fit 48 KB of shared
     // memory, up to about 880 bins); the rest row by row
-    // (the backprojection reads a bin's 8 values in one 32-byte load: the scratch must start on 32 bytes)
-    const bool aligned = (reinterpret_cast<uintptr_t>(scratch) & 31) == 0;
-    const int il_groups = (n >= 8 && fsm8 <= 48 * 1024 && aligned) ? n / kBpGroup : 0;
+    const int il_groups = (n >= 8 && fsm8 <= 48 * 1024) ? n / kBpGroup : 0;
     const long long sstride = (long long)g.n_views * g.n_bins;
     int k = 0;
     if (il_groups > 0) {
