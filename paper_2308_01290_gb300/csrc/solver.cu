@@ -1625,6 +1625,72 @@ __global__ void __launch_bounds__(kStencilThreads) k_mg_restrict(ItemList L, con
     }
 }
 
+// Level geometries 0 .. n of the a^2 restriction (device arrays, one entry per slice).
+constexpr int kMgRestrictFused = 5;   // most levels one fine tile forms in k_mg_restrict_all (64 x 32 -> 2 x 1)
+struct MgLevelGeoms {
+    const SliceGeom* g[kMgRestrictFused + 1];
+};
+
+// a^2 of levels 1 .. nlev from the fine a^2 in one pass over the fine tiles:
+// a tile's 2x2 means of level l are formed from its level-l cells in shared
+// memory (the tile's own cells: 2x2 means stay within a tile whose sides are
+// multiples of 2^nlev), each written to its level.  Every value is the sum
+// k_mg_restrict forms from the same four values, so the levels equal those of
+// one k_mg_restrict launch per level, bit for bit.  A slice stops at its own
+// depth (the next level's width is 0).
+template <typename T>
+__global__ void __launch_bounds__(kStencilThreads) k_mg_restrict_all(ItemList L, MgLevelGeoms LG, int nlev,
+                                                                     const SliceState* S, const T* a, T* pa,
+                                                                     unsigned long long* acct) {
+    constexpr int TH = TileDim<T>::TH;
+    __shared__ T sm[2][TH / 2][kTileW / 2];
+    for (int w = blockIdx.x; w < L.n_items; w += gridDim.x) {
+        const Item it = L.items[w];
+        if (!__ldg(&S[it.slice].active)) continue;
+        const SliceGeom g = LG.g[0][it.slice], g1 = LG.g[1][it.slice];
+        account(acct, KF_MG_SETUP, tile_px<T>(g, it) * 5 * (long long)sizeof(T) / 4);
+        int cw = kTileW / 2, ch = TH / 2;
+        for (int q = threadIdx.x; q < cw * ch; q += blockDim.x) {
+            const int cy = q / cw, cx = q - cy * cw;
+            const int x = it.a + 2 * cx, y = it.b + 2 * cy;
+            T v = T(0);
+            if (x < g.nx && y < g.ny) {
+                const long long d = g.off + (long long)y * g.pitch + x;
+                v = T(0.25) * ((a[d] + a[d + 1]) + (a[d + g.pitch] + a[d + g.pitch + 1]));
+                pa[g1.off + (long long)(y / 2) * g1.pitch + x / 2] = v;
+            }
+            sm[0][cy][cx] = v;
+        }
+        __syncthreads();
+        int buf = 0;
+        for (int l = 1; l < nlev && (ch >> 1) > 0; ++l) {
+            const SliceGeom gl = LG.g[l][it.slice], gn = LG.g[l + 1][it.slice];
+            if (gn.nx == 0) break;   // the slice has no level l + 1 (the same for the whole block)
+            const int x0 = it.a >> l, y0 = it.b >> l;   // the tile's origin on level l
+            {
+                const int w = gl.nx - x0 < cw ? gl.nx - x0 : cw, h = gl.ny - y0 < ch ? gl.ny - y0 : ch;
+                const long long px = (long long)(w > 0 ? w : 0) * (h > 0 ? h : 0);
+                account(acct, KF_MG_SETUP, px * 5 * (long long)sizeof(T) / 4);
+            }
+            cw >>= 1;
+            ch >>= 1;
+            for (int q = threadIdx.x; q < cw * ch; q += blockDim.x) {
+                const int cy = q / cw, cx = q - cy * cw;
+                const int x = x0 + 2 * cx, y = y0 + 2 * cy;
+                T v = T(0);
+                if (x < gl.nx && y < gl.ny) {
+                    v = T(0.25) * ((sm[buf][2 * cy][2 * cx] + sm[buf][2 * cy][2 * cx + 1]) +
+                                   (sm[buf][2 * cy + 1][2 * cx] + sm[buf][2 * cy + 1][2 * cx + 1]));
+                    pa[gn.off + (long long)(y / 2) * gn.pitch + x / 2] = v;
+                }
+                sm[buf ^ 1][cy][cx] = v;
+            }
+            __syncthreads();
+            buf ^= 1;
+        }
+    }
+}
+
 // Start the copies of NM maps of the tile at (tx0, ty0) with its one-pixel
 // periodic halo into sm[m] (layout of load_tile).
 template <typename T, int NM>
@@ -2920,7 +2986,19 @@ template <typename T>
 void mg_restrict_a2(Ctx& c, bool timed) {
     MaybeTimer t(c, KF_MG_SETUP, timed);
     T* pa = static_cast<T*>(c.mg_pool[1]);
-    for (int l = 0; l < c.mg_max_lb; ++l) {
+    // levels 1 .. F in one pass over the fine tiles (F = the tile's halvings), deeper levels one launch each
+    constexpr int FT = ilog2c(TileDim<T>::TH);   // halvings of the tile height: 5 (FP32), 4 (FP64)
+    static_assert(FT <= kMgRestrictFused, "level table too small");
+    const int F = c.mg_max_lb < FT ? c.mg_max_lb : FT;
+    if (F > 0) {
+        MgLevelGeoms LG{};
+        for (int l = 0; l <= F; ++l) LG.g[l] = c.d_mg_geom[l];
+        const DevItemList& L = c.mg_tiles[0];
+        k_mg_restrict_all<T><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(
+            L.view(), LG, F, c.d_state, field_t<T>(c, RECON_F_A2), pa, c.d_acct);
+        c.launches += 1;
+    }
+    for (int l = F; l < c.mg_max_lb; ++l) {
         const DevItemList& L = c.mg_tiles[l];
         const T* a = l == 0 ? field_t<T>(c, RECON_F_A2) : pa;
         k_mg_restrict<T><<<grid_for(c, L.n), kStencilThreads, 0, c.stream>>>(L.view(), c.d_mg_geom[l],
