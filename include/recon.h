@@ -202,7 +202,21 @@ int recon_step(recon_ctx* ctx, int32_t n_iters, recon_stats* stats);
  * Z^m <= 0), rho_e, f1, f2; any pointer may be NULL; host or device. */
 int recon_get(recon_ctx* ctx, float* Z, float* rhoe, float* f1, float* f2, int on_device);
 
-/* Blocks until the handle's queued work is done. */
+/* recon_get into host buffers without waiting for the copies: the maps are
+ * extracted on the handle's stream into output staging of the handle's own
+ * (two unpadded float maps, allocated on the first call) and copied to the
+ * host, one group of up to 8 slices at a time, on a device-to-host stream of
+ * the handle.  The next recon_set_data and recon_step may run while the
+ * copies proceed, so a stream of volumes overlaps each volume's maps going
+ * out with the next one's work.  The host buffers (pinned memory, for the
+ * copies to overlap) must stay valid, and are not complete, until
+ * recon_sync returns; a later recon_get_async into the same buffers is
+ * ordered after the earlier copies.  Errors: RECON_EINVAL (null handle),
+ * RECON_ESTATE (before recon_set_data), RECON_ENOMEM / RECON_ECUDA. */
+int recon_get_async(recon_ctx* ctx, float* Z, float* rhoe, float* f1, float* f2);
+
+/* Blocks until the handle's queued work is done, including host copies
+ * started by recon_set_data and recon_get_async. */
 int recon_sync(recon_ctx* ctx);
 
 /* Outputs of the comparison the paper's Sec. III makes (they do not change

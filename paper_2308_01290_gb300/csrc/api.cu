@@ -65,6 +65,13 @@ void free_ctx(Ctx& c) {
     for (cudaEvent_t e : c.copy_ev)
         if (e) cudaEventDestroy(e);
     c.copy_stream = nullptr;
+    if (c.d2h_stream) {
+        cudaStreamSynchronize(c.d2h_stream);
+        cudaStreamDestroy(c.d2h_stream);
+    }
+    for (cudaEvent_t e : c.d2h_ev)
+        if (e) cudaEventDestroy(e);
+    c.d2h_stream = nullptr;
     for (void* p : c.allocations) cudaFree(p);
     c.allocations.clear();
     if (c.h_cg_pending) cudaFreeHost(c.h_cg_pending);
@@ -458,9 +465,53 @@ int recon_mono(recon_ctx* h, int32_t n_e, const double* kev, float* out, int on_
     return RECON_OK;
 }
 
+int recon_get_async(recon_ctx* h, float* Z, float* rhoe, float* f1, float* f2) {
+    if (!h) return RECON_EINVAL;
+    Ctx& c = h->c;
+    if (!c.has_data) {
+        set_error("recon_get_async before recon_set_data");
+        return RECON_ESTATE;
+    }
+    int rc;
+    if (!c.d2h_stream) {
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = cudaMalloc((void**)&c.d_out[i], sizeof(float) * (c.ext_elems > 0 ? c.ext_elems : 1));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc output staging");
+            c.allocations.push_back(c.d_out[i]);
+        }
+        RECON_CUDA(cudaStreamCreateWithFlags(&c.d2h_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t& e : c.d2h_ev) RECON_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    float* outs[4] = {Z, rhoe, f1, f2};
+    for (int k = 0; k < 4; k += 2) {
+        float* a = outs[k] ? c.d_out[0] : nullptr;
+        float* b = outs[k + 1] ? c.d_out[1] : nullptr;
+        if (!a && !b) continue;
+        // the output staging is free once the copies queued before (this call's or an earlier one's) are done
+        RECON_CUDA(cudaEventRecord(c.d2h_ev[0], c.d2h_stream));
+        RECON_CUDA(cudaStreamWaitEvent(c.stream, c.d2h_ev[0], 0));
+        for (int s0 = 0; s0 < c.n; s0 += kFbpGroup) {
+            const int s1 = s0 + kFbpGroup < c.n ? s0 + kFbpGroup : c.n;
+            if (k == 0) rc = solver_extract_range(c, s0, s1, a, b, nullptr, nullptr);
+            else rc = solver_extract_range(c, s0, s1, nullptr, nullptr, a, b);
+            if (rc) return rc;
+            RECON_CUDA(cudaEventRecord(c.d2h_ev[1], c.stream));
+            RECON_CUDA(cudaStreamWaitEvent(c.d2h_stream, c.d2h_ev[1], 0));
+            const long long e0 = c.sg[s0].ext_off, e1 = s1 < c.n ? c.sg[s1].ext_off : c.ext_elems;
+            const size_t bytes = sizeof(float) * (size_t)(e1 - e0);
+            if (a) RECON_CUDA(cudaMemcpyAsync(outs[k] + e0, a + e0, bytes, cudaMemcpyDeviceToHost, c.d2h_stream));
+            if (b)
+                RECON_CUDA(cudaMemcpyAsync(outs[k + 1] + e0, b + e0, bytes, cudaMemcpyDeviceToHost, c.d2h_stream));
+        }
+    }
+    return RECON_OK;
+}
+
 int recon_sync(recon_ctx* h) {
     if (!h) return RECON_EINVAL;
     RECON_CUDA(cudaStreamSynchronize(h->c.stream));
+    if (h->c.copy_stream) RECON_CUDA(cudaStreamSynchronize(h->c.copy_stream));
+    if (h->c.d2h_stream) RECON_CUDA(cudaStreamSynchronize(h->c.d2h_stream));
     return RECON_OK;
 }
 

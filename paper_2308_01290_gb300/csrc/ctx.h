@@ -114,6 +114,11 @@ struct Ctx {
     // `stream` filters and backprojects the groups before (recon_set_data)
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t copy_ev[2] = {nullptr, nullptr};
+    // recon_get_async: maps extracted into d_out on `stream`, copied to the host on d2h_stream while the
+    // handle goes on with the next inputs (created on the first call)
+    cudaStream_t d2h_stream = nullptr;
+    cudaEvent_t d2h_ev[2] = {nullptr, nullptr};
+    float* d_out[2] = {};
     // one iteration captured as a CUDA graph (recon_set_graph): the Z^m PCG
     // runs as a conditional WHILE node of two PCG steps per body
     bool graph_on = false;

@@ -84,6 +84,7 @@ def _load():
         "recon_set_data": (I, [VP, VP, VP, I]),
         "recon_step": (I, [VP, C.c_int32, P(Stats)]),
         "recon_get": (I, [VP, VP, VP, VP, VP, I]),
+        "recon_get_async": (I, [VP, VP, VP, VP, VP]),
         "recon_sync": (I, [VP]),
         "recon_direct": (I, [VP, VP, VP, I]),
         "recon_mono": (I, [VP, C.c_int32, P(D), VP, I]),
@@ -137,6 +138,7 @@ def _check_layout():
 
 _check_layout()
 EXPORTS = ("recon_default_params", "recon_init", "recon_init_batch", "recon_set_data", "recon_step", "recon_get",
+           "recon_get_async",
            "recon_sync", "recon_destroy", "recon_solve", "recon_strerror", "recon_last_error", "recon_project",
            "recon_backproject", "recon_fbp", "recon_fbp_noalloc", "recon_simulate", "recon_model_tables", "recon_debug_field",
            "recon_debug_op", "recon_debug_io", "recon_debug_scalars", "recon_kernel_launches", "recon_set_graph",
@@ -278,6 +280,11 @@ class Solver:
                 off += g.nx * g.ny
             res.append(parts)
         return res
+
+    def get_async(self, Z=None, rhoe=None, f1=None, f2=None):
+        """Host maps without waiting for the copies (recon_get_async): the
+        buffers (host addresses, pinned for overlap) are complete after sync()."""
+        _check(lib.recon_get_async(self.h, _ptr(Z), _ptr(rhoe), _ptr(f1), _ptr(f2)), "recon_get_async")
 
     def sync(self):
         _check(lib.recon_sync(self.h), "recon_sync")

@@ -151,6 +151,52 @@ def test_host_sinograms_equal_device_sinograms(rc, small_case):
     assert not np.array_equal(outs["device"][0], outs["device2"][0])
 
 
+def test_get_async_equals_get(rc, small_case):
+    """recon_get_async: two volumes (20 slices each: groups of 8, 8, 4) go
+    through set_data, step and get_async back to back into two pairs of
+    pinned buffers, the second volume's work running while the first one's
+    maps are copied out; after sync each pair equals the synchronous
+    recon_get of its volume bit for bit, and so do f1 and f2.  A third round
+    into the first pair again is ordered after its earlier copies."""
+    torch = pytest.importorskip("torch")
+    c = small_case
+    acq = c["acq"]
+    n = 20
+    g = rc.geometry_from_acq(acq)
+    p = rc.default_params(low=acq.low, high=acq.high, iters=3)
+    npx = n * acq.nx * acq.ny
+    vols = []
+    for v in range(2):
+        sL = np.concatenate([(c["sL"] * (1.0 + 0.01 * s + 0.1 * v)).astype(np.float32).ravel() for s in range(n)])
+        sH = np.concatenate([(c["sH"] * (1.0 + 0.01 * s + 0.1 * v)).astype(np.float32).ravel() for s in range(n)])
+        vols.append((torch.from_numpy(sL).pin_memory(), torch.from_numpy(sH).pin_memory()))
+    s = rc.Solver([g] * n, [p] * n)
+    ref = []
+    for lo, hi in vols:
+        s.set_data(lo.data_ptr(), hi.data_ptr(), on_device=False)
+        s.step(3)
+        outs = [np.empty(npx, np.float32) for _ in range(4)]
+        s.get(*outs)
+        ref.append(outs)
+    bufs = [[torch.empty(npx).pin_memory() for _ in range(4)] for _ in range(2)]
+    for v, (lo, hi) in enumerate(vols):
+        s.set_data(lo.data_ptr(), hi.data_ptr(), on_device=False)
+        s.step(3)
+        s.get_async(*[b.data_ptr() for b in bufs[v]])
+    s.sync()
+    for v in range(2):
+        for k in range(4):
+            assert np.array_equal(bufs[v][k].numpy(), ref[v][k]), (v, k)
+    assert not np.array_equal(ref[0][0], ref[1][0])
+    lo, hi = vols[0]
+    s.set_data(lo.data_ptr(), hi.data_ptr(), on_device=False)
+    s.step(3)
+    s.get_async(Z=bufs[1][0].data_ptr(), rhoe=bufs[1][1].data_ptr())
+    s.sync()
+    assert np.array_equal(bufs[1][0].numpy(), ref[0][0]) and np.array_equal(bufs[1][1].numpy(), ref[0][1])
+    s.close()
+
+
 def test_one_shot_solve_equals_handle(rc, small_case):
     c = small_case
     acq = c["acq"]
