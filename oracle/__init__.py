@@ -21,6 +21,8 @@ FP64:
 * ``modeb``  -- the sinogram-domain data terms of the f updates.
 * ``iqa``    -- monoenergetic images at any energy, the two-step image-based
   comparator of Sec. III and the image-quality metrics PSNR, NMAD, SSIM.
+* ``alg1_3d`` -- Algorithm 1 over a volume with the 3-D multi-domain
+  regulariser (a third periodic difference across slices).
 
 Parity status of every function is given in its docstring; functions with no
 independent pin say "parity unpinned".
