@@ -83,3 +83,20 @@ def test_spectrum_weights():
     lo = model.spectrum_bins(ph.Spectrum("kramers", kvp=80.0, filters=(ph.AL_2MM,)))
     # tin filtration hardens the high arm: its mean energy is far above the low arm's
     assert (E * w).sum() > (lo[0] * lo[1]).sum() + 20
+
+
+def test_basis_attenuations_span_two_energy_functions():
+    """Under the photoelectric + Compton model of Sec. II-B every material's
+    mu_hat(E) = rho_e (Cp Z^m / E^n + KN(E)) is a combination of the same two
+    functions of energy, so any three or more materials are linearly
+    dependent at any set of energies: a decomposition into more than two
+    bases (the multi-basis variant of Sec. IV) is not identifiable within
+    this model.  The rank also checks mu_hat against its two terms directly."""
+    E = np.array([40.0, 50.0, 60.0, 70.0, 80.0, 90.0, 100.0, 120.0])
+    mats = [(1.0, 7.45), (1.7, 13.0), (1.9, 20.0), (1.1, 6.0)]
+    A = np.array([[model.mu_hat(r, z, e) for e in E] for r, z in mats])
+    s = np.linalg.svd(A, compute_uv=False)
+    assert s[1] > 1e-3 * s[0] and s[2] < 1e-12 * s[0]
+    two = np.array([[model.photo_coeff(e) for e in E], [model.klein_nishina_barn(e) for e in E]])
+    coef, *_ = np.linalg.lstsq(two.T, A.T, rcond=None)
+    assert np.allclose(two.T @ coef, A.T, rtol=1e-12, atol=0)
